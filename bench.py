@@ -1,0 +1,452 @@
+"""Benchmark: batched Parareal on a 64^3 lid-driven cavity (one GB300).
+
+One step = one Parareal iteration (Eq. 6) of the 64^3 cavity at Re = 1000:
+the fine propagator F over all 32 slices (50 steps of dt = 5e-4 each) in one
+batched sweep, then the serial coarse sweep G (5 steps of 5e-3 per slice) with
+the fused Parareal update and the FP64 defect.  The metric counts the fine
+sweep's cell-steps (32 x 50 x 64^3 per step) over the whole iteration's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32_refine|fp64] [--no-comparators]
+
+N > 1 runs N independent replicas (one cavity trajectory per GPU, no
+collective on the data path); the value is the sum over ranks.  The
+`reference` implementation is the FP64 CPU oracle timed on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Parareal fine-sweep cell-steps/s (FP32+refine vs FP64) and % of HBM roofline"
+UNIT = "cell-steps/s"
+
+# workload: the 64^3 batched-Parareal cavity
+N_CELLS = 64
+RE = 1000.0
+N_SLICES = 32
+FINE_STEPS = 50
+DT_FINE = 5e-4
+# coarse propagator: 5 steps of 5e-3 per slice (10 fine steps per coarse step),
+# the largest coarse step of the slice that keeps forward Euler stable here
+COARSE_STEPS = 5
+WORKLOAD = ("64^3 lid-driven cavity, Re=1000, u_lid=1, walls on all faces; initial field = "
+            "16^3 cavity (Re=100) at t=0.2 trilinearly upsampled + N(0,1e-3^2) face noise "
+            "(seed 0), projected; 32 Parareal slices x 50 fine steps (dt=5e-4); coarse "
+            "propagator 5 steps of 5e-3 per slice; one step = one Parareal iteration")
+
+# algorithmic bytes per cell and Krylov iteration for each BiCGStab phase
+# (each array read or written once per launch; neighbour reads come from cache)
+WORDS_PER_CELL = {"krylov_A": 6, "krylov_B": 3, "krylov_C": 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32_refine", "fp64"], default="fp32_refine")
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(x: float, pg, device=None) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device.index])
+        else:
+            pg.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def initial_field_gpu(precision: str):
+    """The 64^3 start state, computed with the CUDA path: the 16^3 Re=100
+    cavity at t = 0.2, upsampled, noised and projected."""
+    from paper_1705_06149_gb300 import Grid, inputs
+    g16 = Grid(16, 16, 16, re=100.0, precision="fp64", batch=1)
+    s16 = g16.zeros(1)
+    g16.step_fine(s16, 1e-3, 200)
+    coarse = [a[0] for a in s16.numpy()]
+    g16.close()
+    up = inputs.upsample_cavity(coarse, 16, N_CELLS, u_lid=1.0)
+    return inputs.add_face_noise(up, 1e-3, seed=0)
+
+
+def initial_field_oracle():
+    """The same start state computed by the CPU oracle (for the CPU leg)."""
+    import oracle
+    from paper_1705_06149_gb300 import inputs
+    o16 = oracle.Grid(16, 16, 16, re=100.0)
+    s16 = o16.zeros()
+    o16.step(s16, 1e-3, 200)
+    up = inputs.upsample_cavity(s16, 16, N_CELLS, u_lid=1.0)
+    st = inputs.add_face_noise(up, 1e-3, seed=0)
+    o64 = oracle.Grid(N_CELLS, N_CELLS, N_CELLS, re=RE)
+    u, v, w, _ = o64.project(*st[:3])
+    return o64, [u, v, w, np.zeros_like(st[3])]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference implementation)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(o64, start, nslices: int):
+    """Time one fine step of nslices copies of the start state, advanced in
+    parallel over the host cores after one untimed warm step (so that the
+    pressure solve starts warm as it does inside the sweep)."""
+    import oracle
+    states = [oracle.copy_state(start) for _ in range(nslices)]
+    o64.run_batch(states, DT_FINE, 1)
+    t0 = time.perf_counter()
+    o64.run_batch(states, DT_FINE, 1)
+    dt = time.perf_counter() - t0
+    return nslices * N_CELLS ** 3 / dt, dt
+
+
+def cpu_cores() -> int:
+    import oracle
+    return oracle.threads()
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    o64, start = initial_field_oracle()
+    cores = cpu_cores()
+    nsl = max(1, cores)
+    for _ in range(args.warmup):
+        oracle_sample(o64, start, nsl)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, t = oracle_sample(o64, start, nsl)
+        rates.append(r)
+        times.append(t)
+    value = float(np.mean(rates))
+    sample = (f"{nsl} copies of the 64^3 start state, 1 fine step each (after 1 warm step), "
+              f"OpenMP over copies, per timed step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (plain C, BiCGStab)",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1705_06149_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return k.get("dram_bytes_per_cell_iter")
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    from paper_1705_06149_gb300 import Grid
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision
+    peaks, peak_kind = measured_peaks()
+
+    init = initial_field_gpu(prec)
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, u_lid=1.0, precision=prec, batch=N_SLICES)
+    u0 = g.state_from(init)
+    g.project(u0)
+    slices = g.zeros(N_SLICES + 1)
+    g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=0)
+    for _ in range(args.warmup):
+        g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=1, resume=True)
+    torch.cuda.synchronize()
+
+    # ---- timed region --------------------------------------------------------
+    g.profile(True, min_batch=N_SLICES)
+    launches0 = g.stats()["launches"]
+    krylov0 = g.stats()["krylov_iters"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    defects = []
+    for _ in range(args.steps):
+        _, d = g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=1,
+                          resume=True)
+        defects += d
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    clock_rec = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    prof = g.profile_read()
+    g.profile(False)
+    st = g.stats()
+    launches = st["launches"] - launches0
+    ms_step = max_over_ranks(ms_total / args.steps, pg, dev)
+    cell_steps = N_SLICES * FINE_STEPS * N_CELLS ** 3
+    value = world * cell_steps / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel (live CUDA-event timing) -------------
+    esz = 4 if prec == "fp32_refine" else 8
+    kern = max(WORDS_PER_CELL, key=lambda k: prof[k]["ms"])
+    kp = prof[kern]
+    bytes_alg = kp["cell_units"] * WORDS_PER_CELL[kern] * esz
+    achieved = bytes_alg / (kp["ms"] / 1e3) / 1e9 if kp["ms"] > 0 else 0.0
+    peak = float(peaks["hbm_gbs"])
+    traffic = traffic_for(kern)
+    per_launch_units = kp["cell_units"] / max(kp["launches"], 1)
+    roofline = {"bound": "hbm", "kernel": f"k_bicg_{kern[-1]}", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": per_launch_units * WORDS_PER_CELL[kern] * esz,
+                "avg_launch_us": 1e3 * kp["ms"] / max(kp["launches"], 1),
+                "traffic": (traffic * per_launch_units) if traffic else None}
+    fine_kernel_ms = sum(v["ms"] for v in prof.values()) / args.steps
+    kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
+               for k, v in prof.items() if v["launches"]}
+    iters_per_cell_step = (st["krylov_iters"] - krylov0) / max(1, args.steps)
+
+    # ---- end to end through the public API with host buffers ------------------
+    host = slices.to("cpu")
+    host = type(host)(*[t.pin_memory() for t in host.fields()])
+    e2e_steps = max(1, min(2, args.steps))
+    barrier(pg, dev)
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        _, _, bi, bo = g.parareal_host(u0, host, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE,
+                                       kmax=1, resume=True, slices_dev=slices)
+        h2d, d2h = bi, bo
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, pg, dev)
+    e2e = {"value": world * cell_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    # ---- comparators: FP64 batched and plain per-slice FP64 ------------------
+    comparators = None
+    if not args.no_comparators and rank == 0:
+        comparators = fp64_comparators(init)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        import oracle
+        oracle.build()
+        o64, start = initial_field_oracle()
+        cores = cpu_cores()
+        rate, secs = oracle_sample(o64, start, max(1, cores))
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{max(1, cores)} copies of the 64^3 start state, 1 fine step each "
+                         f"after 1 warm step ({secs:.1f} s timed), OpenMP over copies"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64refine" if prec == "fp32_refine" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": prec, "slices": N_SLICES,
+                   "fine_steps_per_slice": FINE_STEPS, "coarse_steps_per_slice": COARSE_STEPS,
+                   "grid": [N_CELLS] * 3, "parallelism": f"replicas x{world}",
+                   "l2": "working set > L2 (no flush needed): ~%.0f MB of Krylov vectors"
+                         % (N_SLICES * N_CELLS ** 3 * esz * 8 / 1e6)},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clock_rec,
+        "fine_sweep": {"kernel_ms_per_step": fine_kernel_ms,
+                       "cell_steps_per_s_kernels": cell_steps / (fine_kernel_ms / 1e3)
+                       if fine_kernel_ms > 0 else None,
+                       "krylov_iters_per_step_all_solves": iters_per_cell_step,
+                       "kernels": kernels},
+        "defects": defects,
+        "comparators": comparators,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
+def fp64_comparators(init):
+    """Rates of the FP64 batched sweep and of the plain per-slice FP64 path (one
+    slice per call), each over a bounded sample of the same workload."""
+    import torch
+    from paper_1705_06149_gb300 import Grid
+    out = {}
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision="fp64", batch=N_SLICES)
+    st = g.state_from(init)
+    g.project(st)
+    batch = g.state_from([t.expand((N_SLICES,) + tuple(t.shape[1:])).cpu().numpy()
+                          for t in st.fields()])
+    g.step_fine(batch, DT_FINE, 2)  # warm
+    torch.cuda.synchronize()
+    steps = 4
+    t0 = time.perf_counter()
+    g.step_fine(batch, DT_FINE, steps)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["fp64_batched"] = {"value": N_SLICES * steps * N_CELLS ** 3 / t, "unit": UNIT,
+                           "sample": f"{N_SLICES} slices x {steps} fine steps"}
+    nsl = 4
+    one = [batch.slice(s).clone() for s in range(nsl)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(nsl):
+        g.step_fine(one[s], DT_FINE, steps)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["fp64_per_slice"] = {"value": nsl * steps * N_CELLS ** 3 / t, "unit": UNIT,
+                             "sample": f"{nsl} slices x {steps} fine steps, one slice per call"}
+    g.close()
+    return out
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank, pg)
+    else:
+        rc = run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * ns.h -- C ABI of the GB300 (sm_103a) batched projection stepper and Parareal
+ * driver for the incompressible Navier-Stokes equations, after Croce, Ruprecht
+ * & Krause, "Parallel-in-Space-and-Time Simulation of the Three-Dimensional,
+ * Unsteady Navier-Stokes Equations for Incompressible Flow" (arXiv 1705.06149).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A state is (u, v, w, p) on a uniform staggered (MAC) grid with nx*ny*nz
+ *   cells on [0,lx]x[0,ly]x[0,lz] (Section 2), stored in DEVICE memory owned
+ *   by the caller, x fastest, leading batch dimension:
+ *       u [batch][nz][ny][nx+1]   v [batch][nz][ny+1][nx]
+ *       w [batch][nz+1][ny][nx]   p [batch][nz][ny][nx]
+ *   Along a periodic axis the normal component has n faces instead of n+1.
+ *   Wall-normal boundary faces are stored and hold zero on output.
+ * - Element types follow the grid's precision: NS_FP64 -> double everywhere;
+ *   NS_FP32_REFINE -> float u, v, w and double p.
+ * - The library owns only the workspace inside an ns_grid; it never frees or
+ *   keeps caller pointers beyond a call.
+ * - Calls run on the grid's CUDA stream.  Calls that iterate to a tolerance
+ *   synchronise that stream to read per-slice convergence flags; all calls
+ *   have returned their results to the caller's buffers when they return.
+ * - No C++ exception crosses the ABI.  On a non-OK status the contents of
+ *   output buffers are unspecified; ns_last_error() describes the failure.
+ * - A grid object must not be used by two host threads at once.
+ */
+#ifndef NS_H
+#define NS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NS_OK = 0,
+    NS_ERR_ARG = 1,            /* invalid argument (null pointer, size, step...) */
+    NS_ERR_CUDA = 2,           /* a CUDA runtime call failed                     */
+    NS_ERR_OOM = 3,            /* workspace allocation failed                    */
+    NS_ERR_NOT_CONVERGED = 4,  /* a pressure solve hit its iteration limit       */
+    NS_ERR_NONFINITE = 5,      /* NaN/Inf met in a residual or a defect          */
+    NS_ERR_TIMEOUT = 6         /* a bounded device-side wait gave up             */
+} ns_status;
+
+typedef enum { NS_FP64 = 0, NS_FP32_REFINE = 1 } ns_precision;
+
+/* Boundary condition of one axis, applied at both ends.  NS_BC_WALL is the
+ * no-slip wall of the cavity (Section 3); the top face y = ly additionally
+ * moves with speed u_lid along +x.  NS_BC_SLIP keeps the normal component at
+ * zero and the tangential derivative at zero. */
+typedef enum { NS_BC_WALL = 0, NS_BC_PERIODIC = 1, NS_BC_SLIP = 2 } ns_bc;
+
+typedef struct {
+    int nx, ny, nz;          /* cells per axis, each >= 2                            */
+    double lx, ly, lz;       /* box size                                             */
+    double re;               /* Reynolds number of Eq. 1 (> 0)                       */
+    double u_lid;            /* speed of the lid y = ly along +x                     */
+    int bc[3];               /* ns_bc per axis                                       */
+    const uint8_t *solid_mask; /* host, nz*ny*nx, 1 = solid cell; NULL = none; copied.
+                                  Solid cells are supported by the pressure solve only
+                                  in this version: a non-NULL mask is rejected.      */
+    int precision;           /* ns_precision                                         */
+    double poisson_rtol;     /* FP64: stop when ||b - L p||_2 <= rtol ||b||_2        */
+    int poisson_maxit;       /* iteration limit per Krylov solve (<= 0: 20*max(n))   */
+    double refine_rtol;      /* FP32_REFINE: outer FP64 relative residual target     */
+    double inner_rtol;       /* FP32_REFINE: inner FP32 relative residual per outer
+                                step (<= 0: 1e-4)                                    */
+    int batch;               /* capacity: largest batch one call may advance (>= 1)  */
+} ns_grid_desc;
+
+/* Caller-owned device buffers of `batch` states (1 <= batch <= grid capacity). */
+typedef struct {
+    void *u, *v, *w, *p;
+    int batch;
+} ns_state;
+
+typedef struct ns_grid ns_grid;
+
+/* Counters accumulated since creation (or the last ns_reset_stats). */
+typedef struct {
+    long long launches;         /* kernels launched by the library                   */
+    long long steps;            /* state-steps taken (one state, one time step)      */
+    long long solves;           /* per-state pressure solves                          */
+    long long krylov_iters;     /* Krylov iterations summed over per-state solves
+                                   (inner FP32 iterations in FP32_REFINE)             */
+    long long refine_steps;     /* FP32_REFINE outer corrections, summed over states */
+    int last_max_iters;         /* largest per-state iteration count of the last solve */
+    double last_rel_residual;   /* largest relative residual of the last solve        */
+} ns_stats;
+
+/* Create a grid object: validates the description, chooses the CUDA tiling
+ * and allocates the workspace for `batch` states.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns the
+ * workspace until ns_destroy_grid. */
+ns_status ns_create_grid(const ns_grid_desc *desc, void *cuda_stream, ns_grid **out);
+ns_status ns_destroy_grid(ns_grid *grid);
+ns_status ns_set_stream(ns_grid *grid, void *cuda_stream);
+
+/* The fine propagator F of Parareal (Section 2.1.2): nsteps forward-Euler
+ * Chorin-Temam projection steps of size dt (Section 2), applied in place to
+ * every state of io, all states in the same launches:
+ *   F*      = u^n + dt (Re^-1 lap_h u^n - div_h(u^n u^n))   (SMART convection)
+ *   L p     = D F* / dt   (L = D G, Neumann, BiCGStab, warm start p^n,
+ *                          fluid mean removed from the right side and from p)
+ *   u^{n+1} = F* - dt G p^{n+1}.
+ * nsteps = 0 is a no-op. */
+ns_status ns_step_fine(ns_grid *grid, ns_state io, double dt, int nsteps);
+
+/* The coarse propagator G (Section 2.1.2): the same scheme with the coarse
+ * step dt_coarse = N_r dt; kept separate so that F and G can be told apart in
+ * traces and statistics. */
+ns_status ns_step_coarse(ns_grid *grid, ns_state io, double dt_coarse, int nsteps);
+
+/* The projection on its own (Section 2, Chorin-Temam): u <- u - G phi with
+ * L phi = D u; p is left unchanged.  Used to make seeded inputs
+ * divergence-free. */
+ns_status ns_project(ns_grid *grid, ns_state io);
+
+/* The predictor alone: F* of ns_step_fine for every state of `in`, written to
+ * caller device buffers fu, fv, fw laid out like u, v, w (zero on inactive
+ * faces).  Exposed for stage-by-stage checks. */
+ns_status ns_predict(ns_grid *grid, ns_state in, double dt, void *fu, void *fv, void *fw);
+
+/* The gauged pressure solve alone: for each of `batch` right-hand sides b
+ * (double, [batch][nz][ny][nx], device), removes the fluid mean of b, solves
+ * L p = b from the warm start in p (device, precision's p type = double) and
+ * removes the fluid mean of p.  b is not modified.  *iters (host, may be
+ * NULL) receives the largest per-state iteration count. */
+ns_status ns_poisson_solve(ns_grid *grid, const double *b, double *p, int batch, int *iters);
+
+/* Parareal (Section 2.1.2, Eq. 6) for one trajectory of n_slices slices:
+ *   y_0 = u0;  iteration 0 is the serial coarse sweep y^0_{n+1} = G(y^0_n);
+ *   then for k = 0..kmax-1:  all F(y^k_n) in one batched sweep, followed by the
+ *   serial update y^{k+1}_{n+1} = F(y^k_n) + (G(y^{k+1}_n) - G(y^k_n)).
+ * u0: batch-1 state.  slices: n_slices+1 states y_0..y_N (output; y_0 = u0).
+ * Each slice spans fine_steps_per_slice steps of dt_fine (F) and
+ * coarse_steps_per_slice steps of dt_fine*fine/coarse (G).  The grid's
+ * capacity must be >= n_slices.  Stops after kmax iterations or once the
+ * defect max_{n,field} |y^{k+1}_n - y^k_n| <= defect_tol (tol > 0).
+ * resume = 0 starts from u0 (coarse sweep first); resume = 1 continues from
+ * the y^k held in `slices` and the coarse values G(y^k_n) this grid stored at
+ * the end of the previous call with the same slices (NS_ERR_ARG if none).
+ * *k_done (host) receives the iterations performed, defects (host, kmax
+ * entries, may be NULL) the FP64 defect of each. */
+ns_status ns_parareal_iterate(ns_grid *grid, ns_state u0, ns_state slices, int n_slices,
+                              int fine_steps_per_slice, int coarse_steps_per_slice,
+                              double dt_fine, int kmax, double defect_tol, int resume,
+                              int *k_done, double *defects);
+
+/* Gradient of J = 1/2 sum over active faces of (component^2) h_x h_y h_z at
+ * the end of nsteps fine steps from u0, with respect to every face of u0 and
+ * to the lid speed, by the discrete adjoint of the fine step with checkpoints
+ * every ckpt_every steps.  Not available in this version: returns
+ * NS_ERR_ARG. */
+ns_status ns_adjoint(ns_grid *grid, ns_state u0, double dt, int nsteps, int ckpt_every,
+                     double *J, ns_state grad_u0, double *dJ_dulid);
+
+ns_status ns_get_stats(const ns_grid *grid, ns_stats *out);
+ns_status ns_reset_stats(ns_grid *grid);
+
+/* Kernel kinds timed by the profiler (index into ns_profile_read's array). */
+typedef enum {
+    NS_K_PREDICT = 0,      /* F* = u + dt (Re^-1 lap u - div(u u))            */
+    NS_K_DIVERGENCE = 1,   /* b = D F* / dt and its partial sums               */
+    NS_K_SOLVE_INIT = 2,   /* start of a pressure solve (FP64 init / refine init) */
+    NS_K_KRYLOV_A = 3,     /* BiCGStab phase A: p update, v = L p, (r_hat, v)  */
+    NS_K_KRYLOV_B = 4,     /* BiCGStab phase B: s, t = L s, (t,s), (t,t)       */
+    NS_K_KRYLOV_C = 5,     /* BiCGStab phase C: x, r updates, (r_hat,r), (r,r) */
+    NS_K_INNER_INIT = 6,   /* FP32+refine: outer test and inner start          */
+    NS_K_REFINE = 7,       /* FP32+refine: FP64 update p += e, r = b - L p     */
+    NS_K_CORRECT = 8,      /* u = F* - dt G p, p - mean(p)                     */
+    NS_K_PARAREAL = 9,     /* Parareal update of Eq. 6 and the defect          */
+    NS_K_KINDS = 10
+} ns_kernel_kind;
+
+typedef struct {
+    double ms;             /* summed device time of the timed launches (CUDA events) */
+    long long launches;    /* timed launches                                         */
+    long long cell_units;  /* cells processed by them: for the Krylov phases the sum
+                              over states of (iterations x cells), elsewhere
+                              (states x cells) per launch                          */
+} ns_kernel_time;
+
+/* Turns per-launch timing on (on != 0) or off.  While on, every launch made by
+ * a call whose batch is >= min_batch is bracketed by two CUDA events on the
+ * grid's stream; times are collected at the call's synchronisation points.
+ * Turning it on clears the accumulated times. */
+ns_status ns_profile_enable(ns_grid *grid, int on, int min_batch);
+
+/* Copies min(n, NS_K_KINDS) accumulated entries to out (host). */
+ns_status ns_profile_read(ns_grid *grid, ns_kernel_time *out, int n);
+
+/* Message of the last failure on the calling host thread ("" if none). */
+const char *ns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_H */

@@ -1,0 +1,255 @@
+"""Python binding of the C ABI: torch tensors in, the same calls out.
+
+Only argument marshalling lives here: shapes and dtypes are checked, device
+pointers and the current CUDA stream are handed to libns.so, and host (CPU)
+tensors are staged through device memory for the end-to-end calls.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .inputs import shapes as _shapes
+
+_BC = {"wall": N.NS_BC_WALL, "periodic": N.NS_BC_PERIODIC, "slip": N.NS_BC_SLIP}
+_PREC = {"fp64": N.NS_FP64, "fp32_refine": N.NS_FP32_REFINE}
+
+
+@dataclass
+class State:
+    """A batch of states (u, v, w, p) in the canonical layout."""
+    u: torch.Tensor
+    v: torch.Tensor
+    w: torch.Tensor
+    p: torch.Tensor
+
+    @property
+    def batch(self) -> int:
+        return int(self.u.shape[0])
+
+    def fields(self) -> List[torch.Tensor]:
+        return [self.u, self.v, self.w, self.p]
+
+    def clone(self) -> "State":
+        return State(*[t.clone() for t in self.fields()])
+
+    def to(self, device, non_blocking: bool = False) -> "State":
+        return State(*[t.to(device, non_blocking=non_blocking) for t in self.fields()])
+
+    def numpy(self) -> List[np.ndarray]:
+        return [t.detach().cpu().numpy() for t in self.fields()]
+
+    def slice(self, i: int, n: int = 1) -> "State":
+        return State(*[t[i:i + n] for t in self.fields()])
+
+    def _c(self) -> N.StateC:
+        return N.StateC(self.u.data_ptr(), self.v.data_ptr(), self.w.data_ptr(),
+                        self.p.data_ptr(), self.batch)
+
+
+class Grid:
+    """One MAC grid with its workspace on the current CUDA device.
+
+    precision: "fp64" (all FP64) or "fp32_refine" (FP32 velocity, stencils and
+    inner Krylov iterations; FP64 pressure, refinement residual/correction,
+    means and defects).  batch is the largest number of states one call
+    advances (the number of Parareal slices).
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0,
+                 lz: float = 1.0, re: float = 100.0, u_lid: float = 1.0,
+                 bc: Sequence[str] = ("wall", "wall", "wall"), precision: str = "fp64",
+                 poisson_rtol: float = 1e-12, poisson_maxit: int = 0,
+                 refine_rtol: float = 1e-10, inner_rtol: float = 1e-4, batch: int = 1,
+                 device: Optional[torch.device] = None):
+        self.lib = N.load()
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.bc = tuple(bc)
+        self.precision = precision
+        self.capacity = batch
+        self.vel_dtype = torch.float32 if precision == "fp32_refine" else torch.float64
+        desc = N.GridDesc()
+        desc.nx, desc.ny, desc.nz = nx, ny, nz
+        desc.lx, desc.ly, desc.lz = lx, ly, lz
+        desc.re, desc.u_lid = re, u_lid
+        for a in range(3):
+            desc.bc[a] = _BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+        desc.solid_mask = None
+        desc.precision = _PREC[precision]
+        desc.poisson_rtol = poisson_rtol
+        desc.poisson_maxit = poisson_maxit
+        desc.refine_rtol = refine_rtol
+        desc.inner_rtol = inner_rtol
+        desc.batch = batch
+        self._desc = desc
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            h = ctypes.c_void_p()
+            N.check(self.lib.ns_create_grid(ctypes.byref(desc), ctypes.c_void_p(stream),
+                                            ctypes.byref(h)), "ns_create_grid")
+        self._h = h
+        self._stream = stream
+
+    # --- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.ns_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            N.check(self.lib.ns_set_stream(self._h, ctypes.c_void_p(s)), "ns_set_stream")
+            self._stream = s
+
+    # --- states -----------------------------------------------------------
+    def shapes(self):
+        return _shapes(self.nx, self.ny, self.nz, self.bc)
+
+    def zeros(self, batch: int = 1, device=None) -> State:
+        dev = self.device if device is None else device
+        shp = self.shapes()
+        return State(*[torch.zeros((batch,) + s, dtype=self.vel_dtype, device=dev)
+                       for s in shp[:3]],
+                     torch.zeros((batch,) + shp[3], dtype=torch.float64, device=dev))
+
+    def state_from(self, arrays: Sequence, device=None) -> State:
+        """State from per-field arrays shaped [batch][...] or [...] (batch 1)."""
+        dev = self.device if device is None else device
+        shp = self.shapes()
+        out = []
+        for c, a in enumerate(arrays):
+            t = torch.as_tensor(np.asarray(a))
+            if t.dim() == 3:
+                t = t.unsqueeze(0)
+            assert tuple(t.shape[1:]) == shp[c], (t.shape, shp[c])
+            dt = torch.float64 if c == 3 else self.vel_dtype
+            out.append(t.to(device=dev, dtype=dt).contiguous())
+        return State(*out)
+
+    def _check(self, st: State, what: str):
+        shp = self.shapes()
+        for c, t in enumerate(st.fields()):
+            want = torch.float64 if c == 3 else self.vel_dtype
+            if t.dtype != want or not t.is_contiguous() or t.device != self.device:
+                raise ValueError(f"{what}: field {c} must be a contiguous {want} tensor on "
+                                 f"{self.device}")
+            if tuple(t.shape[1:]) != shp[c] or t.shape[0] != st.batch:
+                raise ValueError(f"{what}: field {c} has shape {tuple(t.shape)}, expected "
+                                 f"[batch]{shp[c]}")
+
+    # --- the C ABI calls ------------------------------------------------------
+    def step_fine(self, st: State, dt: float, nsteps: int) -> State:
+        self._check(st, "step_fine")
+        self._sync_stream()
+        N.check(self.lib.ns_step_fine(self._h, st._c(), dt, nsteps), "ns_step_fine")
+        return st
+
+    def step_coarse(self, st: State, dt: float, nsteps: int) -> State:
+        self._check(st, "step_coarse")
+        self._sync_stream()
+        N.check(self.lib.ns_step_coarse(self._h, st._c(), dt, nsteps), "ns_step_coarse")
+        return st
+
+    def project(self, st: State) -> State:
+        self._check(st, "project")
+        self._sync_stream()
+        N.check(self.lib.ns_project(self._h, st._c()), "ns_project")
+        return st
+
+    def predict(self, st: State, dt: float) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+        self._check(st, "predict")
+        self._sync_stream()
+        out = [torch.empty_like(t) for t in (st.u, st.v, st.w)]
+        N.check(self.lib.ns_predict(self._h, st._c(), dt, *[o.data_ptr() for o in out]),
+                "ns_predict")
+        return tuple(out)
+
+    def poisson_solve(self, b: torch.Tensor, p: torch.Tensor) -> int:
+        """Gauged solve of L p = b for a batch; p is the warm start and the output."""
+        for t in (b, p):
+            if t.dtype != torch.float64 or not t.is_contiguous() or t.device != self.device:
+                raise ValueError("poisson_solve: b and p must be contiguous float64 on device")
+        if b.dim() == 3:
+            b, p = b.unsqueeze(0), p.unsqueeze(0)
+        self._sync_stream()
+        it = ctypes.c_int(0)
+        N.check(self.lib.ns_poisson_solve(self._h, b.data_ptr(), p.data_ptr(), int(b.shape[0]),
+                                          ctypes.byref(it)), "ns_poisson_solve")
+        return it.value
+
+    def parareal(self, u0: State, slices: State, n_slices: int, fine_steps: int,
+                 coarse_steps: int, dt_fine: float, kmax: int, tol: float = 0.0,
+                 resume: bool = False):
+        """Parareal (Eq. 6).  Returns (iterations done, list of defects)."""
+        self._check(u0, "parareal(u0)")
+        self._check(slices, "parareal(slices)")
+        self._sync_stream()
+        k = ctypes.c_int(0)
+        d = (ctypes.c_double * max(kmax, 1))()
+        N.check(self.lib.ns_parareal_iterate(self._h, u0._c(), slices._c(), n_slices, fine_steps,
+                                             coarse_steps, dt_fine, kmax, tol, int(resume),
+                                             ctypes.byref(k), d), "ns_parareal_iterate")
+        return k.value, [d[i] for i in range(k.value)]
+
+    def parareal_host(self, u0: State, slices_host: State, n_slices: int, fine_steps: int,
+                      coarse_steps: int, dt_fine: float, kmax: int, tol: float = 0.0,
+                      resume: bool = False, slices_dev: Optional[State] = None):
+        """End-to-end Parareal with the slices in host memory: copies them to
+        the device (from pinned memory when they are pinned), runs, copies
+        them back.  Returns (iterations, defects, bytes H2D, bytes D2H)."""
+        dev = slices_dev if slices_dev is not None else self.zeros(slices_host.batch)
+        h2d = 0
+        for src, dst in zip(slices_host.fields(), dev.fields()):
+            dst.copy_(src, non_blocking=True)
+            h2d += src.numel() * src.element_size()
+        k, d = self.parareal(u0, dev, n_slices, fine_steps, coarse_steps, dt_fine, kmax, tol,
+                             resume)
+        d2h = 0
+        for src, dst in zip(dev.fields(), slices_host.fields()):
+            dst.copy_(src, non_blocking=True)
+            d2h += src.numel() * src.element_size()
+        torch.cuda.current_stream(self.device).synchronize()
+        return k, d, h2d, d2h
+
+    def adjoint(self, u0: State, dt: float, nsteps: int, ckpt_every: int):
+        self._sync_stream()
+        J = ctypes.c_double(0)
+        dl = ctypes.c_double(0)
+        grad = self.zeros(1)
+        N.check(self.lib.ns_adjoint(self._h, u0._c(), dt, nsteps, ckpt_every, ctypes.byref(J),
+                                    grad._c(), ctypes.byref(dl)), "ns_adjoint")
+        return J.value, grad, dl.value
+
+    def stats(self) -> dict:
+        s = N.Stats()
+        N.check(self.lib.ns_get_stats(self._h, ctypes.byref(s)), "ns_get_stats")
+        return {f: getattr(s, f) for f, _ in N.Stats._fields_}
+
+    def reset_stats(self):
+        N.check(self.lib.ns_reset_stats(self._h), "ns_reset_stats")
+
+    def profile(self, on: bool, min_batch: int = 1):
+        """Per-launch CUDA-event timing of calls with batch >= min_batch."""
+        N.check(self.lib.ns_profile_enable(self._h, int(on), int(min_batch)),
+                "ns_profile_enable")
+
+    def profile_read(self) -> dict:
+        arr = (N.KernelTime * len(N.KERNEL_KINDS))()
+        N.check(self.lib.ns_profile_read(self._h, arr, len(N.KERNEL_KINDS)), "ns_profile_read")
+        return {k: {"ms": arr[i].ms, "launches": arr[i].launches,
+                    "cell_units": arr[i].cell_units}
+                for i, k in enumerate(N.KERNEL_KINDS)}

@@ -1,0 +1,800 @@
+// C ABI (include/ns.h): grid objects, workspace, and the host-side drivers of
+// the projection step, the pressure solves and Parareal.  All arithmetic runs
+// in the kernels of ns_kernels.cuh; the host only sequences launches and reads
+// the per-state convergence flags.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ns.h"
+#include "ns_kernels.cuh"
+
+using namespace nsk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ns_status fail(ns_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define NS_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(NS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define NS_TRY(expr)                         \
+    do {                                     \
+        ns_status s_ = (expr);               \
+        if (s_ != NS_OK) return s_;          \
+    } while (0)
+
+constexpr int kMaxOuter = 40;
+
+}  // namespace
+
+struct ns_grid {
+    ns_grid_desc d{};
+    Geo geo{};
+    cudaStream_t stream = nullptr;
+    int cap = 0;
+    bool fp32 = false;
+    int maxit = 0;
+    double inner_rtol = 1e-4;
+    // workspace, [cap][...]
+    void* fs[3] = {nullptr, nullptr, nullptr};  // F* (element type of the precision)
+    double* b = nullptr;                        // right side of the pressure equation
+    void* kv[8] = {};                           // Krylov vectors: x r rhat P0 P1 V0 V1 t
+    double* p64[2] = {nullptr, nullptr};        // FP32+refine: FP64 pressure iterates
+    double* part_div = nullptr;
+    double* part_a = nullptr;
+    double* part_b = nullptr;
+    double* part_c = nullptr;
+    double* part_r = nullptr;
+    SliceCtl* ctl = nullptr;
+    SliceCtl* h_ctl = nullptr;                  // pinned host mirror
+    unsigned long long* d_defect = nullptr;
+    unsigned long long* h_defect = nullptr;
+    int iter_hint = 16;
+    ns_stats stats{};
+    // per-launch timing (ns_profile_enable)
+    struct Prof {
+        bool on = false;
+        bool active = false;  // the current call is timed (batch >= min_batch)
+        int min_batch = 1;
+        int cap = 0;          // event pairs in the pool
+        int n = 0;            // pairs recorded and not yet harvested
+        std::vector<cudaEvent_t> ev;
+        std::vector<int> kind;
+        std::vector<long long> units;
+        ns_kernel_time acc[NS_K_KINDS];
+    } prof;
+    // Parareal buffers (allocated on first use)
+    void* pr_f[4] = {};
+    void* pr_gold[4] = {};
+    void* pr_g[4] = {};
+    int pr_n = 0;
+    const void* pr_slices_u = nullptr;
+    bool pr_valid = false;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+size_t elem_vel(const ns_grid* g) { return g->fp32 ? sizeof(float) : sizeof(double); }
+
+ns_status dalloc(ns_grid* g, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(NS_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) +
+                                    " bytes failed: " + cudaGetErrorString(e));
+    }
+    g->allocs.push_back(*p);
+    return NS_OK;
+}
+
+void free_all(ns_grid* g) {
+    for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
+    g->prof.ev.clear();
+    for (void* p : g->allocs) cudaFree(p);
+    g->allocs.clear();
+    if (g->h_ctl) cudaFreeHost(g->h_ctl);
+    if (g->h_defect) cudaFreeHost(g->h_defect);
+    g->h_ctl = nullptr;
+    g->h_defect = nullptr;
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+void setup_geo(ns_grid* g) {
+    Geo& G = g->geo;
+    const ns_grid_desc& d = g->d;
+    G.n[0] = d.nx;
+    G.n[1] = d.ny;
+    G.n[2] = d.nz;
+    const double L[3] = {d.lx, d.ly, d.lz};
+    for (int a = 0; a < 3; ++a) {
+        G.bc[a] = d.bc[a];
+        G.h[a] = L[a] / G.n[a];
+        G.ih[a] = 1.0 / G.h[a];
+        G.ih2[a] = 1.0 / (G.h[a] * G.h[a]);
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a)
+            G.ext[c][a] = G.n[a] + ((c == a && G.bc[a] != BC_PERIODIC) ? 1 : 0);
+    for (int c = 0; c < 3; ++c)
+        G.cnt[c] = (long long)G.ext[c][0] * G.ext[c][1] * G.ext[c][2];
+    G.cnt[3] = (long long)G.n[0] * G.n[1] * G.n[2];
+    G.inv_re = 1.0 / d.re;
+    G.u_lid = d.u_lid;
+    // cells per thread along z: fixed per grid (not per batch) so that every
+    // state is reduced over the same CTAs whatever the batch size
+    G.tz = std::min(8, G.n[2]);
+    G.bx = ceil_div(G.n[0], TX);
+    G.by = ceil_div(G.n[1], TY);
+    G.bz = ceil_div(G.n[2], G.tz);
+    G.ctas = G.bx * G.by * G.bz;
+    G.fbx = ceil_div(G.n[0] + 1, TX);
+    G.fby = ceil_div(G.n[1] + 1, TY);
+    G.fbz = ceil_div(G.n[2] + 1, G.tz);
+    G.fctas = G.fbx * G.fby * G.fbz;
+    G.n_fluid = G.n[0] * G.n[1] * G.n[2];
+}
+
+ns_status check_state(const ns_grid* g, const ns_state& s, const char* what) {
+    if (!s.u || !s.v || !s.w || !s.p)
+        return fail(NS_ERR_ARG, std::string(what) + ": null state pointer");
+    if (s.batch < 1 || s.batch > g->cap)
+        return fail(NS_ERR_ARG, std::string(what) + ": batch " + std::to_string(s.batch) +
+                                    " outside [1, " + std::to_string(g->cap) + "]");
+    return NS_OK;
+}
+
+template <typename T>
+KBuf<T> kbuf(const ns_grid* g) {
+    KBuf<T> k;
+    k.x = (T*)g->kv[0];
+    k.r = (T*)g->kv[1];
+    k.rhat = (T*)g->kv[2];
+    k.P[0] = (T*)g->kv[3];
+    k.P[1] = (T*)g->kv[4];
+    k.V[0] = (T*)g->kv[5];
+    k.V[1] = (T*)g->kv[6];
+    k.t = (T*)g->kv[7];
+    return k;
+}
+
+dim3 block_dim() { return dim3(TX, TY, 1); }
+
+// Accumulates the event pairs recorded so far; the stream must have been
+// synchronised since the last one was recorded.
+ns_status prof_harvest(ns_grid* g) {
+    auto& P = g->prof;
+    for (int q = 0; q < P.n; ++q) {
+        float ms = 0.0f;
+        NS_CUDA(cudaEventElapsedTime(&ms, P.ev[2 * q], P.ev[2 * q + 1]));
+        ns_kernel_time& a = P.acc[P.kind[q]];
+        a.ms += ms;
+        a.launches += 1;
+        a.cell_units += P.units[q];
+    }
+    P.n = 0;
+    return NS_OK;
+}
+
+ns_status sync_stream(ns_grid* g) {
+    NS_CUDA(cudaStreamSynchronize(g->stream));
+    if (g->prof.n) NS_TRY(prof_harvest(g));
+    return NS_OK;
+}
+
+void prof_begin(ns_grid* g, int kind, long long units) {
+    auto& P = g->prof;
+    if (!(P.on && P.active)) return;
+    if (P.n == P.cap) {
+        if (sync_stream(g) != NS_OK) return;
+    }
+    cudaEventRecord(P.ev[2 * P.n], g->stream);
+    P.kind[P.n] = kind;
+    P.units[P.n] = units;
+}
+
+void prof_end(ns_grid* g) {
+    auto& P = g->prof;
+    g->stats.launches += 1;
+    if (!(P.on && P.active)) return;
+    cudaEventRecord(P.ev[2 * P.n + 1], g->stream);
+    P.n += 1;
+}
+
+#define NS_LAUNCH(g, kind, units, ...)    \
+    do {                                  \
+        prof_begin((g), (kind), (units)); \
+        __VA_ARGS__;                      \
+        prof_end((g));                    \
+    } while (0)
+
+ns_status poll_ctl(ns_grid* g, int batch) {
+    NS_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(SliceCtl) * batch, cudaMemcpyDeviceToHost,
+                            g->stream));
+    return sync_stream(g);
+}
+
+// Runs BiCGStab iterations (phases A, B, C) on every state whose status is
+// ST_ITER until none is; the host polls the flags only near the expected
+// iteration count, so most iterations are launched back to back.
+template <typename T>
+ns_status run_krylov(ns_grid* g, int batch, double rtol, int* max_iters, double* max_rel) {
+    const Geo& G = g->geo;
+    KBuf<T> kb = kbuf<T>(g);
+    const dim3 grid(G.ctas, batch);
+    const double tol2 = rtol * rtol;
+    int next_poll = std::max(1, g->iter_hint - 2);
+    int it = 1;
+    for (;; ++it) {
+        const int par = it & 1;
+        NS_LAUNCH(g, NS_K_KRYLOV_A, 0,
+                  k_bicg_A<T><<<grid, block_dim(), 0, g->stream>>>(G, kb, g->ctl, g->part_c,
+                                                                   g->part_a, tol2, g->maxit, par));
+        NS_LAUNCH(g, NS_K_KRYLOV_B, 0,
+                  k_bicg_B<T><<<grid, block_dim(), 0, g->stream>>>(G, kb, g->ctl, g->part_a,
+                                                                   g->part_b, par));
+        NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
+                  k_bicg_C<T><<<grid, block_dim(), 0, g->stream>>>(G, kb, g->ctl, g->part_b,
+                                                                   g->part_c, par));
+        NS_CUDA(cudaGetLastError());
+        if (it >= next_poll) {
+            NS_TRY(poll_ctl(g, batch));
+            bool any = false;
+            for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].status == ST_ITER;
+            if (!any) break;
+            if (it > g->maxit + 2) break;
+            next_poll = it + std::max(2, it / 8);
+        }
+    }
+    int mx = 0;
+    double mr = 0.0;
+    ns_status st = NS_OK;
+    long long cell_iters = 0;
+    for (int s = 0; s < batch; ++s) {
+        const SliceCtl& c = g->h_ctl[s];
+        if (c.status == ST_IDLE) continue;  // not part of this solve
+        cell_iters += (long long)c.it_cur * G.cnt[3];
+        mx = std::max(mx, c.it_cur);
+        const double rel = c.bb > 0 ? std::sqrt(c.rr / c.bb) : std::sqrt(c.rr);
+        mr = std::max(mr, rel);
+        if (c.status == ST_NONFINITE)
+            st = fail(NS_ERR_NONFINITE, "non-finite residual in the pressure solve");
+        else if ((c.status == ST_MAXIT || c.status == ST_ITER) && st == NS_OK)
+            st = fail(NS_ERR_NOT_CONVERGED,
+                      "pressure solve reached its iteration limit (" + std::to_string(g->maxit) +
+                          "), relative residual " + std::to_string(rel));
+        g->stats.krylov_iters += c.it_cur;
+    }
+    if (g->prof.on && g->prof.active)
+        for (int kind : {NS_K_KRYLOV_A, NS_K_KRYLOV_B, NS_K_KRYLOV_C})
+            g->prof.acc[kind].cell_units += cell_iters;
+    g->iter_hint = std::max(1, mx);
+    if (max_iters) *max_iters = std::max(*max_iters, mx);
+    if (max_rel) *max_rel = std::max(*max_rel, mr);
+    return st;
+}
+
+// Gauged pressure solve.  Input: g->b (double, [batch][cells]) and its partial
+// sums in g->part_div; warm start p_in (double, device).  Result: the solution
+// buffer of each state (FP64: kv x; FP32+refine: p64[p_final]) and its sum in
+// SliceCtl.sx.
+ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
+    const Geo& G = g->geo;
+    const dim3 grid(G.ctas, batch);
+    int max_iters = 0;
+    double max_rel = 0.0;
+    if (!g->fp32) {
+        KBuf<double> kb = kbuf<double>(g);
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, G.cnt[3] * batch,
+                  k_bicg_init_warm<double><<<grid, block_dim(), 0, g->stream>>>(
+                      G, kb, g->ctl, g->part_div, g->b, p_in, g->part_c));
+        NS_CUDA(cudaGetLastError());
+        NS_TRY(run_krylov<double>(g, batch, g->d.poisson_rtol, &max_iters, &max_rel));
+    } else {
+        KBuf<float> kb = kbuf<float>(g);
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, G.cnt[3] * batch,
+                  k_refine_init<<<grid, block_dim(), 0, g->stream>>>(G, g->ctl, g->part_div, g->b,
+                                                                     p_in, g->p64[0], kb.r,
+                                                                     g->part_r));
+        NS_CUDA(cudaGetLastError());
+        const double tol2 = g->d.refine_rtol * g->d.refine_rtol;
+        int m = 0;
+        for (;; ++m) {
+            NS_LAUNCH(g, NS_K_INNER_INIT, G.cnt[3] * batch,
+                      k_inner_init<<<grid, block_dim(), 0, g->stream>>>(
+                          G, kb, g->ctl, g->part_r, g->part_c, tol2, m, kMaxOuter));
+            NS_CUDA(cudaGetLastError());
+            NS_TRY(poll_ctl(g, batch));
+            bool any = false;
+            for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].o_status == OS_REFINE;
+            if (!any) break;
+            ns_status st = run_krylov<float>(g, batch, g->inner_rtol, &max_iters, nullptr);
+            if (st == NS_ERR_NONFINITE) return st;
+            // a stalled inner solve still improves p; the outer test decides
+            (void)st;
+            g_last_error.clear();
+            NS_LAUNCH(g, NS_K_REFINE, G.cnt[3] * batch,
+                      k_refine_update<<<grid, block_dim(), 0, g->stream>>>(
+                          G, g->ctl, g->b, g->p64[m & 1], g->p64[(m + 1) & 1], kb.x, kb.r,
+                          g->part_r));
+            NS_CUDA(cudaGetLastError());
+        }
+        for (int s = 0; s < batch; ++s) {
+            const SliceCtl& c = g->h_ctl[s];
+            const double rel = c.o_bb > 0 ? std::sqrt(c.o_rr / c.o_bb) : std::sqrt(c.o_rr);
+            max_rel = std::max(max_rel, rel);
+            g->stats.refine_steps += c.o_steps;
+            if (c.o_status == OS_NONFINITE)
+                return fail(NS_ERR_NONFINITE, "non-finite residual in the pressure solve");
+            if (c.o_status != OS_DONE)
+                return fail(NS_ERR_NOT_CONVERGED,
+                            "iterative refinement did not reach refine_rtol (relative residual " +
+                                std::to_string(rel) + ")");
+        }
+    }
+    g->stats.solves += batch;
+    g->stats.last_max_iters = max_iters;
+    g->stats.last_rel_residual = max_rel;
+    return NS_OK;
+}
+
+template <typename T>
+ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
+    const Geo& G = g->geo;
+    const int B = io.batch;
+    const dim3 gcell(G.ctas, B), gface(G.fctas, B);
+    T* u = (T*)io.u;
+    T* v = (T*)io.v;
+    T* w = (T*)io.w;
+    double* p = (double*)io.p;
+    T* fu = (T*)g->fs[0];
+    T* fv = (T*)g->fs[1];
+    T* fw = (T*)g->fs[2];
+    const double* x0 = g->fp32 ? g->p64[0] : (const double*)g->kv[0];
+    const double* x1 = g->fp32 ? g->p64[1] : (const double*)g->kv[0];
+    g->prof.active = B >= g->prof.min_batch;
+    const long long cells = G.cnt[3] * B;
+    for (int n = 0; n < nsteps; ++n) {
+        NS_LAUNCH(g, NS_K_PREDICT, cells,
+                  k_predict<T><<<gface, block_dim(), 0, g->stream>>>(G, u, v, w, fu, fv, fw, dt));
+        NS_LAUNCH(g, NS_K_DIVERGENCE, cells,
+                  k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(G, fu, fv, fw, g->b,
+                                                                        g->part_div, 1.0 / dt));
+        NS_CUDA(cudaGetLastError());
+        NS_TRY(solve_pressure(g, B, p));
+        NS_LAUNCH(g, NS_K_CORRECT, cells,
+                  k_correct<T><<<gface, block_dim(), 0, g->stream>>>(G, g->ctl, fu, fv, fw, u, v,
+                                                                     w, x0, x1, p, dt));
+        NS_CUDA(cudaGetLastError());
+        g->stats.steps += B;
+    }
+    return NS_OK;
+}
+
+ns_status step_any(ns_grid* g, const ns_state& io, double dt, int nsteps, const char* what) {
+    if (!g) return fail(NS_ERR_ARG, std::string(what) + ": null grid");
+    NS_TRY(check_state(g, io, what));
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return fail(NS_ERR_ARG, std::string(what) + ": dt must be positive and finite");
+    if (nsteps < 0) return fail(NS_ERR_ARG, std::string(what) + ": nsteps < 0");
+    if (nsteps == 0) return NS_OK;
+    return g->fp32 ? step_impl<float>(g, io, dt, nsteps) : step_impl<double>(g, io, dt, nsteps);
+}
+
+template <typename T>
+ns_status project_impl(ns_grid* g, const ns_state& io) {
+    const Geo& G = g->geo;
+    const int B = io.batch;
+    const dim3 gcell(G.ctas, B), gface(G.fctas, B);
+    T* u = (T*)io.u;
+    T* v = (T*)io.v;
+    T* w = (T*)io.w;
+    g->prof.active = B >= g->prof.min_batch;
+    NS_LAUNCH(g, NS_K_DIVERGENCE, G.cnt[3] * B,
+              k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(G, u, v, w, g->b, g->part_div,
+                                                                    1.0));
+    NS_CUDA(cudaMemsetAsync(g->p64[1], 0, sizeof(double) * G.cnt[3] * B, g->stream));
+    NS_CUDA(cudaGetLastError());
+    // zero warm start: p64[1] is free scratch at this point in both precisions
+    NS_TRY(solve_pressure(g, B, g->p64[1]));
+    const double* x0 = g->fp32 ? g->p64[0] : (const double*)g->kv[0];
+    const double* x1 = g->fp32 ? g->p64[1] : (const double*)g->kv[0];
+    NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
+              k_correct<T><<<gface, block_dim(), 0, g->stream>>>(G, g->ctl, u, v, w, u, v, w, x0,
+                                                                 x1, nullptr, 1.0));
+    NS_CUDA(cudaGetLastError());
+    return NS_OK;
+}
+
+template <typename T>
+ns_status copy_states(ns_grid* g, void* const dst[4], const void* const src[4], long long di,
+                      long long si, long long count) {
+    const Geo& G = g->geo;
+    for (int c = 0; c < 4; ++c) {
+        const size_t es = c == 3 ? sizeof(double) : sizeof(T);
+        const size_t per = (size_t)G.cnt[c] * es;
+        NS_CUDA(cudaMemcpyAsync((char*)dst[c] + di * per, (const char*)src[c] + si * per,
+                                per * count, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    return NS_OK;
+}
+
+template <typename T>
+ns_status parareal_update(ns_grid* g, const void* const fy[4], const void* const gnew[4],
+                          void* const gold[4], void* const y[4], long long fi, long long gi,
+                          long long yi) {
+    const Geo& G = g->geo;
+    for (int c = 0; c < 4; ++c) {
+        const long long n = G.cnt[c];
+        const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+        if (c < 3) {
+            NS_LAUNCH(g, NS_K_PARAREAL, n,
+                      k_parareal_update<T><<<blocks, 256, 0, g->stream>>>(
+                          n, (const T*)fy[c] + fi * n, (const T*)gnew[c] + 0,
+                          (T*)gold[c] + gi * n, (T*)y[c] + yi * n, g->d_defect));
+        } else {
+            NS_LAUNCH(g, NS_K_PARAREAL, n,
+                      k_parareal_update<double><<<blocks, 256, 0, g->stream>>>(
+                          n, (const double*)fy[c] + fi * n, (const double*)gnew[c] + 0,
+                          (double*)gold[c] + gi * n, (double*)y[c] + yi * n, g->d_defect));
+        }
+    }
+    NS_CUDA(cudaGetLastError());
+    return NS_OK;
+}
+
+template <typename T>
+ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, int M,
+                        double dt, int kmax, double tol, int resume, int* k_done,
+                        double* defects) {
+    const Geo& G = g->geo;
+    if (!g->pr_f[0] || g->pr_n < N) {
+        for (int c = 0; c < 4; ++c) {
+            const size_t es = c == 3 ? sizeof(double) : sizeof(T);
+            NS_TRY(dalloc(g, &g->pr_f[c], (size_t)G.cnt[c] * es * g->cap));
+            NS_TRY(dalloc(g, &g->pr_gold[c], (size_t)G.cnt[c] * es * g->cap));
+            NS_TRY(dalloc(g, &g->pr_g[c], (size_t)G.cnt[c] * es));
+        }
+        g->pr_n = g->cap;
+        g->pr_valid = false;
+    }
+    void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
+    const void* u0s[4] = {u0.u, u0.v, u0.w, u0.p};
+    const double dtc = dt * S / M;
+    ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
+    if (resume) {
+        if (!g->pr_valid || g->pr_slices_u != slices.u || g->pr_n < N)
+            return fail(NS_ERR_ARG, "ns_parareal_iterate: resume=1 without stored coarse values "
+                                    "for these slices");
+    } else {
+        NS_TRY(copy_states<T>(g, ys, u0s, 0, 0, 1));
+        for (int n = 0; n < N; ++n) {
+            NS_TRY(copy_states<T>(g, ys, ys, n + 1, n, 1));
+            ns_state one{(char*)slices.u + (size_t)(n + 1) * G.cnt[0] * sizeof(T),
+                         (char*)slices.v + (size_t)(n + 1) * G.cnt[1] * sizeof(T),
+                         (char*)slices.w + (size_t)(n + 1) * G.cnt[2] * sizeof(T),
+                         (char*)slices.p + (size_t)(n + 1) * G.cnt[3] * sizeof(double), 1};
+            NS_TRY(step_impl<T>(g, one, dtc, M));
+            NS_TRY(copy_states<T>(g, g->pr_gold, ys, n, n + 1, 1));
+        }
+    }
+    g->pr_valid = false;
+    int k = 0;
+    for (; k < kmax; ++k) {
+        // F(y^k_n) for all n in one batched sweep
+        NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
+        ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
+        NS_TRY(step_impl<T>(g, fb, dt, S));
+        NS_CUDA(cudaMemsetAsync(g->d_defect, 0, sizeof(unsigned long long), g->stream));
+        // serial coarse sweep with the update of Eq. 6
+        for (int n = 0; n < N; ++n) {
+            NS_TRY(copy_states<T>(g, g->pr_g, ys, 0, n, 1));
+            NS_TRY(step_impl<T>(g, gs, dtc, M));
+            NS_TRY(parareal_update<T>(g, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
+        }
+        NS_CUDA(cudaMemcpyAsync(g->h_defect, g->d_defect, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, g->stream));
+        NS_TRY(sync_stream(g));
+        double dk;
+        std::memcpy(&dk, g->h_defect, sizeof(double));
+        if (defects) defects[k] = dk;
+        if (!std::isfinite(dk)) {
+            if (k_done) *k_done = k + 1;
+            return fail(NS_ERR_NONFINITE, "non-finite Parareal defect");
+        }
+        if (tol > 0.0 && dk <= tol) {
+            ++k;
+            break;
+        }
+    }
+    if (k_done) *k_done = k;
+    g->pr_valid = true;
+    g->pr_slices_u = slices.u;
+    return sync_stream(g);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ns_last_error(void) { return g_last_error.c_str(); }
+
+ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** out) {
+    g_last_error.clear();
+    if (!desc || !out) return fail(NS_ERR_ARG, "ns_create_grid: null argument");
+    *out = nullptr;
+    const ns_grid_desc& d = *desc;
+    if (d.nx < 2 || d.ny < 2 || d.nz < 2)
+        return fail(NS_ERR_ARG, "ns_create_grid: every axis needs at least 2 cells");
+    if ((long long)d.nx * d.ny * d.nz > (1LL << 31) - 1)
+        return fail(NS_ERR_ARG, "ns_create_grid: more than 2^31-1 cells");
+    if (!(d.lx > 0) || !(d.ly > 0) || !(d.lz > 0))
+        return fail(NS_ERR_ARG, "ns_create_grid: box sizes must be positive");
+    if (!(d.re > 0) || !std::isfinite(d.re))
+        return fail(NS_ERR_ARG, "ns_create_grid: re must be positive and finite");
+    if (!std::isfinite(d.u_lid)) return fail(NS_ERR_ARG, "ns_create_grid: u_lid not finite");
+    for (int a = 0; a < 3; ++a)
+        if (d.bc[a] != NS_BC_WALL && d.bc[a] != NS_BC_PERIODIC && d.bc[a] != NS_BC_SLIP)
+            return fail(NS_ERR_ARG, "ns_create_grid: unknown boundary condition");
+    if (d.solid_mask)
+        return fail(NS_ERR_ARG, "ns_create_grid: solid cells are not supported by the stepper "
+                                "in this version");
+    if (d.precision != NS_FP64 && d.precision != NS_FP32_REFINE)
+        return fail(NS_ERR_ARG, "ns_create_grid: unknown precision");
+    if (!(d.poisson_rtol > 0) && d.precision == NS_FP64)
+        return fail(NS_ERR_ARG, "ns_create_grid: poisson_rtol must be positive");
+    if (d.precision == NS_FP32_REFINE && !(d.refine_rtol > 0))
+        return fail(NS_ERR_ARG, "ns_create_grid: refine_rtol must be positive");
+    if (d.batch < 1) return fail(NS_ERR_ARG, "ns_create_grid: batch must be >= 1");
+
+    ns_grid* g = new (std::nothrow) ns_grid();
+    if (!g) return fail(NS_ERR_OOM, "ns_create_grid: host allocation failed");
+    g->d = d;
+    g->d.solid_mask = nullptr;
+    g->stream = (cudaStream_t)cuda_stream;
+    g->cap = d.batch;
+    g->fp32 = d.precision == NS_FP32_REFINE;
+    g->maxit = d.poisson_maxit > 0 ? d.poisson_maxit : 20 * std::max(d.nx, std::max(d.ny, d.nz));
+    g->inner_rtol = d.inner_rtol > 0 ? d.inner_rtol : 1e-4;
+    setup_geo(g);
+    const Geo& G = g->geo;
+    const size_t B = (size_t)g->cap;
+    const size_t ncell = (size_t)G.cnt[3];
+    const size_t ev = elem_vel(g);
+    ns_status st = NS_OK;
+    auto A = [&](void** p, size_t bytes) {
+        if (st == NS_OK) st = dalloc(g, p, bytes);
+    };
+    for (int c = 0; c < 3; ++c) A(&g->fs[c], (size_t)G.cnt[c] * ev * B);
+    A((void**)&g->b, ncell * sizeof(double) * B);
+    for (int q = 0; q < 8; ++q) A(&g->kv[q], ncell * ev * B);
+    A((void**)&g->p64[0], ncell * sizeof(double) * B);
+    A((void**)&g->p64[1], ncell * sizeof(double) * B);
+    const size_t nparts = (size_t)G.ctas * B;
+    A((void**)&g->part_div, nparts * sizeof(double));
+    A((void**)&g->part_a, nparts * sizeof(double));
+    A((void**)&g->part_b, nparts * 2 * sizeof(double));
+    A((void**)&g->part_c, nparts * 4 * sizeof(double));
+    A((void**)&g->part_r, nparts * 3 * sizeof(double));
+    A((void**)&g->ctl, sizeof(SliceCtl) * B);
+    A((void**)&g->d_defect, sizeof(unsigned long long));
+    if (st == NS_OK) {
+        if (cudaMallocHost((void**)&g->h_ctl, sizeof(SliceCtl) * B) != cudaSuccess ||
+            cudaMallocHost((void**)&g->h_defect, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(NS_ERR_OOM, "ns_create_grid: pinned host allocation failed");
+        }
+    }
+    if (st == NS_OK) {
+        // zero once: P/V of the idle parity and the wall faces of F*
+        for (int c = 0; c < 3; ++c)
+            if (cudaMemsetAsync(g->fs[c], 0, (size_t)G.cnt[c] * ev * B, g->stream) != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        for (int q = 0; q < 8 && st == NS_OK; ++q)
+            if (cudaMemsetAsync(g->kv[q], 0, ncell * ev * B, g->stream) != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        if (st == NS_OK &&
+            cudaMemsetAsync(g->ctl, 0, sizeof(SliceCtl) * B, g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        if (st == NS_OK && cudaStreamSynchronize(g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "ns_create_grid: stream synchronize failed");
+    }
+    if (st != NS_OK) {
+        free_all(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return NS_OK;
+}
+
+ns_status ns_destroy_grid(ns_grid* grid) {
+    if (!grid) return NS_OK;
+    cudaStreamSynchronize(grid->stream);
+    free_all(grid);
+    delete grid;
+    return NS_OK;
+}
+
+ns_status ns_set_stream(ns_grid* grid, void* cuda_stream) {
+    if (!grid) return fail(NS_ERR_ARG, "ns_set_stream: null grid");
+    grid->stream = (cudaStream_t)cuda_stream;
+    return NS_OK;
+}
+
+ns_status ns_step_fine(ns_grid* grid, ns_state io, double dt, int nsteps) {
+    g_last_error.clear();
+    return step_any(grid, io, dt, nsteps, "ns_step_fine");
+}
+
+ns_status ns_step_coarse(ns_grid* grid, ns_state io, double dt_coarse, int nsteps) {
+    g_last_error.clear();
+    return step_any(grid, io, dt_coarse, nsteps, "ns_step_coarse");
+}
+
+ns_status ns_project(ns_grid* grid, ns_state io) {
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_project: null grid");
+    NS_TRY(check_state(grid, io, "ns_project"));
+    ns_status st = grid->fp32 ? project_impl<float>(grid, io) : project_impl<double>(grid, io);
+    if (st == NS_OK) NS_TRY(sync_stream(grid));
+    return st;
+}
+
+ns_status ns_predict(ns_grid* grid, ns_state in, double dt, void* fu, void* fv, void* fw) {
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_predict: null grid");
+    NS_TRY(check_state(grid, in, "ns_predict"));
+    if (!fu || !fv || !fw) return fail(NS_ERR_ARG, "ns_predict: null output pointer");
+    if (!std::isfinite(dt)) return fail(NS_ERR_ARG, "ns_predict: dt not finite");
+    const Geo& G = grid->geo;
+    const dim3 gface(G.fctas, in.batch);
+    grid->prof.active = in.batch >= grid->prof.min_batch;
+    if (grid->fp32)
+        NS_LAUNCH(grid, NS_K_PREDICT, G.cnt[3] * in.batch,
+                  k_predict<float><<<gface, block_dim(), 0, grid->stream>>>(
+                      G, (const float*)in.u, (const float*)in.v, (const float*)in.w, (float*)fu,
+                      (float*)fv, (float*)fw, dt));
+    else
+        NS_LAUNCH(grid, NS_K_PREDICT, G.cnt[3] * in.batch,
+                  k_predict<double><<<gface, block_dim(), 0, grid->stream>>>(
+                      G, (const double*)in.u, (const double*)in.v, (const double*)in.w,
+                      (double*)fu, (double*)fv, (double*)fw, dt));
+    NS_CUDA(cudaGetLastError());
+    NS_TRY(sync_stream(grid));
+    return NS_OK;
+}
+
+ns_status ns_poisson_solve(ns_grid* grid, const double* b, double* p, int batch, int* iters) {
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_poisson_solve: null grid");
+    if (!b || !p) return fail(NS_ERR_ARG, "ns_poisson_solve: null pointer");
+    if (batch < 1 || batch > grid->cap)
+        return fail(NS_ERR_ARG, "ns_poisson_solve: batch outside [1, capacity]");
+    const Geo& G = grid->geo;
+    const dim3 gcell(G.ctas, batch), gface(G.fctas, batch);
+    NS_CUDA(cudaMemcpyAsync(grid->b, b, sizeof(double) * G.cnt[3] * batch,
+                            cudaMemcpyDeviceToDevice, grid->stream));
+    grid->prof.active = batch >= grid->prof.min_batch;
+    NS_LAUNCH(grid, NS_K_DIVERGENCE, G.cnt[3] * batch,
+              k_sum_cells<<<gcell, block_dim(), 0, grid->stream>>>(G, grid->b, grid->part_div));
+    NS_CUDA(cudaGetLastError());
+    NS_TRY(solve_pressure(grid, batch, p));
+    // write p - mean(p) back through the correction kernel's cell part, with
+    // the face part pointed at the (unused) F* buffers
+    const double* x0 = grid->fp32 ? grid->p64[0] : (const double*)grid->kv[0];
+    const double* x1 = grid->fp32 ? grid->p64[1] : (const double*)grid->kv[0];
+    if (grid->fp32)
+        NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
+                  k_correct<float><<<gface, block_dim(), 0, grid->stream>>>(
+                      G, grid->ctl, (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2],
+                      (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2], x0, x1, p,
+                      0.0));
+    else
+        NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
+                  k_correct<double><<<gface, block_dim(), 0, grid->stream>>>(
+                      G, grid->ctl, (double*)grid->fs[0], (double*)grid->fs[1],
+                      (double*)grid->fs[2], (double*)grid->fs[0], (double*)grid->fs[1],
+                      (double*)grid->fs[2], x0, x1, p, 0.0));
+    NS_CUDA(cudaGetLastError());
+    NS_TRY(sync_stream(grid));
+    if (iters) *iters = grid->stats.last_max_iters;
+    return NS_OK;
+}
+
+ns_status ns_parareal_iterate(ns_grid* grid, ns_state u0, ns_state slices, int n_slices,
+                              int fine_steps_per_slice, int coarse_steps_per_slice,
+                              double dt_fine, int kmax, double defect_tol, int resume,
+                              int* k_done, double* defects) {
+    g_last_error.clear();
+    if (k_done) *k_done = 0;
+    if (!grid) return fail(NS_ERR_ARG, "ns_parareal_iterate: null grid");
+    if (n_slices < 1 || n_slices > grid->cap)
+        return fail(NS_ERR_ARG, "ns_parareal_iterate: n_slices outside [1, capacity]");
+    if (u0.batch != 1) return fail(NS_ERR_ARG, "ns_parareal_iterate: u0 must hold one state");
+    NS_TRY(check_state(grid, u0, "ns_parareal_iterate(u0)"));
+    if (!slices.u || !slices.v || !slices.w || !slices.p || slices.batch != n_slices + 1)
+        return fail(NS_ERR_ARG, "ns_parareal_iterate: slices must hold n_slices+1 states");
+    if (fine_steps_per_slice < 1 || coarse_steps_per_slice < 1)
+        return fail(NS_ERR_ARG, "ns_parareal_iterate: steps per slice must be >= 1");
+    if (!(dt_fine > 0) || !std::isfinite(dt_fine))
+        return fail(NS_ERR_ARG, "ns_parareal_iterate: dt_fine must be positive");
+    if (kmax < 0) return fail(NS_ERR_ARG, "ns_parareal_iterate: kmax < 0");
+    if (resume != 0 && resume != 1) return fail(NS_ERR_ARG, "ns_parareal_iterate: resume 0/1");
+    ns_status st = grid->fp32
+                       ? parareal_impl<float>(grid, u0, slices, n_slices, fine_steps_per_slice,
+                                              coarse_steps_per_slice, dt_fine, kmax, defect_tol,
+                                              resume, k_done, defects)
+                       : parareal_impl<double>(grid, u0, slices, n_slices, fine_steps_per_slice,
+                                               coarse_steps_per_slice, dt_fine, kmax, defect_tol,
+                                               resume, k_done, defects);
+    return st;
+}
+
+ns_status ns_adjoint(ns_grid* grid, ns_state u0, double dt, int nsteps, int ckpt_every, double* J,
+                     ns_state grad_u0, double* dJ_dulid) {
+    (void)grid; (void)u0; (void)dt; (void)nsteps; (void)ckpt_every; (void)J; (void)grad_u0;
+    (void)dJ_dulid;
+    return fail(NS_ERR_ARG, "ns_adjoint: not available in this version");
+}
+
+ns_status ns_profile_enable(ns_grid* grid, int on, int min_batch) {
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_profile_enable: null grid");
+    auto& P = grid->prof;
+    if (on && P.cap == 0) {
+        const int pairs = 8192;
+        P.ev.resize(2 * pairs);
+        for (auto& e : P.ev) NS_CUDA(cudaEventCreate(&e));
+        P.kind.resize(pairs);
+        P.units.resize(pairs);
+        P.cap = pairs;
+    }
+    NS_TRY(sync_stream(grid));
+    P.on = on != 0;
+    P.min_batch = std::max(1, min_batch);
+    P.n = 0;
+    for (auto& a : P.acc) a = ns_kernel_time{};
+    return NS_OK;
+}
+
+ns_status ns_profile_read(ns_grid* grid, ns_kernel_time* out, int n) {
+    g_last_error.clear();
+    if (!grid || !out) return fail(NS_ERR_ARG, "ns_profile_read: null argument");
+    NS_TRY(sync_stream(grid));
+    for (int q = 0; q < std::min<int>(n, NS_K_KINDS); ++q) out[q] = grid->prof.acc[q];
+    return NS_OK;
+}
+
+ns_status ns_get_stats(const ns_grid* grid, ns_stats* out) {
+    if (!grid || !out) return fail(NS_ERR_ARG, "ns_get_stats: null argument");
+    *out = grid->stats;
+    return NS_OK;
+}
+
+ns_status ns_reset_stats(ns_grid* grid) {
+    if (!grid) return fail(NS_ERR_ARG, "ns_reset_stats: null argument");
+    grid->stats = ns_stats{};
+    return NS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// Device-side building blocks of the batched MAC-grid projection stepper:
+// grid geometry, boundary (ghost) rules, the SMART face value, the masked
+// 7-point Laplacian and deterministic per-state reductions.
+//
+// Discretisation (Croce, Ruprecht & Krause, Section 2): uniform Cartesian
+// staggered mesh, forward-Euler Chorin-Temam projection, central differences
+// for diffusion and the pressure gradient, SMART (bounded QUICK) upwinding for
+// the conservative convective fluxes, homogeneous Neumann pressure conditions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nsk {
+
+enum { BC_WALL = 0, BC_PERIODIC = 1, BC_SLIP = 2 };
+
+// CTA shape of every cell/face kernel: TX x TY threads, each thread marching
+// over `tz` cells along z.
+constexpr int TX = 32;
+constexpr int TY = 4;
+constexpr int NTHREADS = TX * TY;
+constexpr int NWARPS = NTHREADS / 32;
+
+struct Geo {
+    int n[3];            // cells per axis
+    int bc[3];           // BC_* per axis
+    int ext[3][3];       // ext[c][d]: stored positions of velocity component c along axis d
+    long long cnt[4];    // elements of u, v, w, p in one state
+    double h[3], ih[3], ih2[3];
+    double inv_re, u_lid;
+    int tz;              // cells per thread along z
+    int bx, by, bz, ctas;      // cell kernels: CTA tiles per state
+    int fbx, fby, fbz, fctas;  // face kernels: CTA tiles over (n+1) per axis
+    int n_fluid;         // fluid cells per state
+};
+
+__device__ __forceinline__ int tid_flat() { return threadIdx.y * TX + threadIdx.x; }
+
+__device__ __forceinline__ void tile_origin(const Geo& g, int cta, int bx, int by, int& i, int& j,
+                                            int& k0) {
+    int tx = cta % bx;
+    int r = cta / bx;
+    int ty = r % by;
+    int tzb = r / by;
+    i = tx * TX + threadIdx.x;
+    j = ty * TY + threadIdx.y;
+    k0 = tzb * g.tz;
+}
+
+__device__ __forceinline__ long long vindex(const Geo& g, int c, int i, int j, int k) {
+    return ((long long)k * g.ext[c][1] + j) * g.ext[c][0] + i;
+}
+
+__device__ __forceinline__ long long cindex(const Geo& g, int i, int j, int k) {
+    return ((long long)k * g.n[1] + j) * g.n[0] + i;
+}
+
+// Value of velocity component c at (i,j,k), up to two positions outside the
+// stored range.  Ghost rules per axis d:
+//   periodic                  wrap;
+//   normal component (d == c) odd reflection about the wall face (value 0 there);
+//   tangential, wall          2*u_wall - mirror (u_wall = u_lid for u on y = ly);
+//   tangential, slip          +mirror.
+template <typename T>
+__device__ __forceinline__ T vel(const Geo& g, int c, const T* __restrict__ a, int i, int j,
+                                 int k) {
+    int q[3] = {i, j, k};
+    T sign = T(1);
+    T add = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int e = g.ext[c][d];
+        int x = q[d];
+        if (x < 0 || x >= e) {
+            const int n = g.n[d];
+            if (g.bc[d] == BC_PERIODIC) {
+                x = x < 0 ? x + e : x - e;
+            } else if (d == c) {
+                x = x < 0 ? -x : 2 * n - x;
+                sign = -sign;
+            } else {
+                const bool hi = x >= e;
+                x = hi ? 2 * n - 1 - x : -x - 1;
+                if (g.bc[d] == BC_WALL) {
+                    sign = -sign;
+                    if (c == 0 && d == 1 && hi) add = T(2.0 * g.u_lid);
+                }
+            }
+            q[d] = x;
+        }
+    }
+    return add + sign * a[vindex(g, c, q[0], q[1], q[2])];
+}
+
+// SMART face value from far-upwind U, upwind C and downwind D node values,
+// written without a division: with cc = C-U, dd = D-U the normalised variable
+// is cc/dd, and the face value U + f(cc/dd)*dd is
+//   C                         if cc/dd is outside [0,1] (first-order upwind),
+//   U + 3 cc                  on [0, 1/6],
+//   U + 3/4 cc + 3/8 dd       on [1/6, 5/6] (QUICK),
+//   D                         on [5/6, 1];
+// a flat far field (dd == 0) takes C.
+template <typename T>
+__device__ __forceinline__ T smart_face(T U, T C, T D) {
+    const T dd = D - U;
+    const T cc = C - U;
+    if (dd == T(0)) return C;
+    const T a = dd > T(0) ? cc : -cc;
+    const T b = fabs(dd);
+    if (a < T(0) || a > b) return C;
+    if (T(6) * a <= b) return U + T(3) * cc;
+    if (T(6) * a <= T(5) * b) return U + T(0.75) * cc + T(0.375) * dd;
+    return D;
+}
+
+// Convective flux uf * phi_face through a face between node values b (lower
+// index) and f (higher index); bb lies behind b and ff in front of f.
+template <typename T>
+__device__ __forceinline__ T smart_flux(T uf, T bb, T b, T f, T ff) {
+    if (uf > T(0)) return uf * smart_face(bb, b, f);
+    if (uf < T(0)) return uf * smart_face(ff, f, b);
+    return T(0);
+}
+
+// 7-point Laplacian at cell (i,j,k) of the field returned by val(i,j,k), with
+// the value at the cell already in vc.  Wall faces are dropped (homogeneous
+// Neumann); periodic axes wrap.  Terms are added axis by axis, the high face
+// before the low face.
+template <typename T, typename F>
+__device__ __forceinline__ T lap_cell(const Geo& g, const F& val, int i, int j, int k, T vc) {
+    T s = T(0);
+    const int c[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int n = g.n[d];
+        const T w = T(g.ih2[d]);
+        int hi[3] = {c[0], c[1], c[2]};
+        int lo[3] = {c[0], c[1], c[2]};
+        if (g.bc[d] == BC_PERIODIC) {
+            hi[d] = c[d] + 1 == n ? 0 : c[d] + 1;
+            lo[d] = c[d] == 0 ? n - 1 : c[d] - 1;
+            s += (val(hi[0], hi[1], hi[2]) - vc) * w;
+            s -= (vc - val(lo[0], lo[1], lo[2])) * w;
+        } else {
+            hi[d] = c[d] + 1;
+            lo[d] = c[d] - 1;
+            if (hi[d] < n) s += (val(hi[0], hi[1], hi[2]) - vc) * w;
+            if (lo[d] >= 0) s -= (vc - val(lo[0], lo[1], lo[2])) * w;
+        }
+    }
+    return s;
+}
+
+// Sum of NV per-thread values over the CTA; the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sm[NV][NWARPS];
+    const int t = tid_flat();
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sm[q][warp] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = lane < NWARPS ? sm[q][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            v[q] = x;
+        }
+    }
+}
+
+// Deterministic sum of the per-CTA partials [ctas][NV] of one state, computed
+// by every CTA that needs it (same order in every CTA), broadcast to all
+// threads of the CTA.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ctas,
+                                                double (&out)[NV]) {
+    __shared__ double bc[NV];
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int c = tid_flat(); c < ctas; c += NTHREADS) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] += part[(long long)c * NV + q];
+    }
+    block_sum<NV>(v);
+    if (tid_flat() == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) bc[q] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = bc[q];
+    __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ void write_partials(double (&v)[NV], double* __restrict__ part) {
+    block_sum<NV>(v);
+    if (tid_flat() == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) part[q] = v[q];
+    }
+}
+
+}  // namespace nsk

@@ -1,0 +1,637 @@
+// Kernels of one forward-Euler Chorin-Temam projection step on the MAC grid
+// (Croce, Ruprecht & Krause, Section 2) for a batch of independent states,
+// the BiCGStab pressure solve (FP64, or FP32 inner iterations inside an FP64
+// iterative refinement), and the Parareal update of Eq. 6.
+//
+// Every kernel runs one CTA per (tile, state): blockIdx.y is the state and
+// blockIdx.x the tile inside it, so the per-state reductions (dot products,
+// means) are sums over a fixed set of CTAs in a fixed order, independent of the
+// batch size.  Per-state Krylov scalars live in SliceCtl; partial sums of each
+// phase are reduced redundantly by every CTA of the next phase, so one
+// iteration needs three launches and no host round trip.
+#pragma once
+
+#include "ns_device.cuh"
+
+namespace nsk {
+
+enum { ST_ITER = 0, ST_CONV = 1, ST_MAXIT = 2, ST_NONFINITE = 3, ST_IDLE = 4 };
+enum { OS_REFINE = 0, OS_DONE = 1, OS_FAIL = 2, OS_NONFINITE = 3 };
+
+struct SliceCtl {
+    int status;        // ST_*: state of the current Krylov solve
+    int it_cur;        // iterations completed (written by phase C / init)
+    int it_next;       // iteration in progress (written by phase A)
+    int restart;       // phase A restarted the recurrence (p := r)
+    double rho[2];     // (r_hat, r) of the last two iterations, by parity
+    double alpha, omega;
+    double bb;         // ||b||^2 of the current solve
+    double rr;         // ||r||^2 when the solve stopped
+    double sx;         // sum of the solution over the state when the solve stopped
+    int o_status;      // OS_*: FP32+refine outer loop
+    int o_steps;       // outer corrections applied
+    int p_final;       // FP32+refine: p64 buffer holding the result
+    int pad;
+    double o_bb, o_rr;
+    long long total_iters;  // Krylov iterations accumulated over solves
+};
+
+template <typename T>
+struct KBuf {       // Krylov vectors of all states, [batch][cells]
+    T* x;           // solution (FP64 mode) / inner correction e (FP32 mode)
+    T* r;           // residual (FP32 mode: the outer residual r32 in place)
+    T* rhat;        // shadow residual
+    T* P[2];        // search direction, ping-pong by iteration parity
+    T* V[2];        // L P, ping-pong by iteration parity
+    T* t;           // L s
+};
+
+// ---------------------------------------------------------------------------
+// predictor  F* = u + dt (Re^-1 lap u - div(u u))
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void predict_face(const Geo& g, int c, const T* const* vel3, T* out,
+                                             int i, int j, int k, T dt) {
+    const long long id = vindex(g, c, i, j, k);
+    const int f[3] = {i, j, k};
+    const bool active = g.bc[c] == BC_PERIODIC || (f[c] > 0 && f[c] < g.n[c]);
+    if (!active) {
+        out[id] = T(0);
+        return;
+    }
+    T conv = T(0), diff = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        T a[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            int q[3] = {f[0], f[1], f[2]};
+            q[d] += m - 2;
+            a[m] = vel(g, c, vel3[c], q[0], q[1], q[2]);
+        }
+        T up, um;
+        if (d == c) {
+            // fluxes at the cell centres on either side of the face
+            up = T(0.5) * (a[2] + a[3]);
+            um = T(0.5) * (a[1] + a[2]);
+        } else {
+            // fluxes at the cell edges: component d averaged over the two
+            // positions of this face along axis c
+            int q0[3] = {f[0], f[1], f[2]};
+            int q1[3] = {f[0], f[1], f[2]};
+            q0[c] = f[c] - 1;
+            q0[d] = f[d] + 1;
+            q1[d] = f[d] + 1;
+            up = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                           vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+            q0[d] = f[d];
+            q1[d] = f[d];
+            um = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                           vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+        }
+        const T fp = smart_flux(up, a[1], a[2], a[3], a[4]);
+        const T fm = smart_flux(um, a[0], a[1], a[2], a[3]);
+        conv += (fp - fm) * T(g.ih[d]);
+        diff += (a[3] - T(2) * a[2] + a[1]) * T(g.ih2[d]);
+    }
+    out[id] = vel3[c][id] + dt * (T(g.inv_re) * diff - conv);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_predict(Geo g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+              T* __restrict__ fu, T* __restrict__ fv, T* __restrict__ fw, double dt) {
+    const long long s = blockIdx.y;
+    const T* vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
+    T* out[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
+    const int k1 = min(k0 + g.tz, g.n[2] + 1);
+    for (int k = k0; k < k1; ++k) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (i < g.ext[c][0] && j < g.ext[c][1] && k < g.ext[c][2])
+                predict_face(g, c, vel3, out[c], i, j, k, T(dt));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// b = D F* / dt, per-CTA partial sums of b (for the fluid mean)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_divergence(Geo g, const T* __restrict__ fu, const T* __restrict__ fv,
+                 const T* __restrict__ fw, double* __restrict__ b, double* __restrict__ part,
+                 double inv_dt) {
+    const long long s = blockIdx.y;
+    fu += s * g.cnt[0];
+    fv += s * g.cnt[1];
+    fw += s * g.cnt[2];
+    b += s * g.cnt[3];
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[1] = {0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        const int ip = (g.bc[0] == BC_PERIODIC && i + 1 == g.n[0]) ? 0 : i + 1;
+        const int jp = (g.bc[1] == BC_PERIODIC && j + 1 == g.n[1]) ? 0 : j + 1;
+        for (int k = k0; k < k1; ++k) {
+            const int kp = (g.bc[2] == BC_PERIODIC && k + 1 == g.n[2]) ? 0 : k + 1;
+            T dv = (fu[vindex(g, 0, ip, j, k)] - fu[vindex(g, 0, i, j, k)]) * T(g.ih[0]);
+            dv += (fv[vindex(g, 1, i, jp, k)] - fv[vindex(g, 1, i, j, k)]) * T(g.ih[1]);
+            dv += (fw[vindex(g, 2, i, j, kp)] - fw[vindex(g, 2, i, j, k)]) * T(g.ih[2]);
+            const double bv = double(dv) * inv_dt;
+            b[cindex(g, i, j, k)] = bv;
+            acc[0] += bv;
+        }
+    }
+    write_partials<1>(acc, part + (s * g.ctas + blockIdx.x));
+}
+
+// partial sums of a cell field (for the mean of a caller-supplied right side)
+__global__ void __launch_bounds__(NTHREADS)
+    k_sum_cells(Geo g, const double* __restrict__ x, double* __restrict__ part) {
+    const long long s = blockIdx.y;
+    x += s * g.cnt[3];
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[1] = {0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        for (int k = k0; k < k1; ++k) acc[0] += x[cindex(g, i, j, k)];
+    }
+    write_partials<1>(acc, part + (s * g.ctas + blockIdx.x));
+}
+
+// ---------------------------------------------------------------------------
+// BiCGStab (van der Vorst), three phases per iteration
+// ---------------------------------------------------------------------------
+
+// Start of a solve with a warm start x0 (FP64 mode): b <- b - mean(b);
+// x = x0; r = b - L x0; r_hat = r.  Partials: (r_hat,r), (r,r), sum x, (b,b).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_bicg_init_warm(Geo g, KBuf<T> kb, SliceCtl* __restrict__ ctl,
+                     const double* __restrict__ part_b, T* __restrict__ bvec,
+                     const T* __restrict__ x0, double* __restrict__ part_c) {
+    const long long s = blockIdx.y;
+    double sb[1];
+    reduce_partials<1>(part_b + s * g.ctas, g.ctas, sb);
+    const T mean = T(sb[0] / g.n_fluid);
+    const long long off = s * g.cnt[3];
+    T* b = bvec + off;
+    const T* xs = x0 + off;
+    T* x = kb.x + off;
+    T* r = kb.r + off;
+    T* rh = kb.rhat + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        auto xv = [&](int a, int bb, int c) { return xs[cindex(g, a, bb, c)]; };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const T bv = b[id] - mean;
+            const T xc = xs[id];
+            const T rv = bv - lap_cell(g, xv, i, j, k, xc);
+            b[id] = bv;
+            x[id] = xc;
+            r[id] = rv;
+            rh[id] = rv;
+            acc[1] += double(rv) * double(rv);
+            acc[2] += double(xc);
+            acc[3] += double(bv) * double(bv);
+        }
+    }
+    acc[0] = acc[1];
+    write_partials<4>(acc, part_c + (s * g.ctas + blockIdx.x) * 4);
+    if (blockIdx.x == 0 && tid_flat() == 0) {
+        SliceCtl* c = ctl + s;
+        c->status = ST_ITER;
+        c->it_cur = 0;
+        c->it_next = 0;
+        c->omega = 1.0;
+        c->alpha = 1.0;
+    }
+}
+
+// Phase A of iteration i (parity par = i & 1): convergence test on the
+// residual of iteration i-1, then p = r + beta (p - omega v) (or p = r on a
+// (re)start), v = L p.  Partial: (r_hat, v).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_bicg_A(Geo g, KBuf<T> kb, SliceCtl* __restrict__ ctl, const double* __restrict__ part_c,
+             double* __restrict__ part_a, double tol2, int maxit, int par) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    double red[4];
+    reduce_partials<4>(part_c + s * g.ctas * 4, g.ctas, red);
+    const int done = c->it_cur;
+    const int it = done + 1;
+    double rho = red[0];
+    const double rr = red[1];
+    const double bb = it == 1 ? red[3] : c->bb;
+    const bool lead = blockIdx.x == 0 && tid_flat() == 0;
+    if (!isfinite(rr) || !isfinite(rho)) {
+        if (lead) {
+            c->status = ST_NONFINITE;
+            c->rr = rr;
+        }
+        return;
+    }
+    if (rr <= tol2 * bb) {
+        if (lead) {
+            c->status = ST_CONV;
+            c->rr = rr;
+            c->sx = red[2];
+            if (it == 1) c->bb = bb;
+        }
+        return;
+    }
+    if (done >= maxit) {
+        if (lead) {
+            c->status = ST_MAXIT;
+            c->rr = rr;
+            if (it == 1) c->bb = bb;
+        }
+        return;
+    }
+    const bool restart = it == 1 || rho == 0.0 || c->omega == 0.0;
+    double beta = 0.0;
+    if (restart)
+        rho = rr;
+    else
+        beta = (rho / c->rho[par ^ 1]) * (c->alpha / c->omega);
+    if (lead) {
+        c->rho[par] = rho;
+        c->it_next = it;
+        c->restart = restart ? 1 : 0;
+        if (it == 1) c->bb = bb;
+    }
+    const T tb = T(beta), tw = T(c->omega);
+    const long long off = s * g.cnt[3];
+    const T* r = kb.r + off;
+    T* rh = kb.rhat + off;
+    const T* po = kb.P[par ^ 1] + off;
+    const T* vo = kb.V[par ^ 1] + off;
+    T* pn = kb.P[par] + off;
+    T* vn = kb.V[par] + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[1] = {0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        auto pnew = [&](int a, int b, int cc) {
+            const long long q = cindex(g, a, b, cc);
+            return restart ? r[q] : r[q] + tb * (po[q] - tw * vo[q]);
+        };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const T pc = pnew(i, j, k);
+            const T lv = lap_cell(g, pnew, i, j, k, pc);
+            pn[id] = pc;
+            vn[id] = lv;
+            T rhv;
+            if (restart && it > 1) {
+                rhv = r[id];
+                rh[id] = rhv;
+            } else {
+                rhv = restart ? r[id] : rh[id];
+            }
+            acc[0] += double(rhv * lv);
+        }
+    }
+    write_partials<1>(acc, part_a + (s * g.ctas + blockIdx.x));
+}
+
+// Phase B: alpha = rho / (r_hat, v); s = r - alpha v; t = L s.
+// Partials: (t, s), (t, t).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_bicg_B(Geo g, KBuf<T> kb, SliceCtl* __restrict__ ctl, const double* __restrict__ part_a,
+             double* __restrict__ part_b, int par) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    double red[1];
+    reduce_partials<1>(part_a + s * g.ctas, g.ctas, red);
+    const double alpha = c->rho[par] / red[0];
+    if (blockIdx.x == 0 && tid_flat() == 0) c->alpha = alpha;
+    const T ta = T(alpha);
+    const long long off = s * g.cnt[3];
+    const T* r = kb.r + off;
+    const T* vn = kb.V[par] + off;
+    T* t = kb.t + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[2] = {0.0, 0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        auto sv = [&](int a, int b, int cc) {
+            const long long q = cindex(g, a, b, cc);
+            return r[q] - ta * vn[q];
+        };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const T sc = sv(i, j, k);
+            const T tv = lap_cell(g, sv, i, j, k, sc);
+            t[id] = tv;
+            acc[0] += double(tv * sc);
+            acc[1] += double(tv * tv);
+        }
+    }
+    write_partials<2>(acc, part_b + (s * g.ctas + blockIdx.x) * 2);
+}
+
+// Phase C: omega = (t,s)/(t,t); x += alpha p + omega s; r = s - omega t.
+// Partials: (r_hat, r), (r, r), sum x.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_bicg_C(Geo g, KBuf<T> kb, SliceCtl* __restrict__ ctl, const double* __restrict__ part_b,
+             double* __restrict__ part_c, int par) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    double red[2];
+    reduce_partials<2>(part_b + s * g.ctas * 2, g.ctas, red);
+    const double omega = red[1] != 0.0 ? red[0] / red[1] : 0.0;
+    const double alpha = c->alpha;
+    if (blockIdx.x == 0 && tid_flat() == 0) {
+        c->omega = omega;
+        c->it_cur = c->it_next;
+        c->total_iters += 1;
+    }
+    const T ta = T(alpha), tw = T(omega);
+    const long long off = s * g.cnt[3];
+    T* x = kb.x + off;
+    T* r = kb.r + off;
+    const T* rh = kb.rhat + off;
+    const T* pn = kb.P[par] + off;
+    const T* vn = kb.V[par] + off;
+    const T* t = kb.t + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const T sc = r[id] - ta * vn[id];
+            const T xv = x[id] + (ta * pn[id] + tw * sc);
+            const T rv = sc - tw * t[id];
+            x[id] = xv;
+            r[id] = rv;
+            acc[0] += double(rh[id] * rv);
+            acc[1] += double(rv * rv);
+            acc[2] += double(xv);
+        }
+    }
+    write_partials<4>(acc, part_c + (s * g.ctas + blockIdx.x) * 4);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 storage + FP64 iterative refinement of the pressure solve
+// ---------------------------------------------------------------------------
+
+// Outer start: b <- b - mean(b) (FP64); p64 = p; r64 = b - L p (FP64);
+// r32 = float(r64).  Partials: (r,r), (b,b), sum p.
+__global__ void __launch_bounds__(NTHREADS)
+    k_refine_init(Geo g, SliceCtl* __restrict__ ctl, const double* __restrict__ part_b,
+                  double* __restrict__ bvec, const double* __restrict__ p_in,
+                  double* __restrict__ p64, float* __restrict__ r32, double* __restrict__ part_r) {
+    const long long s = blockIdx.y;
+    double sb[1];
+    reduce_partials<1>(part_b + s * g.ctas, g.ctas, sb);
+    const double mean = sb[0] / g.n_fluid;
+    const long long off = s * g.cnt[3];
+    double* b = bvec + off;
+    const double* ps = p_in + off;
+    double* pd = p64 + off;
+    float* r = r32 + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        auto pv = [&](int a, int bb, int c) { return ps[cindex(g, a, bb, c)]; };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const double bv = b[id] - mean;
+            const double pc = ps[id];
+            const double rv = bv - lap_cell(g, pv, i, j, k, pc);
+            b[id] = bv;
+            pd[id] = pc;
+            r[id] = float(rv);
+            acc[0] += rv * rv;
+            acc[1] += bv * bv;
+            acc[2] += pc;
+        }
+    }
+    write_partials<3>(acc, part_r + (s * g.ctas + blockIdx.x) * 3);
+    if (blockIdx.x == 0 && tid_flat() == 0) {
+        SliceCtl* c = ctl + s;
+        c->o_status = OS_REFINE;
+        c->o_steps = 0;
+        c->p_final = 0;
+        c->status = ST_IDLE;
+    }
+}
+
+// Outer convergence test for outer step m, then the start of the inner FP32
+// solve of L e = r32 from e = 0: r_hat = r32, e = 0.
+__global__ void __launch_bounds__(NTHREADS)
+    k_inner_init(Geo g, KBuf<float> kb, SliceCtl* __restrict__ ctl,
+                 const double* __restrict__ part_r, double* __restrict__ part_c, double tol2,
+                 int m, int max_outer) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->o_status != OS_REFINE) return;
+    double red[3];
+    reduce_partials<3>(part_r + s * g.ctas * 3, g.ctas, red);
+    const double rr = red[0];
+    const double bb = m == 0 ? red[1] : c->o_bb;
+    const bool lead = blockIdx.x == 0 && tid_flat() == 0;
+    if (!isfinite(rr)) {
+        if (lead) {
+            c->o_status = OS_NONFINITE;
+            c->o_rr = rr;
+            c->status = ST_IDLE;
+        }
+        return;
+    }
+    if (rr <= tol2 * bb) {
+        if (lead) {
+            c->o_status = OS_DONE;
+            c->o_rr = rr;
+            c->o_bb = bb;
+            c->p_final = m & 1;
+            c->sx = red[2];
+            c->status = ST_IDLE;
+        }
+        return;
+    }
+    if (m >= max_outer) {
+        if (lead) {
+            c->o_status = OS_FAIL;
+            c->o_rr = rr;
+            c->o_bb = bb;
+            c->status = ST_IDLE;
+        }
+        return;
+    }
+    const long long off = s * g.cnt[3];
+    const float* r = kb.r + off;
+    float* rh = kb.rhat + off;
+    float* e = kb.x + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const float rv = r[id];
+            rh[id] = rv;
+            e[id] = 0.0f;
+            acc[1] += double(rv) * double(rv);
+        }
+    }
+    acc[0] = acc[1];
+    acc[3] = acc[1];
+    write_partials<4>(acc, part_c + (s * g.ctas + blockIdx.x) * 4);
+    if (lead) {
+        c->status = ST_ITER;
+        c->it_cur = 0;
+        c->it_next = 0;
+        c->omega = 1.0;
+        c->alpha = 1.0;
+        c->o_steps = m;
+        if (m == 0) c->o_bb = bb;
+    }
+}
+
+// Outer correction: p_new = p_old + e (FP64); r64 = b - L p_new (FP64, p_new
+// recomputed at the neighbours); r32 = float(r64).  Partials: (r,r), 0, sum p.
+__global__ void __launch_bounds__(NTHREADS)
+    k_refine_update(Geo g, SliceCtl* __restrict__ ctl, const double* __restrict__ bvec,
+                    const double* __restrict__ p_old, double* __restrict__ p_new,
+                    const float* __restrict__ e_in, float* __restrict__ r32,
+                    double* __restrict__ part_r) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->o_status != OS_REFINE) return;
+    if (c->status == ST_NONFINITE) {
+        if (blockIdx.x == 0 && tid_flat() == 0) c->o_status = OS_NONFINITE;
+        return;
+    }
+    // a converged inner solve, or one stopped at its iteration limit, still
+    // improves p; the outer residual test decides when to stop
+    const long long off = s * g.cnt[3];
+    const double* b = bvec + off;
+    const double* po = p_old + off;
+    double* pn = p_new + off;
+    const float* e = e_in + off;
+    float* r = r32 + off;
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (i < g.n[0] && j < g.n[1]) {
+        const int k1 = min(k0 + g.tz, g.n[2]);
+        auto pv = [&](int a, int bb, int cc) {
+            const long long q = cindex(g, a, bb, cc);
+            return po[q] + double(e[q]);
+        };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = cindex(g, i, j, k);
+            const double pc = pv(i, j, k);
+            const double rv = b[id] - lap_cell(g, pv, i, j, k, pc);
+            pn[id] = pc;
+            r[id] = float(rv);
+            acc[0] += rv * rv;
+            acc[2] += pc;
+        }
+    }
+    write_partials<3>(acc, part_r + (s * g.ctas + blockIdx.x) * 3);
+}
+
+// ---------------------------------------------------------------------------
+// velocity correction u = F* - dt G p and the gauged pressure p - mean(p)
+// ---------------------------------------------------------------------------
+
+// xsrc[buf] selects the solution buffer of each state: FP64 mode passes the
+// same pointer twice; FP32+refine passes p64[0], p64[1] and the state's
+// SliceCtl.p_final picks one.  fs == vel is allowed (in-place projection).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_correct(Geo g, const SliceCtl* __restrict__ ctl, const T* fu, const T* fv, const T* fw,
+              T* u, T* v, T* w, const double* __restrict__ x0, const double* __restrict__ x1,
+              double* __restrict__ p_out, double dt) {
+    const long long s = blockIdx.y;
+    const SliceCtl* c = ctl + s;
+    const double* x = (c->p_final ? x1 : x0) + s * g.cnt[3];
+    const double mean = c->sx / g.n_fluid;
+    const T* f3[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
+    T* o3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
+    const int k1 = min(k0 + g.tz, g.n[2] + 1);
+    for (int k = k0; k < k1; ++k) {
+        const int q[3] = {i, j, k};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (i < g.ext[d][0] && j < g.ext[d][1] && k < g.ext[d][2]) {
+                const long long id = vindex(g, d, i, j, k);
+                const bool active = g.bc[d] == BC_PERIODIC || (q[d] > 0 && q[d] < g.n[d]);
+                if (!active) {
+                    o3[d][id] = T(0);
+                } else {
+                    int lo[3] = {i, j, k};
+                    lo[d] = q[d] == 0 ? g.n[d] - 1 : q[d] - 1;
+                    const double gp =
+                        (x[cindex(g, i, j, k)] - x[cindex(g, lo[0], lo[1], lo[2])]) * g.ih[d];
+                    o3[d][id] = f3[d][id] - T(dt * gp);
+                }
+            }
+        }
+        if (p_out && i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+            const long long id = cindex(g, i, j, k);
+            p_out[s * g.cnt[3] + id] = x[id] - mean;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Parareal update (Eq. 6): y_next = F + (G_new - G_old), G_old <- G_new,
+// defect = max |y_next - y_next_previous| (FP64, atomic max on the bits of a
+// non-negative double, so the result does not depend on the order).
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_parareal_update(long long n, const T* __restrict__ fy, const T* __restrict__ gnew,
+                      T* __restrict__ gold, T* __restrict__ y, unsigned long long* defect) {
+    double dmax = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const T gn = gnew[q];
+        const T nv = fy[q] + (gn - gold[q]);
+        const double d = fabs(double(nv) - double(y[q]));
+        dmax = (d > dmax || d != d) ? d : dmax;
+        y[q] = nv;
+        gold[q] = gn;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, dmax, o);
+        dmax = (other > dmax || other != other) ? other : dmax;
+    }
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(defect, (unsigned long long)__double_as_longlong(dmax));
+}
+
+}  // namespace nsk

@@ -1,0 +1,263 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances: FP64 relative L2 <= 1e-10 per field; FP32 storage with FP64
+refinement relative L2 <= 1e-5 per field (the targets of the method's
+precision modes).  Stage tests (predictor) use a max-norm bound relative to
+the field's maximum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import parareal as opr
+from paper_1705_06149_gb300 import Grid, NSError
+from paper_1705_06149_gb300 import _native as N
+from paper_1705_06149_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32_refine": 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def assert_state_close(got, want, tol, what=""):
+    for c in range(4):
+        e = rel(got[c], want[c])
+        assert e <= tol, f"{what} field {'uvwp'[c]}: relative L2 {e:.3e} > {tol:.1e}"
+
+
+def np_divergence(st, h):
+    u, v, w = st[:3]
+    return (np.diff(u, axis=-1) / h[0] + np.diff(v, axis=-2) / h[1] + np.diff(w, axis=-3) / h[2])
+
+
+# ---------------------------------------------------------------------------
+# stages
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,bc", [((16, 16, 16), ("wall",) * 3),
+                                     ((19, 13, 11), ("wall",) * 3),
+                                     ((37, 9, 10), ("periodic", "wall", "slip")),
+                                     ((8, 10, 6), ("periodic",) * 3),
+                                     ((2, 2, 2), ("wall",) * 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_predictor_matches_oracle(dims, bc, prec):
+    rs = inputs.random_state(*dims, seed=3, sigma=1.0, bc=bc)
+    og = oracle.Grid(*dims, 1.0, 1.3, 0.8, re=50.0, u_lid=1.0, bc=bc)
+    want = og.predict(*rs[:3], 2e-3)
+    g = Grid(*dims, 1.0, 1.3, 0.8, re=50.0, u_lid=1.0, bc=bc, precision=prec, batch=2)
+    st = g.state_from([np.stack([a, a]) for a in rs])
+    got = [t.cpu().numpy() for t in g.predict(st, 2e-3)]
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for c in range(3):
+        scale = max(np.max(np.abs(want[c])), 1e-30)
+        for b in range(2):
+            err = np.max(np.abs(got[c][b] - want[c])) / scale
+            assert err <= tol, (c, b, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_poisson_solve_matches_oracle(prec):
+    dims = (24, 20, 18)
+    rng = np.random.default_rng(4)
+    og = oracle.Grid(*dims, rtol=1e-13)
+    B = 3
+    b = rng.normal(size=(B,) + og.shape(3))
+    g = Grid(*dims, precision=prec, poisson_rtol=1e-13, refine_rtol=1e-13, batch=B)
+    bt = torch.tensor(b, device="cuda")
+    pt = torch.zeros_like(bt)
+    g.poisson_solve(bt, pt)
+    got = pt.cpu().numpy()
+    for s in range(B):
+        want, _ = og.poisson(b[s], rtol=1e-13)
+        assert rel(got[s], want) <= 1e-10, (s, rel(got[s], want))
+        assert abs(got[s].mean()) <= 1e-12 * np.abs(got[s]).max()
+
+
+# ---------------------------------------------------------------------------
+# one and several fine steps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,bc", [((12, 12, 12), ("wall",) * 3),
+                                     ((19, 13, 11), ("wall",) * 3),
+                                     ((16, 12, 6), ("periodic", "wall", "slip")),
+                                     ((2, 2, 2), ("wall",) * 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_fine_steps_match_oracle(dims, bc, prec):
+    steps, dt = 4, 1e-3
+    B = 3
+    inits = [inputs.random_state(*dims, seed=20 + s, sigma=0.2, bc=bc) for s in range(B)]
+    og = oracle.Grid(*dims, re=100.0, bc=bc)
+    g = Grid(*dims, re=100.0, bc=bc, precision=prec, batch=B)
+    st = g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
+    g.step_fine(st, dt, steps)
+    got = st.numpy()
+    for s in range(B):
+        want = oracle.copy_state(inits[s])
+        og.step(want, dt, steps)
+        assert_state_close([got[c][s] for c in range(4)], want, TOL[prec], f"slice {s}")
+
+
+def test_taylor_green_matches_oracle():
+    n = 16
+    L = 2 * np.pi
+    bc = ("periodic",) * 3
+    og = oracle.Grid(n, n, 4, L, L, L / 4, re=10.0, bc=bc)
+    st0 = og.zeros()
+    x_f = np.arange(n) * L / n
+    x_c = (np.arange(n) + 0.5) * L / n
+    st0[0][:] = np.sin(x_f)[None, None, :] * np.cos(x_c)[None, :, None]
+    st0[1][:] = -np.cos(x_c)[None, None, :] * np.sin(x_f)[None, :, None]
+    want = oracle.copy_state(st0)
+    og.step(want, 5e-3, 20)
+    g = Grid(n, n, 4, L, L, L / 4, re=10.0, bc=bc, batch=1)
+    st = g.state_from(st0)
+    g.step_fine(st, 5e-3, 20)
+    assert_state_close([a[0] for a in st.numpy()], want, 1e-10, "taylor-green")
+
+
+# ---------------------------------------------------------------------------
+# the 16^3 lid-driven cavity: serial fine run and Parareal
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cavity16_oracle():
+    og = oracle.Grid(16, 16, 16, re=100.0, u_lid=1.0)
+    u0 = og.zeros()
+    F = opr.fine_propagator(og, 1e-3, 50)
+    G = opr.coarse_propagator(og, 1e-2, 5)
+    serial = opr.serial_fine(u0, 4, F)
+    y, defects = opr.parareal(u0, 4, F, G, kmax=4)
+    return serial, y, defects
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_cavity16_serial_200_steps(cavity16_oracle, prec):
+    serial, _, _ = cavity16_oracle
+    g = Grid(16, 16, 16, re=100.0, precision=prec, batch=1)
+    st = g.zeros(1)
+    g.step_fine(st, 1e-3, 200)
+    got = [a[0] for a in st.numpy()]
+    assert_state_close(got, serial[4], TOL[prec], "t=0.2")
+    div = np_divergence(got, (1 / 16,) * 3)
+    assert np.max(np.abs(div)) <= (1e-12 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_cavity16_parareal(cavity16_oracle, prec):
+    _, y_ref, d_ref = cavity16_oracle
+    g = Grid(16, 16, 16, re=100.0, precision=prec, batch=4)
+    u0 = g.zeros(1)
+    slices = g.zeros(5)
+    k, defects = g.parareal(u0, slices, 4, 50, 5, 1e-3, kmax=4)
+    assert k == 4
+    got = slices.numpy()
+    for n in range(5):
+        assert_state_close([a[n] for a in got], y_ref[n], TOL[prec], f"slice {n}")
+    for a, b in zip(defects[:3], d_ref[:3]):
+        assert abs(a - b) <= 1e-3 * b
+    if prec == "fp64":
+        # K = N: every slice equals the serial fine solution computed on the GPU
+        ser = g.zeros(1)
+        for n in range(4):
+            g.step_fine(ser, 1e-3, 50)
+            for c in range(4):
+                assert torch.equal(ser.fields()[c][0], slices.fields()[c][n + 1]), (n, c)
+
+
+def test_parareal_resume_and_tolerance():
+    g = Grid(12, 12, 12, re=100.0, batch=3)
+    u0 = g.zeros(1)
+    a = g.zeros(4)
+    k1, d1 = g.parareal(u0, a, 3, 20, 4, 1e-3, kmax=1)
+    k2, d2 = g.parareal(u0, a, 3, 20, 4, 1e-3, kmax=1, resume=True)
+    b = g.zeros(4)
+    k3, d3 = g.parareal(u0, b, 3, 20, 4, 1e-3, kmax=2)
+    assert (k1, k2, k3) == (1, 1, 2)
+    assert d3 == [d1[0], d2[0]]
+    for c in range(4):
+        assert torch.equal(a.fields()[c], b.fields()[c])
+    c_ = g.zeros(4)
+    k4, d4 = g.parareal(u0, c_, 3, 20, 4, 1e-3, kmax=10, tol=d3[1] * 1.0001)
+    assert k4 == 2
+    with pytest.raises(NSError) as e:
+        g.parareal(u0, g.zeros(4), 3, 20, 4, 1e-3, kmax=1, resume=True)
+    assert e.value.status == N.NS_ERR_ARG
+
+
+# ---------------------------------------------------------------------------
+# full size of the batched sweep: 64^3, 32 slices, sampled against the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_batched_64cubed_32_slices_sampled(prec):
+    n, B, dt = 64, 32, 5e-4
+    og = oracle.Grid(n, n, n, re=1000.0)
+    g = Grid(n, n, n, re=1000.0, precision=prec, batch=B)
+    inits = [inputs.random_state(n, n, n, seed=100 + s, sigma=0.05) for s in range(B)]
+    st = g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
+    g.project(st)
+    proj = st.numpy()
+    g.step_fine(st, dt, 1)
+    got = st.numpy()
+    for s in (0, B - 1):
+        start = [np.array(proj[c][s], dtype=np.float64) for c in range(4)]
+        want = oracle.copy_state(start)
+        og.step(want, dt, 1)
+        assert_state_close([got[c][s] for c in range(4)], want, TOL[prec], f"slice {s}")
+    lim = 1e-12 if prec == "fp64" else 1e-3
+    for s in range(B):
+        div = np_divergence([got[c][s].astype(np.float64) for c in range(3)], (1 / n,) * 3)
+        assert np.max(np.abs(div)) <= lim, (s, np.max(np.abs(div)))
+
+
+# ---------------------------------------------------------------------------
+# arguments and failures
+# ---------------------------------------------------------------------------
+
+def test_argument_errors():
+    g = Grid(8, 8, 8, batch=2)
+    st = g.zeros(3)
+    with pytest.raises(ValueError):
+        g.step_fine(g.state_from([a.cpu().numpy() for a in st.fields()], device="cpu"), 1e-3, 1)
+    with pytest.raises(NSError) as e:
+        g.step_fine(st, 1e-3, 1)  # batch 3 > capacity 2
+    assert e.value.status == N.NS_ERR_ARG
+    st = g.zeros(2)
+    with pytest.raises(NSError) as e:
+        g.step_fine(st, 0.0, 1)
+    assert e.value.status == N.NS_ERR_ARG
+    before = [t.clone() for t in st.fields()]
+    g.step_fine(st, 1e-3, 0)
+    assert all(torch.equal(a, b) for a, b in zip(before, st.fields()))
+    with pytest.raises(NSError) as e:
+        Grid(1, 8, 8)
+    assert e.value.status == N.NS_ERR_ARG
+
+
+def test_nonfinite_input_is_reported():
+    g = Grid(8, 8, 8, batch=1)
+    st = g.zeros(1)
+    st.u[0, 3, 3, 3] = float("nan")
+    with pytest.raises(NSError) as e:
+        g.step_fine(st, 1e-3, 1)
+    assert e.value.status == N.NS_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_iteration_limit_is_reported(prec):
+    g = Grid(16, 16, 16, precision=prec, poisson_maxit=2, batch=1)
+    st = g.zeros(1)
+    with pytest.raises(NSError) as e:
+        g.step_fine(st, 1e-3, 1)
+    assert e.value.status == N.NS_ERR_NOT_CONVERGED
+    # the grid stays usable afterwards
+    g2 = Grid(16, 16, 16, precision=prec, batch=1)
+    g2.step_fine(g2.zeros(1), 1e-3, 1)
