@@ -191,6 +191,38 @@ ns_status ns_profile_enable(ns_grid *grid, int on, int min_batch);
 /* Copies min(n, NS_K_KINDS) accumulated entries to out (host). */
 ns_status ns_profile_read(ns_grid *grid, ns_kernel_time *out, int n);
 
+/* Largest grid (nx*ny*nz cells) ns_poisson_solve_noalloc accepts. */
+#define NS_NOALLOC_MAX_CELLS 65536
+
+/* ns_poisson_solve without any allocation, for callers that cannot allocate
+ * GPU memory when they need a solve (code running inside an allocator or
+ * memory pool it does not own, frameworks that forbid cudaMalloc on their
+ * hot path, processes whose memory budget is already committed).  There is
+ * no counterpart in the paper: it is the same gauged FP64 solve (fluid mean
+ * removed from b, BiCGStab on L p = b from the warm start in p, mean removed
+ * from p) for ONE state on an nx*ny*nz grid of box lx*ly*lz with boundary
+ * conditions bc[3], tolerance rtol and iteration limit maxit (<= 0:
+ * 20*max(n)), with no ns_grid object.
+ *   - b (device, nz*ny*nx doubles) is read only; p (device) is the warm start
+ *     and the result.  cuda_stream is a cudaStream_t (NULL = default stream);
+ *     the call synchronises it.  *iters (host, may be NULL) gets the count.
+ *   - Scratch: one file-scope device array of about 5 MB, reserved on every
+ *     GPU that loads the library until the process exits.  Grids larger than
+ *     NS_NOALLOC_MAX_CELLS cells are rejected with NS_ERR_ARG.
+ *   - No cudaMalloc, cudaFree or other allocating routine is called.  The
+ *     first call on each device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (two
+ *     streams, two host threads) race and give wrong results.  The array
+ *     keeps the previous call's contents; the call clears what must start at
+ *     zero itself.
+ *   - Failures are reported by the status code only; ns_last_error() is not
+ *     updated (storing a message would allocate). */
+ns_status ns_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly, double lz,
+                                   const int *bc, double rtol, int maxit, const double *b,
+                                   double *p, void *cuda_stream, int *iters);
+
 /* Message of the last failure on the calling host thread ("" if none). */
 const char *ns_last_error(void);
 

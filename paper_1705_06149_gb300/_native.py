@@ -19,7 +19,8 @@ STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_CUDA", 3: "NS_ERR_OOM",
 EXPORTS = ("ns_create_grid", "ns_destroy_grid", "ns_set_stream", "ns_step_fine",
            "ns_step_coarse", "ns_project", "ns_predict", "ns_poisson_solve",
            "ns_parareal_iterate", "ns_adjoint", "ns_get_stats", "ns_reset_stats",
-           "ns_profile_enable", "ns_profile_read", "ns_last_error")
+           "ns_profile_enable", "ns_profile_read", "ns_poisson_solve_noalloc",
+           "ns_last_error")
 
 KERNEL_KINDS = ("predict", "divergence", "solve_init", "krylov_A", "krylov_B", "krylov_C",
                 "inner_init", "refine", "correct", "parareal")
@@ -101,6 +102,9 @@ def load(build_if_missing: bool = False):
             "ns_reset_stats": [vp],
             "ns_profile_enable": [vp, ctypes.c_int, ctypes.c_int],
             "ns_profile_read": [vp, ctypes.POINTER(KernelTime), ctypes.c_int],
+            "ns_poisson_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ip, ctypes.c_double,
+                                         ctypes.c_int, vp, vp, vp, ip],
         }
         for name, args in sig.items():
             f = getattr(lib, name)

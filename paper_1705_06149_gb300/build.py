@@ -46,7 +46,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, os.path.join(CSRC, "ns_api.cu"), "-o", tmp]
+           "-I", INCLUDE, os.path.join(CSRC, "ns_api.cu"), os.path.join(CSRC, "ns_noalloc.cu"),
+           "-o", tmp]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(NTHREADS)
 }
 
 // partial sums of a cell field (for the mean of a caller-supplied right side)
-__global__ void __launch_bounds__(NTHREADS)
+static __global__ void __launch_bounds__(NTHREADS)
     k_sum_cells(Geo g, const double* __restrict__ x, double* __restrict__ part) {
     const long long s = blockIdx.y;
     x += s * g.cnt[3];
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(NTHREADS)
 
 // Outer start: b <- b - mean(b) (FP64); p64 = p; r64 = b - L p (FP64);
 // r32 = float(r64).  Partials: (r,r), (b,b), sum p.
-__global__ void __launch_bounds__(NTHREADS)
+static __global__ void __launch_bounds__(NTHREADS)
     k_refine_init(Geo g, SliceCtl* __restrict__ ctl, const double* __restrict__ part_b,
                   double* __restrict__ bvec, const double* __restrict__ p_in,
                   double* __restrict__ p64, float* __restrict__ r32, double* __restrict__ part_r) {
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(NTHREADS)
 
 // Outer convergence test for outer step m, then the start of the inner FP32
 // solve of L e = r32 from e = 0: r_hat = r32, e = 0.
-__global__ void __launch_bounds__(NTHREADS)
+static __global__ void __launch_bounds__(NTHREADS)
     k_inner_init(Geo g, KBuf<float> kb, SliceCtl* __restrict__ ctl,
                  const double* __restrict__ part_r, double* __restrict__ part_c, double tol2,
                  int m, int max_outer) {
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(NTHREADS)
 
 // Outer correction: p_new = p_old + e (FP64); r64 = b - L p_new (FP64, p_new
 // recomputed at the neighbours); r32 = float(r64).  Partials: (r,r), 0, sum p.
-__global__ void __launch_bounds__(NTHREADS)
+static __global__ void __launch_bounds__(NTHREADS)
     k_refine_update(Geo g, SliceCtl* __restrict__ ctl, const double* __restrict__ bvec,
                     const double* __restrict__ p_old, double* __restrict__ p_new,
                     const float* __restrict__ e_in, float* __restrict__ r32,
