@@ -46,9 +46,28 @@ WORKLOAD = ("64^3 lid-driven cavity, Re=1000, u_lid=1, walls on all faces; initi
             "(seed 0), projected; 32 Parareal slices x 50 fine steps (dt=5e-4); coarse "
             "propagator 5 steps of 5e-3 per slice; one step = one Parareal iteration")
 
-# algorithmic bytes per cell and Krylov iteration for each BiCGStab phase
-# (each array read or written once per launch; neighbour reads come from cache)
-WORDS_PER_CELL = {"krylov_A": 6, "krylov_B": 3, "krylov_C": 8}
+# Algorithmic traffic of the finest-level solver kernels, in words (FP32 or
+# FP64 values) per cell per launch: each array is read or written once per
+# launch, neighbour reads come from cache.  Multigrid path (finest-level
+# smoothing on):
+#   krylov_A   p = r + beta (p - omega v) and 2 Jacobi sweeps: r, p, v -> p, y
+#   mg_restrict0  residual of the sweeps, restricted: p|s, y -> coarse (1/8)
+#   mg_prolong0   y += P e: y, coarse e (1/8) -> y
+#   mg_lap_v   v = L y, (r_hat, v): y, r_hat -> v
+#   krylov_B   s = r - alpha v and 2 Jacobi sweeps: r, v -> s, z
+#   mg_lap_t   t = L z, (t, s), (t, t): z, s -> t
+#   krylov_C   x += alpha y + omega z, r = s - omega t: x, y, z, s, t, r_hat -> x, r
+WORDS_MG = {"krylov_A": 5, "mg_restrict0": 2.125, "mg_prolong0": 2.125, "mg_lap_v": 3,
+            "krylov_B": 4, "mg_lap_t": 3, "krylov_C": 8}
+# plain BiCGStab: A reads r, p, v, r_hat, writes p, v; B reads r, v, writes t;
+# C reads x, p, r, v, t, r_hat, writes x, r
+WORDS_PLAIN = {"krylov_A": 6, "krylov_B": 3, "krylov_C": 8}
+
+
+KERNEL_NAMES = {"krylov_A": "k_mg_src<SRC_P> / k_bicg_A", "krylov_B": "k_mg_src<SRC_S> / k_bicg_B",
+                "krylov_C": "k_mg_update / k_bicg_C", "mg_lap_v": "k_mg_lapdot_v",
+                "mg_lap_t": "k_mg_lapdot_t", "mg_restrict0": "k_mg_restrict (finest)",
+                "mg_prolong0": "k_mg_prolong (finest)"}
 
 
 def parse():
@@ -60,6 +79,10 @@ def parse():
     ap.add_argument("--precision", choices=["fp32_refine", "fp64"], default="fp32_refine")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--preconditioner", choices=["multigrid", "none"], default="multigrid")
+    ap.add_argument("--mode", choices=["bench", "kernels"], default="bench",
+                    help="kernels: only `steps` batched fine steps of the 32-slice sweep "
+                         "(a short run for profilers), prints one line")
     return ap.parse_args()
 
 
@@ -281,7 +304,8 @@ def run_ours(args, world, rank, local, pg):
     peaks, peak_kind = measured_peaks()
 
     init = initial_field_gpu(prec)
-    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, u_lid=1.0, precision=prec, batch=N_SLICES)
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, u_lid=1.0, precision=prec, batch=N_SLICES,
+             preconditioner=args.preconditioner)
     u0 = g.state_from(init)
     g.project(u0)
     slices = g.zeros(N_SLICES + 1)
@@ -322,19 +346,30 @@ def run_ours(args, world, rank, local, pg):
 
     # ---- roofline of the dominant kernel (live CUDA-event timing) -------------
     esz = 4 if prec == "fp32_refine" else 8
-    kern = max(WORDS_PER_CELL, key=lambda k: prof[k]["ms"])
-    kp = prof[kern]
-    bytes_alg = kp["cell_units"] * WORDS_PER_CELL[kern] * esz
-    achieved = bytes_alg / (kp["ms"] / 1e3) / 1e9 if kp["ms"] > 0 else 0.0
+    words = WORDS_MG if args.preconditioner == "multigrid" else WORDS_PLAIN
     peak = float(peaks["hbm_gbs"])
+    per_kernel = {}
+    for k, wpc in words.items():
+        kp = prof[k]
+        if kp["ms"] <= 0 or kp["launches"] == 0:
+            continue
+        bytes_alg = kp["cell_units"] * wpc * esz
+        per_kernel[k] = {"achieved_gbs": bytes_alg / (kp["ms"] / 1e3) / 1e9,
+                         "ms_per_step": kp["ms"] / args.steps,
+                         "avg_launch_us": 1e3 * kp["ms"] / kp["launches"],
+                         "launches": kp["launches"]}
+    kern = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
+    kp = prof[kern]
+    achieved = per_kernel[kern]["achieved_gbs"]
     traffic = traffic_for(kern)
     per_launch_units = kp["cell_units"] / max(kp["launches"], 1)
-    roofline = {"bound": "hbm", "kernel": f"k_bicg_{kern[-1]}", "achieved": achieved,
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[kern], "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": per_launch_units * WORDS_PER_CELL[kern] * esz,
+                "algorithmic_bytes_per_launch": per_launch_units * words[kern] * esz,
                 "avg_launch_us": 1e3 * kp["ms"] / max(kp["launches"], 1),
-                "traffic": (traffic * per_launch_units) if traffic else None}
+                "traffic": (traffic * per_launch_units) if traffic else None,
+                "solver_kernels": per_kernel}
     fine_kernel_ms = sum(v["ms"] for v in prof.values()) / args.steps
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
                for k, v in prof.items() if v["launches"]}
@@ -379,6 +414,8 @@ def run_ours(args, world, rank, local, pg):
         "dtype": "f32+f64refine" if prec == "fp32_refine" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": prec, "slices": N_SLICES,
+                   "solver": "BiCGStab + multigrid V(2,0) right preconditioner"
+                   if args.preconditioner == "multigrid" else "BiCGStab",
                    "fine_steps_per_slice": FINE_STEPS, "coarse_steps_per_slice": COARSE_STEPS,
                    "grid": [N_CELLS] * 3, "parallelism": f"replicas x{world}",
                    "l2": "working set > L2 (no flush needed): ~%.0f MB of Krylov vectors"
@@ -398,6 +435,32 @@ def run_ours(args, world, rank, local, pg):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
+def run_kernels_only(args):
+    """A short run of the batched fine sweep alone, for profilers: the 64^3
+    start state copied to all 32 slices, `steps` fine steps."""
+    import torch
+    from paper_1705_06149_gb300 import Grid
+    init = initial_field_gpu(args.precision)
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=N_SLICES,
+             preconditioner=args.preconditioner)
+    st = g.state_from(init)
+    g.project(st)
+    batch = g.state_from([t.expand((N_SLICES,) + tuple(t.shape[1:])).cpu().numpy()
+                          for t in st.fields()])
+    g.step_fine(batch, DT_FINE, args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step_fine(batch, DT_FINE, args.steps)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    print(json.dumps({"mode": "kernels", "precision": args.precision,
+                      "preconditioner": args.preconditioner, "steps": args.steps,
+                      "cell_steps_per_s": N_SLICES * args.steps * N_CELLS ** 3 / t,
+                      "stats": g.stats()}), flush=True)
     g.close()
     return 0
 
@@ -439,7 +502,9 @@ def fp64_comparators(init):
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
-    if args.impl == "reference":
+    if args.mode == "kernels":
+        rc = run_kernels_only(args)
+    elif args.impl == "reference":
         rc = run_reference(args, world, rank, pg)
     else:
         rc = run_ours(args, world, rank, local, pg)

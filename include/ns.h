@@ -67,7 +67,13 @@ typedef struct {
     double inner_rtol;       /* FP32_REFINE: inner FP32 relative residual per outer
                                 step (<= 0: 1e-4)                                    */
     int batch;               /* capacity: largest batch one call may advance (>= 1)  */
+    int preconditioner;      /* ns_preconditioner: BiCGStab as in Section 2 without
+                                (NS_PC_NONE) or with one multigrid V-cycle as right
+                                preconditioner (NS_PC_MULTIGRID; falls back to
+                                NS_PC_NONE on grids it cannot coarsen far enough) */
 } ns_grid_desc;
+
+typedef enum { NS_PC_NONE = 0, NS_PC_MULTIGRID = 1 } ns_preconditioner;
 
 /* Caller-owned device buffers of `batch` states (1 <= batch <= grid capacity). */
 typedef struct {
@@ -149,12 +155,23 @@ ns_status ns_parareal_iterate(ns_grid *grid, ns_state u0, ns_state slices, int n
                               int *k_done, double *defects);
 
 /* Gradient of J = 1/2 sum over active faces of (component^2) h_x h_y h_z at
- * the end of nsteps fine steps from u0, with respect to every face of u0 and
- * to the lid speed, by the discrete adjoint of the fine step with checkpoints
- * every ckpt_every steps.  Not available in this version: returns
- * NS_ERR_ARG. */
+ * the end of nsteps fine steps (Section 2) from each state of u0, with
+ * respect to every active face of u0 (inactive faces get 0) and to the lid
+ * speed, by the discrete adjoint of the fine step:
+ *   mu = P lambda (P = I - G L^-1 D, the projection, symmetric),
+ *   lambda <- mu + dt (dR/du)^T mu,  dJ/du_lid += dt (dR/du_lid)^T mu,
+ * with R = Re^-1 lap_h u - div_h(u u) (SMART faces, the branch the forward
+ * took).  The forward states are recomputed from (u, p) checkpoints taken
+ * every ckpt_every steps; the pressure solves are taken as exact.
+ * NS_FP64 grids only (NS_ERR_ARG otherwise).  u0: device state, batch B.
+ * J, dJ_dulid: host arrays of B doubles.  grad_u0: device u, v, w buffers of
+ * batch B (p unused).  Workspace (checkpoints, one segment of states, the
+ * adjoint fields) is allocated for the call and freed before it returns. */
 ns_status ns_adjoint(ns_grid *grid, ns_state u0, double dt, int nsteps, int ckpt_every,
                      double *J, ns_state grad_u0, double *dJ_dulid);
+
+/* Sets the lid speed u_lid of the grid (for derivative checks in u_lid). */
+ns_status ns_set_lid_speed(ns_grid *grid, double u_lid);
 
 ns_status ns_get_stats(const ns_grid *grid, ns_stats *out);
 ns_status ns_reset_stats(ns_grid *grid);
@@ -164,14 +181,22 @@ typedef enum {
     NS_K_PREDICT = 0,      /* F* = u + dt (Re^-1 lap u - div(u u))            */
     NS_K_DIVERGENCE = 1,   /* b = D F* / dt and its partial sums               */
     NS_K_SOLVE_INIT = 2,   /* start of a pressure solve (FP64 init / refine init) */
-    NS_K_KRYLOV_A = 3,     /* BiCGStab phase A: p update, v = L p, (r_hat, v)  */
-    NS_K_KRYLOV_B = 4,     /* BiCGStab phase B: s, t = L s, (t,s), (t,t)       */
+    NS_K_KRYLOV_A = 3,     /* BiCGStab phase A: p update, v = L p, (r_hat, v);
+                              multigrid path: p update + finest-level smoothing */
+    NS_K_KRYLOV_B = 4,     /* BiCGStab phase B: s, t = L s, (t,s), (t,t);
+                              multigrid path: s + finest-level smoothing         */
     NS_K_KRYLOV_C = 5,     /* BiCGStab phase C: x, r updates, (r_hat,r), (r,r) */
     NS_K_INNER_INIT = 6,   /* FP32+refine: outer test and inner start          */
     NS_K_REFINE = 7,       /* FP32+refine: FP64 update p += e, r = b - L p     */
     NS_K_CORRECT = 8,      /* u = F* - dt G p, p - mean(p)                     */
     NS_K_PARAREAL = 9,     /* Parareal update of Eq. 6 and the defect          */
-    NS_K_KINDS = 10
+    NS_K_MG_LAP_V = 10,    /* multigrid path: v = L y, (r_hat, v)              */
+    NS_K_MG_LAP_T = 11,    /* multigrid path: t = L z, (t,s), (t,t)            */
+    NS_K_MG_RESTRICT0 = 12,/* multigrid: finest-level residual, restricted     */
+    NS_K_MG_PROLONG0 = 13, /* multigrid: finest-level trilinear correction     */
+    NS_K_MG_COARSE = 14,   /* multigrid: every coarser level, incl. the one-CTA levels */
+    NS_K_ADJOINT = 15,     /* adjoint: (dR/du)^T mu scatter, terminal and update kernels */
+    NS_K_KINDS = 16
 } ns_kernel_kind;
 
 typedef struct {

@@ -85,6 +85,9 @@ def _load():
                                          ctypes.c_int]
             lib.og_threads.restype = ctypes.c_int
             lib.og_project.argtypes = [gp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int, ip]
+            lib.og_rhs_adjoint.argtypes = [gp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+            lib.og_adjoint.argtypes = [gp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -219,6 +222,46 @@ class Grid:
                                   self.rtol if rtol is None else rtol, self.maxit,
                                   ctypes.byref(it)), "project")
         return u, v, w, phi
+
+    def rhs_adjoint(self, u, v, w, mu):
+        """((dR/du)^T mu per component, (dR/du_lid)^T mu) for R = Re^-1 lap u - div(u u)."""
+        out = [np.empty(self.shape(c)) for c in range(3)]
+        dl = ctypes.c_double(0)
+        _check(_load().og_rhs_adjoint(self._g(), _ptr(u), _ptr(v), _ptr(w),
+                                      *[_ptr(np.ascontiguousarray(m)) for m in mu],
+                                      *[_ptr(o) for o in out], ctypes.byref(dl)), "rhs_adjoint")
+        return out, dl.value
+
+    def adjoint(self, state0, dt, nsteps, rtol=None):
+        """(J, dJ/du0 per component, dJ/du_lid) for J = 1/2 sum over active
+        faces of component^2 * hx*hy*hz after nsteps fine steps from state0."""
+        st = [np.ascontiguousarray(a, dtype=np.float64) for a in state0]
+        grads = [np.empty(self.shape(c)) for c in range(3)]
+        J = ctypes.c_double(0)
+        dl = ctypes.c_double(0)
+        _check(_load().og_adjoint(self._g(), *[_ptr(a) for a in st], dt, nsteps,
+                                  self.rtol if rtol is None else rtol, self.maxit,
+                                  ctypes.byref(J), *[_ptr(o) for o in grads], ctypes.byref(dl)),
+               "adjoint")
+        return J.value, grads, dl.value
+
+    def kinetic_objective(self, state):
+        """J = 1/2 sum over active faces of component^2 * hx*hy*hz."""
+        hx, hy, hz = self.h
+        vol = hx * hy * hz
+        total = 0.0
+        for c in range(3):
+            a = np.array(state[c], copy=True)
+            ax = 2 - c
+            if self._c.bc[c] != PERIODIC:
+                sl0 = [slice(None)] * 3
+                sl1 = [slice(None)] * 3
+                sl0[ax] = 0
+                sl1[ax] = -1
+                a[tuple(sl0)] = 0.0
+                a[tuple(sl1)] = 0.0
+            total += 0.5 * vol * float(np.sum(a * a))
+        return total
 
     # --- time stepping ----------------------------------------------------
     def step(self, state, dt, nsteps=1, iters=None):

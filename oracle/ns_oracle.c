@@ -652,3 +652,268 @@ int og_project(const og_grid *g, double *u, double *v, double *w, double *phi, d
     free(b);
     return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* discrete adjoint of the fine step (reverse mode, exact pressure solve)     */
+/* ------------------------------------------------------------------------- */
+
+/* One step is u+ = P(u + dt R(u; u_lid)) with P = I - G L^-1 D (the
+ * projection, symmetric because D = -G^T on the MAC grid) and
+ * R = Re^-1 lap_h u - div_h(u u) (SMART faces), both reading ghost values that
+ * depend on the interior values and on the lid speed.  The adjoint of the step
+ * maps lambda (= dJ/du+) to (dJ/du, dJ/du_lid):
+ *   mu = P lambda;   dJ/du = mu + dt (dR/du)^T mu;   dJ/du_lid += dt (dR/du_lid)^T mu.
+ * (dR/du)^T mu is formed by differentiating every stencil term of R with
+ * respect to the stored values it reads and scattering; where the SMART map
+ * switches branches the derivative of the branch the forward took is used,
+ * and a flux with zero transporting velocity takes the derivative of its
+ * left-upwind form. */
+
+/* Where vget's value comes from: value = sign * a[idx] + lid * u_lid
+ * (idx < 0: a constant, e.g. nothing stored). */
+typedef struct { long idx; double sign; double lid; } og_src;
+
+static og_src vsrc(const og_grid *g, int c, int i, int j, int k)
+{
+    og_src r = {-1, 0.0, 0.0};
+    int idx[3] = {i, j, k};
+    int out_axis = -1;
+    for (int d = 0; d < 3; d++) {
+        int n = npos(g, c, d);
+        if (idx[d] < 0 || idx[d] >= n) {
+            if (g->bc[d] == OG_PERIODIC) {
+                idx[d] = wrap(idx[d], n);
+            } else {
+                if (out_axis >= 0) abort();
+                out_axis = d;
+            }
+        }
+    }
+    if (out_axis < 0) {
+        r.idx = vidx(g, c, idx[0], idx[1], idx[2]);
+        r.sign = 1.0;
+        return r;
+    }
+    int d = out_axis;
+    int n = ncell(g, d);
+    int side = idx[d] < 0 ? 0 : 1;
+    if (c == d) {
+        idx[d] = side == 0 ? -idx[d] : 2 * n - idx[d];
+        r.idx = vidx(g, c, idx[0], idx[1], idx[2]);
+        r.sign = -1.0;
+        return r;
+    }
+    idx[d] = side == 0 ? -idx[d] - 1 : 2 * n - 1 - idx[d];
+    r.idx = vidx(g, c, idx[0], idx[1], idx[2]);
+    if (g->bc[d] == OG_SLIP) {
+        r.sign = 1.0;
+        return r;
+    }
+    r.sign = -1.0;
+    r.lid = (c == 0 && d == 1 && side == 1) ? 2.0 : 0.0;
+    return r;
+}
+
+/* partial derivatives of og_smart(U, C, D) with respect to U, C, D, on the
+ * branch og_smart takes */
+static void smart_partials(double U, double C, double D, double *dU, double *dC, double *dD)
+{
+    *dU = 0.0;
+    *dC = 0.0;
+    *dD = 0.0;
+    if (D == U) { *dC = 1.0; return; }
+    double ph = (C - U) / (D - U);
+    if (ph < 0.0 || ph > 1.0) { *dC = 1.0; }
+    else if (ph <= 1.0 / 6.0) { *dU = -2.0; *dC = 3.0; }        /* U + 3 (C - U)   */
+    else if (ph <= 5.0 / 6.0) { *dU = -0.125; *dC = 0.75; *dD = 0.375; } /* QUICK */
+    else { *dD = 1.0; }
+}
+
+/* flux Uf * phi through the face between b and f (bb behind b, ff in front of
+ * f); derivatives with respect to Uf and the four node values */
+static void smart_flux_partials(double Uf, double bb, double b, double f, double ff,
+                                double *dUf, double d4[4])
+{
+    double dU, dC, dD;
+    d4[0] = d4[1] = d4[2] = d4[3] = 0.0;
+    if (Uf < 0.0) {
+        /* upwind from the front: (U, C, D) = (ff, f, b) */
+        *dUf = og_smart(ff, f, b);
+        smart_partials(ff, f, b, &dU, &dC, &dD);
+        d4[3] = Uf * dU;
+        d4[2] = Uf * dC;
+        d4[1] = Uf * dD;
+    } else {
+        /* Uf > 0, and Uf == 0 takes the same (left-upwind) form */
+        *dUf = og_smart(bb, b, f);
+        smart_partials(bb, b, f, &dU, &dC, &dD);
+        d4[0] = Uf * dU;
+        d4[1] = Uf * dC;
+        d4[2] = Uf * dD;
+    }
+}
+
+static void scatter(double *out[3], int c, og_src s, double w, double *dlid)
+{
+    if (s.idx >= 0) out[c][s.idx] += s.sign * w;
+    *dlid += s.lid * w;
+}
+
+/* out = (dR/du)^T mu on every stored face (inactive faces get whatever the
+ * scatter gives; callers zero them), dlid = (dR/du_lid)^T mu. */
+int og_rhs_adjoint(const og_grid *g, const double *u, const double *v, const double *w,
+                   const double *mu_u, const double *mu_v, const double *mu_w, double *ou,
+                   double *ov, double *ow, double *dlid)
+{
+    if (solid_arms_unsupported(g)) return OG_ERR_ARG;
+    const double *vel[3] = {u, v, w};
+    const double *mu[3] = {mu_u, mu_v, mu_w};
+    double *out[3] = {ou, ov, ow};
+    double inv_re = g->re > 0.0 ? 1.0 / g->re : 0.0;
+    for (int c = 0; c < 3; c++) memset(out[c], 0, sizeof(double) * og_count(g, c));
+    *dlid = 0.0;
+    for (int c = 0; c < 3; c++)
+        for (int k = 0; k < npos(g, c, 2); k++)
+            for (int j = 0; j < npos(g, c, 1); j++)
+                for (int i = 0; i < npos(g, c, 0); i++) {
+                    if (!face_active(g, c, i, j, k)) continue;
+                    double m = mu[c][vidx(g, c, i, j, k)];
+                    if (m == 0.0) continue;
+                    int f[3] = {i, j, k};
+                    for (int d = 0; d < 3; d++) {
+                        double h = hstep(g, d);
+                        og_src sa[5];
+                        double a[5];
+                        for (int q = -2; q <= 2; q++) {
+                            int p3[3] = {f[0], f[1], f[2]};
+                            p3[d] += q;
+                            sa[q + 2] = vsrc(g, c, p3[0], p3[1], p3[2]);
+                            a[q + 2] = vget(g, c, vel[c], p3[0], p3[1], p3[2]);
+                        }
+                        /* diffusion: Re^-1 (a3 - 2 a2 + a1) / h^2 */
+                        double wd = inv_re / (h * h) * m;
+                        scatter(out, c, sa[3], wd, dlid);
+                        scatter(out, c, sa[2], -2.0 * wd, dlid);
+                        scatter(out, c, sa[1], wd, dlid);
+                        /* convection: -(Fp - Fm) / h */
+                        double Up, Um;
+                        og_src tp[2], tm[2];
+                        int tcomp;
+                        if (d == c) {
+                            tcomp = c;
+                            tp[0] = sa[2]; tp[1] = sa[3];
+                            tm[0] = sa[1]; tm[1] = sa[2];
+                            Up = 0.5 * (a[2] + a[3]);
+                            Um = 0.5 * (a[1] + a[2]);
+                        } else {
+                            tcomp = d;
+                            int q0[3] = {f[0], f[1], f[2]};
+                            int q1[3] = {f[0], f[1], f[2]};
+                            q0[c] = f[c] - 1;
+                            q0[d] = f[d] + 1;
+                            q1[d] = f[d] + 1;
+                            tp[0] = vsrc(g, d, q0[0], q0[1], q0[2]);
+                            tp[1] = vsrc(g, d, q1[0], q1[1], q1[2]);
+                            Up = 0.5 * (vget(g, d, vel[d], q0[0], q0[1], q0[2]) +
+                                        vget(g, d, vel[d], q1[0], q1[1], q1[2]));
+                            q0[d] = f[d];
+                            q1[d] = f[d];
+                            tm[0] = vsrc(g, d, q0[0], q0[1], q0[2]);
+                            tm[1] = vsrc(g, d, q1[0], q1[1], q1[2]);
+                            Um = 0.5 * (vget(g, d, vel[d], q0[0], q0[1], q0[2]) +
+                                        vget(g, d, vel[d], q1[0], q1[1], q1[2]));
+                        }
+                        double dUp, dUm, dp[4], dm[4];
+                        smart_flux_partials(Up, a[1], a[2], a[3], a[4], &dUp, dp);
+                        smart_flux_partials(Um, a[0], a[1], a[2], a[3], &dUm, dm);
+                        double wc = -m / h;
+                        /* d(Fp)/d(nodes a1..a4) and d(Fm)/d(nodes a0..a3) */
+                        for (int q = 0; q < 4; q++) {
+                            scatter(out, c, sa[q + 1], wc * dp[q], dlid);
+                            scatter(out, c, sa[q], -wc * dm[q], dlid);
+                        }
+                        /* transporting velocities, each the mean of two values */
+                        for (int q = 0; q < 2; q++) {
+                            scatter(out, tcomp, tp[q], 0.5 * wc * dUp, dlid);
+                            scatter(out, tcomp, tm[q], -0.5 * wc * dUm, dlid);
+                        }
+                    }
+                }
+    return OG_OK;
+}
+
+/* Gradient of J = 1/2 sum over active faces of component^2 * hx*hy*hz at the
+ * end of nsteps fine steps from (u0, p0), with respect to every active face of
+ * u0 (inactive faces get 0) and to the lid speed.  The forward states are kept
+ * in memory (no checkpointing in the oracle).  p0 is only the warm start. */
+int og_adjoint(const og_grid *g, const double *u0, const double *v0, const double *w0,
+               const double *p0, double dt, int nsteps, double rtol, int maxit, double *J,
+               double *gu, double *gv, double *gw, double *dJ_dlid)
+{
+    long nc[4];
+    for (int c = 0; c < 4; c++) nc[c] = og_count(g, c);
+    long per = nc[0] + nc[1] + nc[2];
+    double *hist = malloc(sizeof(double) * per * (nsteps + 1));
+    double *p = malloc(sizeof(double) * nc[3]);
+    double *phi = malloc(sizeof(double) * nc[3]);
+    double *mu[3], *tmp[3];
+    for (int c = 0; c < 3; c++) {
+        mu[c] = malloc(sizeof(double) * nc[c]);
+        tmp[c] = malloc(sizeof(double) * nc[c]);
+    }
+    double vol = hstep(g, 0) * hstep(g, 1) * hstep(g, 2);
+    int st = OG_OK;
+    memcpy(hist, u0, sizeof(double) * nc[0]);
+    memcpy(hist + nc[0], v0, sizeof(double) * nc[1]);
+    memcpy(hist + nc[0] + nc[1], w0, sizeof(double) * nc[2]);
+    memcpy(p, p0, sizeof(double) * nc[3]);
+    for (int n = 0; n < nsteps && st == OG_OK; n++) {
+        double *cur = hist + (long)(n + 1) * per;
+        memcpy(cur, hist + (long)n * per, sizeof(double) * per);
+        st = og_step(g, cur, cur + nc[0], cur + nc[0] + nc[1], p, dt, rtol, maxit, NULL);
+    }
+    if (st == OG_OK) {
+        /* J and lambda = dJ/du^N */
+        double *uN = hist + (long)nsteps * per;
+        double Jv = 0.0;
+        double *lam[3] = {gu, gv, gw};
+        long off = 0;
+        for (int c = 0; c < 3; c++) {
+            for (int k = 0; k < npos(g, c, 2); k++)
+                for (int j = 0; j < npos(g, c, 1); j++)
+                    for (int i = 0; i < npos(g, c, 0); i++) {
+                        long id = vidx(g, c, i, j, k);
+                        double x = face_active(g, c, i, j, k) ? uN[off + id] : 0.0;
+                        Jv += 0.5 * x * x * vol;
+                        lam[c][id] = x * vol;
+                    }
+            off += nc[c];
+        }
+        *J = Jv;
+        double dl = 0.0;
+        for (int n = nsteps - 1; n >= 0 && st == OG_OK; n--) {
+            /* mu = P lambda */
+            for (int c = 0; c < 3; c++) memcpy(mu[c], lam[c], sizeof(double) * nc[c]);
+            st = og_project(g, mu[0], mu[1], mu[2], phi, rtol, maxit, NULL);
+            if (st != OG_OK) break;
+            double *un = hist + (long)n * per;
+            double dstep;
+            st = og_rhs_adjoint(g, un, un + nc[0], un + nc[0] + nc[1], mu[0], mu[1], mu[2],
+                                tmp[0], tmp[1], tmp[2], &dstep);
+            dl += dt * dstep;
+            for (int c = 0; c < 3; c++)
+                for (int k = 0; k < npos(g, c, 2); k++)
+                    for (int j = 0; j < npos(g, c, 1); j++)
+                        for (int i = 0; i < npos(g, c, 0); i++) {
+                            long id = vidx(g, c, i, j, k);
+                            lam[c][id] = face_active(g, c, i, j, k)
+                                             ? mu[c][id] + dt * tmp[c][id]
+                                             : 0.0;
+                        }
+        }
+        *dJ_dlid = dl;
+    }
+    free(hist); free(p); free(phi);
+    for (int c = 0; c < 3; c++) { free(mu[c]); free(tmp[c]); }
+    return st;
+}

@@ -11,6 +11,7 @@ NS_OK, NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_NOT_CONVERGED, NS_ERR_NONFINI
     NS_ERR_TIMEOUT = range(7)
 NS_FP64, NS_FP32_REFINE = 0, 1
 NS_BC_WALL, NS_BC_PERIODIC, NS_BC_SLIP = 0, 1, 2
+NS_PC_NONE, NS_PC_MULTIGRID = 0, 1
 
 STATUS_NAMES = {0: "NS_OK", 1: "NS_ERR_ARG", 2: "NS_ERR_CUDA", 3: "NS_ERR_OOM",
                 4: "NS_ERR_NOT_CONVERGED", 5: "NS_ERR_NONFINITE", 6: "NS_ERR_TIMEOUT"}
@@ -20,10 +21,11 @@ EXPORTS = ("ns_create_grid", "ns_destroy_grid", "ns_set_stream", "ns_step_fine",
            "ns_step_coarse", "ns_project", "ns_predict", "ns_poisson_solve",
            "ns_parareal_iterate", "ns_adjoint", "ns_get_stats", "ns_reset_stats",
            "ns_profile_enable", "ns_profile_read", "ns_poisson_solve_noalloc",
-           "ns_last_error")
+           "ns_set_lid_speed", "ns_last_error")
 
 KERNEL_KINDS = ("predict", "divergence", "solve_init", "krylov_A", "krylov_B", "krylov_C",
-                "inner_init", "refine", "correct", "parareal")
+                "inner_init", "refine", "correct", "parareal", "mg_lap_v", "mg_lap_t",
+                "mg_restrict0", "mg_prolong0", "mg_coarse", "adjoint")
 
 
 class NSError(RuntimeError):
@@ -39,7 +41,8 @@ class GridDesc(ctypes.Structure):
                 ("bc", ctypes.c_int * 3), ("solid_mask", ctypes.c_void_p),
                 ("precision", ctypes.c_int), ("poisson_rtol", ctypes.c_double),
                 ("poisson_maxit", ctypes.c_int), ("refine_rtol", ctypes.c_double),
-                ("inner_rtol", ctypes.c_double), ("batch", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("batch", ctypes.c_int),
+                ("preconditioner", ctypes.c_int)]
 
 
 class StateC(ctypes.Structure):
@@ -96,9 +99,10 @@ def load(build_if_missing: bool = False):
             "ns_parareal_iterate": [vp, StateC, StateC, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     ip, dp],
-            "ns_adjoint": [vp, StateC, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, StateC,
-                           dp],
+            "ns_adjoint": [vp, StateC, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, StateC,
+                           vp],
             "ns_get_stats": [vp, ctypes.POINTER(Stats)],
+            "ns_set_lid_speed": [vp, ctypes.c_double],
             "ns_reset_stats": [vp],
             "ns_profile_enable": [vp, ctypes.c_int, ctypes.c_int],
             "ns_profile_read": [vp, ctypes.POINTER(KernelTime), ctypes.c_int],

@@ -58,7 +58,9 @@ class Grid:
     precision: "fp64" (all FP64) or "fp32_refine" (FP32 velocity, stencils and
     inner Krylov iterations; FP64 pressure, refinement residual/correction,
     means and defects).  batch is the largest number of states one call
-    advances (the number of Parareal slices).
+    advances (the number of Parareal slices).  preconditioner: "multigrid"
+    (BiCGStab with one V-cycle as right preconditioner) or "none" (plain
+    BiCGStab).
     """
 
     def __init__(self, nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0,
@@ -66,7 +68,7 @@ class Grid:
                  bc: Sequence[str] = ("wall", "wall", "wall"), precision: str = "fp64",
                  poisson_rtol: float = 1e-12, poisson_maxit: int = 0,
                  refine_rtol: float = 1e-10, inner_rtol: float = 1e-4, batch: int = 1,
-                 device: Optional[torch.device] = None):
+                 preconditioner: str = "multigrid", device: Optional[torch.device] = None):
         self.lib = N.load()
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
@@ -88,6 +90,8 @@ class Grid:
         desc.refine_rtol = refine_rtol
         desc.inner_rtol = inner_rtol
         desc.batch = batch
+        desc.preconditioner = {"none": N.NS_PC_NONE, "multigrid": N.NS_PC_MULTIGRID}[preconditioner]
+        self.preconditioner = preconditioner
         self._desc = desc
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
@@ -225,14 +229,22 @@ class Grid:
         torch.cuda.current_stream(self.device).synchronize()
         return k, d, h2d, d2h
 
-    def adjoint(self, u0: State, dt: float, nsteps: int, ckpt_every: int):
+    def adjoint(self, u0: State, dt: float, nsteps: int, ckpt_every: int = 25):
+        """Discrete adjoint of nsteps fine steps (FP64 grids).  Returns
+        (J per state, gradient State (u, v, w; p zero), dJ/du_lid per state)
+        for J = 1/2 sum over active faces of component^2 * hx*hy*hz."""
+        self._check(u0, "adjoint(u0)")
         self._sync_stream()
-        J = ctypes.c_double(0)
-        dl = ctypes.c_double(0)
-        grad = self.zeros(1)
-        N.check(self.lib.ns_adjoint(self._h, u0._c(), dt, nsteps, ckpt_every, ctypes.byref(J),
-                                    grad._c(), ctypes.byref(dl)), "ns_adjoint")
-        return J.value, grad, dl.value
+        B = u0.batch
+        J = (ctypes.c_double * B)()
+        dl = (ctypes.c_double * B)()
+        grad = self.zeros(B)
+        N.check(self.lib.ns_adjoint(self._h, u0._c(), dt, nsteps, ckpt_every, J, grad._c(), dl),
+                "ns_adjoint")
+        return [J[i] for i in range(B)], grad, [dl[i] for i in range(B)]
+
+    def set_lid_speed(self, u_lid: float):
+        N.check(self.lib.ns_set_lid_speed(self._h, float(u_lid)), "ns_set_lid_speed")
 
     def stats(self) -> dict:
         s = N.Stats()

@@ -7,13 +7,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "ns.h"
-#include "ns_kernels.cuh"
+#include "ns_adjoint.cuh"
+#include "ns_mg.cuh"
 
 using namespace nsk;
 
@@ -56,6 +58,15 @@ struct ns_grid {
     double* b = nullptr;                        // right side of the pressure equation
     void* kv[8] = {};                           // Krylov vectors: x r rhat P0 P1 V0 V1 t
     double* p64[2] = {nullptr, nullptr};        // FP32+refine: FP64 pressure iterates
+    // multigrid-preconditioned BiCGStab
+    bool mg = false;
+    MgPlan plan{};
+    size_t mg_smem = 0;
+    void* mg_vec[3] = {};                       // Y, Z, S at level 0
+    void* mg_B[MG_MAX_LEVELS] = {};             // restricted right sides, levels 1..lc
+    void* mg_Y[MG_MAX_LEVELS] = {};             // level iterates, levels 1..lc
+    unsigned int* counter = nullptr;            // per state: CTAs arrived
+    double* part_mg = nullptr;                  // [cap][ctas][4]
     double* part_div = nullptr;
     double* part_a = nullptr;
     double* part_b = nullptr;
@@ -152,6 +163,58 @@ void setup_geo(ns_grid* g) {
     G.fbz = ceil_div(G.n[2] + 1, G.tz);
     G.fctas = G.fbx * G.fby * G.fbz;
     G.n_fluid = G.n[0] * G.n[1] * G.n[2];
+}
+
+// Multigrid hierarchy: halve every size while all are even and >= 4; the
+// levels from the first one with at most `block_cells` cells down run in one
+// CTA per state.  Returns false when the hierarchy is not usable (the block
+// levels would not fit in shared memory).
+bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
+    const Geo& G = g->geo;
+    MgPlan& P = g->plan;
+    P = MgPlan{};
+    auto fill = [](Lev& L) {
+        L.cells = (long long)L.n[0] * L.n[1] * L.n[2];
+        L.tz = std::min(8, L.n[2]);
+        L.bx = ceil_div(L.n[0], TX);
+        L.by = ceil_div(L.n[1], TY);
+        L.bz = ceil_div(L.n[2], L.tz);
+        L.ctas = L.bx * L.by * L.bz;
+    };
+    Lev L0{};
+    for (int a = 0; a < 3; ++a) {
+        L0.n[a] = G.n[a];
+        L0.bc[a] = G.bc[a];
+        L0.ih2[a] = G.ih2[a];
+    }
+    fill(L0);
+    P.lev[0] = L0;
+    P.nlev = 1;
+    while (P.nlev < MG_MAX_LEVELS) {
+        const Lev& L = P.lev[P.nlev - 1];
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok = ok && L.n[a] % 2 == 0 && L.n[a] >= 4;
+        if (!ok) break;
+        Lev C{};
+        for (int a = 0; a < 3; ++a) {
+            C.n[a] = L.n[a] / 2;
+            C.bc[a] = L.bc[a];
+            C.ih2[a] = L.ih2[a] * 0.25;
+        }
+        fill(C);
+        P.lev[P.nlev++] = C;
+    }
+    P.lc = P.nlev - 1;
+    for (int m = 0; m < P.nlev; ++m)
+        if (P.lev[m].cells <= block_cells) {
+            P.lc = m;
+            break;
+        }
+    size_t smem = 0;
+    for (int m = P.lc; m < P.nlev; ++m) smem += 3 * (size_t)P.lev[m].cells * elem;
+    g->mg_smem = smem;
+    P.block_ok = smem <= 200 * 1024 ? 1 : 0;
+    return P.block_ok != 0;
 }
 
 ns_status check_state(const ns_grid* g, const ns_state& s, const char* what) {
@@ -293,11 +356,196 @@ ns_status run_krylov(ns_grid* g, int batch, double rtol, int* max_iters, double*
     return st;
 }
 
+template <typename T>
+MgBuf<T> mgbuf(const ns_grid* g) {
+    MgBuf<T> m{};
+    m.x = (T*)g->kv[0];
+    m.r = (T*)g->kv[1];
+    m.rhat = (T*)g->kv[2];
+    m.P[0] = (T*)g->kv[3];
+    m.P[1] = (T*)g->kv[4];
+    m.V[0] = (T*)g->kv[5];
+    m.V[1] = (T*)g->kv[6];
+    m.Tt = (T*)g->kv[7];
+    m.Y = (T*)g->mg_vec[0];
+    m.Z = (T*)g->mg_vec[1];
+    m.S = (T*)g->mg_vec[2];
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) {
+        m.B[l] = (T*)g->mg_B[l];
+        m.Yl[l] = (T*)g->mg_Y[l];
+    }
+    m.counter = g->counter;
+    return m;
+}
+
+// One application of the V-cycle to the level-0 vector `src` (written by the
+// source kernel of the given mode), result in `dst`.
+template <typename T, int MODE>
+void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* dst, int par) {
+    const MgPlan& P = g->plan;
+    const int lc = P.lc;
+    const dim3 blk = block_dim();
+    const Lev& L0 = P.lev[0];
+    if (lc > 0)
+        NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
+                  (k_mg_src<T, MODE, true><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, nullptr, dst, par)));
+    else
+        NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
+                  (k_mg_src<T, MODE, false><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, nullptr, dst, par)));
+    for (int l = 0; l < lc; ++l) {
+        const T* bsrc = l == 0 ? src : mb.B[l];
+        const T* ysrc = l == 0 ? dst : mb.Yl[l];
+        NS_LAUNCH(g, l == 0 ? NS_K_MG_RESTRICT0 : NS_K_MG_COARSE, 0,
+                  k_mg_restrict<T><<<dim3(P.lev[l].ctas, batch), blk, 0, g->stream>>>(
+                      P.lev[l], P.lev[l + 1], g->ctl, bsrc, ysrc, mb.B[l + 1]));
+        if (l + 1 < lc)
+            NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+                      (k_mg_src<T, SRC_ARR, true>
+                       <<<dim3(P.lev[l + 1].ctas, batch), blk, 0, g->stream>>>(
+                           P.lev[l + 1], mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1], par)));
+    }
+    T* bin = lc == 0 ? src : mb.B[lc];
+    T* bout = lc == 0 ? dst : mb.Yl[lc];
+    NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+              k_mg_block<T><<<batch, MG_BLOCK_THREADS, g->mg_smem, g->stream>>>(P, g->ctl, bin,
+                                                                                 bout));
+    for (int l = lc - 1; l >= 0; --l) {
+        T* y = l == 0 ? dst : mb.Yl[l];
+        NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
+                  k_mg_prolong<T><<<dim3(P.lev[l].ctas, batch), blk, 0, g->stream>>>(
+                      P.lev[l], P.lev[l + 1], g->ctl, y, mb.Yl[l + 1]));
+    }
+}
+
+// Preconditioned BiCGStab iterations on every state whose status is ST_ITER,
+// until none is.  zero_start: the solve started from x = 0 (FP32 inner).
+template <typename T>
+ns_status run_mg(ns_grid* g, int batch, double rtol, int zero_start, int* max_iters,
+                 double* max_rel) {
+    const Lev& L0 = g->plan.lev[0];
+    MgBuf<T> mb = mgbuf<T>(g);
+    const dim3 grid(L0.ctas, batch), blk = block_dim();
+    const double tol2 = rtol * rtol;
+    int next_poll = std::max(1, g->iter_hint);
+    for (int it = 1;; ++it) {
+        const int par = it & 1;
+        mg_apply<T, SRC_P>(g, batch, mb, mb.P[par], mb.Y, par);
+        NS_LAUNCH(g, NS_K_MG_LAP_V, 0,
+                  k_mg_lapdot_v<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, par));
+        mg_apply<T, SRC_S>(g, batch, mb, mb.S, mb.Z, par);
+        NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
+                  k_mg_lapdot_t<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
+        NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
+                  k_mg_update<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, tol2,
+                                                               g->maxit, zero_start));
+        NS_CUDA(cudaGetLastError());
+        if (it >= next_poll) {
+            NS_TRY(poll_ctl(g, batch));
+            bool any = false;
+            for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].status == ST_ITER;
+            if (!any) break;
+            if (it > g->maxit + 2) break;
+            next_poll = it + 1;
+        }
+    }
+    int mx = 0;
+    double mr = 0.0;
+    ns_status st = NS_OK;
+    long long cell_iters = 0;
+    for (int s = 0; s < batch; ++s) {
+        const SliceCtl& c = g->h_ctl[s];
+        if (c.status == ST_IDLE) continue;
+        cell_iters += (long long)c.it_cur * L0.cells;
+        mx = std::max(mx, c.it_cur);
+        const double rel = c.bb > 0 ? std::sqrt(c.rr / c.bb) : std::sqrt(c.rr);
+        mr = std::max(mr, rel);
+        if (c.status == ST_NONFINITE)
+            st = fail(NS_ERR_NONFINITE, "non-finite residual in the pressure solve");
+        else if ((c.status == ST_MAXIT || c.status == ST_ITER) && st == NS_OK)
+            st = fail(NS_ERR_NOT_CONVERGED,
+                      "pressure solve reached its iteration limit (" + std::to_string(g->maxit) +
+                          "), relative residual " + std::to_string(rel));
+        g->stats.krylov_iters += c.it_cur;
+    }
+    if (g->prof.on && g->prof.active) {
+        // finest-level kernels: once per iteration (restrict/prolong twice)
+        for (int kind : {NS_K_KRYLOV_A, NS_K_KRYLOV_B, NS_K_KRYLOV_C, NS_K_MG_LAP_V,
+                         NS_K_MG_LAP_T})
+            g->prof.acc[kind].cell_units += cell_iters;
+        if (g->plan.lc > 0)
+            for (int kind : {NS_K_MG_RESTRICT0, NS_K_MG_PROLONG0})
+                g->prof.acc[kind].cell_units += 2 * cell_iters;
+    }
+    g->iter_hint = std::max(1, mx);
+    if (max_iters) *max_iters = std::max(*max_iters, mx);
+    if (max_rel) *max_rel = std::max(*max_rel, mr);
+    return st;
+}
+
+ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
+    const Lev& L0 = g->plan.lev[0];
+    const dim3 grid(L0.ctas, batch), blk = block_dim();
+    int max_iters = 0;
+    double max_rel = 0.0;
+    if (!g->fp32) {
+        MgBuf<double> mb = mgbuf<double>(g);
+        const double tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
+                  k_mg_init_warm<double><<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->part_mg, tol2,
+                      g->maxit));
+        NS_CUDA(cudaGetLastError());
+        NS_TRY(run_mg<double>(g, batch, g->d.poisson_rtol, 0, &max_iters, &max_rel));
+    } else {
+        MgBuf<float> mb = mgbuf<float>(g);
+        const double otol2 = g->d.refine_rtol * g->d.refine_rtol;
+        const double itol2 = g->inner_rtol * g->inner_rtol;
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
+                  k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->p64[0],
+                      g->part_mg, otol2, itol2, g->maxit));
+        NS_CUDA(cudaGetLastError());
+        for (int m = 0;; ++m) {
+            NS_TRY(poll_ctl(g, batch));
+            bool any = false;
+            for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].o_status == OS_REFINE;
+            if (!any || m > kMaxOuter + 1) break;
+            ns_status st = run_mg<float>(g, batch, g->inner_rtol, 1, &max_iters, nullptr);
+            if (st == NS_ERR_NONFINITE) return st;
+            g_last_error.clear();
+            NS_LAUNCH(g, NS_K_REFINE, L0.cells * batch,
+                      k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
+                          L0, mb, g->ctl, g->b, g->p64[m & 1], g->p64[(m + 1) & 1], g->part_mg,
+                          otol2, itol2, g->maxit, kMaxOuter, (m + 1) & 1));
+            NS_CUDA(cudaGetLastError());
+        }
+        for (int s = 0; s < batch; ++s) {
+            const SliceCtl& c = g->h_ctl[s];
+            const double rel = c.o_bb > 0 ? std::sqrt(c.o_rr / c.o_bb) : std::sqrt(c.o_rr);
+            max_rel = std::max(max_rel, rel);
+            g->stats.refine_steps += c.o_steps;
+            if (c.o_status == OS_NONFINITE)
+                return fail(NS_ERR_NONFINITE, "non-finite residual in the pressure solve");
+            if (c.o_status != OS_DONE)
+                return fail(NS_ERR_NOT_CONVERGED,
+                            "iterative refinement did not reach refine_rtol (relative residual " +
+                                std::to_string(rel) + ")");
+        }
+    }
+    g->stats.solves += batch;
+    g->stats.last_max_iters = max_iters;
+    g->stats.last_rel_residual = max_rel;
+    return NS_OK;
+}
+
 // Gauged pressure solve.  Input: g->b (double, [batch][cells]) and its partial
 // sums in g->part_div; warm start p_in (double, device).  Result: the solution
 // buffer of each state (FP64: kv x; FP32+refine: p64[p_final]) and its sum in
 // SliceCtl.sx.
 ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
+    if (g->mg) return solve_pressure_mg(g, batch, p_in);
     const Geo& G = g->geo;
     const dim3 grid(G.ctas, batch);
     int max_iters = 0;
@@ -357,8 +605,17 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
     return NS_OK;
 }
 
+// FP64 states take F* = u + dt RHS as in Section 2.  FP32 states take the
+// increment form: the predictor stores dt RHS and the correction adds
+// (dt RHS - dt G p) to u in FP64 before one rounding, so that the small
+// increment is not lost against u in FP32.  The first step of a call projects
+// the whole u + dt RHS (b = D(u + dt RHS)/dt, each part differenced exactly);
+// later steps start from the divergence-free result of the previous one and
+// take b = D(dt RHS)/dt, which keeps FP32 rounding noise of the stored u out
+// of the pressure.
 template <typename T>
 ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
+    constexpr bool INCR = sizeof(T) == sizeof(float);
     const Geo& G = g->geo;
     const int B = io.batch;
     const dim3 gcell(G.ctas, B), gface(G.fctas, B);
@@ -375,15 +632,18 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
     const long long cells = G.cnt[3] * B;
     for (int n = 0; n < nsteps; ++n) {
         NS_LAUNCH(g, NS_K_PREDICT, cells,
-                  k_predict<T><<<gface, block_dim(), 0, g->stream>>>(G, u, v, w, fu, fv, fw, dt));
+                  k_predict<T, INCR><<<gface, block_dim(), 0, g->stream>>>(G, u, v, w, fu, fv,
+                                                                           fw, dt));
+        const bool with_u = INCR && n == 0;
         NS_LAUNCH(g, NS_K_DIVERGENCE, cells,
-                  k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(G, fu, fv, fw, g->b,
-                                                                        g->part_div, 1.0 / dt));
+                  k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(
+                      G, fu, fv, fw, with_u ? u : nullptr, with_u ? v : nullptr,
+                      with_u ? w : nullptr, g->b, g->part_div, 1.0 / dt));
         NS_CUDA(cudaGetLastError());
         NS_TRY(solve_pressure(g, B, p));
         NS_LAUNCH(g, NS_K_CORRECT, cells,
-                  k_correct<T><<<gface, block_dim(), 0, g->stream>>>(G, g->ctl, fu, fv, fw, u, v,
-                                                                     w, x0, x1, p, dt));
+                  k_correct<T, INCR><<<gface, block_dim(), 0, g->stream>>>(
+                      G, g->ctl, fu, fv, fw, u, v, w, x0, x1, p, dt));
         NS_CUDA(cudaGetLastError());
         g->stats.steps += B;
     }
@@ -410,8 +670,8 @@ ns_status project_impl(ns_grid* g, const ns_state& io) {
     T* w = (T*)io.w;
     g->prof.active = B >= g->prof.min_batch;
     NS_LAUNCH(g, NS_K_DIVERGENCE, G.cnt[3] * B,
-              k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(G, u, v, w, g->b, g->part_div,
-                                                                    1.0));
+              k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(
+                  G, u, v, w, nullptr, nullptr, nullptr, g->b, g->part_div, 1.0));
     NS_CUDA(cudaMemsetAsync(g->p64[1], 0, sizeof(double) * G.cnt[3] * B, g->stream));
     NS_CUDA(cudaGetLastError());
     // zero warm start: p64[1] is free scratch at this point in both precisions
@@ -419,8 +679,8 @@ ns_status project_impl(ns_grid* g, const ns_state& io) {
     const double* x0 = g->fp32 ? g->p64[0] : (const double*)g->kv[0];
     const double* x1 = g->fp32 ? g->p64[1] : (const double*)g->kv[0];
     NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
-              k_correct<T><<<gface, block_dim(), 0, g->stream>>>(G, g->ctl, u, v, w, u, v, w, x0,
-                                                                 x1, nullptr, 1.0));
+              k_correct<T, false><<<gface, block_dim(), 0, g->stream>>>(
+                  G, g->ctl, u, v, w, u, v, w, x0, x1, nullptr, 1.0));
     NS_CUDA(cudaGetLastError());
     return NS_OK;
 }
@@ -532,6 +792,146 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
     return sync_stream(g);
 }
 
+// Reverse mode through nsteps fine steps with checkpoints of (u, p) every
+// ckpt_every steps: forward once storing checkpoints, then per segment (last
+// first) recompute its states from the checkpoint and run the adjoint steps
+// back through it.  All buffers are allocated for the call and freed after.
+ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, double* J,
+                       const ns_state& grad, double* dlid_out) {
+    const Geo& G = g->geo;
+    const int B = u0.batch;
+    const size_t nv[3] = {(size_t)G.cnt[0] * B, (size_t)G.cnt[1] * B, (size_t)G.cnt[2] * B};
+    const size_t np = (size_t)G.cnt[3] * B;
+    const size_t vel_elems = nv[0] + nv[1] + nv[2];
+    const int nck = N > 0 ? (N + C - 1) / C : 0;
+    const int seg_len = std::min(C, std::max(N, 1));
+    std::vector<void*> mine;
+    auto alloc = [&](size_t bytes) -> double* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        mine.push_back(p);
+        return (double*)p;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(g->stream);
+        for (void* p : mine) cudaFree(p);
+        mine.clear();
+    };
+    double* cur = alloc(sizeof(double) * (vel_elems + np));
+    double* ck = alloc(sizeof(double) * (vel_elems + np) * std::max(nck, 1));
+    double* seg = alloc(sizeof(double) * vel_elems * seg_len);
+    double* lam = alloc(sizeof(double) * vel_elems);
+    double* mu = alloc(sizeof(double) * vel_elems);
+    double* acc = alloc(sizeof(double) * vel_elems);
+    double* pmu = alloc(sizeof(double) * np);
+    double* dJ = alloc(sizeof(double) * 2 * B);
+    if (mine.size() != 8) {
+        release();
+        return fail(NS_ERR_OOM, "ns_adjoint: workspace allocation failed");
+    }
+    auto state_at = [&](double* base, int batch) {
+        ns_state st{base, base + nv[0], base + nv[0] + nv[1], base + vel_elems, batch};
+        return st;
+    };
+    auto vel_at = [&](double* base) {
+        ns_state st{base, base + nv[0], base + nv[0] + nv[1], pmu, B};
+        return st;
+    };
+    const void* src0[4] = {u0.u, u0.v, u0.w, u0.p};
+    ns_state cs = state_at(cur, B);
+    void* dst0[4] = {cs.u, cs.v, cs.w, cs.p};
+    ns_status st = copy_states<double>(g, dst0, src0, 0, 0, B);
+    NS_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * vel_elems, g->stream));
+    NS_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double) * 2 * B, g->stream));
+    const size_t state_bytes = sizeof(double) * (vel_elems + np);
+    // forward with checkpoints
+    for (int n = 0; n < N && st == NS_OK; ++n) {
+        if (n % C == 0)
+            if (cudaMemcpyAsync((char*)ck + (size_t)(n / C) * state_bytes, cur, state_bytes,
+                                cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_adjoint: checkpoint copy failed");
+        if (st == NS_OK) st = step_impl<double>(g, cs, dt, 1);
+    }
+    // terminal adjoint and J
+    const double vol = G.h[0] * G.h[1] * G.h[2];
+    if (st == NS_OK) {
+        for (int c = 0; c < 3; ++c) {
+            const size_t off = c == 0 ? 0 : (c == 1 ? nv[0] : nv[0] + nv[1]);
+            const int blocks = (int)std::min<long long>((G.cnt[c] + 255) / 256, 1024);
+            NS_LAUNCH(g, NS_K_ADJOINT, 0,
+                      k_adj_terminal<<<dim3(blocks, B), 256, 0, g->stream>>>(
+                          G, c, cur + off, lam + off, dJ, vol));
+        }
+        if (cudaGetLastError() != cudaSuccess) st = fail(NS_ERR_CUDA, "ns_adjoint: launch failed");
+    }
+    // reverse, segment by segment
+    for (int sg = nck - 1; sg >= 0 && st == NS_OK; --sg) {
+        const int n0 = sg * C, n1 = std::min(N, n0 + C);
+        if (cudaMemcpyAsync(cur, (char*)ck + (size_t)sg * state_bytes, state_bytes,
+                            cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "ns_adjoint: checkpoint copy failed");
+        for (int n = n0; n < n1 && st == NS_OK; ++n) {
+            if (cudaMemcpyAsync(seg + (size_t)(n - n0) * vel_elems, cur,
+                                sizeof(double) * vel_elems, cudaMemcpyDeviceToDevice,
+                                g->stream) != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_adjoint: segment copy failed");
+            if (st == NS_OK && n + 1 < n1) st = step_impl<double>(g, cs, dt, 1);
+        }
+        for (int n = n1 - 1; n >= n0 && st == NS_OK; --n) {
+            // mu = P lambda
+            if (cudaMemcpyAsync(mu, lam, sizeof(double) * vel_elems, cudaMemcpyDeviceToDevice,
+                                g->stream) != cudaSuccess) {
+                st = fail(NS_ERR_CUDA, "ns_adjoint: copy failed");
+                break;
+            }
+            st = project_impl<double>(g, vel_at(mu));
+            if (st != NS_OK) break;
+            // acc = (dR/du)^T mu at u^n, dJ/du_lid += dt (dR/du_lid)^T mu
+            double* un = seg + (size_t)(n - n0) * vel_elems;
+            NS_LAUNCH(g, NS_K_ADJOINT, 0,
+                      k_adj_rhs<<<dim3(G.fctas, B), block_dim(), 0, g->stream>>>(
+                          G, un, un + nv[0], un + nv[0] + nv[1], mu, mu + nv[0],
+                          mu + nv[0] + nv[1], acc, acc + nv[0], acc + nv[0] + nv[1], dJ + B));
+            // lambda = mu + dt acc (active faces); acc <- 0
+            for (int c = 0; c < 3; ++c) {
+                const size_t off = c == 0 ? 0 : (c == 1 ? nv[0] : nv[0] + nv[1]);
+                const int blocks = (int)std::min<long long>(((long long)nv[c] + 255) / 256, 4096);
+                NS_LAUNCH(g, NS_K_ADJOINT, 0,
+                          k_adj_finish<<<blocks, 256, 0, g->stream>>>(
+                              G, c, (long long)nv[c], mu + off, acc + off, lam + off, dt));
+            }
+            if (cudaGetLastError() != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_adjoint: launch failed");
+        }
+    }
+    if (st == NS_OK) {
+        void* gd[3] = {grad.u, grad.v, grad.w};
+        for (int c = 0; c < 3 && st == NS_OK; ++c) {
+            const size_t off = c == 0 ? 0 : (c == 1 ? nv[0] : nv[0] + nv[1]);
+            if (cudaMemcpyAsync(gd[c], lam + off, sizeof(double) * nv[c],
+                                cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_adjoint: gradient copy failed");
+        }
+        std::vector<double> h(2 * B);
+        if (st == NS_OK &&
+            (cudaMemcpyAsync(h.data(), dJ, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost,
+                             g->stream) != cudaSuccess ||
+             cudaStreamSynchronize(g->stream) != cudaSuccess))
+            st = fail(NS_ERR_CUDA, "ns_adjoint: result copy failed");
+        if (st == NS_OK) {
+            for (int b = 0; b < B; ++b) {
+                J[b] = h[b];
+                dlid_out[b] = dt * h[B + b];
+            }
+        }
+    }
+    release();
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -596,6 +996,20 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     A((void**)&g->part_c, nparts * 4 * sizeof(double));
     A((void**)&g->part_r, nparts * 3 * sizeof(double));
     A((void**)&g->ctl, sizeof(SliceCtl) * B);
+    if (d.preconditioner == NS_PC_MULTIGRID) {
+        const char* env = std::getenv("NS_MG_BLOCK_CELLS");
+        const int block_cells = env ? std::max(8, std::atoi(env)) : 4096;
+        g->mg = setup_mg(g, block_cells, ev);
+    }
+    if (g->mg) {
+        for (int q = 0; q < 3; ++q) A(&g->mg_vec[q], ncell * ev * B);
+        for (int l = 1; l <= g->plan.lc; ++l) {
+            A(&g->mg_B[l], (size_t)g->plan.lev[l].cells * ev * B);
+            A(&g->mg_Y[l], (size_t)g->plan.lev[l].cells * ev * B);
+        }
+        A((void**)&g->counter, sizeof(unsigned int) * B);
+        A((void**)&g->part_mg, nparts * 4 * sizeof(double));
+    }
     A((void**)&g->d_defect, sizeof(unsigned long long));
     if (st == NS_OK) {
         if (cudaMallocHost((void**)&g->h_ctl, sizeof(SliceCtl) * B) != cudaSuccess ||
@@ -615,6 +1029,24 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         if (st == NS_OK &&
             cudaMemsetAsync(g->ctl, 0, sizeof(SliceCtl) * B, g->stream) != cudaSuccess)
             st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        if (st == NS_OK && g->mg) {
+            if (cudaMemsetAsync(g->counter, 0, sizeof(unsigned int) * B, g->stream) !=
+                cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+            for (int q = 0; q < 3 && st == NS_OK; ++q)
+                if (cudaMemsetAsync(g->mg_vec[q], 0, ncell * ev * B, g->stream) != cudaSuccess)
+                    st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+            const cudaError_t e1 = g->fp32
+                ? cudaFuncSetAttribute(k_mg_block<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)g->mg_smem)
+                : cudaFuncSetAttribute(k_mg_block<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)g->mg_smem);
+            if (st == NS_OK && e1 != cudaSuccess)
+                st = fail(NS_ERR_CUDA, std::string("ns_create_grid: shared memory attribute: ") +
+                                           cudaGetErrorString(e1));
+        }
         if (st == NS_OK && cudaStreamSynchronize(g->stream) != cudaSuccess)
             st = fail(NS_ERR_CUDA, "ns_create_grid: stream synchronize failed");
     }
@@ -671,12 +1103,12 @@ ns_status ns_predict(ns_grid* grid, ns_state in, double dt, void* fu, void* fv, 
     grid->prof.active = in.batch >= grid->prof.min_batch;
     if (grid->fp32)
         NS_LAUNCH(grid, NS_K_PREDICT, G.cnt[3] * in.batch,
-                  k_predict<float><<<gface, block_dim(), 0, grid->stream>>>(
+                  k_predict<float, false><<<gface, block_dim(), 0, grid->stream>>>(
                       G, (const float*)in.u, (const float*)in.v, (const float*)in.w, (float*)fu,
                       (float*)fv, (float*)fw, dt));
     else
         NS_LAUNCH(grid, NS_K_PREDICT, G.cnt[3] * in.batch,
-                  k_predict<double><<<gface, block_dim(), 0, grid->stream>>>(
+                  k_predict<double, false><<<gface, block_dim(), 0, grid->stream>>>(
                       G, (const double*)in.u, (const double*)in.v, (const double*)in.w,
                       (double*)fu, (double*)fv, (double*)fw, dt));
     NS_CUDA(cudaGetLastError());
@@ -705,13 +1137,13 @@ ns_status ns_poisson_solve(ns_grid* grid, const double* b, double* p, int batch,
     const double* x1 = grid->fp32 ? grid->p64[1] : (const double*)grid->kv[0];
     if (grid->fp32)
         NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
-                  k_correct<float><<<gface, block_dim(), 0, grid->stream>>>(
+                  k_correct<float, false><<<gface, block_dim(), 0, grid->stream>>>(
                       G, grid->ctl, (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2],
                       (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2], x0, x1, p,
                       0.0));
     else
         NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
-                  k_correct<double><<<gface, block_dim(), 0, grid->stream>>>(
+                  k_correct<double, false><<<gface, block_dim(), 0, grid->stream>>>(
                       G, grid->ctl, (double*)grid->fs[0], (double*)grid->fs[1],
                       (double*)grid->fs[2], (double*)grid->fs[0], (double*)grid->fs[1],
                       (double*)grid->fs[2], x0, x1, p, 0.0));
@@ -752,9 +1184,25 @@ ns_status ns_parareal_iterate(ns_grid* grid, ns_state u0, ns_state slices, int n
 
 ns_status ns_adjoint(ns_grid* grid, ns_state u0, double dt, int nsteps, int ckpt_every, double* J,
                      ns_state grad_u0, double* dJ_dulid) {
-    (void)grid; (void)u0; (void)dt; (void)nsteps; (void)ckpt_every; (void)J; (void)grad_u0;
-    (void)dJ_dulid;
-    return fail(NS_ERR_ARG, "ns_adjoint: not available in this version");
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_adjoint: null grid");
+    NS_TRY(check_state(grid, u0, "ns_adjoint(u0)"));
+    if (grid->fp32) return fail(NS_ERR_ARG, "ns_adjoint: needs an NS_FP64 grid");
+    if (!grad_u0.u || !grad_u0.v || !grad_u0.w || grad_u0.batch != u0.batch)
+        return fail(NS_ERR_ARG, "ns_adjoint: grad_u0 must hold u0.batch velocity fields");
+    if (!J || !dJ_dulid) return fail(NS_ERR_ARG, "ns_adjoint: null J or dJ_dulid");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || ckpt_every < 1)
+        return fail(NS_ERR_ARG, "ns_adjoint: need dt > 0, nsteps >= 0, ckpt_every >= 1");
+    return adjoint_impl(grid, u0, dt, nsteps, ckpt_every, J, grad_u0, dJ_dulid);
+}
+
+ns_status ns_set_lid_speed(ns_grid* grid, double u_lid) {
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_set_lid_speed: null grid");
+    if (!std::isfinite(u_lid)) return fail(NS_ERR_ARG, "ns_set_lid_speed: u_lid not finite");
+    grid->d.u_lid = u_lid;
+    grid->geo.u_lid = u_lid;
+    return NS_OK;
 }
 
 ns_status ns_profile_enable(ns_grid* grid, int on, int min_batch) {

@@ -34,6 +34,7 @@ struct SliceCtl {
     int pad;
     double o_bb, o_rr;
     long long total_iters;  // Krylov iterations accumulated over solves
+    double beta;       // multigrid path: beta of the next iteration
 };
 
 template <typename T>
@@ -50,7 +51,8 @@ struct KBuf {       // Krylov vectors of all states, [batch][cells]
 // predictor  F* = u + dt (Re^-1 lap u - div(u u))
 // ---------------------------------------------------------------------------
 
-template <typename T>
+// INCR: write the increment dt (Re^-1 lap u - div(u u)) instead of F*.
+template <typename T, bool INCR>
 __device__ __forceinline__ void predict_face(const Geo& g, int c, const T* const* vel3, T* out,
                                              int i, int j, int k, T dt) {
     const long long id = vindex(g, c, i, j, k);
@@ -95,10 +97,12 @@ __device__ __forceinline__ void predict_face(const Geo& g, int c, const T* const
         conv += (fp - fm) * T(g.ih[d]);
         diff += (a[3] - T(2) * a[2] + a[1]) * T(g.ih2[d]);
     }
-    out[id] = vel3[c][id] + dt * (T(g.inv_re) * diff - conv);
+    const T incr = dt * (T(g.inv_re) * diff - conv);
+    out[id] = INCR ? incr : vel3[c][id] + incr;
 }
 
-template <typename T>
+// F* (INCR = false) or its increment F* - u (INCR = true) on every face.
+template <typename T, bool INCR>
 __global__ void __launch_bounds__(NTHREADS)
     k_predict(Geo g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
               T* __restrict__ fu, T* __restrict__ fv, T* __restrict__ fw, double dt) {
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(NTHREADS)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (i < g.ext[c][0] && j < g.ext[c][1] && k < g.ext[c][2])
-                predict_face(g, c, vel3, out[c], i, j, k, T(dt));
+                predict_face<T, INCR>(g, c, vel3, out[c], i, j, k, T(dt));
         }
     }
 }
@@ -121,15 +125,25 @@ __global__ void __launch_bounds__(NTHREADS)
 // b = D F* / dt, per-CTA partial sums of b (for the fluid mean)
 // ---------------------------------------------------------------------------
 
+// With u, v, w non-null (the increment form's first step) the divergence is
+// that of (u + F*) -- F* then holds the increment -- each part differenced
+// exactly in FP64.
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_divergence(Geo g, const T* __restrict__ fu, const T* __restrict__ fv,
-                 const T* __restrict__ fw, double* __restrict__ b, double* __restrict__ part,
+                 const T* __restrict__ fw, const T* __restrict__ u, const T* __restrict__ v,
+                 const T* __restrict__ w, double* __restrict__ b, double* __restrict__ part,
                  double inv_dt) {
     const long long s = blockIdx.y;
     fu += s * g.cnt[0];
     fv += s * g.cnt[1];
     fw += s * g.cnt[2];
+    const bool with_u = u != nullptr;
+    if (with_u) {
+        u += s * g.cnt[0];
+        v += s * g.cnt[1];
+        w += s * g.cnt[2];
+    }
     b += s * g.cnt[3];
     int i, j, k0;
     tile_origin(g, blockIdx.x, g.bx, g.by, i, j, k0);
@@ -140,10 +154,21 @@ __global__ void __launch_bounds__(NTHREADS)
         const int jp = (g.bc[1] == BC_PERIODIC && j + 1 == g.n[1]) ? 0 : j + 1;
         for (int k = k0; k < k1; ++k) {
             const int kp = (g.bc[2] == BC_PERIODIC && k + 1 == g.n[2]) ? 0 : k + 1;
-            T dv = (fu[vindex(g, 0, ip, j, k)] - fu[vindex(g, 0, i, j, k)]) * T(g.ih[0]);
-            dv += (fv[vindex(g, 1, i, jp, k)] - fv[vindex(g, 1, i, j, k)]) * T(g.ih[1]);
-            dv += (fw[vindex(g, 2, i, j, kp)] - fw[vindex(g, 2, i, j, k)]) * T(g.ih[2]);
-            const double bv = double(dv) * inv_dt;
+            // differences of the stored values taken in FP64 (exact for FP32 data)
+            double dv = (double(fu[vindex(g, 0, ip, j, k)]) - double(fu[vindex(g, 0, i, j, k)])) *
+                        g.ih[0];
+            dv += (double(fv[vindex(g, 1, i, jp, k)]) - double(fv[vindex(g, 1, i, j, k)])) * g.ih[1];
+            dv += (double(fw[vindex(g, 2, i, j, kp)]) - double(fw[vindex(g, 2, i, j, k)])) * g.ih[2];
+            if (with_u) {
+                double du = (double(u[vindex(g, 0, ip, j, k)]) - double(u[vindex(g, 0, i, j, k)])) *
+                            g.ih[0];
+                du += (double(v[vindex(g, 1, i, jp, k)]) - double(v[vindex(g, 1, i, j, k)])) *
+                      g.ih[1];
+                du += (double(w[vindex(g, 2, i, j, kp)]) - double(w[vindex(g, 2, i, j, k)])) *
+                      g.ih[2];
+                dv += du;
+            }
+            const double bv = dv * inv_dt;
             b[cindex(g, i, j, k)] = bv;
             acc[0] += bv;
         }
@@ -563,10 +588,12 @@ static __global__ void __launch_bounds__(NTHREADS)
 // velocity correction u = F* - dt G p and the gauged pressure p - mean(p)
 // ---------------------------------------------------------------------------
 
-// xsrc[buf] selects the solution buffer of each state: FP64 mode passes the
-// same pointer twice; FP32+refine passes p64[0], p64[1] and the state's
+// x0/x1 select the solution buffer of each state: FP64 mode passes the same
+// pointer twice; FP32+refine passes p64[0], p64[1] and the state's
 // SliceCtl.p_final picks one.  fs == vel is allowed (in-place projection).
-template <typename T>
+// INCR = false: u = F* - dt G p.  INCR = true: fs holds the increment F* - u
+// and u = u + (increment - dt G p), summed in FP64 and rounded once.
+template <typename T, bool INCR>
 __global__ void __launch_bounds__(NTHREADS)
     k_correct(Geo g, const SliceCtl* __restrict__ ctl, const T* fu, const T* fv, const T* fw,
               T* u, T* v, T* w, const double* __restrict__ x0, const double* __restrict__ x1,
@@ -594,7 +621,10 @@ __global__ void __launch_bounds__(NTHREADS)
                     lo[d] = q[d] == 0 ? g.n[d] - 1 : q[d] - 1;
                     const double gp =
                         (x[cindex(g, i, j, k)] - x[cindex(g, lo[0], lo[1], lo[2])]) * g.ih[d];
-                    o3[d][id] = f3[d][id] - T(dt * gp);
+                    if (INCR)
+                        o3[d][id] = T(double(o3[d][id]) + (double(f3[d][id]) - dt * gp));
+                    else
+                        o3[d][id] = f3[d][id] - T(dt * gp);
                 }
             }
         }

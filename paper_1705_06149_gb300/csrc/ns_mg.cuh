@@ -1,0 +1,767 @@
+// Multigrid-preconditioned BiCGStab for the pressure equation L p = b of the
+// projection step (Section 2 names BiCGStab as the solver).  The Krylov
+// iteration is BiCGStab with right preconditioning; the preconditioner is one
+// geometric multigrid V-cycle on the cell-centred pressure grid:
+//   - levels: the grid halved in every direction while all sizes are even and
+//     >= 4; each level uses the same Neumann / periodic rules with doubled h;
+//   - smoothing: two damped-Jacobi sweeps (weight 6/7) from zero before each
+//     restriction, none after the correction (a V(2,0) cycle);
+//   - restriction: mean of the 8 children; prolongation: trilinear
+//     (weights 3/4 and 1/4 per direction, mirrored at walls, wrapped when
+//     periodic);
+//   - the small levels (<= MG_BLOCK_CELLS cells) run inside one CTA per state,
+//     in shared memory; their coarsest level gets a fixed number of sweeps.
+// The V-cycle is a fixed linear operator, so BiCGStab's recurrences hold.
+//
+// Per-state reductions finish in the CTA that arrives last (a per-state
+// counter): it sums the per-CTA partials in a fixed order and writes the
+// scalars the next phase needs into SliceCtl, so no phase re-reduces.
+#pragma once
+
+#include "ns_kernels.cuh"
+
+namespace nsk {
+
+constexpr int MG_MAX_LEVELS = 14;
+constexpr double MG_OMEGA = 6.0 / 7.0;
+constexpr int MG_BLOCK_THREADS = 512;
+constexpr int MG_COARSEST_SWEEPS = 32;
+
+struct Lev {
+    int n[3];
+    int bc[3];
+    double ih2[3];
+    long long cells;
+    int tz, bx, by, bz, ctas;
+};
+
+struct MgPlan {
+    int nlev;                 // levels in the hierarchy (grid + block)
+    int lc;                   // first level handled by the block kernel
+    int block_ok;             // 1: levels >= lc fit in one CTA's shared memory
+    Lev lev[MG_MAX_LEVELS];
+};
+
+template <typename T>
+struct MgBuf {
+    T* x;      // solution / inner correction
+    T* r;      // residual
+    T* rhat;   // shadow residual
+    T* P[2];   // search direction by parity
+    T* V[2];   // L y by parity
+    T* Y;      // M^-1 p
+    T* Z;      // M^-1 s
+    T* S;      // s = r - alpha v
+    T* Tt;     // L z
+    T* B[MG_MAX_LEVELS];   // restricted right sides, levels 1..lc
+    T* Yl[MG_MAX_LEVELS];  // smoothed / corrected iterates, levels 1..lc
+    unsigned int* counter; // per state: CTAs arrived
+};
+
+__device__ __forceinline__ long long lindex(const Lev& L, int i, int j, int k) {
+    return ((long long)k * L.n[1] + j) * L.n[0] + i;
+}
+
+// Jacobi diagonal of L at (i,j,k): minus the sum of the active-face weights.
+template <typename T, typename GEO>
+__device__ __forceinline__ T diag_at(const GEO& L, int i, int j, int k) {
+    const int c[3] = {i, j, k};
+    T d = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T w = T(L.ih2[a]);
+        if (L.bc[a] == BC_PERIODIC) {
+            d -= T(2) * w;
+        } else {
+            if (c[a] > 0) d -= w;
+            if (c[a] + 1 < L.n[a]) d -= w;
+        }
+    }
+    return d;
+}
+
+// The same Laplacian as lap_cell, on a multigrid level.
+template <typename T, typename F>
+__device__ __forceinline__ T lap_lev(const Lev& L, const F& val, int i, int j, int k, T vc) {
+    T s = T(0);
+    const int c[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int n = L.n[d];
+        const T w = T(L.ih2[d]);
+        int hi[3] = {c[0], c[1], c[2]};
+        int lo[3] = {c[0], c[1], c[2]};
+        if (L.bc[d] == BC_PERIODIC) {
+            hi[d] = c[d] + 1 == n ? 0 : c[d] + 1;
+            lo[d] = c[d] == 0 ? n - 1 : c[d] - 1;
+            s += (val(hi[0], hi[1], hi[2]) - vc) * w;
+            s -= (vc - val(lo[0], lo[1], lo[2])) * w;
+        } else {
+            hi[d] = c[d] + 1;
+            lo[d] = c[d] - 1;
+            if (hi[d] < n) s += (val(hi[0], hi[1], hi[2]) - vc) * w;
+            if (lo[d] >= 0) s -= (vc - val(lo[0], lo[1], lo[2])) * w;
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ void lev_origin(const Lev& L, int cta, int& i, int& j, int& k0) {
+    int tx = cta % L.bx;
+    int r = cta / L.bx;
+    int ty = r % L.by;
+    int tzb = r / L.by;
+    i = tx * TX + threadIdx.x;
+    j = ty * TY + threadIdx.y;
+    k0 = tzb * L.tz;
+}
+
+// Arrival at the per-state counter after this CTA's partials are written.
+// Returns true in the last CTA of the state, which may then read all partials.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, int ctas) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid_flat() == 0) {
+        const unsigned int prev = atomicAdd(counter, 1u);
+        last = prev + 1 == (unsigned int)ctas;
+        if (last) *counter = 0u;  // every other CTA has arrived: reset for the next phase
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last != 0;
+}
+
+// Fixed-order sum of [ctas][NV] partials, read through L2, in the last CTA.
+template <int NV>
+__device__ __forceinline__ void sum_partials_l2(const double* part, int ctas, double (&out)[NV]) {
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int c = tid_flat(); c < ctas; c += NTHREADS) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] += __ldcg(part + (long long)c * NV + q);
+    }
+    block_sum<NV>(v);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = v[q];  // valid in thread 0
+}
+
+// Writes this CTA's partials (block-reduced) and returns whether it is last.
+template <int NV>
+__device__ __forceinline__ bool partials_and_arrive(double (&acc)[NV], double* part_state,
+                                                    unsigned int* counter, int ctas,
+                                                    double (&total)[NV]) {
+    block_sum<NV>(acc);
+    if (tid_flat() == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) part_state[(long long)blockIdx.x * NV + q] = acc[q];
+    }
+    if (!arrive_last(counter, ctas)) return false;
+    sum_partials_l2<NV>(part_state, ctas, total);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// level-0 sources and the pre-smoothing of a level
+// ---------------------------------------------------------------------------
+
+enum { SRC_P = 0, SRC_S = 1, SRC_ARR = 2 };
+
+// MODE SRC_P: p = r + beta (p_old - omega v_old) (p = r on a (re)start), stored.
+// MODE SRC_S: s = r - alpha v, stored.
+// MODE SRC_ARR: b = the level's restricted right side.
+// PRE: also two Jacobi sweeps from zero on L y = b, stored in ydst:
+//   y0 = w b / d,  y1 = y0 + w (b - L y0) / d.
+template <typename T, int MODE, bool PRE>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_src(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, const T* __restrict__ barr,
+             T* __restrict__ ydst, int par) {
+    const long long s = blockIdx.y;
+    const SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const long long off = s * L.cells;
+    const T* r = mb.r + off;
+    T* rh = mb.rhat + off;
+    const T* po = mb.P[par ^ 1] + off;
+    const T* vo = mb.V[par ^ 1] + off;
+    T* pn = mb.P[par] + off;
+    const T* vn = mb.V[par] + off;
+    T* sv = mb.S + off;
+    const T* ba = (MODE == SRC_ARR) ? barr + off : nullptr;
+    T* y = PRE ? ydst + off : nullptr;
+    const bool restart = c->restart != 0;
+    const bool first = c->it_cur == 0;
+    const T tb = T(c->beta), tw = T(c->omega), ta = T(c->alpha);
+    auto src = [&](int a, int b, int cc) -> T {
+        const long long q = lindex(L, a, b, cc);
+        if (MODE == SRC_P) return restart ? r[q] : r[q] + tb * (po[q] - tw * vo[q]);
+        if (MODE == SRC_S) return r[q] - ta * vn[q];
+        return ba[q];
+    };
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    if (i >= L.n[0] || j >= L.n[1]) return;
+    const int k1 = min(k0 + L.tz, L.n[2]);
+    const T w = T(MG_OMEGA);
+    for (int k = k0; k < k1; ++k) {
+        const long long id = lindex(L, i, j, k);
+        const T bc = src(i, j, k);
+        if (MODE == SRC_P) {
+            pn[id] = bc;
+            if (restart && !first) rh[id] = r[id];
+        }
+        if (MODE == SRC_S) sv[id] = bc;
+        if (PRE) {
+            auto y0 = [&](int a, int b, int cc) -> T {
+                return w * src(a, b, cc) / diag_at<T>(L, a, b, cc);
+            };
+            const T yc = y0(i, j, k);
+            const T d = diag_at<T>(L, i, j, k);
+            y[id] = yc + w * (bc - lap_lev(L, y0, i, j, k, yc)) / d;
+        }
+    }
+}
+
+// Residual b - L y on level l, restricted (mean of the 8 children) to level l+1.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_restrict(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, const T* __restrict__ bsrc,
+                  const T* __restrict__ ysrc, T* __restrict__ bdst) {
+    const long long s = blockIdx.y;
+    if (ctl[s].status != ST_ITER) return;
+    const T* b = bsrc + s * L.cells;
+    const T* y = ysrc + s * L.cells;
+    T* bc = bdst + s * Lc.cells;
+    __shared__ T row[TY][TX / 2];
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    const bool in = i < L.n[0] && j < L.n[1];
+    const int k1 = min(k0 + L.tz, L.n[2]);
+    auto yv = [&](int a, int bb, int cc) -> T { return y[lindex(L, a, bb, cc)]; };
+    T accz = T(0);
+    for (int k = k0; k < k1; ++k) {
+        T res = T(0);
+        if (in) {
+            const long long id = lindex(L, i, j, k);
+            res = b[id] - lap_lev(L, yv, i, j, k, y[id]);
+        }
+        res += __shfl_xor_sync(0xffffffffu, res, 1);  // x pair
+        if ((threadIdx.x & 1) == 0) row[threadIdx.y][threadIdx.x >> 1] = res;
+        __syncthreads();
+        if ((threadIdx.x & 1) == 0 && (threadIdx.y & 1) == 0)
+            accz += row[threadIdx.y][threadIdx.x >> 1] + row[threadIdx.y + 1][threadIdx.x >> 1];
+        __syncthreads();
+        if ((k & 1) == 1) {  // z pair complete
+            if (in && (threadIdx.x & 1) == 0 && (threadIdx.y & 1) == 0)
+                bc[lindex(Lc, i >> 1, j >> 1, k >> 1)] = accz * T(0.125);
+            accz = T(0);
+        }
+    }
+}
+
+// Trilinear prolongation of the coarse correction, added in place:
+// y_l += P e_{l+1}.
+template <typename T>
+__device__ __forceinline__ void tri_axis(int f, int nc, int bc, int& c0, int& c1, T& w1) {
+    c0 = f >> 1;
+    const int nb = (f & 1) ? c0 + 1 : c0 - 1;
+    w1 = T(0.25);
+    if (nb < 0 || nb >= nc) {
+        if (bc == BC_PERIODIC) {
+            c1 = nb < 0 ? nb + nc : nb - nc;
+        } else {
+            c1 = c0;  // mirrored ghost equals the boundary cell
+        }
+    } else {
+        c1 = nb;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T prolong_at(const Lev& Lc, const T* e, int i, int j, int k) {
+    int x0, x1, y0, y1, z0, z1;
+    T wx, wy, wz;
+    tri_axis<T>(i, Lc.n[0], Lc.bc[0], x0, x1, wx);
+    tri_axis<T>(j, Lc.n[1], Lc.bc[1], y0, y1, wy);
+    tri_axis<T>(k, Lc.n[2], Lc.bc[2], z0, z1, wz);
+    const T ax = T(1) - wx, ay = T(1) - wy, az = T(1) - wz;
+    auto E = [&](int a, int b, int c) { return e[lindex(Lc, a, b, c)]; };
+    const T lo = ay * (ax * E(x0, y0, z0) + wx * E(x1, y0, z0)) +
+                 wy * (ax * E(x0, y1, z0) + wx * E(x1, y1, z0));
+    const T hi = ay * (ax * E(x0, y0, z1) + wx * E(x1, y0, z1)) +
+                 wy * (ax * E(x0, y1, z1) + wx * E(x1, y1, z1));
+    return az * lo + wz * hi;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_prolong(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
+                 const T* __restrict__ ecoarse) {
+    const long long s = blockIdx.y;
+    if (ctl[s].status != ST_ITER) return;
+    T* y = ydst + s * L.cells;
+    const T* e = ecoarse + s * Lc.cells;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    if (i >= L.n[0] || j >= L.n[1]) return;
+    const int k1 = min(k0 + L.tz, L.n[2]);
+    for (int k = k0; k < k1; ++k) {
+        const long long id = lindex(L, i, j, k);
+        y[id] += prolong_at(Lc, e, i, j, k);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the small levels in one CTA per state (shared memory)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T lap_smem(const Lev& L, const T* a, int i, int j, int k) {
+    auto v = [&](int x, int y, int z) { return a[lindex(L, x, y, z)]; };
+    return lap_lev(L, v, i, j, k, a[lindex(L, i, j, k)]);
+}
+
+// V(2,0) cycle on levels plan.lc .. nlev-1 for the right side `in` (global,
+// level lc); writes the result to `out` (global, level lc).  Shared memory per
+// level m: b_m, y_m, t_m.
+template <typename T>
+__global__ void __launch_bounds__(MG_BLOCK_THREADS)
+    k_mg_block(MgPlan plan, SliceCtl* __restrict__ ctl, const T* __restrict__ in,
+               T* __restrict__ out) {
+    const long long s = blockIdx.x;
+    if (ctl[s].status != ST_ITER) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const int lc = plan.lc, nl = plan.nlev;
+    T* bq[MG_MAX_LEVELS];
+    T* yq[MG_MAX_LEVELS];
+    T* tq[MG_MAX_LEVELS];
+    {
+        long long o = 0;
+        for (int m = lc; m < nl; ++m) {
+            const long long n = plan.lev[m].cells;
+            bq[m] = sm + o;
+            yq[m] = sm + o + n;
+            tq[m] = sm + o + 2 * n;
+            o += 3 * n;
+        }
+    }
+    const int t = threadIdx.x;
+    const T w = T(MG_OMEGA);
+    {
+        const Lev& L = plan.lev[lc];
+        const T* src = in + s * L.cells;
+        for (long long q = t; q < L.cells; q += blockDim.x) bq[lc][q] = src[q];
+    }
+    __syncthreads();
+    // down: two Jacobi sweeps from zero, restrict the residual
+    for (int m = lc; m < nl - 1; ++m) {
+        const Lev& L = plan.lev[m];
+        const Lev& Lc = plan.lev[m + 1];
+        for (long long q = t; q < L.cells; q += blockDim.x) {
+            const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
+                      k = int(q / ((long long)L.n[0] * L.n[1]));
+            tq[m][q] = w * bq[m][q] / diag_at<T>(L, i, j, k);
+        }
+        __syncthreads();
+        for (long long q = t; q < L.cells; q += blockDim.x) {
+            const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
+                      k = int(q / ((long long)L.n[0] * L.n[1]));
+            yq[m][q] = tq[m][q] + w * (bq[m][q] - lap_smem(L, tq[m], i, j, k)) /
+                                      diag_at<T>(L, i, j, k);
+        }
+        __syncthreads();
+        for (long long q = t; q < Lc.cells; q += blockDim.x) {
+            const int I = int(q % Lc.n[0]), J = int((q / Lc.n[0]) % Lc.n[1]),
+                      K = int(q / ((long long)Lc.n[0] * Lc.n[1]));
+            T acc = T(0);
+            for (int dz = 0; dz < 2; ++dz)
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                        const long long f = lindex(L, i, j, k);
+                        acc += bq[m][f] - lap_smem(L, yq[m], i, j, k);
+                    }
+            bq[m + 1][q] = acc * T(0.125);
+        }
+        __syncthreads();
+    }
+    // coarsest level: Jacobi sweeps from zero (ping-pong y / t)
+    {
+        const int m = nl - 1;
+        const Lev& L = plan.lev[m];
+        for (long long q = t; q < L.cells; q += blockDim.x) yq[m][q] = T(0);
+        __syncthreads();
+        T* a = yq[m];
+        T* b = tq[m];
+        for (int sweep = 0; sweep < MG_COARSEST_SWEEPS; ++sweep) {
+            for (long long q = t; q < L.cells; q += blockDim.x) {
+                const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
+                          k = int(q / ((long long)L.n[0] * L.n[1]));
+                b[q] = a[q] + w * (bq[m][q] - lap_smem(L, a, i, j, k)) / diag_at<T>(L, i, j, k);
+            }
+            __syncthreads();
+            T* tmp = a;
+            a = b;
+            b = tmp;
+        }
+        // MG_COARSEST_SWEEPS is even: the result is back in yq[m]
+    }
+    // up: add the prolonged coarse correction
+    for (int m = nl - 2; m >= lc; --m) {
+        const Lev& L = plan.lev[m];
+        const Lev& Lc = plan.lev[m + 1];
+        for (long long q = t; q < L.cells; q += blockDim.x) {
+            const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
+                      k = int(q / ((long long)L.n[0] * L.n[1]));
+            yq[m][q] += prolong_at(Lc, yq[m + 1], i, j, k);
+        }
+        __syncthreads();
+    }
+    {
+        const Lev& L = plan.lev[lc];
+        T* dst = out + s * L.cells;
+        for (long long q = t; q < L.cells; q += blockDim.x) dst[q] = yq[lc][q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BiCGStab phases around the preconditioner (level 0)
+// ---------------------------------------------------------------------------
+
+// v = L y, (r_hat, v); the last CTA sets alpha = rho / (r_hat, v).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_lapdot_v(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
+                  int par) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const long long off = s * L.cells;
+    const T* y = mb.Y + off;
+    const T* rh = mb.rhat + off;
+    T* v = mb.V[par] + off;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    T acc_t = T(0);
+    if (i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        auto yv = [&](int a, int b, int cc) -> T { return y[lindex(L, a, b, cc)]; };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = lindex(L, i, j, k);
+            const T lv = lap_lev(L, yv, i, j, k, y[id]);
+            v[id] = lv;
+            acc_t += rh[id] * lv;
+        }
+    }
+    double acc[1] = {double(acc_t)};
+    double tot[1];
+    if (partials_and_arrive<1>(acc, part + s * L.ctas, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0)
+        c->alpha = c->rho[0] / tot[0];
+}
+
+// t = L z, (t, s), (t, t); the last CTA sets omega = (t,s)/(t,t).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_lapdot_t(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const long long off = s * L.cells;
+    const T* z = mb.Z + off;
+    const T* sv = mb.S + off;
+    T* t = mb.Tt + off;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    T ts = T(0), tt = T(0);
+    if (i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        auto zv = [&](int a, int b, int cc) -> T { return z[lindex(L, a, b, cc)]; };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = lindex(L, i, j, k);
+            const T tv = lap_lev(L, zv, i, j, k, z[id]);
+            t[id] = tv;
+            ts += tv * sv[id];
+            tt += tv * tv;
+        }
+    }
+    double acc[2] = {double(ts), double(tt)};
+    double tot[2];
+    if (partials_and_arrive<2>(acc, part + s * L.ctas * 2, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0)
+        c->omega = tot[1] != 0.0 ? tot[0] / tot[1] : 0.0;
+}
+
+// Decision after an iteration (or after a start), in the last CTA:
+// convergence on (r, r) <= tol2 bb, the iteration limit, or the next beta.
+__device__ __forceinline__ void bicg_decide(SliceCtl* c, double rho_new, double rr, double sx,
+                                            double tol2, int maxit) {
+    const int it = c->it_cur;
+    c->rr = rr;
+    c->sx = sx;
+    if (!isfinite(rr) || !isfinite(rho_new)) {
+        c->status = ST_NONFINITE;
+        return;
+    }
+    if (rr <= tol2 * c->bb) {
+        c->status = ST_CONV;
+        return;
+    }
+    if (it >= maxit) {
+        c->status = ST_MAXIT;
+        return;
+    }
+    const bool restart = it == 0 || rho_new == 0.0 || c->omega == 0.0;
+    if (restart) {
+        c->beta = 0.0;
+        c->rho[0] = rr;  // the shadow residual becomes r
+    } else {
+        c->beta = (rho_new / c->rho[0]) * (c->alpha / c->omega);
+        c->rho[0] = rho_new;
+    }
+    c->restart = restart ? 1 : 0;
+    c->status = ST_ITER;
+}
+
+// x += alpha y + omega z (x = alpha y + omega z on the first iteration of a
+// solve that starts from zero); r = s - omega t; (r_hat, r), (r, r), sum x.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_update(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
+                double tol2, int maxit, int zero_start) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const long long off = s * L.cells;
+    T* x = mb.x + off;
+    T* r = mb.r + off;
+    const T* rh = mb.rhat + off;
+    const T* y = mb.Y + off;
+    const T* z = mb.Z + off;
+    const T* sv = mb.S + off;
+    const T* t = mb.Tt + off;
+    const T ta = T(c->alpha), tw = T(c->omega);
+    const bool fresh = zero_start && c->it_cur == 0;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    if (i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        for (int k = k0; k < k1; ++k) {
+            const long long id = lindex(L, i, j, k);
+            const T xv = (fresh ? T(0) : x[id]) + (ta * y[id] + tw * z[id]);
+            const T rv = sv[id] - tw * t[id];
+            x[id] = xv;
+            r[id] = rv;
+            a0 += rh[id] * rv;
+            a1 += rv * rv;
+            a2 += xv;
+        }
+    }
+    double acc[3] = {double(a0), double(a1), double(a2)};
+    double tot[3];
+    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0) {
+        c->it_cur += 1;
+        c->total_iters += 1;
+        bicg_decide(c, tot[0], tot[1], tot[2], tol2, maxit);
+    }
+}
+
+// FP64 start from a warm x0: b <- b - mean(b); x = x0; r = b - L x0;
+// r_hat = r; the last CTA sets bb, rho and the first decision.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_init_warm(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl,
+                   const double* __restrict__ part_b, int nfluid, T* __restrict__ bvec,
+                   const T* __restrict__ x0, double* __restrict__ part, double tol2, int maxit) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    double sb[1];
+    reduce_partials<1>(part_b + s * L.ctas, L.ctas, sb);
+    const T mean = T(sb[0] / nfluid);
+    const long long off = s * L.cells;
+    T* b = bvec + off;
+    const T* xs = x0 + off;
+    T* x = mb.x + off;
+    T* r = mb.r + off;
+    T* rh = mb.rhat + off;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    if (i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        auto xv = [&](int a, int bb, int cc) -> T { return xs[lindex(L, a, bb, cc)]; };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = lindex(L, i, j, k);
+            const T bv = b[id] - mean;
+            const T xc = xs[id];
+            const T rv = bv - lap_lev(L, xv, i, j, k, xc);
+            b[id] = bv;
+            x[id] = xc;
+            r[id] = rv;
+            rh[id] = rv;
+            a0 += rv * rv;
+            a1 += xc;
+            a2 += bv * bv;
+        }
+    }
+    double acc[3] = {double(a0), double(a1), double(a2)};
+    double tot[3];
+    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0) {
+        c->it_cur = 0;
+        c->bb = tot[2];
+        c->omega = 1.0;
+        c->alpha = 1.0;
+        c->p_final = 0;
+        bicg_decide(c, tot[0], tot[0], tot[1], tol2, maxit);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 inner iterations inside FP64 iterative refinement
+// ---------------------------------------------------------------------------
+
+// Start: b <- b - mean(b); p64 = p; r64 = b - L p (FP64); r = float(r64);
+// r_hat = r (r64 itself is not stored).  The last CTA tests the outer residual and starts the inner
+// solve (from e = 0) where it is not yet small enough.
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_refine_init(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
+                     const double* __restrict__ part_b, int nfluid, double* __restrict__ bvec,
+                     const double* __restrict__ p_in, double* __restrict__ p64,
+                     double* __restrict__ part, double otol2,
+                     double itol2, int maxit) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    double sb[1];
+    reduce_partials<1>(part_b + s * L.ctas, L.ctas, sb);
+    const double mean = sb[0] / nfluid;
+    const long long off = s * L.cells;
+    double* b = bvec + off;
+    const double* ps = p_in + off;
+    double* pd = p64 + off;
+    float* r = mb.r + off;
+    float* rh = mb.rhat + off;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    float a3 = 0.0f;
+    if (i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        auto pv = [&](int a, int bb, int cc) -> double { return ps[lindex(L, a, bb, cc)]; };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = lindex(L, i, j, k);
+            const double bv = b[id] - mean;
+            const double pc = ps[id];
+            const double rv = bv - lap_lev(L, pv, i, j, k, pc);
+            const float rf = float(rv);
+            b[id] = bv;
+            pd[id] = pc;
+            r[id] = rf;
+            rh[id] = rf;
+            a0 += rv * rv;
+            a1 += bv * bv;
+            a2 += pc;
+            a3 += rf * rf;
+        }
+    }
+    double acc[4] = {a0, a1, a2, double(a3)};
+    double tot[4];
+    if (partials_and_arrive<4>(acc, part + s * L.ctas * 4, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0) {
+        c->o_bb = tot[1];
+        c->o_rr = tot[0];
+        c->o_steps = 0;
+        c->p_final = 0;
+        c->sx = tot[2];
+        if (!isfinite(tot[0])) {
+            c->o_status = OS_NONFINITE;
+            c->status = ST_IDLE;
+        } else if (tot[0] <= otol2 * tot[1]) {
+            c->o_status = OS_DONE;
+            c->status = ST_IDLE;
+        } else {
+            c->o_status = OS_REFINE;
+            c->it_cur = 0;
+            c->bb = tot[3];
+            c->omega = 1.0;
+            c->alpha = 1.0;
+            bicg_decide(c, tot[3], tot[3], 0.0, itol2, maxit);
+        }
+    }
+}
+
+// Outer correction m: p_new = p_old + e (FP64, ping-pong buffers); the true
+// FP64 residual r64 = b - L p_new (p_new recomputed at the neighbours);
+// r = float(r64); r_hat = r.  The last CTA tests the outer residual and
+// restarts the inner solve, or stops (converged / out of outer steps).
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_refine_update(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
+                       const double* __restrict__ bvec, const double* __restrict__ p_old,
+                       double* __restrict__ p_new, double* __restrict__ part, double otol2,
+                       double itol2, int maxit, int max_outer, int new_buf) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->o_status != OS_REFINE) return;
+    const bool bad = c->status == ST_NONFINITE;
+    const long long off = s * L.cells;
+    const double* b = bvec + off;
+    const double* po = p_old + off;
+    double* pn = p_new + off;
+    const float* e = mb.x + off;
+    float* r = mb.r + off;
+    float* rh = mb.rhat + off;
+    int i, j, k0;
+    lev_origin(L, blockIdx.x, i, j, k0);
+    double a0 = 0.0, a1 = 0.0;
+    float a2 = 0.0f;
+    if (!bad && i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        auto pv = [&](int a, int bb, int cc) -> double {
+            const long long q = lindex(L, a, bb, cc);
+            return po[q] + double(e[q]);
+        };
+        for (int k = k0; k < k1; ++k) {
+            const long long id = lindex(L, i, j, k);
+            const double pc = pv(i, j, k);
+            const double rv = b[id] - lap_lev(L, pv, i, j, k, pc);
+            const float rf = float(rv);
+            pn[id] = pc;
+            r[id] = rf;
+            rh[id] = rf;
+            a0 += rv * rv;
+            a1 += pc;
+            a2 += rf * rf;
+        }
+    }
+    double acc[3] = {a0, a1, double(a2)};
+    double tot[3];
+    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0) {
+        c->o_steps += 1;
+        c->o_rr = tot[0];
+        c->sx = tot[1];
+        c->p_final = new_buf;
+        if (bad || !isfinite(tot[0])) {
+            c->o_status = OS_NONFINITE;
+            c->status = ST_IDLE;
+        } else if (tot[0] <= otol2 * c->o_bb) {
+            c->o_status = OS_DONE;
+            c->status = ST_IDLE;
+        } else if (c->o_steps >= max_outer) {
+            c->o_status = OS_FAIL;
+            c->status = ST_IDLE;
+        } else {
+            c->it_cur = 0;
+            c->bb = tot[2];
+            c->omega = 1.0;
+            c->alpha = 1.0;
+            bicg_decide(c, tot[2], tot[2], 0.0, itol2, maxit);
+        }
+    }
+}
+
+}  // namespace nsk

@@ -1,0 +1,112 @@
+"""The CUDA adjoint (ns_adjoint) against the oracle's adjoint, central finite
+differences, and itself under different checkpoint intervals."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1705_06149_gb300 import Grid, inputs
+from paper_1705_06149_gb300.autograd import kinetic_energy
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _start(dims, moving, seed=12):
+    og = oracle.Grid(*dims, re=40.0, u_lid=1.0, rtol=1e-13)
+    if not moving:
+        return og.zeros()
+    rs = inputs.random_state(*dims, seed=seed, sigma=0.3)
+    u, v, w, _ = og.project(*rs[:3], rtol=1e-14)
+    return [u, v, w, np.zeros(og.shape(3))]
+
+
+@pytest.mark.parametrize("moving", [False, True])
+def test_adjoint_matches_oracle(moving):
+    dims, dt, steps = (12, 10, 8), 2e-3, 8
+    st0 = _start(dims, moving)
+    og = oracle.Grid(*dims, re=40.0, u_lid=1.0, rtol=1e-13)
+    Jr, gr, dlr = og.adjoint(st0, dt, steps, rtol=1e-13)
+    g = Grid(*dims, re=40.0, u_lid=1.0, poisson_rtol=1e-13, batch=2)
+    st = g.state_from([np.stack([a, a]) for a in st0])
+    J, grad, dl = g.adjoint(st, dt, steps, ckpt_every=3)
+    for b in range(2):
+        assert abs(J[b] - Jr) <= 1e-10 * Jr
+        assert abs(dl[b] - dlr) <= 1e-9 * abs(dlr)
+        vg = np.concatenate([t[b].cpu().numpy().ravel() for t in (grad.u, grad.v, grad.w)])
+        vr = np.concatenate([a.ravel() for a in gr])
+        assert rel(vg, vr) <= 1e-9, rel(vg, vr)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    dims, dt, steps = (10, 10, 10), 2e-3, 7
+    st0 = _start(dims, True, seed=3)
+    g = Grid(*dims, re=40.0, batch=1)
+    st = g.state_from(st0)
+    outs = [g.adjoint(st, dt, steps, ckpt_every=c) for c in (1, 3, 7, 100)]
+    J0, g0, d0 = outs[0]
+    v0 = torch.cat([g0.u.flatten(), g0.v.flatten(), g0.w.flatten()])
+    for J, gr, d in outs[1:]:
+        assert J[0] == J0[0]
+        v = torch.cat([gr.u.flatten(), gr.v.flatten(), gr.w.flatten()])
+        assert float((v - v0).norm() / v0.norm()) <= 1e-13
+        assert abs(d[0] - d0[0]) <= 1e-12 * abs(d0[0])
+
+
+def test_gradient_matches_central_differences_on_the_gpu():
+    dims, dt, steps = (16, 16, 16), 1e-3, 10
+    g = Grid(*dims, re=100.0, u_lid=1.0, poisson_rtol=1e-14, batch=1)
+    st0 = g.state_from(_start(dims, True, seed=21))
+    J, grad, dl = g.adjoint(st0, dt, steps, ckpt_every=4)
+    rng = np.random.default_rng(0)
+
+    def objective(state, lid=1.0):
+        g.set_lid_speed(lid)
+        s = state.clone()
+        g.step_fine(s, dt, steps)
+        g.set_lid_speed(1.0)
+        og = oracle.Grid(*dims)
+        return og.kinetic_objective([a[0] for a in s.numpy()])
+
+    h = 1e-6
+    for trial in range(4):
+        d = [rng.normal(size=tuple(t.shape)) for t in (st0.u, st0.v, st0.w)]
+        for c, a in enumerate(d):  # zero on wall-normal faces
+            ax = a.ndim - 1 - c
+            sl0 = [slice(None)] * a.ndim
+            sl1 = [slice(None)] * a.ndim
+            sl0[ax] = 0
+            sl1[ax] = -1
+            a[tuple(sl0)] = 0
+            a[tuple(sl1)] = 0
+        nrm = np.sqrt(sum(np.sum(a * a) for a in d))
+        d = [torch.tensor(a / nrm, device="cuda") for a in d]
+        plus = st0.clone()
+        minus = st0.clone()
+        for c, t in enumerate((plus.u, plus.v, plus.w)):
+            t += h * d[c]
+        for c, t in enumerate((minus.u, minus.v, minus.w)):
+            t -= h * d[c]
+        fd = (objective(plus) - objective(minus)) / (2 * h)
+        ad = float(sum((gr * dd).sum() for gr, dd in zip((grad.u, grad.v, grad.w), d)))
+        assert abs(fd - ad) <= 1e-4 * abs(ad) + 1e-12, (trial, fd, ad)
+    fd = (objective(st0, 1.0 + h) - objective(st0, 1.0 - h)) / (2 * h)
+    assert abs(fd - dl[0]) <= 1e-4 * abs(dl[0]), (fd, dl[0])
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    dims, dt, steps = (10, 10, 10), 2e-3, 5
+    g = Grid(*dims, re=40.0, batch=1)
+    st0 = g.state_from(_start(dims, True, seed=5))
+    u = st0.u.clone().requires_grad_(True)
+    v = st0.v.clone().requires_grad_(True)
+    w = st0.w.clone().requires_grad_(True)
+    lid = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    J = kinetic_energy(u, v, w, lid, g, dt, steps, 2)
+    (2.0 * J.sum()).backward()
+    Jr, gr, dl = g.adjoint(st0, dt, steps, 2)
+    assert torch.allclose(u.grad, 2.0 * gr.u, rtol=1e-12, atol=0)
+    assert abs(float(lid.grad) - 2.0 * dl[0]) <= 1e-12 * abs(dl[0])
