@@ -80,9 +80,10 @@ def parse():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preconditioner", choices=["multigrid", "none"], default="multigrid")
-    ap.add_argument("--mode", choices=["bench", "kernels"], default="bench",
-                    help="kernels: only `steps` batched fine steps of the 32-slice sweep "
-                         "(a short run for profilers), prints one line")
+    ap.add_argument("--mode", choices=["bench", "kernels", "coarse"], default="bench",
+                    help="kernels: only `steps` batched fine steps of the 32-slice sweep; "
+                         "coarse: only the serial coarse chain (32 slices x 5 coarse steps, "
+                         "one slice per call); short runs for profilers, one line each")
     return ap.parse_args()
 
 
@@ -454,12 +455,46 @@ def run_kernels_only(args):
     g.step_fine(batch, DT_FINE, args.warmup)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("sweep")  # profilers select this range
     g.step_fine(batch, DT_FINE, args.steps)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     print(json.dumps({"mode": "kernels", "precision": args.precision,
                       "preconditioner": args.preconditioner, "steps": args.steps,
                       "cell_steps_per_s": N_SLICES * args.steps * N_CELLS ** 3 / t,
+                      "stats": g.stats()}), flush=True)
+    g.close()
+    return 0
+
+
+def run_coarse_only(args):
+    """The serial coarse chain alone (the G sweep of one Parareal iteration,
+    without the update kernels), for profilers: `steps` repetitions."""
+    import torch
+    from paper_1705_06149_gb300 import Grid
+    init = initial_field_gpu(args.precision)
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=N_SLICES,
+             preconditioner=args.preconditioner)
+    st = g.state_from(init)
+    g.project(st)
+    dtc = DT_FINE * FINE_STEPS / COARSE_STEPS
+    for _ in range(args.warmup):
+        g.step_coarse(st.clone(), dtc, COARSE_STEPS)
+    torch.cuda.synchronize()
+    g.reset_stats()
+    t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("coarse")
+    for _ in range(args.steps):
+        s = st.clone()
+        for n in range(N_SLICES):
+            g.step_coarse(s, dtc, COARSE_STEPS)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    print(json.dumps({"mode": "coarse", "precision": args.precision,
+                      "ms_per_chain": 1e3 * t / args.steps,
+                      "ms_per_coarse_step": 1e3 * t / (args.steps * N_SLICES * COARSE_STEPS),
                       "stats": g.stats()}), flush=True)
     g.close()
     return 0
@@ -504,6 +539,8 @@ def main():
     world, rank, local, pg = dist_setup(args)
     if args.mode == "kernels":
         rc = run_kernels_only(args)
+    elif args.mode == "coarse":
+        rc = run_coarse_only(args)
     elif args.impl == "reference":
         rc = run_reference(args, world, rank, pg)
     else:

@@ -66,6 +66,7 @@ struct ns_grid {
     void* mg_B[MG_MAX_LEVELS] = {};             // restricted right sides, levels 1..lc
     void* mg_Y[MG_MAX_LEVELS] = {};             // level iterates, levels 1..lc
     unsigned int* counter = nullptr;            // per state: CTAs arrived
+    double* p_prev = nullptr;                   // p of the previous step (warm-start extrapolation)
     double* part_mg = nullptr;                  // [cap][ctas][4]
     double* part_div = nullptr;
     double* part_a = nullptr;
@@ -484,7 +485,7 @@ ns_status run_mg(ns_grid* g, int batch, double rtol, int zero_start, int* max_it
     return st;
 }
 
-ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
+ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const double* p_prev) {
     const Lev& L0 = g->plan.lev[0];
     const dim3 grid(L0.ctas, batch), blk = block_dim();
     int max_iters = 0;
@@ -494,8 +495,8 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
         const double tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
         NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
                   k_mg_init_warm<double><<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->part_mg, tol2,
-                      g->maxit));
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, p_prev,
+                      g->part_mg, tol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         NS_TRY(run_mg<double>(g, batch, g->d.poisson_rtol, 0, &max_iters, &max_rel));
     } else {
@@ -504,7 +505,7 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
         const double itol2 = g->inner_rtol * g->inner_rtol;
         NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
                   k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->p64[0],
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, p_prev, g->p64[0],
                       g->part_mg, otol2, itol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         for (int m = 0;; ++m) {
@@ -544,8 +545,9 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
 // sums in g->part_div; warm start p_in (double, device).  Result: the solution
 // buffer of each state (FP64: kv x; FP32+refine: p64[p_final]) and its sum in
 // SliceCtl.sx.
-ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
-    if (g->mg) return solve_pressure_mg(g, batch, p_in);
+ns_status solve_pressure(ns_grid* g, int batch, const double* p_in,
+                         const double* p_prev = nullptr) {
+    if (g->mg) return solve_pressure_mg(g, batch, p_in, p_prev);
     const Geo& G = g->geo;
     const dim3 grid(G.ctas, batch);
     int max_iters = 0;
@@ -607,8 +609,8 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
 
 // FP64 states take F* = u + dt RHS as in Section 2.  FP32 states take the
 // increment form: the predictor stores dt RHS and the correction adds
-// (dt RHS - dt G p) to u in FP64 before one rounding, so that the small
-// increment is not lost against u in FP32.  The first step of a call projects
+// (dt RHS - dt G p) to u, so that the small increment is not lost against u
+// in FP32 (F* = u + dt RHS rounded to FP32 would keep only its leading bits).  The first step of a call projects
 // the whole u + dt RHS (b = D(u + dt RHS)/dt, each part differenced exactly);
 // later steps start from the divergence-free result of the previous one and
 // take b = D(dt RHS)/dt, which keeps FP32 rounding noise of the stored u out
@@ -640,10 +642,14 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
                       G, fu, fv, fw, with_u ? u : nullptr, with_u ? v : nullptr,
                       with_u ? w : nullptr, g->b, g->part_div, 1.0 / dt));
         NS_CUDA(cudaGetLastError());
-        NS_TRY(solve_pressure(g, B, p));
+        // multigrid path: from the second step of a call the solve starts from
+        // 2 p^n - p^(n-1); the correction keeps p^n for that
+        const bool extrap = g->mg && n > 0;
+        NS_TRY(solve_pressure(g, B, p, extrap ? g->p_prev : nullptr));
         NS_LAUNCH(g, NS_K_CORRECT, cells,
                   k_correct<T, INCR><<<gface, block_dim(), 0, g->stream>>>(
-                      G, g->ctl, fu, fv, fw, u, v, w, x0, x1, p, dt));
+                      G, g->ctl, fu, fv, fw, u, v, w, x0, x1, p, dt,
+                      g->mg && n + 1 < nsteps ? g->p_prev : nullptr));
         NS_CUDA(cudaGetLastError());
         g->stats.steps += B;
     }
@@ -997,8 +1003,10 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     A((void**)&g->part_r, nparts * 3 * sizeof(double));
     A((void**)&g->ctl, sizeof(SliceCtl) * B);
     if (d.preconditioner == NS_PC_MULTIGRID) {
+        // levels at or below this size run in one CTA per state; FP64 keeps
+        // that CTA's share small (one SM's FP64 rate is low)
         const char* env = std::getenv("NS_MG_BLOCK_CELLS");
-        const int block_cells = env ? std::max(8, std::atoi(env)) : 4096;
+        const int block_cells = env ? std::max(8, std::atoi(env)) : (g->fp32 ? 4096 : 512);
         g->mg = setup_mg(g, block_cells, ev);
     }
     if (g->mg) {
@@ -1008,6 +1016,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
             A(&g->mg_Y[l], (size_t)g->plan.lev[l].cells * ev * B);
         }
         A((void**)&g->counter, sizeof(unsigned int) * B);
+        A((void**)&g->p_prev, ncell * sizeof(double) * B);
         A((void**)&g->part_mg, nparts * 4 * sizeof(double));
     }
     A((void**)&g->d_defect, sizeof(unsigned long long));

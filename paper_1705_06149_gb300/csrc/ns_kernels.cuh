@@ -62,15 +62,27 @@ __device__ __forceinline__ void predict_face(const Geo& g, int c, const T* const
         out[id] = T(0);
         return;
     }
+    // faces two or more positions away from every end of every axis read
+    // their stencil with plain strides; the others go through the ghost rules
+    bool interior = true;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) interior = interior && f[e] >= 2 && f[e] + 3 <= g.ext[c][e];
     T conv = T(0), diff = T(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         T a[5];
+        if (interior) {
+            const long long st = d == 0 ? 1 : (d == 1 ? g.ext[c][0]
+                                                      : (long long)g.ext[c][0] * g.ext[c][1]);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            int q[3] = {f[0], f[1], f[2]};
-            q[d] += m - 2;
-            a[m] = vel(g, c, vel3[c], q[0], q[1], q[2]);
+            for (int m = 0; m < 5; ++m) a[m] = vel3[c][id + (m - 2) * st];
+        } else {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                int q[3] = {f[0], f[1], f[2]};
+                q[d] += m - 2;
+                a[m] = vel(g, c, vel3[c], q[0], q[1], q[2]);
+            }
         }
         T up, um;
         if (d == c) {
@@ -85,12 +97,23 @@ __device__ __forceinline__ void predict_face(const Geo& g, int c, const T* const
             q0[c] = f[c] - 1;
             q0[d] = f[d] + 1;
             q1[d] = f[d] + 1;
-            up = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
-                           vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
-            q0[d] = f[d];
-            q1[d] = f[d];
-            um = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
-                           vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+            if (interior) {
+                // in range: f[c] >= 2 and f[d] + 1 < ext[d][d] for an interior face
+                const T* vd = vel3[d];
+                up = T(0.5) * (vd[vindex(g, d, q0[0], q0[1], q0[2])] +
+                               vd[vindex(g, d, q1[0], q1[1], q1[2])]);
+                q0[d] = f[d];
+                q1[d] = f[d];
+                um = T(0.5) * (vd[vindex(g, d, q0[0], q0[1], q0[2])] +
+                               vd[vindex(g, d, q1[0], q1[1], q1[2])]);
+            } else {
+                up = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                               vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+                q0[d] = f[d];
+                q1[d] = f[d];
+                um = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                               vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+            }
         }
         const T fp = smart_flux(up, a[1], a[2], a[3], a[4]);
         const T fm = smart_flux(um, a[0], a[1], a[2], a[3]);
@@ -154,12 +177,15 @@ __global__ void __launch_bounds__(NTHREADS)
         const int jp = (g.bc[1] == BC_PERIODIC && j + 1 == g.n[1]) ? 0 : j + 1;
         for (int k = k0; k < k1; ++k) {
             const int kp = (g.bc[2] == BC_PERIODIC && k + 1 == g.n[2]) ? 0 : k + 1;
-            // differences of the stored values taken in FP64 (exact for FP32 data)
-            double dv = (double(fu[vindex(g, 0, ip, j, k)]) - double(fu[vindex(g, 0, i, j, k)])) *
-                        g.ih[0];
-            dv += (double(fv[vindex(g, 1, i, jp, k)]) - double(fv[vindex(g, 1, i, j, k)])) * g.ih[1];
-            dv += (double(fw[vindex(g, 2, i, j, kp)]) - double(fw[vindex(g, 2, i, j, k)])) * g.ih[2];
+            // D of the stored F* (or increment) in the storage precision; in
+            // FP32 this is the increment, whose differences carry no
+            // cancellation against u
+            T dt_ = (fu[vindex(g, 0, ip, j, k)] - fu[vindex(g, 0, i, j, k)]) * T(g.ih[0]);
+            dt_ += (fv[vindex(g, 1, i, jp, k)] - fv[vindex(g, 1, i, j, k)]) * T(g.ih[1]);
+            dt_ += (fw[vindex(g, 2, i, j, kp)] - fw[vindex(g, 2, i, j, k)]) * T(g.ih[2]);
+            double dv = double(dt_);
             if (with_u) {
+                // the stored u itself: differences taken exactly in FP64
                 double du = (double(u[vindex(g, 0, ip, j, k)]) - double(u[vindex(g, 0, i, j, k)])) *
                             g.ih[0];
                 du += (double(v[vindex(g, 1, i, jp, k)]) - double(v[vindex(g, 1, i, j, k)])) *
@@ -592,12 +618,12 @@ static __global__ void __launch_bounds__(NTHREADS)
 // pointer twice; FP32+refine passes p64[0], p64[1] and the state's
 // SliceCtl.p_final picks one.  fs == vel is allowed (in-place projection).
 // INCR = false: u = F* - dt G p.  INCR = true: fs holds the increment F* - u
-// and u = u + (increment - dt G p), summed in FP64 and rounded once.
+// and u = u + (increment - dt G p).
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(NTHREADS)
     k_correct(Geo g, const SliceCtl* __restrict__ ctl, const T* fu, const T* fv, const T* fw,
               T* u, T* v, T* w, const double* __restrict__ x0, const double* __restrict__ x1,
-              double* __restrict__ p_out, double dt) {
+              double* __restrict__ p_out, double dt, double* __restrict__ p_keep = nullptr) {
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     const double* x = (c->p_final ? x1 : x0) + s * g.cnt[3];
@@ -621,8 +647,10 @@ __global__ void __launch_bounds__(NTHREADS)
                     lo[d] = q[d] == 0 ? g.n[d] - 1 : q[d] - 1;
                     const double gp =
                         (x[cindex(g, i, j, k)] - x[cindex(g, lo[0], lo[1], lo[2])]) * g.ih[d];
+                    // the pressure difference is taken in FP64; in the increment
+                    // form u + (increment - dt G p) is rounded once
                     if (INCR)
-                        o3[d][id] = T(double(o3[d][id]) + (double(f3[d][id]) - dt * gp));
+                        o3[d][id] = o3[d][id] + (f3[d][id] - T(dt * gp));
                     else
                         o3[d][id] = f3[d][id] - T(dt * gp);
                 }
@@ -630,6 +658,8 @@ __global__ void __launch_bounds__(NTHREADS)
         }
         if (p_out && i < g.n[0] && j < g.n[1] && k < g.n[2]) {
             const long long id = cindex(g, i, j, k);
+            // p_keep (optional) receives the pressure being replaced
+            if (p_keep) p_keep[s * g.cnt[3] + id] = p_out[s * g.cnt[3] + id];
             p_out[s * g.cnt[3] + id] = x[id] - mean;
         }
     }

@@ -58,8 +58,8 @@ struct MgBuf {
     unsigned int* counter; // per state: CTAs arrived
 };
 
-__device__ __forceinline__ long long lindex(const Lev& L, int i, int j, int k) {
-    return ((long long)k * L.n[1] + j) * L.n[0] + i;
+__device__ __forceinline__ int lindex(const Lev& L, int i, int j, int k) {
+    return (k * L.n[1] + j) * L.n[0] + i;
 }
 
 // Jacobi diagonal of L at (i,j,k): minus the sum of the active-face weights.
@@ -106,6 +106,21 @@ __device__ __forceinline__ T lap_lev(const Lev& L, const F& val, int i, int j, i
     return s;
 }
 
+// Laplacian at a cell with all six neighbours inside the level (no wall face,
+// no periodic seam), from a value accessor taking the linear index.
+template <typename T, typename F>
+__device__ __forceinline__ T lap_interior(const Lev& L, const F& val, int id, T vc) {
+    const int sy = L.n[0], sz = L.n[0] * L.n[1];
+    const T two = T(2);
+    return (val(id + 1) + val(id - 1) - two * vc) * T(L.ih2[0]) +
+           (val(id + sy) + val(id - sy) - two * vc) * T(L.ih2[1]) +
+           (val(id + sz) + val(id - sz) - two * vc) * T(L.ih2[2]);
+}
+
+__device__ __forceinline__ bool inside(const Lev& L, int i, int j, int k, int m) {
+    return i >= m && j >= m && k >= m && i + m < L.n[0] && j + m < L.n[1] && k + m < L.n[2];
+}
+
 __device__ __forceinline__ void lev_origin(const Lev& L, int cta, int& i, int& j, int& k0) {
     int tx = cta % L.bx;
     int r = cta / L.bx;
@@ -147,6 +162,52 @@ __device__ __forceinline__ void sum_partials_l2(const double* part, int ctas, do
     for (int q = 0; q < NV; ++q) out[q] = v[q];  // valid in thread 0
 }
 
+// Sum over the CTA of per-thread values: a warp-shuffle tree in the values'
+// own precision, then the warp sums in FP64 (valid in thread 0).  For FP32
+// kernels this keeps the FP64 pipe out of the per-thread work.
+template <typename A, int NV>
+__device__ __forceinline__ void block_sum_mixed(A (&v)[NV], double (&out)[NV]) {
+    __shared__ double sm[NV][NWARPS];
+    const int t = tid_flat();
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sm[q][warp] = double(v[q]);
+    }
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = 0.0;
+            for (int w = 0; w < NWARPS; ++w) x += sm[q][w];
+            out[q] = x;
+        }
+    }
+}
+
+// Writes this CTA's partials and returns whether it is the last CTA of the
+// state; the last one then holds the state's totals in thread 0.
+template <typename A, int NV>
+__device__ __forceinline__ bool partials_arrive(A (&acc)[NV], double* part_state,
+                                                unsigned int* counter, int ctas,
+                                                double (&total)[NV]) {
+    double blk[NV];
+    block_sum_mixed<A, NV>(acc, blk);
+    if (tid_flat() == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) part_state[(long long)blockIdx.x * NV + q] = blk[q];
+    }
+    if (!arrive_last(counter, ctas)) return false;
+    sum_partials_l2<NV>(part_state, ctas, total);
+    return true;
+}
+
 // Writes this CTA's partials (block-reduced) and returns whether it is last.
 template <int NV>
 __device__ __forceinline__ bool partials_and_arrive(double (&acc)[NV], double* part_state,
@@ -181,31 +242,34 @@ __global__ void __launch_bounds__(NTHREADS)
     const SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
     const long long off = s * L.cells;
-    const T* r = mb.r + off;
-    T* rh = mb.rhat + off;
-    const T* po = mb.P[par ^ 1] + off;
-    const T* vo = mb.V[par ^ 1] + off;
-    T* pn = mb.P[par] + off;
-    const T* vn = mb.V[par] + off;
-    T* sv = mb.S + off;
-    const T* ba = (MODE == SRC_ARR) ? barr + off : nullptr;
-    T* y = PRE ? ydst + off : nullptr;
+    const T* __restrict__ r = mb.r + off;
+    T* __restrict__ rh = mb.rhat + off;
+    const T* __restrict__ po = mb.P[par ^ 1] + off;
+    const T* __restrict__ vo = mb.V[par ^ 1] + off;
+    T* __restrict__ pn = mb.P[par] + off;
+    const T* __restrict__ vn = mb.V[par] + off;
+    T* __restrict__ sv = mb.S + off;
+    const T* __restrict__ ba = (MODE == SRC_ARR) ? barr + off : nullptr;
+    T* __restrict__ y = PRE ? ydst + off : nullptr;
     const bool restart = c->restart != 0;
     const bool first = c->it_cur == 0;
     const T tb = T(c->beta), tw = T(c->omega), ta = T(c->alpha);
-    auto src = [&](int a, int b, int cc) -> T {
-        const long long q = lindex(L, a, b, cc);
+    auto srcq = [&](int q) -> T {
         if (MODE == SRC_P) return restart ? r[q] : r[q] + tb * (po[q] - tw * vo[q]);
         if (MODE == SRC_S) return r[q] - ta * vn[q];
         return ba[q];
     };
+    auto src = [&](int a, int b, int cc) -> T { return srcq(lindex(L, a, b, cc)); };
+    // Jacobi diagonal of a cell with all faces active, and its reciprocal
+    const T d_in = -T(2) * (T(L.ih2[0]) + T(L.ih2[1]) + T(L.ih2[2]));
+    const T wd = T(MG_OMEGA) / d_in;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     if (i >= L.n[0] || j >= L.n[1]) return;
     const int k1 = min(k0 + L.tz, L.n[2]);
     const T w = T(MG_OMEGA);
     for (int k = k0; k < k1; ++k) {
-        const long long id = lindex(L, i, j, k);
+        const int id = lindex(L, i, j, k);
         const T bc = src(i, j, k);
         if (MODE == SRC_P) {
             pn[id] = bc;
@@ -213,12 +277,18 @@ __global__ void __launch_bounds__(NTHREADS)
         }
         if (MODE == SRC_S) sv[id] = bc;
         if (PRE) {
-            auto y0 = [&](int a, int b, int cc) -> T {
-                return w * src(a, b, cc) / diag_at<T>(L, a, b, cc);
-            };
-            const T yc = y0(i, j, k);
-            const T d = diag_at<T>(L, i, j, k);
-            y[id] = yc + w * (bc - lap_lev(L, y0, i, j, k, yc)) / d;
+            if (inside(L, i, j, k, 2)) {
+                // every neighbour has the interior diagonal: L y0 = (w/d) L b
+                const T lb = lap_interior(L, srcq, id, bc);
+                y[id] = wd * bc + wd * (bc - wd * lb);
+            } else {
+                auto y0 = [&](int a, int b, int cc) -> T {
+                    return w * src(a, b, cc) / diag_at<T>(L, a, b, cc);
+                };
+                const T yc = y0(i, j, k);
+                const T d = diag_at<T>(L, i, j, k);
+                y[id] = yc + w * (bc - lap_lev(L, y0, i, j, k, yc)) / d;
+            }
         }
     }
 }
@@ -230,21 +300,24 @@ __global__ void __launch_bounds__(NTHREADS)
                   const T* __restrict__ ysrc, T* __restrict__ bdst) {
     const long long s = blockIdx.y;
     if (ctl[s].status != ST_ITER) return;
-    const T* b = bsrc + s * L.cells;
-    const T* y = ysrc + s * L.cells;
-    T* bc = bdst + s * Lc.cells;
+    const T* __restrict__ b = bsrc + s * L.cells;
+    const T* __restrict__ y = ysrc + s * L.cells;
+    T* __restrict__ bc = bdst + s * Lc.cells;
     __shared__ T row[TY][TX / 2];
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     const bool in = i < L.n[0] && j < L.n[1];
     const int k1 = min(k0 + L.tz, L.n[2]);
     auto yv = [&](int a, int bb, int cc) -> T { return y[lindex(L, a, bb, cc)]; };
+    auto yq = [&](int q) -> T { return y[q]; };
     T accz = T(0);
     for (int k = k0; k < k1; ++k) {
         T res = T(0);
         if (in) {
-            const long long id = lindex(L, i, j, k);
-            res = b[id] - lap_lev(L, yv, i, j, k, y[id]);
+            const int id = lindex(L, i, j, k);
+            const T yc = y[id];
+            res = b[id] - (inside(L, i, j, k, 1) ? lap_interior(L, yq, id, yc)
+                                                 : lap_lev(L, yv, i, j, k, yc));
         }
         res += __shfl_xor_sync(0xffffffffu, res, 1);  // x pair
         if ((threadIdx.x & 1) == 0) row[threadIdx.y][threadIdx.x >> 1] = res;
@@ -300,14 +373,14 @@ __global__ void __launch_bounds__(NTHREADS)
                  const T* __restrict__ ecoarse) {
     const long long s = blockIdx.y;
     if (ctl[s].status != ST_ITER) return;
-    T* y = ydst + s * L.cells;
-    const T* e = ecoarse + s * Lc.cells;
+    T* __restrict__ y = ydst + s * L.cells;
+    const T* __restrict__ e = ecoarse + s * Lc.cells;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     if (i >= L.n[0] || j >= L.n[1]) return;
     const int k1 = min(k0 + L.tz, L.n[2]);
     for (int k = k0; k < k1; ++k) {
-        const long long id = lindex(L, i, j, k);
+        const int id = lindex(L, i, j, k);
         y[id] += prolong_at(Lc, e, i, j, k);
     }
 }
@@ -332,7 +405,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     const long long s = blockIdx.x;
     if (ctl[s].status != ST_ITER) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
+    T* __restrict__ sm = reinterpret_cast<T*>(smem_raw);
     const int lc = plan.lc, nl = plan.nlev;
     T* bq[MG_MAX_LEVELS];
     T* yq[MG_MAX_LEVELS];
@@ -351,7 +424,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     const T w = T(MG_OMEGA);
     {
         const Lev& L = plan.lev[lc];
-        const T* src = in + s * L.cells;
+        const T* __restrict__ src = in + s * L.cells;
         for (long long q = t; q < L.cells; q += blockDim.x) bq[lc][q] = src[q];
     }
     __syncthreads();
@@ -380,7 +453,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
                 for (int dy = 0; dy < 2; ++dy)
                     for (int dx = 0; dx < 2; ++dx) {
                         const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                        const long long f = lindex(L, i, j, k);
+                        const int f = lindex(L, i, j, k);
                         acc += bq[m][f] - lap_smem(L, yq[m], i, j, k);
                     }
             bq[m + 1][q] = acc * T(0.125);
@@ -393,9 +466,13 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
         const Lev& L = plan.lev[m];
         for (long long q = t; q < L.cells; q += blockDim.x) yq[m][q] = T(0);
         __syncthreads();
-        T* a = yq[m];
+        T* a = yq[m];  // ping-pong pair: not restrict-qualified
         T* b = tq[m];
-        for (int sweep = 0; sweep < MG_COARSEST_SWEEPS; ++sweep) {
+        // enough sweeps for the coarsest level's size (an even count, so the
+        // result ends in yq[m]); a 2^3 level needs few
+        const int nmax = max(L.n[0], max(L.n[1], L.n[2]));
+        const int sweeps = min(MG_COARSEST_SWEEPS, 4 * ((nmax + 1) / 2) * 2);
+        for (int sweep = 0; sweep < sweeps; ++sweep) {
             for (long long q = t; q < L.cells; q += blockDim.x) {
                 const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
                           k = int(q / ((long long)L.n[0] * L.n[1]));
@@ -406,7 +483,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
             a = b;
             b = tmp;
         }
-        // MG_COARSEST_SWEEPS is even: the result is back in yq[m]
+        // an even number of sweeps: the result is back in yq[m]
     }
     // up: add the prolonged coarse correction
     for (int m = nl - 2; m >= lc; --m) {
@@ -421,7 +498,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     }
     {
         const Lev& L = plan.lev[lc];
-        T* dst = out + s * L.cells;
+        T* __restrict__ dst = out + s * L.cells;
         for (long long q = t; q < L.cells; q += blockDim.x) dst[q] = yq[lc][q];
     }
 }
@@ -439,25 +516,28 @@ __global__ void __launch_bounds__(NTHREADS)
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
     const long long off = s * L.cells;
-    const T* y = mb.Y + off;
-    const T* rh = mb.rhat + off;
-    T* v = mb.V[par] + off;
+    const T* __restrict__ y = mb.Y + off;
+    const T* __restrict__ rh = mb.rhat + off;
+    T* __restrict__ v = mb.V[par] + off;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     T acc_t = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         auto yv = [&](int a, int b, int cc) -> T { return y[lindex(L, a, b, cc)]; };
+        auto yq = [&](int q) -> T { return y[q]; };
         for (int k = k0; k < k1; ++k) {
-            const long long id = lindex(L, i, j, k);
-            const T lv = lap_lev(L, yv, i, j, k, y[id]);
+            const int id = lindex(L, i, j, k);
+            const T yc = y[id];
+            const T lv = inside(L, i, j, k, 1) ? lap_interior(L, yq, id, yc)
+                                               : lap_lev(L, yv, i, j, k, yc);
             v[id] = lv;
             acc_t += rh[id] * lv;
         }
     }
-    double acc[1] = {double(acc_t)};
+    T acc[1] = {acc_t};
     double tot[1];
-    if (partials_and_arrive<1>(acc, part + s * L.ctas, mb.counter + s, L.ctas, tot) &&
+    if (partials_arrive<T, 1>(acc, part + s * L.ctas, mb.counter + s, L.ctas, tot) &&
         tid_flat() == 0)
         c->alpha = c->rho[0] / tot[0];
 }
@@ -470,26 +550,29 @@ __global__ void __launch_bounds__(NTHREADS)
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
     const long long off = s * L.cells;
-    const T* z = mb.Z + off;
-    const T* sv = mb.S + off;
-    T* t = mb.Tt + off;
+    const T* __restrict__ z = mb.Z + off;
+    const T* __restrict__ sv = mb.S + off;
+    T* __restrict__ t = mb.Tt + off;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     T ts = T(0), tt = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         auto zv = [&](int a, int b, int cc) -> T { return z[lindex(L, a, b, cc)]; };
+        auto zq = [&](int q) -> T { return z[q]; };
         for (int k = k0; k < k1; ++k) {
-            const long long id = lindex(L, i, j, k);
-            const T tv = lap_lev(L, zv, i, j, k, z[id]);
+            const int id = lindex(L, i, j, k);
+            const T zc = z[id];
+            const T tv = inside(L, i, j, k, 1) ? lap_interior(L, zq, id, zc)
+                                               : lap_lev(L, zv, i, j, k, zc);
             t[id] = tv;
             ts += tv * sv[id];
             tt += tv * tv;
         }
     }
-    double acc[2] = {double(ts), double(tt)};
+    T acc[2] = {ts, tt};
     double tot[2];
-    if (partials_and_arrive<2>(acc, part + s * L.ctas * 2, mb.counter + s, L.ctas, tot) &&
+    if (partials_arrive<T, 2>(acc, part + s * L.ctas * 2, mb.counter + s, L.ctas, tot) &&
         tid_flat() == 0)
         c->omega = tot[1] != 0.0 ? tot[0] / tot[1] : 0.0;
 }
@@ -535,13 +618,13 @@ __global__ void __launch_bounds__(NTHREADS)
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
     const long long off = s * L.cells;
-    T* x = mb.x + off;
-    T* r = mb.r + off;
-    const T* rh = mb.rhat + off;
-    const T* y = mb.Y + off;
-    const T* z = mb.Z + off;
-    const T* sv = mb.S + off;
-    const T* t = mb.Tt + off;
+    T* __restrict__ x = mb.x + off;
+    T* __restrict__ r = mb.r + off;
+    const T* __restrict__ rh = mb.rhat + off;
+    const T* __restrict__ y = mb.Y + off;
+    const T* __restrict__ z = mb.Z + off;
+    const T* __restrict__ sv = mb.S + off;
+    const T* __restrict__ t = mb.Tt + off;
     const T ta = T(c->alpha), tw = T(c->omega);
     const bool fresh = zero_start && c->it_cur == 0;
     int i, j, k0;
@@ -550,7 +633,7 @@ __global__ void __launch_bounds__(NTHREADS)
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         for (int k = k0; k < k1; ++k) {
-            const long long id = lindex(L, i, j, k);
+            const int id = lindex(L, i, j, k);
             const T xv = (fresh ? T(0) : x[id]) + (ta * y[id] + tw * z[id]);
             const T rv = sv[id] - tw * t[id];
             x[id] = xv;
@@ -560,9 +643,9 @@ __global__ void __launch_bounds__(NTHREADS)
             a2 += xv;
         }
     }
-    double acc[3] = {double(a0), double(a1), double(a2)};
+    T acc[3] = {a0, a1, a2};
     double tot[3];
-    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+    if (partials_arrive<T, 3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
         tid_flat() == 0) {
         c->it_cur += 1;
         c->total_iters += 1;
@@ -576,28 +659,32 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_init_warm(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl,
                    const double* __restrict__ part_b, int nfluid, T* __restrict__ bvec,
-                   const T* __restrict__ x0, double* __restrict__ part, double tol2, int maxit) {
+                   const T* __restrict__ x0, const T* __restrict__ xprev,
+                   double* __restrict__ part, double tol2, int maxit) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     double sb[1];
     reduce_partials<1>(part_b + s * L.ctas, L.ctas, sb);
     const T mean = T(sb[0] / nfluid);
     const long long off = s * L.cells;
-    T* b = bvec + off;
-    const T* xs = x0 + off;
-    T* x = mb.x + off;
-    T* r = mb.r + off;
-    T* rh = mb.rhat + off;
+    T* __restrict__ b = bvec + off;
+    const T* __restrict__ xs = x0 + off;
+    const T* __restrict__ xp = xprev ? xprev + off : nullptr;
+    T* __restrict__ x = mb.x + off;
+    T* __restrict__ r = mb.r + off;
+    T* __restrict__ rh = mb.rhat + off;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     T a0 = T(0), a1 = T(0), a2 = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto xv = [&](int a, int bb, int cc) -> T { return xs[lindex(L, a, bb, cc)]; };
+        // warm start: x0, or 2 x0 - xprev (linear extrapolation in time)
+        auto xq = [&](int q) -> T { return xp ? T(2) * xs[q] - xp[q] : xs[q]; };
+        auto xv = [&](int a, int bb, int cc) -> T { return xq(lindex(L, a, bb, cc)); };
         for (int k = k0; k < k1; ++k) {
-            const long long id = lindex(L, i, j, k);
+            const int id = lindex(L, i, j, k);
             const T bv = b[id] - mean;
-            const T xc = xs[id];
+            const T xc = xq(id);
             const T rv = bv - lap_lev(L, xv, i, j, k, xc);
             b[id] = bv;
             x[id] = xc;
@@ -631,8 +718,8 @@ __global__ void __launch_bounds__(NTHREADS)
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_refine_init(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
                      const double* __restrict__ part_b, int nfluid, double* __restrict__ bvec,
-                     const double* __restrict__ p_in, double* __restrict__ p64,
-                     double* __restrict__ part, double otol2,
+                     const double* __restrict__ p_in, const double* __restrict__ p_prev,
+                     double* __restrict__ p64, double* __restrict__ part, double otol2,
                      double itol2, int maxit) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
@@ -640,22 +727,25 @@ __global__ void __launch_bounds__(NTHREADS)
     reduce_partials<1>(part_b + s * L.ctas, L.ctas, sb);
     const double mean = sb[0] / nfluid;
     const long long off = s * L.cells;
-    double* b = bvec + off;
-    const double* ps = p_in + off;
-    double* pd = p64 + off;
-    float* r = mb.r + off;
-    float* rh = mb.rhat + off;
+    double* __restrict__ b = bvec + off;
+    const double* __restrict__ ps = p_in + off;
+    const double* __restrict__ pp = p_prev ? p_prev + off : nullptr;
+    double* __restrict__ pd = p64 + off;
+    float* __restrict__ r = mb.r + off;
+    float* __restrict__ rh = mb.rhat + off;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     float a3 = 0.0f;
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto pv = [&](int a, int bb, int cc) -> double { return ps[lindex(L, a, bb, cc)]; };
+        // warm start: p, or 2 p - p_prev (linear extrapolation in time)
+        auto pq = [&](int q) -> double { return pp ? 2.0 * ps[q] - pp[q] : ps[q]; };
+        auto pv = [&](int a, int bb, int cc) -> double { return pq(lindex(L, a, bb, cc)); };
         for (int k = k0; k < k1; ++k) {
-            const long long id = lindex(L, i, j, k);
+            const int id = lindex(L, i, j, k);
             const double bv = b[id] - mean;
-            const double pc = ps[id];
+            const double pc = pq(id);
             const double rv = bv - lap_lev(L, pv, i, j, k, pc);
             const float rf = float(rv);
             b[id] = bv;
@@ -708,12 +798,12 @@ __global__ void __launch_bounds__(NTHREADS)
     if (c->o_status != OS_REFINE) return;
     const bool bad = c->status == ST_NONFINITE;
     const long long off = s * L.cells;
-    const double* b = bvec + off;
-    const double* po = p_old + off;
-    double* pn = p_new + off;
-    const float* e = mb.x + off;
-    float* r = mb.r + off;
-    float* rh = mb.rhat + off;
+    const double* __restrict__ b = bvec + off;
+    const double* __restrict__ po = p_old + off;
+    double* __restrict__ pn = p_new + off;
+    const float* __restrict__ e = mb.x + off;
+    float* __restrict__ r = mb.r + off;
+    float* __restrict__ rh = mb.rhat + off;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     double a0 = 0.0, a1 = 0.0;
@@ -721,11 +811,11 @@ __global__ void __launch_bounds__(NTHREADS)
     if (!bad && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         auto pv = [&](int a, int bb, int cc) -> double {
-            const long long q = lindex(L, a, bb, cc);
+            const int q = lindex(L, a, bb, cc);
             return po[q] + double(e[q]);
         };
         for (int k = k0; k < k1; ++k) {
-            const long long id = lindex(L, i, j, k);
+            const int id = lindex(L, i, j, k);
             const double pc = pv(i, j, k);
             const double rv = b[id] - lap_lev(L, pv, i, j, k, pc);
             const float rf = float(rv);
