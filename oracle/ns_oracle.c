@@ -210,11 +210,78 @@ static double smart_flux(double Uf, double bb, double b, double f, double ff)
 /* predictor:  F* = u + dt (Re^-1 lap(u) - div(u u))                           */
 /* ------------------------------------------------------------------------- */
 
-/* Obstacle-aware stencil arms are not part of this oracle yet: the predictor
- * refuses grids with solid cells (the Poisson part supports them). */
+/* The adjoint does not take solid cells (the forward does). */
 static int solid_arms_unsupported(const og_grid *g)
 {
     return g->solid != NULL;
+}
+
+/* Is the stored face of component c at (i,j,k) (in range) inside a solid,
+ * i.e. are both cells next to it along axis c solid? */
+static int face_in_solid(const og_grid *g, int c, const int q[3])
+{
+    int n = ncell(g, c);
+    int lo[3] = {q[0], q[1], q[2]}, hi[3] = {q[0], q[1], q[2]};
+    lo[c] = q[c] - 1;
+    hi[c] = q[c];
+    if (g->bc[c] == OG_PERIODIC) {
+        lo[c] = wrap(lo[c], n);
+        hi[c] = wrap(hi[c], n);
+    } else if (lo[c] < 0 || hi[c] >= n) {
+        return 0; /* a wall face */
+    }
+    return is_solid(g, lo[0], lo[1], lo[2]) && is_solid(g, hi[0], hi[1], hi[2]);
+}
+
+/* Value of component c at offset m (|m| <= 2) from face f along axis d, as
+ * seen by f's stencil arm when the grid has solid cells: stored values up to
+ * the first interface the arm meets, reflected across it beyond.
+ *   normal arm (d == c): the first inactive face (a wall face or a face on a
+ *     solid surface, value 0) is the interface; beyond it the arm takes the
+ *     odd reflection about that face.
+ *   tangential arm (d != c): the first position past a wall or inside a solid
+ *     starts the ghost region; ghost = 2 u_wall - mirror (u_wall = 0 at
+ *     solids, the lid speed at the lid; +mirror at a slip wall).
+ * Without an interface within |m| positions the plain vget value is used. */
+static double arm_value(const og_grid *g, int c, const double *a, const int f[3], int d, int m)
+{
+    if (m == 0) return a[vidx(g, c, f[0], f[1], f[2])];
+    int sg = m > 0 ? 1 : -1;
+    int am = m > 0 ? m : -m;
+    for (int s = 1; s <= am; s++) {
+        int q[3] = {f[0], f[1], f[2]};
+        q[d] += sg * s;
+        int n = npos(g, c, d);
+        if (g->bc[d] == OG_PERIODIC) q[d] = wrap(q[d], n);
+        if (c == d) {
+            if (q[d] < 0 || q[d] >= n) break; /* cannot happen before a wall face */
+            if (!face_active(g, c, q[0], q[1], q[2])) {
+                if (s == am) return 0.0;
+                /* s < am: reflect the remaining offset about this face */
+                int r[3] = {f[0], f[1], f[2]};
+                r[d] += sg * (2 * s - am);
+                if (g->bc[d] == OG_PERIODIC) r[d] = wrap(r[d], n);
+                return -a[vidx(g, c, r[0], r[1], r[2])];
+            }
+        } else {
+            int outside = q[d] < 0 || q[d] >= n;
+            if (outside || face_in_solid(g, c, q)) {
+                /* interface between offsets s-1 and s; mirror of offset am
+                 * (offset -1 when s = 1 and am = 2: read through the wall rules) */
+                int r[3] = {f[0], f[1], f[2]};
+                r[d] += sg * (2 * s - 1 - am);
+                double mirror = vget(g, c, a, r[0], r[1], r[2]);
+                if (outside) {
+                    if (g->bc[d] == OG_SLIP) return mirror;
+                    return 2.0 * wall_speed(g, c, d, q[d] < 0 ? 0 : 1) - mirror;
+                }
+                return -mirror;
+            }
+        }
+    }
+    int q[3] = {f[0], f[1], f[2]};
+    q[d] += m;
+    return vget(g, c, a, q[0], q[1], q[2]);
 }
 
 /* conv and diff of component c at face (i,j,k) of state (u,v,w) */
@@ -227,9 +294,13 @@ static void rhs_terms(const og_grid *g, int c, const double *const vel[3],
         double h = hstep(g, d);
         double a[5];
         for (int m = -2; m <= 2; m++) {
-            int q[3] = {f[0], f[1], f[2]};
-            q[d] += m;
-            a[m + 2] = vget(g, c, vel[c], q[0], q[1], q[2]);
+            if (g->solid) {
+                a[m + 2] = arm_value(g, c, vel[c], f, d, m);
+            } else {
+                int q[3] = {f[0], f[1], f[2]};
+                q[d] += m;
+                a[m + 2] = vget(g, c, vel[c], q[0], q[1], q[2]);
+            }
         }
         double Up, Um;
         if (d == c) {
@@ -266,7 +337,6 @@ static void rhs_terms(const og_grid *g, int c, const double *const vel[3],
 int og_rhs(const og_grid *g, const double *u, const double *v, const double *w,
            double *cu, double *cv, double *cw, double *du, double *dv, double *dw)
 {
-    if (solid_arms_unsupported(g)) return OG_ERR_ARG;
     const double *vel[3] = {u, v, w};
     double *co[3] = {cu, cv, cw};
     double *di[3] = {du, dv, dw};
@@ -288,7 +358,6 @@ int og_rhs(const og_grid *g, const double *u, const double *v, const double *w,
 int og_predict(const og_grid *g, const double *u, const double *v, const double *w,
                double dt, double *fu, double *fv, double *fw)
 {
-    if (solid_arms_unsupported(g)) return OG_ERR_ARG;
     const double *vel[3] = {u, v, w};
     double *out[3] = {fu, fv, fw};
     double inv_re = g->re > 0.0 ? 1.0 / g->re : 0.0;
