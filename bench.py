@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preconditioner", choices=["multigrid", "none"], default="multigrid")
+    ap.add_argument("--inner-rtol", type=float, default=1e-4,
+                    help="FP32+refine: relative residual of each inner FP32 solve")
     ap.add_argument("--mode", choices=["bench", "kernels", "coarse"], default="bench",
                     help="kernels: only `steps` batched fine steps of the 32-slice sweep; "
                          "coarse: only the serial coarse chain (32 slices x 5 coarse steps, "
@@ -119,6 +121,13 @@ def max_over_ranks(x: float, pg, device=None) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ms_step_local: float, world: int, cell_steps_per_rank: int, pg, device=None):
+    """Whole-job throughput of N replicas: every rank's cell-steps over the
+    slowest rank's time per step (max over ranks).  Returns (value, ms_step)."""
+    ms_step = max_over_ranks(ms_step_local, pg, device)
+    return world * cell_steps_per_rank / (ms_step / 1e3), ms_step
 
 
 def barrier(pg, device=None):
@@ -306,7 +315,7 @@ def run_ours(args, world, rank, local, pg):
 
     init = initial_field_gpu(prec)
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, u_lid=1.0, precision=prec, batch=N_SLICES,
-             preconditioner=args.preconditioner)
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
     u0 = g.state_from(init)
     g.project(u0)
     slices = g.zeros(N_SLICES + 1)
@@ -341,9 +350,8 @@ def run_ours(args, world, rank, local, pg):
     g.profile(False)
     st = g.stats()
     launches = st["launches"] - launches0
-    ms_step = max_over_ranks(ms_total / args.steps, pg, dev)
     cell_steps = N_SLICES * FINE_STEPS * N_CELLS ** 3
-    value = world * cell_steps / (ms_step / 1e3)
+    value, ms_step = job_value(ms_total / args.steps, world, cell_steps, pg, dev)
 
     # ---- roofline of the dominant kernel (live CUDA-event timing) -------------
     esz = 4 if prec == "fp32_refine" else 8
@@ -447,7 +455,7 @@ def run_kernels_only(args):
     from paper_1705_06149_gb300 import Grid
     init = initial_field_gpu(args.precision)
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=N_SLICES,
-             preconditioner=args.preconditioner)
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
     st = g.state_from(init)
     g.project(st)
     batch = g.state_from([t.expand((N_SLICES,) + tuple(t.shape[1:])).cpu().numpy()
@@ -461,6 +469,7 @@ def run_kernels_only(args):
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     print(json.dumps({"mode": "kernels", "precision": args.precision,
+                      "inner_rtol": args.inner_rtol,
                       "preconditioner": args.preconditioner, "steps": args.steps,
                       "cell_steps_per_s": N_SLICES * args.steps * N_CELLS ** 3 / t,
                       "stats": g.stats()}), flush=True)
@@ -475,7 +484,7 @@ def run_coarse_only(args):
     from paper_1705_06149_gb300 import Grid
     init = initial_field_gpu(args.precision)
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=N_SLICES,
-             preconditioner=args.preconditioner)
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
     st = g.state_from(init)
     g.project(st)
     dtc = DT_FINE * FINE_STEPS / COARSE_STEPS

@@ -58,8 +58,11 @@ typedef struct {
     double u_lid;            /* speed of the lid y = ly along +x                     */
     int bc[3];               /* ns_bc per axis                                       */
     const uint8_t *solid_mask; /* host, nz*ny*nx, 1 = solid cell; NULL = none; copied.
-                                  Solid cells are supported by the pressure solve only
-                                  in this version: a non-NULL mask is rejected.      */
+                                  Obstacles by first-order cell decomposition
+                                  (Section 2): faces next to a solid hold zero, the
+                                  stencil arms reflect at solid surfaces like at a
+                                  no-slip wall, the pressure sees Neumann faces.
+                                  With solids the solver is plain BiCGStab.        */
     int precision;           /* ns_precision                                         */
     double poisson_rtol;     /* FP64: stop when ||b - L p||_2 <= rtol ||b||_2        */
     int poisson_maxit;       /* iteration limit per Krylov solve (<= 0: 20*max(n))   */

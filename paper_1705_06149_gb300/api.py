@@ -68,7 +68,8 @@ class Grid:
                  bc: Sequence[str] = ("wall", "wall", "wall"), precision: str = "fp64",
                  poisson_rtol: float = 1e-12, poisson_maxit: int = 0,
                  refine_rtol: float = 1e-10, inner_rtol: float = 1e-4, batch: int = 1,
-                 preconditioner: str = "multigrid", device: Optional[torch.device] = None):
+                 preconditioner: str = "multigrid", solid: Optional[np.ndarray] = None,
+                 device: Optional[torch.device] = None):
         self.lib = N.load()
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
@@ -83,7 +84,12 @@ class Grid:
         desc.re, desc.u_lid = re, u_lid
         for a in range(3):
             desc.bc[a] = _BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
-        desc.solid_mask = None
+        self._solid = None
+        if solid is not None:
+            self._solid = np.ascontiguousarray(np.asarray(solid, dtype=np.uint8).reshape(nz, ny, nx))
+            desc.solid_mask = self._solid.ctypes.data
+        else:
+            desc.solid_mask = None
         desc.precision = _PREC[precision]
         desc.poisson_rtol = poisson_rtol
         desc.poisson_maxit = poisson_maxit

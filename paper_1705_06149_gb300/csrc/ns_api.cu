@@ -152,9 +152,17 @@ void setup_geo(ns_grid* g) {
     G.cnt[3] = (long long)G.n[0] * G.n[1] * G.n[2];
     G.inv_re = 1.0 / d.re;
     G.u_lid = d.u_lid;
+    for (int a = 0; a < 3; ++a) {
+        G.fih[a] = (float)G.ih[a];
+        G.fih2[a] = (float)G.ih2[a];
+    }
+    G.finv_re = (float)G.inv_re;
     // cells per thread along z: fixed per grid (not per batch) so that every
-    // state is reduced over the same CTAs whatever the batch size
-    G.tz = std::min(8, G.n[2]);
+    // state is reduced over the same CTAs whatever the batch size; an even
+    // number so that the multigrid restriction pairs stay inside a CTA
+    const char* tz_env = std::getenv("NS_TZ");
+    const int tz_want = tz_env ? std::max(2, std::atoi(tz_env) & ~1) : 8;
+    G.tz = std::min(tz_want, G.n[2]);
     G.bx = ceil_div(G.n[0], TX);
     G.by = ceil_div(G.n[1], TY);
     G.bz = ceil_div(G.n[2], G.tz);
@@ -174,9 +182,10 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
     const Geo& G = g->geo;
     MgPlan& P = g->plan;
     P = MgPlan{};
-    auto fill = [](Lev& L) {
+    const int tz0 = G.tz;
+    auto fill = [tz0](Lev& L) {
         L.cells = (long long)L.n[0] * L.n[1] * L.n[2];
-        L.tz = std::min(8, L.n[2]);
+        L.tz = std::min(std::max(tz0, 2), L.n[2]);
         L.bx = ceil_div(L.n[0], TX);
         L.by = ceil_div(L.n[1], TY);
         L.bz = ceil_div(L.n[2], L.tz);
@@ -187,6 +196,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
         L0.n[a] = G.n[a];
         L0.bc[a] = G.bc[a];
         L0.ih2[a] = G.ih2[a];
+        L0.fih2[a] = (float)G.ih2[a];
     }
     fill(L0);
     P.lev[0] = L0;
@@ -201,6 +211,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
             C.n[a] = L.n[a] / 2;
             C.bc[a] = L.bc[a];
             C.ih2[a] = L.ih2[a] * 0.25;
+            C.fih2[a] = (float)C.ih2[a];
         }
         fill(C);
         P.lev[P.nlev++] = C;
@@ -607,6 +618,22 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in,
     return NS_OK;
 }
 
+template <typename T, bool INCR>
+void launch_predict(ns_grid* g, int batch, const T* u, const T* v, const T* w, T* fu, T* fv, T* fw,
+                    double dt) {
+    const Geo& G = g->geo;
+    if (G.solid) {
+        k_predict_masked<T, INCR><<<dim3(G.fctas, batch), block_dim(), 0, g->stream>>>(
+            G, u, v, w, fu, fv, fw, dt);
+        return;
+    }
+    const int tbx = ceil_div(G.n[0], PT_X), tby = ceil_div(G.n[1], PT_Y),
+              tbz = ceil_div(G.n[2], PT_Z);
+    const size_t smem = 3 * (size_t)PS_N * sizeof(T);
+    k_predict_tile<T, INCR><<<dim3(tbx * tby * tbz, batch), PT_THREADS, smem, g->stream>>>(
+        G, u, v, w, fu, fv, fw, dt, tbx, tby);
+}
+
 // FP64 states take F* = u + dt RHS as in Section 2.  FP32 states take the
 // increment form: the predictor stores dt RHS and the correction adds
 // (dt RHS - dt G p) to u, so that the small increment is not lost against u
@@ -633,9 +660,7 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
     g->prof.active = B >= g->prof.min_batch;
     const long long cells = G.cnt[3] * B;
     for (int n = 0; n < nsteps; ++n) {
-        NS_LAUNCH(g, NS_K_PREDICT, cells,
-                  k_predict<T, INCR><<<gface, block_dim(), 0, g->stream>>>(G, u, v, w, fu, fv,
-                                                                           fw, dt));
+        NS_LAUNCH(g, NS_K_PREDICT, cells, launch_predict<T, INCR>(g, B, u, v, w, fu, fv, fw, dt));
         const bool with_u = INCR && n == 0;
         NS_LAUNCH(g, NS_K_DIVERGENCE, cells,
                   k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(
@@ -961,9 +986,6 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     for (int a = 0; a < 3; ++a)
         if (d.bc[a] != NS_BC_WALL && d.bc[a] != NS_BC_PERIODIC && d.bc[a] != NS_BC_SLIP)
             return fail(NS_ERR_ARG, "ns_create_grid: unknown boundary condition");
-    if (d.solid_mask)
-        return fail(NS_ERR_ARG, "ns_create_grid: solid cells are not supported by the stepper "
-                                "in this version");
     if (d.precision != NS_FP64 && d.precision != NS_FP32_REFINE)
         return fail(NS_ERR_ARG, "ns_create_grid: unknown precision");
     if (!(d.poisson_rtol > 0) && d.precision == NS_FP64)
@@ -976,6 +998,15 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     if (!g) return fail(NS_ERR_OOM, "ns_create_grid: host allocation failed");
     g->d = d;
     g->d.solid_mask = nullptr;
+    int n_solid = 0;
+    if (d.solid_mask) {
+        const long long nc = (long long)d.nx * d.ny * d.nz;
+        for (long long q = 0; q < nc; ++q) n_solid += d.solid_mask[q] != 0;
+        if (n_solid == nc) {
+            delete g;
+            return fail(NS_ERR_ARG, "ns_create_grid: every cell is solid");
+        }
+    }
     g->stream = (cudaStream_t)cuda_stream;
     g->cap = d.batch;
     g->fp32 = d.precision == NS_FP32_REFINE;
@@ -1002,7 +1033,18 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     A((void**)&g->part_c, nparts * 4 * sizeof(double));
     A((void**)&g->part_r, nparts * 3 * sizeof(double));
     A((void**)&g->ctl, sizeof(SliceCtl) * B);
-    if (d.preconditioner == NS_PC_MULTIGRID) {
+    if (d.solid_mask && st == NS_OK) {
+        // obstacles: a device copy of the cell mask; the multigrid hierarchy
+        // has no coarse masks, so the solves use plain BiCGStab
+        void* m = nullptr;
+        A(&m, ncell);
+        if (st == NS_OK &&
+            cudaMemcpy(m, d.solid_mask, ncell, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "ns_create_grid: mask copy failed");
+        g->geo.solid = (const uint8_t*)m;
+        g->geo.n_fluid = (int)(ncell - n_solid);
+    }
+    if (d.preconditioner == NS_PC_MULTIGRID && !d.solid_mask) {
         // levels at or below this size run in one CTA per state; FP64 keeps
         // that CTA's share small (one SM's FP64 rate is low)
         const char* env = std::getenv("NS_MG_BLOCK_CELLS");
@@ -1038,6 +1080,16 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         if (st == NS_OK &&
             cudaMemsetAsync(g->ctl, 0, sizeof(SliceCtl) * B, g->stream) != cudaSuccess)
             st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        if (st == NS_OK) {
+            const int ps = 3 * PS_N * (int)sizeof(double);
+            if (cudaFuncSetAttribute(k_predict_tile<double, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ps) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(k_predict_tile<double, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ps) !=
+                    cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_create_grid: predictor shared memory attribute");
+        }
         if (st == NS_OK && g->mg) {
             if (cudaMemsetAsync(g->counter, 0, sizeof(unsigned int) * B, g->stream) !=
                 cudaSuccess)
@@ -1110,16 +1162,17 @@ ns_status ns_predict(ns_grid* grid, ns_state in, double dt, void* fu, void* fv, 
     const Geo& G = grid->geo;
     const dim3 gface(G.fctas, in.batch);
     grid->prof.active = in.batch >= grid->prof.min_batch;
+    (void)gface;
     if (grid->fp32)
         NS_LAUNCH(grid, NS_K_PREDICT, G.cnt[3] * in.batch,
-                  k_predict<float, false><<<gface, block_dim(), 0, grid->stream>>>(
-                      G, (const float*)in.u, (const float*)in.v, (const float*)in.w, (float*)fu,
-                      (float*)fv, (float*)fw, dt));
+                  (launch_predict<float, false>(grid, in.batch, (const float*)in.u,
+                                                (const float*)in.v, (const float*)in.w,
+                                                (float*)fu, (float*)fv, (float*)fw, dt)));
     else
         NS_LAUNCH(grid, NS_K_PREDICT, G.cnt[3] * in.batch,
-                  k_predict<double, false><<<gface, block_dim(), 0, grid->stream>>>(
-                      G, (const double*)in.u, (const double*)in.v, (const double*)in.w,
-                      (double*)fu, (double*)fv, (double*)fw, dt));
+                  (launch_predict<double, false>(grid, in.batch, (const double*)in.u,
+                                                 (const double*)in.v, (const double*)in.w,
+                                                 (double*)fu, (double*)fv, (double*)fw, dt)));
     NS_CUDA(cudaGetLastError());
     NS_TRY(sync_stream(grid));
     return NS_OK;
@@ -1197,6 +1250,8 @@ ns_status ns_adjoint(ns_grid* grid, ns_state u0, double dt, int nsteps, int ckpt
     if (!grid) return fail(NS_ERR_ARG, "ns_adjoint: null grid");
     NS_TRY(check_state(grid, u0, "ns_adjoint(u0)"));
     if (grid->fp32) return fail(NS_ERR_ARG, "ns_adjoint: needs an NS_FP64 grid");
+    if (grid->geo.solid) return fail(NS_ERR_ARG, "ns_adjoint: grids with solid cells are not "
+                                                 "supported");
     if (!grad_u0.u || !grad_u0.v || !grad_u0.w || grad_u0.batch != u0.batch)
         return fail(NS_ERR_ARG, "ns_adjoint: grad_u0 must hold u0.batch velocity fields");
     if (!J || !dJ_dulid) return fail(NS_ERR_ARG, "ns_adjoint: null J or dJ_dulid");

@@ -33,7 +33,20 @@ struct Geo {
     int bx, by, bz, ctas;      // cell kernels: CTA tiles per state
     int fbx, fby, fbz, fctas;  // face kernels: CTA tiles over (n+1) per axis
     int n_fluid;         // fluid cells per state
+    const uint8_t* solid;  // device cell mask (1 = solid), nullptr without obstacles
+    float fih[3], fih2[3], finv_re;  // FP32 copies (no FP64 conversions in FP32 kernels)
 };
+
+// h^-1, h^-2 and 1/Re in the kernel's precision
+template <typename T> __device__ __forceinline__ T g_ih(const Geo& g, int d);
+template <> __device__ __forceinline__ float g_ih<float>(const Geo& g, int d) { return g.fih[d]; }
+template <> __device__ __forceinline__ double g_ih<double>(const Geo& g, int d) { return g.ih[d]; }
+template <typename T> __device__ __forceinline__ T g_ih2(const Geo& g, int d);
+template <> __device__ __forceinline__ float g_ih2<float>(const Geo& g, int d) { return g.fih2[d]; }
+template <> __device__ __forceinline__ double g_ih2<double>(const Geo& g, int d) { return g.ih2[d]; }
+template <typename T> __device__ __forceinline__ T g_inv_re(const Geo& g);
+template <> __device__ __forceinline__ float g_inv_re<float>(const Geo& g) { return g.finv_re; }
+template <> __device__ __forceinline__ double g_inv_re<double>(const Geo& g) { return g.inv_re; }
 
 __device__ __forceinline__ int tid_flat() { return threadIdx.y * TX + threadIdx.x; }
 
@@ -123,33 +136,75 @@ __device__ __forceinline__ T smart_flux(T uf, T bb, T b, T f, T ff) {
     return T(0);
 }
 
+__device__ __forceinline__ bool cell_solid(const Geo& g, int i, int j, int k) {
+    return g.solid != nullptr && g.solid[cindex(g, i, j, k)] != 0;
+}
+
 // 7-point Laplacian at cell (i,j,k) of the field returned by val(i,j,k), with
 // the value at the cell already in vc.  Wall faces are dropped (homogeneous
 // Neumann); periodic axes wrap.  Terms are added axis by axis, the high face
 // before the low face.
+// With solid cells, a face next to a solid is dropped like a wall face and a
+// solid cell's own row is zero.
 template <typename T, typename F>
 __device__ __forceinline__ T lap_cell(const Geo& g, const F& val, int i, int j, int k, T vc) {
     T s = T(0);
     const int c[3] = {i, j, k};
+    if (g.solid != nullptr && cell_solid(g, i, j, k)) return s;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const int n = g.n[d];
-        const T w = T(g.ih2[d]);
+        const T w = g_ih2<T>(g, d);
         int hi[3] = {c[0], c[1], c[2]};
         int lo[3] = {c[0], c[1], c[2]};
+        bool has_hi, has_lo;
         if (g.bc[d] == BC_PERIODIC) {
             hi[d] = c[d] + 1 == n ? 0 : c[d] + 1;
             lo[d] = c[d] == 0 ? n - 1 : c[d] - 1;
-            s += (val(hi[0], hi[1], hi[2]) - vc) * w;
-            s -= (vc - val(lo[0], lo[1], lo[2])) * w;
+            has_hi = has_lo = true;
         } else {
             hi[d] = c[d] + 1;
             lo[d] = c[d] - 1;
-            if (hi[d] < n) s += (val(hi[0], hi[1], hi[2]) - vc) * w;
-            if (lo[d] >= 0) s -= (vc - val(lo[0], lo[1], lo[2])) * w;
+            has_hi = hi[d] < n;
+            has_lo = lo[d] >= 0;
         }
+        if (g.solid != nullptr) {
+            has_hi = has_hi && !cell_solid(g, hi[0], hi[1], hi[2]);
+            has_lo = has_lo && !cell_solid(g, lo[0], lo[1], lo[2]);
+        }
+        if (has_hi) s += (val(hi[0], hi[1], hi[2]) - vc) * w;
+        if (has_lo) s -= (vc - val(lo[0], lo[1], lo[2])) * w;
     }
     return s;
+}
+
+// Is the stored face of component c at f a face that moves fluid: not a
+// wall-normal boundary face and, with solids, both neighbouring cells fluid.
+__device__ __forceinline__ bool face_active_dev(const Geo& g, int c, const int f[3]) {
+    const int n = g.n[c];
+    if (g.bc[c] != BC_PERIODIC && (f[c] == 0 || f[c] == n)) return false;
+    if (g.solid == nullptr) return true;
+    int lo[3] = {f[0], f[1], f[2]};
+    lo[c] = f[c] == 0 ? n - 1 : f[c] - 1;  // periodic wrap (walls have f[c] >= 1 here)
+    int hi[3] = {f[0], f[1], f[2]};
+    hi[c] = f[c] == n ? 0 : f[c];
+    return !cell_solid(g, lo[0], lo[1], lo[2]) && !cell_solid(g, hi[0], hi[1], hi[2]);
+}
+
+// Is the stored face of component c at q (in range) inside a solid: both
+// neighbouring cells along c solid (a wall face is not).
+__device__ __forceinline__ bool face_in_solid_dev(const Geo& g, int c, const int q[3]) {
+    const int n = g.n[c];
+    int lo[3] = {q[0], q[1], q[2]}, hi[3] = {q[0], q[1], q[2]};
+    if (g.bc[c] == BC_PERIODIC) {
+        lo[c] = q[c] == 0 ? n - 1 : q[c] - 1;
+        hi[c] = q[c] == n ? 0 : q[c];
+    } else {
+        if (q[c] == 0 || q[c] == n) return false;
+        lo[c] = q[c] - 1;
+        hi[c] = q[c];
+    }
+    return cell_solid(g, lo[0], lo[1], lo[2]) && cell_solid(g, hi[0], hi[1], hi[2]);
 }
 
 // Sum of NV per-thread values over the CTA; the result is valid in thread 0.

@@ -51,95 +51,206 @@ struct KBuf {       // Krylov vectors of all states, [batch][cells]
 // predictor  F* = u + dt (Re^-1 lap u - div(u u))
 // ---------------------------------------------------------------------------
 
-// INCR: write the increment dt (Re^-1 lap u - div(u u)) instead of F*.
+// Tiled predictor: a CTA of PT_X x PT_Y x PT_Z cells stages u, v, w on its
+// tile and a halo of two positions (ghost values applied while staging), then
+// evaluates every face of the tile from shared memory with constant strides.
+// Faces owned by the tile: the low face of each of its cells along each
+// component's axis, plus the high wall face of the last cell of the domain.
+constexpr int PT_X = 32, PT_Y = 8, PT_Z = 4;
+constexpr int PT_THREADS = 256;
+constexpr int PH = 2;  // halo
+constexpr int PS_X = PT_X + 2 * PH, PS_Y = PT_Y + 2 * PH, PS_Z = PT_Z + 2 * PH;
+constexpr int PS_N = PS_X * PS_Y * PS_Z;
+
 template <typename T, bool INCR>
-__device__ __forceinline__ void predict_face(const Geo& g, int c, const T* const* vel3, T* out,
-                                             int i, int j, int k, T dt) {
-    const long long id = vindex(g, c, i, j, k);
-    const int f[3] = {i, j, k};
-    const bool active = g.bc[c] == BC_PERIODIC || (f[c] > 0 && f[c] < g.n[c]);
-    if (!active) {
-        out[id] = T(0);
-        return;
-    }
-    // faces two or more positions away from every end of every axis read
-    // their stencil with plain strides; the others go through the ghost rules
-    bool interior = true;
+__global__ void __launch_bounds__(PT_THREADS)
+    k_predict_tile(Geo g, const T* __restrict__ u, const T* __restrict__ v,
+                   const T* __restrict__ w, T* __restrict__ fu, T* __restrict__ fv,
+                   T* __restrict__ fw, double dt, int tbx, int tby) {
+    extern __shared__ __align__(16) unsigned char psm_raw[];
+    T* sm = reinterpret_cast<T*>(psm_raw);  // [3][PS_Z][PS_Y][PS_X]
+    const long long s = blockIdx.y;
+    const T* vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
+    T* out[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
+    const int cta = blockIdx.x;
+    const int i0 = (cta % tbx) * PT_X;
+    const int j0 = ((cta / tbx) % tby) * PT_Y;
+    const int k0 = (cta / (tbx * tby)) * PT_Z;
+    const int t = threadIdx.x;
+    // stage: positions (i0-2 .. i0+PT_X+1) etc. of every component
+    const bool inner = i0 >= PH && j0 >= PH && k0 >= PH && i0 + PT_X + PH <= g.n[0] &&
+                       j0 + PT_Y + PH <= g.n[1] && k0 + PT_Z + PH <= g.n[2];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) interior = interior && f[e] >= 2 && f[e] + 3 <= g.ext[c][e];
-    T conv = T(0), diff = T(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        T a[5];
-        if (interior) {
-            const long long st = d == 0 ? 1 : (d == 1 ? g.ext[c][0]
-                                                      : (long long)g.ext[c][0] * g.ext[c][1]);
-#pragma unroll
-            for (int m = 0; m < 5; ++m) a[m] = vel3[c][id + (m - 2) * st];
-        } else {
-#pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                int q[3] = {f[0], f[1], f[2]};
-                q[d] += m - 2;
-                a[m] = vel(g, c, vel3[c], q[0], q[1], q[2]);
-            }
-        }
-        T up, um;
-        if (d == c) {
-            // fluxes at the cell centres on either side of the face
-            up = T(0.5) * (a[2] + a[3]);
-            um = T(0.5) * (a[1] + a[2]);
-        } else {
-            // fluxes at the cell edges: component d averaged over the two
-            // positions of this face along axis c
-            int q0[3] = {f[0], f[1], f[2]};
-            int q1[3] = {f[0], f[1], f[2]};
-            q0[c] = f[c] - 1;
-            q0[d] = f[d] + 1;
-            q1[d] = f[d] + 1;
-            if (interior) {
-                // in range: f[c] >= 2 and f[d] + 1 < ext[d][d] for an interior face
-                const T* vd = vel3[d];
-                up = T(0.5) * (vd[vindex(g, d, q0[0], q0[1], q0[2])] +
-                               vd[vindex(g, d, q1[0], q1[1], q1[2])]);
-                q0[d] = f[d];
-                q1[d] = f[d];
-                um = T(0.5) * (vd[vindex(g, d, q0[0], q0[1], q0[2])] +
-                               vd[vindex(g, d, q1[0], q1[1], q1[2])]);
+    for (int c = 0; c < 3; ++c) {
+        for (int r = t; r < PS_N; r += PT_THREADS) {
+            const int x = r % PS_X, y = (r / PS_X) % PS_Y, z = r / (PS_X * PS_Y);
+            const int gi = i0 - PH + x, gj = j0 - PH + y, gk = k0 - PH + z;
+            T val;
+            if (inner) {
+                val = vel3[c][vindex(g, c, gi, gj, gk)];
             } else {
-                up = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
-                               vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
-                q0[d] = f[d];
-                q1[d] = f[d];
-                um = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
-                               vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+                // only positions up to two beyond the domain are ever read
+                const bool near = gi >= -PH && gj >= -PH && gk >= -PH &&
+                                  gi < g.ext[c][0] + PH && gj < g.ext[c][1] + PH &&
+                                  gk < g.ext[c][2] + PH;
+                val = near ? vel(g, c, vel3[c], gi, gj, gk) : T(0);
             }
+            sm[c * PS_N + r] = val;
         }
-        const T fp = smart_flux(up, a[1], a[2], a[3], a[4]);
-        const T fm = smart_flux(um, a[0], a[1], a[2], a[3]);
-        conv += (fp - fm) * T(g.ih[d]);
-        diff += (a[3] - T(2) * a[2] + a[1]) * T(g.ih2[d]);
     }
-    const T incr = dt * (T(g.inv_re) * diff - conv);
-    out[id] = INCR ? incr : vel3[c][id] + incr;
+    __syncthreads();
+    const T tdt = T(dt), inv_re = g_inv_re<T>(g);
+    constexpr int strd[3] = {1, PS_X, PS_X * PS_Y};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+    for (int r = t; r < PT_X * PT_Y * PT_Z; r += PT_THREADS) {
+        const int x = r % PT_X, y = (r / PT_X) % PT_Y, z = r / (PT_X * PT_Y);
+        const int f[3] = {i0 + x, j0 + y, k0 + z};
+        if (f[0] >= g.n[0] || f[1] >= g.n[1] || f[2] >= g.n[2]) continue;
+        const long long id = vindex(g, c, f[0], f[1], f[2]);
+        // the high wall face of the last cell along c is inactive: zero it
+        if (g.bc[c] != BC_PERIODIC && f[c] == g.n[c] - 1) {
+            int h3[3] = {f[0], f[1], f[2]};
+            h3[c] += 1;
+            out[c][vindex(g, c, h3[0], h3[1], h3[2])] = T(0);
+        }
+        const bool active = g.bc[c] == BC_PERIODIC || f[c] > 0;
+        if (!active) {
+            out[c][id] = T(0);
+            continue;
+        }
+        const T* sc = sm + c * PS_N;
+        const int o = ((z + PH) * PS_Y + (y + PH)) * PS_X + (x + PH);
+        T conv = T(0), diff = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int sd = strd[d];
+            const T a0 = sc[o - 2 * sd], a1 = sc[o - sd], a2 = sc[o], a3 = sc[o + sd],
+                    a4 = sc[o + 2 * sd];
+            T up, um;
+            if (d == c) {
+                up = T(0.5) * (a2 + a3);
+                um = T(0.5) * (a1 + a2);
+            } else {
+                // component d at (c-index f_c - 1 and f_c) x (d-index f_d + 1 and f_d)
+                const T* sdc = sm + d * PS_N;
+                const int sc_c = strd[c];
+                up = T(0.5) * (sdc[o - sc_c + sd] + sdc[o + sd]);
+                um = T(0.5) * (sdc[o - sc_c] + sdc[o]);
+            }
+            const T fp = smart_flux(up, a1, a2, a3, a4);
+            const T fm = smart_flux(um, a0, a1, a2, a3);
+            conv += (fp - fm) * g_ih<T>(g, d);
+            diff += (a3 - T(2) * a2 + a1) * g_ih2<T>(g, d);
+        }
+        const T incr = tdt * (inv_re * diff - conv);
+        out[c][id] = INCR ? incr : sc[o] + incr;
+    }
 }
 
-// F* (INCR = false) or its increment F* - u (INCR = true) on every face.
+// ---------------------------------------------------------------------------
+// predictor with solid cells: one thread per face, stencil arms that stop at
+// walls and solid surfaces
+// ---------------------------------------------------------------------------
+
+// Value of component c at offset m (|m| <= 2) from face f along axis d, as f's
+// stencil arm sees it: stored values up to the first interface (an inactive
+// face for the normal arm; a position past a wall or inside a solid for a
+// tangential arm), reflected across it beyond -- odd about the interface face
+// (normal), 2 u_wall - mirror (tangential; u_wall = 0 at solids, +mirror at a
+// slip wall).
+template <typename T>
+__device__ __forceinline__ T arm_value_dev(const Geo& g, int c, const T* a, const int f[3], int d,
+                                           int m) {
+    if (m == 0) return a[vindex(g, c, f[0], f[1], f[2])];
+    const int sg = m > 0 ? 1 : -1;
+    const int am = m > 0 ? m : -m;
+    const int n = g.ext[c][d];
+    for (int s = 1; s <= am; ++s) {
+        int q[3] = {f[0], f[1], f[2]};
+        q[d] += sg * s;
+        if (g.bc[d] == BC_PERIODIC) q[d] = q[d] < 0 ? q[d] + n : (q[d] >= n ? q[d] - n : q[d]);
+        if (c == d) {
+            if (q[d] < 0 || q[d] >= n) break;
+            if (!face_active_dev(g, c, q)) {
+                if (s == am) return T(0);
+                int r[3] = {f[0], f[1], f[2]};
+                r[d] += sg * (2 * s - am);
+                return -vel(g, c, a, r[0], r[1], r[2]);
+            }
+        } else {
+            const bool outside = q[d] < 0 || q[d] >= n;
+            if (outside || face_in_solid_dev(g, c, q)) {
+                int r[3] = {f[0], f[1], f[2]};
+                r[d] += sg * (2 * s - 1 - am);
+                const T mirror = vel(g, c, a, r[0], r[1], r[2]);
+                if (outside) {
+                    if (g.bc[d] == BC_SLIP) return mirror;
+                    const bool hi = q[d] >= n;
+                    const T uw = (c == 0 && d == 1 && hi) ? T(g.u_lid) : T(0);
+                    return T(2) * uw - mirror;
+                }
+                return -mirror;
+            }
+        }
+    }
+    int q[3] = {f[0], f[1], f[2]};
+    q[d] += m;
+    return vel(g, c, a, q[0], q[1], q[2]);
+}
+
 template <typename T, bool INCR>
 __global__ void __launch_bounds__(NTHREADS)
-    k_predict(Geo g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
-              T* __restrict__ fu, T* __restrict__ fv, T* __restrict__ fw, double dt) {
+    k_predict_masked(Geo g, const T* __restrict__ u, const T* __restrict__ v,
+                     const T* __restrict__ w, T* __restrict__ fu, T* __restrict__ fv,
+                     T* __restrict__ fw, double dt) {
     const long long s = blockIdx.y;
     const T* vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
     T* out[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
     int i, j, k0;
     tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
     const int k1 = min(k0 + g.tz, g.n[2] + 1);
+    const T tdt = T(dt);
     for (int k = k0; k < k1; ++k) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            if (i < g.ext[c][0] && j < g.ext[c][1] && k < g.ext[c][2])
-                predict_face<T, INCR>(g, c, vel3, out[c], i, j, k, T(dt));
+            if (!(i < g.ext[c][0] && j < g.ext[c][1] && k < g.ext[c][2])) continue;
+            const int f[3] = {i, j, k};
+            const long long id = vindex(g, c, i, j, k);
+            if (!face_active_dev(g, c, f)) {
+                out[c][id] = T(0);
+                continue;
+            }
+            T conv = T(0), diff = T(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                T a[5];
+#pragma unroll
+                for (int m = 0; m < 5; ++m) a[m] = arm_value_dev(g, c, vel3[c], f, d, m - 2);
+                T up, um;
+                if (d == c) {
+                    up = T(0.5) * (a[2] + a[3]);
+                    um = T(0.5) * (a[1] + a[2]);
+                } else {
+                    int q0[3] = {f[0], f[1], f[2]};
+                    int q1[3] = {f[0], f[1], f[2]};
+                    q0[c] = f[c] - 1;
+                    q0[d] = f[d] + 1;
+                    q1[d] = f[d] + 1;
+                    up = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                                   vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+                    q0[d] = f[d];
+                    q1[d] = f[d];
+                    um = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                                   vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+                }
+                const T fp = smart_flux(up, a[1], a[2], a[3], a[4]);
+                const T fm = smart_flux(um, a[0], a[1], a[2], a[3]);
+                conv += (fp - fm) * g_ih<T>(g, d);
+                diff += (a[3] - T(2) * a[2] + a[1]) * g_ih2<T>(g, d);
+            }
+            const T incr = tdt * (g_inv_re<T>(g) * diff - conv);
+            out[c][id] = INCR ? incr : vel3[c][id] + incr;
         }
     }
 }
@@ -180,9 +291,9 @@ __global__ void __launch_bounds__(NTHREADS)
             // D of the stored F* (or increment) in the storage precision; in
             // FP32 this is the increment, whose differences carry no
             // cancellation against u
-            T dt_ = (fu[vindex(g, 0, ip, j, k)] - fu[vindex(g, 0, i, j, k)]) * T(g.ih[0]);
-            dt_ += (fv[vindex(g, 1, i, jp, k)] - fv[vindex(g, 1, i, j, k)]) * T(g.ih[1]);
-            dt_ += (fw[vindex(g, 2, i, j, kp)] - fw[vindex(g, 2, i, j, k)]) * T(g.ih[2]);
+            T dt_ = (fu[vindex(g, 0, ip, j, k)] - fu[vindex(g, 0, i, j, k)]) * g_ih<T>(g, 0);
+            dt_ += (fv[vindex(g, 1, i, jp, k)] - fv[vindex(g, 1, i, j, k)]) * g_ih<T>(g, 1);
+            dt_ += (fw[vindex(g, 2, i, j, kp)] - fw[vindex(g, 2, i, j, k)]) * g_ih<T>(g, 2);
             double dv = double(dt_);
             if (with_u) {
                 // the stored u itself: differences taken exactly in FP64
@@ -194,7 +305,7 @@ __global__ void __launch_bounds__(NTHREADS)
                       g.ih[2];
                 dv += du;
             }
-            const double bv = dv * inv_dt;
+            const double bv = cell_solid(g, i, j, k) ? 0.0 : dv * inv_dt;
             b[cindex(g, i, j, k)] = bv;
             acc[0] += bv;
         }
@@ -246,8 +357,9 @@ __global__ void __launch_bounds__(NTHREADS)
         auto xv = [&](int a, int bb, int c) { return xs[cindex(g, a, bb, c)]; };
         for (int k = k0; k < k1; ++k) {
             const long long id = cindex(g, i, j, k);
-            const T bv = b[id] - mean;
-            const T xc = xs[id];
+            const bool sol = cell_solid(g, i, j, k);
+            const T bv = sol ? T(0) : b[id] - mean;
+            const T xc = sol ? T(0) : xs[id];
             const T rv = bv - lap_cell(g, xv, i, j, k, xc);
             b[id] = bv;
             x[id] = xc;
@@ -472,8 +584,9 @@ static __global__ void __launch_bounds__(NTHREADS)
         auto pv = [&](int a, int bb, int c) { return ps[cindex(g, a, bb, c)]; };
         for (int k = k0; k < k1; ++k) {
             const long long id = cindex(g, i, j, k);
-            const double bv = b[id] - mean;
-            const double pc = ps[id];
+            const bool sol = cell_solid(g, i, j, k);
+            const double bv = sol ? 0.0 : b[id] - mean;
+            const double pc = sol ? 0.0 : ps[id];
             const double rv = bv - lap_cell(g, pv, i, j, k, pc);
             b[id] = bv;
             pd[id] = pc;
@@ -639,7 +752,7 @@ __global__ void __launch_bounds__(NTHREADS)
         for (int d = 0; d < 3; ++d) {
             if (i < g.ext[d][0] && j < g.ext[d][1] && k < g.ext[d][2]) {
                 const long long id = vindex(g, d, i, j, k);
-                const bool active = g.bc[d] == BC_PERIODIC || (q[d] > 0 && q[d] < g.n[d]);
+                const bool active = face_active_dev(g, d, q);
                 if (!active) {
                     o3[d][id] = T(0);
                 } else {
@@ -660,7 +773,7 @@ __global__ void __launch_bounds__(NTHREADS)
             const long long id = cindex(g, i, j, k);
             // p_keep (optional) receives the pressure being replaced
             if (p_keep) p_keep[s * g.cnt[3] + id] = p_out[s * g.cnt[3] + id];
-            p_out[s * g.cnt[3] + id] = x[id] - mean;
+            p_out[s * g.cnt[3] + id] = cell_solid(g, i, j, k) ? 0.0 : x[id] - mean;
         }
     }
 }

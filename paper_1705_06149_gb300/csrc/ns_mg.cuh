@@ -24,16 +24,89 @@ namespace nsk {
 
 constexpr int MG_MAX_LEVELS = 14;
 constexpr double MG_OMEGA = 6.0 / 7.0;
-constexpr int MG_BLOCK_THREADS = 512;
+constexpr int MG_BLOCK_THREADS = 1024;
 constexpr int MG_COARSEST_SWEEPS = 32;
 
 struct Lev {
     int n[3];
     int bc[3];
     double ih2[3];
+    float fih2[3];  // FP32 copy
     long long cells;
     int tz, bx, by, bz, ctas;
 };
+
+template <typename T> __device__ __forceinline__ T lw(const Lev& L, int d);
+template <> __device__ __forceinline__ float lw<float>(const Lev& L, int d) { return L.fih2[d]; }
+template <> __device__ __forceinline__ double lw<double>(const Lev& L, int d) { return L.ih2[d]; }
+
+// Neighbours of cell (i,j,k) along each axis as linear indices: clamped to the
+// cell itself across a wall, wrapped across a periodic seam.  With a clamped
+// neighbour the face term v[nb] - v[c] of the Laplacian is exactly zero, so
+//   L v = sum_d w_d (v[hi_d] + v[lo_d] - 2 v[c])
+// is the Neumann Laplacian for every cell, without branches.
+struct Nbr {
+    int c;
+    int lo[3], hi[3];
+    int act[3];  // active faces per axis (0, 1 or 2)
+};
+
+__device__ __forceinline__ void axis_nbr(int x, int n, int bc, int& lo, int& hi, int& act) {
+    if (bc == BC_PERIODIC) {
+        lo = x == 0 ? n - 1 : x - 1;
+        hi = x + 1 == n ? 0 : x + 1;
+        act = 2;
+    } else {
+        lo = x > 0 ? x - 1 : x;
+        hi = x + 1 < n ? x + 1 : x;
+        act = (x > 0) + (x + 1 < n);
+    }
+}
+
+__device__ __forceinline__ Nbr make_nbr(const Lev& L, int i, int j, int k) {
+    Nbr b;
+    int lo, hi, act;
+    const int sy = L.n[0], sz = L.n[0] * L.n[1];
+    b.c = k * sz + j * sy + i;
+    axis_nbr(i, L.n[0], L.bc[0], lo, hi, act);
+    b.lo[0] = b.c - i + lo;
+    b.hi[0] = b.c - i + hi;
+    b.act[0] = act;
+    axis_nbr(j, L.n[1], L.bc[1], lo, hi, act);
+    b.lo[1] = b.c + (lo - j) * sy;
+    b.hi[1] = b.c + (hi - j) * sy;
+    b.act[1] = act;
+    axis_nbr(k, L.n[2], L.bc[2], lo, hi, act);
+    b.lo[2] = b.c + (lo - k) * sz;
+    b.hi[2] = b.c + (hi - k) * sz;
+    b.act[2] = act;
+    return b;
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ T lap_nbr(const Lev& L, const Nbr& b, const F& val, T vc) {
+    const T two = T(2);
+    return (val(b.hi[0]) + val(b.lo[0]) - two * vc) * lw<T>(L, 0) +
+           (val(b.hi[1]) + val(b.lo[1]) - two * vc) * lw<T>(L, 1) +
+           (val(b.hi[2]) + val(b.lo[2]) - two * vc) * lw<T>(L, 2);
+}
+
+// -w / d in the preconditioner (deterministic; the V-cycle only has to be a
+// fixed linear operator, so FP32 uses the fast division)
+template <typename T> __device__ __forceinline__ T neg_over(T a, T d);
+template <> __device__ __forceinline__ float neg_over<float>(float a, float d) {
+    return -__fdividef(a, d);
+}
+template <> __device__ __forceinline__ double neg_over<double>(double a, double d) {
+    return -a / d;
+}
+
+// Jacobi diagonal of the Neumann Laplacian at a cell: -sum_d w_d act_d.
+template <typename T>
+__device__ __forceinline__ T diag_axis(const Lev& L, int d, int x) {
+    const int act = L.bc[d] == BC_PERIODIC ? 2 : (x > 0) + (x + 1 < L.n[d]);
+    return T(act) * lw<T>(L, d);
+}
 
 struct MgPlan {
     int nlev;                 // levels in the hierarchy (grid + block)
@@ -63,13 +136,13 @@ __device__ __forceinline__ int lindex(const Lev& L, int i, int j, int k) {
 }
 
 // Jacobi diagonal of L at (i,j,k): minus the sum of the active-face weights.
-template <typename T, typename GEO>
-__device__ __forceinline__ T diag_at(const GEO& L, int i, int j, int k) {
+template <typename T>
+__device__ __forceinline__ T diag_at(const Lev& L, int i, int j, int k) {
     const int c[3] = {i, j, k};
     T d = T(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const T w = T(L.ih2[a]);
+        const T w = lw<T>(L, a);
         if (L.bc[a] == BC_PERIODIC) {
             d -= T(2) * w;
         } else {
@@ -88,7 +161,7 @@ __device__ __forceinline__ T lap_lev(const Lev& L, const F& val, int i, int j, i
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const int n = L.n[d];
-        const T w = T(L.ih2[d]);
+        const T w = lw<T>(L, d);
         int hi[3] = {c[0], c[1], c[2]};
         int lo[3] = {c[0], c[1], c[2]};
         if (L.bc[d] == BC_PERIODIC) {
@@ -104,21 +177,6 @@ __device__ __forceinline__ T lap_lev(const Lev& L, const F& val, int i, int j, i
         }
     }
     return s;
-}
-
-// Laplacian at a cell with all six neighbours inside the level (no wall face,
-// no periodic seam), from a value accessor taking the linear index.
-template <typename T, typename F>
-__device__ __forceinline__ T lap_interior(const Lev& L, const F& val, int id, T vc) {
-    const int sy = L.n[0], sz = L.n[0] * L.n[1];
-    const T two = T(2);
-    return (val(id + 1) + val(id - 1) - two * vc) * T(L.ih2[0]) +
-           (val(id + sy) + val(id - sy) - two * vc) * T(L.ih2[1]) +
-           (val(id + sz) + val(id - sz) - two * vc) * T(L.ih2[2]);
-}
-
-__device__ __forceinline__ bool inside(const Lev& L, int i, int j, int k, int m) {
-    return i >= m && j >= m && k >= m && i + m < L.n[0] && j + m < L.n[1] && k + m < L.n[2];
 }
 
 __device__ __forceinline__ void lev_origin(const Lev& L, int cta, int& i, int& j, int& k0) {
@@ -259,36 +317,42 @@ __global__ void __launch_bounds__(NTHREADS)
         if (MODE == SRC_S) return r[q] - ta * vn[q];
         return ba[q];
     };
-    auto src = [&](int a, int b, int cc) -> T { return srcq(lindex(L, a, b, cc)); };
-    // Jacobi diagonal of a cell with all faces active, and its reciprocal
-    const T d_in = -T(2) * (T(L.ih2[0]) + T(L.ih2[1]) + T(L.ih2[2]));
-    const T wd = T(MG_OMEGA) / d_in;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     if (i >= L.n[0] || j >= L.n[1]) return;
     const int k1 = min(k0 + L.tz, L.n[2]);
     const T w = T(MG_OMEGA);
+    // separable diagonal: x and y parts of this thread's cell and neighbours
+    int il, ih_, jl, jh, act;
+    axis_nbr(i, L.n[0], L.bc[0], il, ih_, act);
+    axis_nbr(j, L.n[1], L.bc[1], jl, jh, act);
+    const T dxc = diag_axis<T>(L, 0, i), dxl = diag_axis<T>(L, 0, il), dxh = diag_axis<T>(L, 0, ih_);
+    const T dyc = diag_axis<T>(L, 1, j), dyl = diag_axis<T>(L, 1, jl), dyh = diag_axis<T>(L, 1, jh);
     for (int k = k0; k < k1; ++k) {
-        const int id = lindex(L, i, j, k);
-        const T bc = src(i, j, k);
+        const Nbr nb = make_nbr(L, i, j, k);
+        const int id = nb.c;
+        const T bc = srcq(id);
         if (MODE == SRC_P) {
             pn[id] = bc;
             if (restart && !first) rh[id] = r[id];
         }
         if (MODE == SRC_S) sv[id] = bc;
         if (PRE) {
-            if (inside(L, i, j, k, 2)) {
-                // every neighbour has the interior diagonal: L y0 = (w/d) L b
-                const T lb = lap_interior(L, srcq, id, bc);
-                y[id] = wd * bc + wd * (bc - wd * lb);
-            } else {
-                auto y0 = [&](int a, int b, int cc) -> T {
-                    return w * src(a, b, cc) / diag_at<T>(L, a, b, cc);
-                };
-                const T yc = y0(i, j, k);
-                const T d = diag_at<T>(L, i, j, k);
-                y[id] = yc + w * (bc - lap_lev(L, y0, i, j, k, yc)) / d;
-            }
+            int kl, kh;
+            axis_nbr(k, L.n[2], L.bc[2], kl, kh, act);
+            const T dzc = diag_axis<T>(L, 2, k), dzl = diag_axis<T>(L, 2, kl),
+                    dzh = diag_axis<T>(L, 2, kh);
+            // y0 = w b / d at the cell and its neighbours (d = -(dx + dy + dz))
+            const T ic = neg_over<T>(w, dxc + dyc + dzc);
+            const T y0c = ic * bc;
+            const T lap =
+                (neg_over<T>(w, dxh + dyc + dzc) * srcq(nb.hi[0]) +
+                 neg_over<T>(w, dxl + dyc + dzc) * srcq(nb.lo[0]) - T(2) * y0c) * lw<T>(L, 0) +
+                (neg_over<T>(w, dxc + dyh + dzc) * srcq(nb.hi[1]) +
+                 neg_over<T>(w, dxc + dyl + dzc) * srcq(nb.lo[1]) - T(2) * y0c) * lw<T>(L, 1) +
+                (neg_over<T>(w, dxc + dyc + dzh) * srcq(nb.hi[2]) +
+                 neg_over<T>(w, dxc + dyc + dzl) * srcq(nb.lo[2]) - T(2) * y0c) * lw<T>(L, 2);
+            y[id] = y0c + ic * (bc - lap);
         }
     }
 }
@@ -308,16 +372,13 @@ __global__ void __launch_bounds__(NTHREADS)
     lev_origin(L, blockIdx.x, i, j, k0);
     const bool in = i < L.n[0] && j < L.n[1];
     const int k1 = min(k0 + L.tz, L.n[2]);
-    auto yv = [&](int a, int bb, int cc) -> T { return y[lindex(L, a, bb, cc)]; };
     auto yq = [&](int q) -> T { return y[q]; };
     T accz = T(0);
     for (int k = k0; k < k1; ++k) {
         T res = T(0);
         if (in) {
-            const int id = lindex(L, i, j, k);
-            const T yc = y[id];
-            res = b[id] - (inside(L, i, j, k, 1) ? lap_interior(L, yq, id, yc)
-                                                 : lap_lev(L, yv, i, j, k, yc));
+            const Nbr nb = make_nbr(L, i, j, k);
+            res = b[nb.c] - lap_nbr(L, nb, yq, y[nb.c]);
         }
         res += __shfl_xor_sync(0xffffffffu, res, 1);  // x pair
         if ((threadIdx.x & 1) == 0) row[threadIdx.y][threadIdx.x >> 1] = res;
@@ -524,13 +585,11 @@ __global__ void __launch_bounds__(NTHREADS)
     T acc_t = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto yv = [&](int a, int b, int cc) -> T { return y[lindex(L, a, b, cc)]; };
         auto yq = [&](int q) -> T { return y[q]; };
         for (int k = k0; k < k1; ++k) {
-            const int id = lindex(L, i, j, k);
-            const T yc = y[id];
-            const T lv = inside(L, i, j, k, 1) ? lap_interior(L, yq, id, yc)
-                                               : lap_lev(L, yv, i, j, k, yc);
+            const Nbr nb = make_nbr(L, i, j, k);
+            const int id = nb.c;
+            const T lv = lap_nbr(L, nb, yq, y[id]);
             v[id] = lv;
             acc_t += rh[id] * lv;
         }
@@ -558,13 +617,11 @@ __global__ void __launch_bounds__(NTHREADS)
     T ts = T(0), tt = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto zv = [&](int a, int b, int cc) -> T { return z[lindex(L, a, b, cc)]; };
         auto zq = [&](int q) -> T { return z[q]; };
         for (int k = k0; k < k1; ++k) {
-            const int id = lindex(L, i, j, k);
-            const T zc = z[id];
-            const T tv = inside(L, i, j, k, 1) ? lap_interior(L, zq, id, zc)
-                                               : lap_lev(L, zv, i, j, k, zc);
+            const Nbr nb = make_nbr(L, i, j, k);
+            const int id = nb.c;
+            const T tv = lap_nbr(L, nb, zq, z[id]);
             t[id] = tv;
             ts += tv * sv[id];
             tt += tv * tv;
@@ -680,12 +737,12 @@ __global__ void __launch_bounds__(NTHREADS)
         const int k1 = min(k0 + L.tz, L.n[2]);
         // warm start: x0, or 2 x0 - xprev (linear extrapolation in time)
         auto xq = [&](int q) -> T { return xp ? T(2) * xs[q] - xp[q] : xs[q]; };
-        auto xv = [&](int a, int bb, int cc) -> T { return xq(lindex(L, a, bb, cc)); };
         for (int k = k0; k < k1; ++k) {
-            const int id = lindex(L, i, j, k);
+            const Nbr nb = make_nbr(L, i, j, k);
+            const int id = nb.c;
             const T bv = b[id] - mean;
             const T xc = xq(id);
-            const T rv = bv - lap_lev(L, xv, i, j, k, xc);
+            const T rv = bv - lap_nbr(L, nb, xq, xc);
             b[id] = bv;
             x[id] = xc;
             r[id] = rv;
@@ -741,12 +798,12 @@ __global__ void __launch_bounds__(NTHREADS)
         const int k1 = min(k0 + L.tz, L.n[2]);
         // warm start: p, or 2 p - p_prev (linear extrapolation in time)
         auto pq = [&](int q) -> double { return pp ? 2.0 * ps[q] - pp[q] : ps[q]; };
-        auto pv = [&](int a, int bb, int cc) -> double { return pq(lindex(L, a, bb, cc)); };
         for (int k = k0; k < k1; ++k) {
-            const int id = lindex(L, i, j, k);
+            const Nbr nb = make_nbr(L, i, j, k);
+            const int id = nb.c;
             const double bv = b[id] - mean;
             const double pc = pq(id);
-            const double rv = bv - lap_lev(L, pv, i, j, k, pc);
+            const double rv = bv - lap_nbr(L, nb, pq, pc);
             const float rf = float(rv);
             b[id] = bv;
             pd[id] = pc;
@@ -810,14 +867,12 @@ __global__ void __launch_bounds__(NTHREADS)
     float a2 = 0.0f;
     if (!bad && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto pv = [&](int a, int bb, int cc) -> double {
-            const int q = lindex(L, a, bb, cc);
-            return po[q] + double(e[q]);
-        };
+        auto pq = [&](int q) -> double { return po[q] + double(e[q]); };
         for (int k = k0; k < k1; ++k) {
-            const int id = lindex(L, i, j, k);
-            const double pc = pv(i, j, k);
-            const double rv = b[id] - lap_lev(L, pv, i, j, k, pc);
+            const Nbr nb = make_nbr(L, i, j, k);
+            const int id = nb.c;
+            const double pc = pq(id);
+            const double rv = b[id] - lap_nbr(L, nb, pq, pc);
             const float rf = float(rv);
             pn[id] = pc;
             r[id] = rf;

@@ -1,0 +1,86 @@
+"""CUDA path with solid cells (obstacles) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import parareal as opr
+from paper_1705_06149_gb300 import Grid, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32_refine": 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def close(got, want, tol, what):
+    vg = np.concatenate([np.ravel(got[c]) for c in range(3)])
+    vw = np.concatenate([np.ravel(want[c]) for c in range(3)])
+    assert rel(vg, vw) <= tol, (what, "velocity", rel(vg, vw))
+    assert rel(got[3], want[3]) <= tol, (what, "pressure", rel(got[3], want[3]))
+
+
+def masked_case(dims, seed, count=3, edge=(0.15, 0.3)):
+    _, solid = inputs.obstacle_boxes(dims, seed=seed, count=count, edge=edge)
+    return solid
+
+
+@pytest.mark.parametrize("dims,bc", [((16, 16, 16), ("wall",) * 3),
+                                     ((20, 14, 12), ("periodic", "wall", "wall"))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_predictor_with_solids_matches_oracle(dims, bc, prec):
+    solid = masked_case(dims, seed=5)
+    rs = inputs.random_state(*dims, seed=6, sigma=1.0, bc=bc, solid=solid)
+    og = oracle.Grid(*dims, re=50.0, u_lid=1.0, bc=bc, solid=solid)
+    want = og.predict(*rs[:3], 2e-3)
+    g = Grid(*dims, re=50.0, u_lid=1.0, bc=bc, precision=prec, solid=solid, batch=1)
+    got = [t[0].cpu().numpy() for t in g.predict(g.state_from(rs), 2e-3)]
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for c in range(3):
+        err = np.max(np.abs(got[c] - want[c])) / np.max(np.abs(want[c]))
+        assert err <= tol, (c, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_steps_with_solids_match_oracle(prec):
+    dims = (20, 18, 16)
+    solid = masked_case(dims, seed=7)
+    og = oracle.Grid(*dims, re=100.0, solid=solid)
+    B = 2
+    inits = [inputs.random_state(*dims, seed=30 + s, sigma=0.2, solid=solid) for s in range(B)]
+    g = Grid(*dims, re=100.0, precision=prec, solid=solid, batch=B)
+    st = g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
+    g.step_fine(st, 1e-3, 4)
+    got = st.numpy()
+    for s in range(B):
+        want = oracle.copy_state(inits[s])
+        og.step(want, 1e-3, 4)
+        close([got[c][s] for c in range(4)], want, TOL[prec], f"slice {s}")
+        assert np.all(got[3][s][solid.astype(bool)] == 0.0)
+
+
+def test_parareal_with_solids_and_a_defect_tolerance():
+    dims = (16, 16, 16)
+    solid = masked_case(dims, seed=3, count=2)
+    og = oracle.Grid(*dims, re=100.0, solid=solid)
+    F = opr.fine_propagator(og, 1e-3, 10)
+    G = opr.coarse_propagator(og, 5e-3, 2)
+    u0 = og.zeros()
+    y_ref, d_ref = opr.parareal(u0, 4, F, G, kmax=4)
+    g = Grid(*dims, re=100.0, solid=solid, batch=4)
+    slices = g.zeros(5)
+    k, defects = g.parareal(g.zeros(1), slices, 4, 10, 2, 1e-3, kmax=4)
+    got = slices.numpy()
+    for n in range(5):
+        close([a[n] for a in got], y_ref[n], 1e-10, f"slice {n}")
+    for a, b in zip(defects, d_ref):
+        assert abs(a - b) <= 1e-3 * b + 1e-14
+    # a tolerance between the second and third defects stops after three
+    tol = 0.5 * (d_ref[1] + d_ref[2])
+    k2, d2 = g.parareal(g.zeros(1), g.zeros(5), 4, 10, 2, 1e-3, kmax=4, tol=tol)
+    assert k2 == 3
