@@ -283,6 +283,16 @@ def run_reference(args, world, rank, pg):
 # our implementation
 # ---------------------------------------------------------------------------
 
+def kernel_source_hash() -> str:
+    """sha256 over the device-code headers (the kernels themselves)."""
+    src = os.path.join(ROOT, "paper_1705_06149_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith(".cuh"):
+            h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_for(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
@@ -291,17 +301,12 @@ def traffic_for(kernel: str):
         rec = json.load(open(path))
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_1705_06149_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("source_sha256") != kernel_source_hash():
         return None
     k = rec.get("kernels", {}).get(kernel)
     if not k:
         return None
-    return k.get("dram_bytes_per_cell_iter")
+    return k.get("dram_bytes_per_cell")
 
 
 def run_ours(args, world, rank, local, pg):

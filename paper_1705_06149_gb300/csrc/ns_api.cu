@@ -67,6 +67,7 @@ struct ns_grid {
     void* mg_Y[MG_MAX_LEVELS] = {};             // level iterates, levels 1..lc
     unsigned int* counter = nullptr;            // per state: CTAs arrived
     double* p_prev = nullptr;                   // p of the previous step (warm-start extrapolation)
+    double* r64 = nullptr;                      // FP32+refine: FP64 outer residual
     double* part_mg = nullptr;                  // [cap][ctas][4]
     double* part_div = nullptr;
     double* part_a = nullptr;
@@ -197,6 +198,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
         L0.bc[a] = G.bc[a];
         L0.ih2[a] = G.ih2[a];
         L0.fih2[a] = (float)G.ih2[a];
+        L0.lih2[a] = (float)(G.ih2[a] - (double)L0.fih2[a]);
     }
     fill(L0);
     P.lev[0] = L0;
@@ -212,6 +214,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
             C.bc[a] = L.bc[a];
             C.ih2[a] = L.ih2[a] * 0.25;
             C.fih2[a] = (float)C.ih2[a];
+            C.lih2[a] = (float)(C.ih2[a] - (double)C.fih2[a]);
         }
         fill(C);
         P.lev[P.nlev++] = C;
@@ -517,7 +520,7 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const dou
         NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
                   k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
                       L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, p_prev, g->p64[0],
-                      g->part_mg, otol2, itol2, g->maxit));
+                      g->r64, g->part_mg, otol2, itol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         for (int m = 0;; ++m) {
             NS_TRY(poll_ctl(g, batch));
@@ -529,8 +532,8 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const dou
             g_last_error.clear();
             NS_LAUNCH(g, NS_K_REFINE, L0.cells * batch,
                       k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
-                          L0, mb, g->ctl, g->b, g->p64[m & 1], g->p64[(m + 1) & 1], g->part_mg,
-                          otol2, itol2, g->maxit, kMaxOuter, (m + 1) & 1));
+                          L0, mb, g->ctl, g->p64[0], g->r64, g->part_mg, otol2, itol2, g->maxit,
+                          kMaxOuter));
             NS_CUDA(cudaGetLastError());
         }
         for (int s = 0; s < batch; ++s) {
@@ -1059,6 +1062,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         }
         A((void**)&g->counter, sizeof(unsigned int) * B);
         A((void**)&g->p_prev, ncell * sizeof(double) * B);
+        if (g->fp32) A((void**)&g->r64, ncell * sizeof(double) * B);
         A((void**)&g->part_mg, nparts * 4 * sizeof(double));
     }
     A((void**)&g->d_defect, sizeof(unsigned long long));

@@ -136,6 +136,26 @@ __device__ __forceinline__ T smart_flux(T uf, T bb, T b, T f, T ff) {
     return T(0);
 }
 
+// The same flux without branches (for warps whose faces take different
+// SMART branches): pick the upwind triple, evaluate every branch, select.
+// uf = 0 gives 0 as above (the face value is finite).
+template <typename T>
+__device__ __forceinline__ T smart_flux_sel(T uf, T bb, T b, T f, T ff) {
+    const bool pos = uf > T(0);
+    const T U = pos ? bb : ff;
+    const T C = pos ? b : f;
+    const T D = pos ? f : b;
+    const T dd = D - U;
+    const T cc = C - U;
+    const T a = dd > T(0) ? cc : -cc;
+    const T bd = fabs(dd);
+    const T quick = fma(T(0.75), cc, fma(T(0.375), dd, U));
+    const T steep = fma(T(3), cc, U);
+    T phi = (T(6) * a <= bd) ? steep : ((T(6) * a <= T(5) * bd) ? quick : D);
+    phi = (dd == T(0) || a < T(0) || a > bd) ? C : phi;
+    return uf * phi;
+}
+
 __device__ __forceinline__ bool cell_solid(const Geo& g, int i, int j, int k) {
     return g.solid != nullptr && g.solid[cindex(g, i, j, k)] != 0;
 }

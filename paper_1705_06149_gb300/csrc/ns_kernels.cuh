@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(PT_THREADS)
                 up = T(0.5) * (sdc[o - sc_c + sd] + sdc[o + sd]);
                 um = T(0.5) * (sdc[o - sc_c] + sdc[o]);
             }
-            const T fp = smart_flux(up, a1, a2, a3, a4);
-            const T fm = smart_flux(um, a0, a1, a2, a3);
+            const T fp = smart_flux_sel(up, a1, a2, a3, a4);
+            const T fm = smart_flux_sel(um, a0, a1, a2, a3);
             conv += (fp - fm) * g_ih<T>(g, d);
             diff += (a3 - T(2) * a2 + a1) * g_ih2<T>(g, d);
         }

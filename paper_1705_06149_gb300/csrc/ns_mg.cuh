@@ -32,6 +32,7 @@ struct Lev {
     int bc[3];
     double ih2[3];
     float fih2[3];  // FP32 copy
+    float lih2[3];  // ih2 - fih2 (the FP32 remainder: fih2 + lih2 = ih2 to ~2^-48)
     long long cells;
     int tz, bx, by, bz, ctas;
 };
@@ -89,6 +90,38 @@ __device__ __forceinline__ T lap_nbr(const Lev& L, const Nbr& b, const F& val, T
     return (val(b.hi[0]) + val(b.lo[0]) - two * vc) * lw<T>(L, 0) +
            (val(b.hi[1]) + val(b.lo[1]) - two * vc) * lw<T>(L, 1) +
            (val(b.hi[2]) + val(b.lo[2]) - two * vc) * lw<T>(L, 2);
+}
+
+// Error-free transformations of FP32 arithmetic (Knuth's TwoSum; the exact
+// product remainder by FMA), used to evaluate L e for an FP32 field e to about
+// FP64 accuracy on the FP32 pipe.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// L e at a cell, as a double, for FP32 e: per axis the second difference
+// e_hi + e_lo - 2 e_c in float-float (exact), times the float-float weight
+// (fih2 + lih2), summed in float-float; only the final combination is FP64.
+__device__ __forceinline__ double lap_ff(const Lev& L, const Nbr& nb, const float* e, float ec) {
+    float acc_hi = 0.0f, acc_lo = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float t_hi, t_lo, u_hi, u_err;
+        two_sum(e[nb.hi[d]], e[nb.lo[d]], t_hi, t_lo);
+        two_sum(t_hi, -2.0f * ec, u_hi, u_err);
+        const float u_lo = t_lo + u_err;
+        const float w_hi = L.fih2[d], w_lo = L.lih2[d];
+        const float p_hi = u_hi * w_hi;
+        const float p_err = fmaf(u_hi, w_hi, -p_hi);
+        const float p_lo = p_err + (u_hi * w_lo + u_lo * w_hi);
+        float s_hi, s_err;
+        two_sum(acc_hi, p_hi, s_hi, s_err);
+        acc_hi = s_hi;
+        acc_lo += s_err + p_lo;
+    }
+    return double(acc_hi) + double(acc_lo);
 }
 
 // -w / d in the preconditioner (deterministic; the V-cycle only has to be a
@@ -776,7 +809,8 @@ __global__ void __launch_bounds__(NTHREADS)
     k_mg_refine_init(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
                      const double* __restrict__ part_b, int nfluid, double* __restrict__ bvec,
                      const double* __restrict__ p_in, const double* __restrict__ p_prev,
-                     double* __restrict__ p64, double* __restrict__ part, double otol2,
+                     double* __restrict__ p64, double* __restrict__ r64,
+                     double* __restrict__ part, double otol2,
                      double itol2, int maxit) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
@@ -788,6 +822,7 @@ __global__ void __launch_bounds__(NTHREADS)
     const double* __restrict__ ps = p_in + off;
     const double* __restrict__ pp = p_prev ? p_prev + off : nullptr;
     double* __restrict__ pd = p64 + off;
+    double* __restrict__ rd = r64 + off;
     float* __restrict__ r = mb.r + off;
     float* __restrict__ rh = mb.rhat + off;
     int i, j, k0;
@@ -807,6 +842,7 @@ __global__ void __launch_bounds__(NTHREADS)
             const float rf = float(rv);
             b[id] = bv;
             pd[id] = pc;
+            rd[id] = rv;
             r[id] = rf;
             rh[id] = rf;
             a0 += rv * rv;
@@ -841,23 +877,22 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
-// Outer correction m: p_new = p_old + e (FP64, ping-pong buffers); the true
-// FP64 residual r64 = b - L p_new (p_new recomputed at the neighbours);
-// r = float(r64); r_hat = r.  The last CTA tests the outer residual and
-// restarts the inner solve, or stops (converged / out of outer steps).
+// Outer correction: p += e (FP64, in place); r64 -= L e, with L e of the FP32
+// correction evaluated exactly in float-float (lap_ff) and the residual kept
+// in FP64; r = float(r64); r_hat = r.  The last CTA tests the outer residual
+// and restarts the inner solve, or stops (converged / out of outer steps).
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_refine_update(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
-                       const double* __restrict__ bvec, const double* __restrict__ p_old,
-                       double* __restrict__ p_new, double* __restrict__ part, double otol2,
-                       double itol2, int maxit, int max_outer, int new_buf) {
+                       double* __restrict__ p64, double* __restrict__ r64,
+                       double* __restrict__ part, double otol2, double itol2, int maxit,
+                       int max_outer) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->o_status != OS_REFINE) return;
     const bool bad = c->status == ST_NONFINITE;
     const long long off = s * L.cells;
-    const double* __restrict__ b = bvec + off;
-    const double* __restrict__ po = p_old + off;
-    double* __restrict__ pn = p_new + off;
+    double* __restrict__ pd = p64 + off;
+    double* __restrict__ rd = r64 + off;
     const float* __restrict__ e = mb.x + off;
     float* __restrict__ r = mb.r + off;
     float* __restrict__ rh = mb.rhat + off;
@@ -867,14 +902,15 @@ __global__ void __launch_bounds__(NTHREADS)
     float a2 = 0.0f;
     if (!bad && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto pq = [&](int q) -> double { return po[q] + double(e[q]); };
         for (int k = k0; k < k1; ++k) {
             const Nbr nb = make_nbr(L, i, j, k);
             const int id = nb.c;
-            const double pc = pq(id);
-            const double rv = b[id] - lap_nbr(L, nb, pq, pc);
+            const float ec = e[id];
+            const double pc = pd[id] + double(ec);
+            const double rv = rd[id] - lap_ff(L, nb, e, ec);
             const float rf = float(rv);
-            pn[id] = pc;
+            pd[id] = pc;
+            rd[id] = rv;
             r[id] = rf;
             rh[id] = rf;
             a0 += rv * rv;
@@ -889,7 +925,7 @@ __global__ void __launch_bounds__(NTHREADS)
         c->o_steps += 1;
         c->o_rr = tot[0];
         c->sx = tot[1];
-        c->p_final = new_buf;
+        c->p_final = 0;
         if (bad || !isfinite(tot[0])) {
             c->o_status = OS_NONFINITE;
             c->status = ST_IDLE;
