@@ -63,11 +63,23 @@ WORDS_MG = {"krylov_A": 5, "mg_restrict0": 2.125, "mg_prolong0": 2.125, "mg_lap_
 # C reads x, p, r, v, t, r_hat, writes x, r
 WORDS_PLAIN = {"krylov_A": 6, "krylov_B": 3, "krylov_C": 8}
 
+# Bytes per cell per launch of the step and refinement kernels, FP32+refine
+# path (velocities and increments FP32, pressure and residual FP64):
+#   predict     u, v, w -> dt*RHS increments:            3*4 + 3*4
+#   divergence  increments -> b (FP64):                   3*4 + 8
+#   correct     u, increments, p64, p -> u, p, p_keep:    3*4 + 3*4 + 8 + 8 + 3*4 + 8 + 8
+#   solve_init  b, p, p_prev -> b, p64, r64, r, r_hat:    3*8 + 3*8 + 2*4
+#   refine      p64, r64, e -> p64, r64, r, r_hat:        2*8 + 4 + 2*8 + 2*4
+BYTES_STEP_FP32 = {"predict": 24, "divergence": 20, "correct": 68, "solve_init": 56,
+                   "refine": 44}
+
 
 KERNEL_NAMES = {"krylov_A": "k_mg_src<SRC_P> / k_bicg_A", "krylov_B": "k_mg_src<SRC_S> / k_bicg_B",
                 "krylov_C": "k_mg_update / k_bicg_C", "mg_lap_v": "k_mg_lapdot_v",
                 "mg_lap_t": "k_mg_lapdot_t", "mg_restrict0": "k_mg_restrict (finest)",
-                "mg_prolong0": "k_mg_prolong (finest)"}
+                "mg_prolong0": "k_mg_prolong (finest)", "predict": "k_predict_tile",
+                "divergence": "k_divergence", "correct": "k_correct",
+                "solve_init": "k_mg_refine_init", "refine": "k_mg_refine_update"}
 
 
 def parse():
@@ -80,12 +92,21 @@ def parse():
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preconditioner", choices=["multigrid", "none"], default="multigrid")
+    ap.add_argument("--parareal-chunk", type=int, default=0,
+                    help="slices per fine-sweep chunk overlapped with the coarse chain "
+                         "(0: one sweep over all slices, then the chain)")
     ap.add_argument("--inner-rtol", type=float, default=1e-4,
                     help="FP32+refine: relative residual of each inner FP32 solve")
-    ap.add_argument("--mode", choices=["bench", "kernels", "coarse"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "kernels", "coarse", "adjoint", "obstacles",
+                                       "mixed"],
+                    default="bench",
                     help="kernels: only `steps` batched fine steps of the 32-slice sweep; "
                          "coarse: only the serial coarse chain (32 slices x 5 coarse steps, "
-                         "one slice per call); short runs for profilers, one line each")
+                         "one slice per call); short runs for profilers, one line each.  "
+                         "adjoint: gradient of the 64^3 cavity's kinetic energy after 500 "
+                         "steps; obstacles: Parareal on the 128^3 cavity with 8 boxes; mixed: "
+                         "16 slices of a 256^3 cavity and 24 cavities of mixed sizes and "
+                         "Reynolds numbers, 20 fine steps per CUDA graph launch")
     return ap.parse_args()
 
 
@@ -320,7 +341,8 @@ def run_ours(args, world, rank, local, pg):
 
     init = initial_field_gpu(prec)
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, u_lid=1.0, precision=prec, batch=N_SLICES,
-             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol,
+             parareal_chunk=args.parareal_chunk)
     u0 = g.state_from(init)
     g.project(u0)
     slices = g.zeros(N_SLICES + 1)
@@ -330,7 +352,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
 
     # ---- timed region --------------------------------------------------------
-    g.profile(True, min_batch=N_SLICES)
+    g.profile(True, min_batch=2)  # the fine sweep (chunks of 8 slices), not batch-1 calls
     launches0 = g.stats()["launches"]
     krylov0 = g.stats()["krylov_iters"]
     clocks = ClockSampler(local)
@@ -363,11 +385,14 @@ def run_ours(args, world, rank, local, pg):
     words = WORDS_MG if args.preconditioner == "multigrid" else WORDS_PLAIN
     peak = float(peaks["hbm_gbs"])
     per_kernel = {}
-    for k, wpc in words.items():
+    bpc = {k: wpc * esz for k, wpc in words.items()}
+    if prec == "fp32_refine" and args.preconditioner == "multigrid":
+        bpc.update(BYTES_STEP_FP32)
+    for k, b in bpc.items():
         kp = prof[k]
         if kp["ms"] <= 0 or kp["launches"] == 0:
             continue
-        bytes_alg = kp["cell_units"] * wpc * esz
+        bytes_alg = kp["cell_units"] * b
         per_kernel[k] = {"achieved_gbs": bytes_alg / (kp["ms"] / 1e3) / 1e9,
                          "ms_per_step": kp["ms"] / args.steps,
                          "avg_launch_us": 1e3 * kp["ms"] / kp["launches"],
@@ -380,7 +405,7 @@ def run_ours(args, world, rank, local, pg):
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[kern], "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "algorithmic_bytes_per_launch": per_launch_units * words[kern] * esz,
+                "algorithmic_bytes_per_launch": per_launch_units * bpc[kern],
                 "avg_launch_us": 1e3 * kp["ms"] / max(kp["launches"], 1),
                 "traffic": (traffic * per_launch_units) if traffic else None,
                 "solver_kernels": per_kernel}
@@ -432,6 +457,10 @@ def run_ours(args, world, rank, local, pg):
                    if args.preconditioner == "multigrid" else "BiCGStab",
                    "fine_steps_per_slice": FINE_STEPS, "coarse_steps_per_slice": COARSE_STEPS,
                    "grid": [N_CELLS] * 3, "parallelism": f"replicas x{world}",
+                   "schedule": ("fine sweep in chunks of %d slices, the coarse chain of each "
+                                "chunk overlapped with the next chunk's sweep"
+                                % args.parareal_chunk)
+                   if args.parareal_chunk > 0 else "fine sweep over all slices, then the chain",
                    "l2": "working set > L2 (no flush needed): ~%.0f MB of Krylov vectors"
                          % (N_SLICES * N_CELLS ** 3 * esz * 8 / 1e6)},
         "roofline": roofline,
@@ -514,6 +543,139 @@ def run_coarse_only(args):
     return 0
 
 
+def run_adjoint(args):
+    """Gradient of J = 1/2 |u(T)|^2 (kinetic energy, FP64) with respect to the
+    initial velocity and the lid speed: 64^3 cavity, Re 400, from rest, 500
+    steps of 1e-3, checkpoints every 25 steps; `steps` timed gradients after
+    `warmup` untimed ones of 25 steps."""
+    import torch
+    from paper_1705_06149_gb300 import Grid
+    n, nsteps, dt, ckpt = 64, 500, 1e-3, 25
+    g = Grid(n, n, n, re=400.0, precision="fp64", batch=1)
+    u0 = g.zeros(1)
+    for _ in range(args.warmup):
+        g.adjoint(u0, dt, 25, ckpt)
+    torch.cuda.synchronize()
+    g.reset_stats()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        J, grad, dl = g.adjoint(u0, dt, nsteps, ckpt)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / args.steps
+    gn = float(sum((f[0].double() ** 2).sum() for f in grad.fields()[:3]) ** 0.5)
+    print(json.dumps({"mode": "adjoint", "workload": "64^3 cavity, Re 400, u_lid 1, from rest, "
+                      "500 steps of 1e-3, checkpoints every 25 steps, FP64",
+                      "metric": "gradient cell-steps/s (forward + checkpoint recompute + "
+                      "adjoint sweep)", "value": nsteps * n ** 3 / t, "unit": UNIT,
+                      "s_per_gradient": t, "J": J[0], "grad_l2": gn, "dJ_dulid": dl[0],
+                      "stats": g.stats()}), flush=True)
+    g.close()
+    return 0
+
+
+def run_obstacles(args):
+    """Parareal on the 128^3 cavity with 8 seeded boxes (Re 1000, from rest):
+    64 slices x 25 fine steps of 5e-4, coarse 5 steps of 2.5e-3 per slice,
+    defect tolerance 1e-6.  The first call makes the coarse sweep and one
+    iteration (untimed); then up to `steps` iterations are timed one by one
+    until the defect reaches the tolerance."""
+    import torch
+    from paper_1705_06149_gb300 import Grid, inputs
+    n, n_sl, fine, coarse, dt, tol = 128, 64, 25, 5, 5e-4, 1e-6
+    _, solid = inputs.obstacle_boxes((n, n, n), seed=0, count=8)
+    g = Grid(n, n, n, re=1000.0, precision=args.precision, batch=n_sl, solid=solid,
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
+    u0 = g.zeros(1)
+    slices = g.zeros(n_sl + 1)
+    _, d = g.parareal(u0, slices, n_sl, fine, coarse, dt, kmax=1)
+    torch.cuda.synchronize()
+    g.reset_stats()
+    defects, times = list(d), []
+    for _ in range(args.steps):
+        if defects[-1] <= tol:
+            break
+        t0 = time.perf_counter()
+        _, d = g.parareal(u0, slices, n_sl, fine, coarse, dt, kmax=1, resume=True)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        defects += d
+    t = sum(times) / max(1, len(times))
+    cells = n ** 3
+    print(json.dumps({"mode": "obstacles", "workload": "128^3 cavity, Re 1000, 8 boxes "
+                      "(seed 0), from rest; 64 slices x 25 steps of 5e-4; coarse 5 x 2.5e-3",
+                      "precision": args.precision, "preconditioner": args.preconditioner,
+                      "fluid_fraction": float(1.0 - solid.mean()),
+                      "metric": "Parareal fine-sweep cell-steps/s per iteration",
+                      "value": n_sl * fine * cells / t if times else None, "unit": UNIT,
+                      "s_per_iteration": t, "iterations_timed": len(times),
+                      "defects": defects, "converged": defects[-1] <= tol,
+                      "stats": g.stats()}), flush=True)
+    g.close()
+    return 0
+
+
+def run_mixed(args):
+    """A mixed batch: 16 states of a 256^3 cavity (Re 1000) and 24 independent
+    cavities with (nx, ny, nz) drawn from {32, 48, 64, 96} and Re ~ U[100,
+    2000] (seed 0), all from rest, dt = 5e-4.  One CUDA graph holds 20 fine
+    steps of every grid as concurrent branches; `steps` graph launches are
+    timed after `warmup` ones, against the same steps issued grid by grid on
+    the stream path."""
+    import torch
+    from paper_1705_06149_gb300 import Grid, StepGraph, inputs
+    dt, per_launch = 5e-4, 20
+    dims, res = inputs.mixed_batch_sizes(24, seed=0)
+    specs = [((256, 256, 256), 1000.0, 16)] + [(d, r, 1) for d, r in zip(dims, res)]
+    grids, states = [], []
+    for d, re, b in specs:
+        g = Grid(*d, re=re, precision=args.precision, batch=b, inner_rtol=args.inner_rtol)
+        grids.append(g)
+        states.append(g.zeros(b))
+    cell_steps = per_launch * sum(b * d[0] * d[1] * d[2] for d, _, b in specs)
+    t0 = time.perf_counter()
+    graph = StepGraph([(g, s, dt, per_launch) for g, s in zip(grids, states)])
+    t_capture = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        graph.launch()
+    graph.check()
+    for g in grids:
+        g.reset_stats()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.launch()
+    e1.record(stream)
+    graph.check()
+    ms_graph = e0.elapsed_time(e1) / args.steps
+    st = [g.stats() for g in grids]
+    # the same work on the stream path, grid after grid
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for g, s in zip(grids, states):
+        g.step_fine(s, dt, per_launch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_stream = e0.elapsed_time(e1)
+    iters = sum(x["krylov_iters"] for x in st) / max(1, sum(x["solves"] for x in st))
+    print(json.dumps({"mode": "mixed", "precision": args.precision,
+                      "workload": "256^3 cavity x 16 states (Re 1000) + 24 cavities, sizes "
+                      "from {32,48,64,96}^3, Re ~ U[100,2000] (seed 0), from rest, dt 5e-4, "
+                      "20 fine steps per graph launch",
+                      "metric": "fine cell-steps/s over the whole mixed batch",
+                      "value": cell_steps / (ms_graph / 1e3), "unit": UNIT,
+                      "ms_per_graph_launch": ms_graph, "ms_stream_path": ms_stream,
+                      "stream_path_value": cell_steps / (ms_stream / 1e3),
+                      "capture_s": t_capture, "branches": len(grids),
+                      "krylov_iters_per_solve": iters,
+                      "shapes": [list(d) for d, _, _ in specs]}), flush=True)
+    graph.close()
+    for g in grids:
+        g.close()
+    return 0
+
+
 def fp64_comparators(init):
     """Rates of the FP64 batched sweep and of the plain per-slice FP64 path (one
     slice per call), each over a bounded sample of the same workload."""
@@ -555,6 +717,12 @@ def main():
         rc = run_kernels_only(args)
     elif args.mode == "coarse":
         rc = run_coarse_only(args)
+    elif args.mode == "adjoint":
+        rc = run_adjoint(args)
+    elif args.mode == "obstacles":
+        rc = run_obstacles(args)
+    elif args.mode == "mixed":
+        rc = run_mixed(args)
     elif args.impl == "reference":
         rc = run_reference(args, world, rank, pg)
     else:

@@ -62,7 +62,8 @@ typedef struct {
                                   (Section 2): faces next to a solid hold zero, the
                                   stencil arms reflect at solid surfaces like at a
                                   no-slip wall, the pressure sees Neumann faces.
-                                  With solids the solver is plain BiCGStab.        */
+                                  The multigrid preconditioner carries the solids
+                                  on its finest level only.                        */
     int precision;           /* ns_precision                                         */
     double poisson_rtol;     /* FP64: stop when ||b - L p||_2 <= rtol ||b||_2        */
     int poisson_maxit;       /* iteration limit per Krylov solve (<= 0: 20*max(n))   */
@@ -74,6 +75,15 @@ typedef struct {
                                 (NS_PC_NONE) or with one multigrid V-cycle as right
                                 preconditioner (NS_PC_MULTIGRID; falls back to
                                 NS_PC_NONE on grids it cannot coarsen far enough) */
+    int tile_z;              /* cells each thread marches along z in the stencil and
+                                solver kernels: an even number >= 2 (clamped to nz);
+                                0: 8.  Results depend on it at rounding level (it
+                                fixes the order of the per-state reductions).       */
+    int parareal_chunk;      /* ns_parareal_iterate: slices per chunk of the fine
+                                sweep (> 0); the coarse chain of a chunk's slices
+                                runs on a second stream while the next chunk's fine
+                                sweep runs.  <= 0: one sweep over all slices, then
+                                the chain.  Results are bit-identical either way.  */
 } ns_grid_desc;
 
 typedef enum { NS_PC_NONE = 0, NS_PC_MULTIGRID = 1 } ns_preconditioner;
@@ -252,6 +262,41 @@ ns_status ns_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
                                    double *p, void *cuda_stream, int *iters);
 
 /* Message of the last failure on the calling host thread ("" if none). */
+/* ---- CUDA graphs of fine steps ------------------------------------------
+ * ns_graph_create captures, for each i < n, nsteps[i] fine steps of grids[i]
+ * on states[i] with time step dts[i] -- exactly what
+ * ns_step_fine(grids[i], states[i], dts[i], nsteps[i]) computes -- into one
+ * CUDA graph whose n branches are independent and run concurrently.  Every
+ * pressure solve iterates inside the graph: the BiCGStab iterations and the
+ * FP32+refine outer corrections are conditional while nodes whose conditions
+ * the solver's own decision kernels set on the device (each loop is also
+ * capped at its iteration limit + 2), so a launch makes no host round trip.
+ * This serves many independent cavities of different sizes and Reynolds
+ * numbers in one launch (one grid per shape, Section 3's workloads as a mixed
+ * batch) and launch-bound small grids.
+ *   grids    n distinct grids, each created with NS_PC_MULTIGRID on a grid it
+ *            can coarsen (else NS_ERR_ARG); a grid may sit in one branch only
+ *   states   n caller-owned device states; their pointers are baked into the
+ *            graph, so they must stay allocated until ns_graph_destroy
+ *   dts, nsteps  n time steps (> 0) and step counts (>= 1)
+ * The grids' streams are synchronised once before the capture.  While a graph
+ * exists, its grids may still be used directly, but never concurrently with a
+ * launch of the graph.
+ * ns_graph_launch enqueues one launch on cuda_stream (NULL: the legacy
+ *   default stream) and returns at once.
+ * ns_graph_check synchronises cuda_stream, adds the executed steps, solves,
+ *   iterations and kernel launches to each grid's ns_stats, and reports a
+ *   solve that failed in any launch since the last check: NS_ERR_NOT_CONVERGED
+ *   (an iteration limit was reached) or NS_ERR_NONFINITE; the failure flags
+ *   are then cleared.  The states hold the last launch's results.
+ * ns_graph_destroy frees the graph (call it after the last launch completed). */
+typedef struct ns_graph ns_graph;
+ns_status ns_graph_create(ns_grid *const *grids, const ns_state *states, const double *dts,
+                          const int *nsteps, int n, ns_graph **out);
+ns_status ns_graph_launch(ns_graph *graph, void *cuda_stream);
+ns_status ns_graph_check(ns_graph *graph, void *cuda_stream);
+ns_status ns_graph_destroy(ns_graph *graph);
+
 const char *ns_last_error(void);
 
 #ifdef __cplusplus

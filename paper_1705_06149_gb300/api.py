@@ -69,6 +69,7 @@ class Grid:
                  poisson_rtol: float = 1e-12, poisson_maxit: int = 0,
                  refine_rtol: float = 1e-10, inner_rtol: float = 1e-4, batch: int = 1,
                  preconditioner: str = "multigrid", solid: Optional[np.ndarray] = None,
+                 tile_z: int = 0, parareal_chunk: int = 0,
                  device: Optional[torch.device] = None):
         self.lib = N.load()
         self.device = torch.device(device) if device is not None else torch.device(
@@ -97,6 +98,8 @@ class Grid:
         desc.inner_rtol = inner_rtol
         desc.batch = batch
         desc.preconditioner = {"none": N.NS_PC_NONE, "multigrid": N.NS_PC_MULTIGRID}[preconditioner]
+        desc.tile_z = tile_z
+        desc.parareal_chunk = parareal_chunk
         self.preconditioner = preconditioner
         self._desc = desc
         with torch.cuda.device(self.device):
@@ -271,3 +274,50 @@ class Grid:
         return {k: {"ms": arr[i].ms, "launches": arr[i].launches,
                     "cell_units": arr[i].cell_units}
                 for i, k in enumerate(N.KERNEL_KINDS)}
+
+
+class StepGraph:
+    """A CUDA graph of fine steps of several grids, one concurrent branch per
+    (grid, state, dt, nsteps): each launch advances every state exactly as
+    grid.step_fine(state, dt, nsteps) would, with every solver loop resident
+    on the device (conditional while nodes).  The states' buffers are captured:
+    keep them alive, and do not reallocate them, while the graph exists."""
+
+    def __init__(self, branches):
+        self.lib = N.load()
+        self._grids = [b[0] for b in branches]
+        self._states = [b[1] for b in branches]  # keeps the captured buffers alive
+        n = len(branches)
+        for g, st in zip(self._grids, self._states):
+            g._sync_stream()
+            g._check(st, "StepGraph")
+        grids = (ctypes.c_void_p * n)(*[g._h.value for g in self._grids])
+        states = (N.StateC * n)(*[st._c() for st in self._states])
+        dts = (ctypes.c_double * n)(*[float(b[2]) for b in branches])
+        steps = (ctypes.c_int * n)(*[int(b[3]) for b in branches])
+        h = ctypes.c_void_p()
+        N.check(self.lib.ns_graph_create(grids, states, dts, steps, n, ctypes.byref(h)),
+                "ns_graph_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        N.check(self.lib.ns_graph_launch(self._h, ctypes.c_void_p(s.cuda_stream)),
+                "ns_graph_launch")
+
+    def check(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        N.check(self.lib.ns_graph_check(self._h, ctypes.c_void_p(s.cuda_stream)),
+                "ns_graph_check")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize()
+            self.lib.ns_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

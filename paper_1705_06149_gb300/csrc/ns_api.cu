@@ -10,7 +10,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <condition_variable>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ns.h"
@@ -66,7 +69,7 @@ struct ns_grid {
     void* mg_B[MG_MAX_LEVELS] = {};             // restricted right sides, levels 1..lc
     void* mg_Y[MG_MAX_LEVELS] = {};             // level iterates, levels 1..lc
     unsigned int* counter = nullptr;            // per state: CTAs arrived
-    double* p_prev = nullptr;                   // p of the previous step (warm-start extrapolation)
+    double* p_prev = nullptr;                   // 2 p^n - p^(n-1): the next solve's warm start
     double* r64 = nullptr;                      // FP32+refine: FP64 outer residual
     double* part_mg = nullptr;                  // [cap][ctas][4]
     double* part_div = nullptr;
@@ -99,6 +102,20 @@ struct ns_grid {
     int pr_n = 0;
     const void* pr_slices_u = nullptr;
     bool pr_valid = false;
+    // graph capture (ns_graph_create): while capturing, every launch goes to
+    // `stream` (a capture stream) and the solver loops become conditional
+    // while nodes whose bodies are captured on body_stream[0] / [1]
+    bool capturing = false;
+    cudaStream_t body_stream[2] = {nullptr, nullptr};
+    LoopCount* loopc = nullptr;
+    long long cap_launches = 0;  // kernels captured so far
+    // chunked Parareal: a batch-1 companion grid (same description, so the
+    // same kernels, tiling and reduction order) runs the coarse chain on its
+    // own stream while this grid sweeps the next chunk
+    std::vector<uint8_t> mask_host;             // copy of the solid mask, for the companion
+    ns_grid* chain = nullptr;
+    cudaStream_t chain_stream = nullptr;
+    std::vector<cudaEvent_t> pipe_ev;
     std::vector<void*> allocs;
 };
 
@@ -161,8 +178,7 @@ void setup_geo(ns_grid* g) {
     // cells per thread along z: fixed per grid (not per batch) so that every
     // state is reduced over the same CTAs whatever the batch size; an even
     // number so that the multigrid restriction pairs stay inside a CTA
-    const char* tz_env = std::getenv("NS_TZ");
-    const int tz_want = tz_env ? std::max(2, std::atoi(tz_env) & ~1) : 8;
+    const int tz_want = d.tile_z > 0 ? std::max(2, d.tile_z & ~1) : 8;
     G.tz = std::min(tz_want, G.n[2]);
     G.bx = ceil_div(G.n[0], TX);
     G.by = ceil_div(G.n[1], TY);
@@ -175,11 +191,39 @@ void setup_geo(ns_grid* g) {
     G.n_fluid = G.n[0] * G.n[1] * G.n[2];
 }
 
+// Face codes of the finest level with solid cells (FC_FLUID and one bit per
+// face joining two fluid cells), by the same rules as the pressure operator.
+std::vector<uint8_t> face_codes(const Geo& G, const uint8_t* solid) {
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    std::vector<uint8_t> code((size_t)nx * ny * nz, 0);
+    auto at = [&](int i, int j, int k) { return solid[((size_t)k * ny + j) * nx + i] == 0; };
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (!at(i, j, k)) continue;
+                unsigned m = FC_FLUID;
+                const int c[3] = {i, j, k};
+                for (int a = 0; a < 3; ++a) {
+                    for (int dir = 0; dir < 2; ++dir) {
+                        int q[3] = {c[0], c[1], c[2]};
+                        q[a] += dir ? 1 : -1;
+                        if (q[a] < 0 || q[a] >= G.n[a]) {
+                            if (G.bc[a] != BC_PERIODIC) continue;
+                            q[a] = q[a] < 0 ? G.n[a] - 1 : 0;
+                        }
+                        if (at(q[0], q[1], q[2])) m |= 1u << (2 * a + dir);
+                    }
+                }
+                code[((size_t)k * ny + j) * nx + i] = (uint8_t)m;
+            }
+    return code;
+}
+
 // Multigrid hierarchy: halve every size while all are even and >= 4; the
 // levels from the first one with at most `block_cells` cells down run in one
 // CTA per state.  Returns false when the hierarchy is not usable (the block
 // levels would not fit in shared memory).
-bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
+bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
     const Geo& G = g->geo;
     MgPlan& P = g->plan;
     P = MgPlan{};
@@ -225,6 +269,12 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem) {
             P.lc = m;
             break;
         }
+    if (masked) {
+        // the solid cells live on the finest level only, which the one-CTA
+        // block kernel does not handle
+        if (P.nlev < 2) return false;
+        P.lc = std::max(P.lc, 1);
+    }
     size_t smem = 0;
     for (int m = P.lc; m < P.nlev; ++m) smem += 3 * (size_t)P.lev[m].cells * elem;
     g->mg_smem = smem;
@@ -281,7 +331,7 @@ ns_status sync_stream(ns_grid* g) {
 
 void prof_begin(ns_grid* g, int kind, long long units) {
     auto& P = g->prof;
-    if (!(P.on && P.active)) return;
+    if (g->capturing || !(P.on && P.active)) return;
     if (P.n == P.cap) {
         if (sync_stream(g) != NS_OK) return;
     }
@@ -292,6 +342,10 @@ void prof_begin(ns_grid* g, int kind, long long units) {
 
 void prof_end(ns_grid* g) {
     auto& P = g->prof;
+    if (g->capturing) {
+        g->cap_launches += 1;
+        return;
+    }
     g->stats.launches += 1;
     if (!(P.on && P.active)) return;
     cudaEventRecord(P.ev[2 * P.n + 1], g->stream);
@@ -393,10 +447,11 @@ MgBuf<T> mgbuf(const ns_grid* g) {
     return m;
 }
 
-// One application of the V-cycle to the level-0 vector `src` (written by the
-// source kernel of the given mode), result in `dst`.
+// One application of the V-cycle to the level-0 vector the source kernel of
+// the given mode writes (src, or for SRC_P the parity's one of src / src_odd),
+// result in `dst`.
 template <typename T, int MODE>
-void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* dst, int par) {
+void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
     const MgPlan& P = g->plan;
     const int lc = P.lc;
     const dim3 blk = block_dim();
@@ -404,28 +459,30 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* dst, int par) {
     if (lc > 0)
         NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
                   (k_mg_src<T, MODE, true><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, nullptr, dst, par)));
+                      L0, mb, g->ctl, nullptr, dst)));
     else
         NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
                   (k_mg_src<T, MODE, false><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, nullptr, dst, par)));
+                      L0, mb, g->ctl, nullptr, dst)));
     for (int l = 0; l < lc; ++l) {
         const T* bsrc = l == 0 ? src : mb.B[l];
+        const T* bsrc_odd = l == 0 ? src_odd : nullptr;
         const T* ysrc = l == 0 ? dst : mb.Yl[l];
         NS_LAUNCH(g, l == 0 ? NS_K_MG_RESTRICT0 : NS_K_MG_COARSE, 0,
                   k_mg_restrict<T><<<dim3(P.lev[l].ctas, batch), blk, 0, g->stream>>>(
-                      P.lev[l], P.lev[l + 1], g->ctl, bsrc, ysrc, mb.B[l + 1]));
+                      P.lev[l], P.lev[l + 1], g->ctl, bsrc, bsrc_odd, ysrc, mb.B[l + 1]));
         if (l + 1 < lc)
             NS_LAUNCH(g, NS_K_MG_COARSE, 0,
                       (k_mg_src<T, SRC_ARR, true>
                        <<<dim3(P.lev[l + 1].ctas, batch), blk, 0, g->stream>>>(
-                           P.lev[l + 1], mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1], par)));
+                           P.lev[l + 1], mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1])));
     }
     T* bin = lc == 0 ? src : mb.B[lc];
+    T* bin_odd = lc == 0 ? src_odd : nullptr;
     T* bout = lc == 0 ? dst : mb.Yl[lc];
     NS_LAUNCH(g, NS_K_MG_COARSE, 0,
-              k_mg_block<T><<<batch, MG_BLOCK_THREADS, g->mg_smem, g->stream>>>(P, g->ctl, bin,
-                                                                                 bout));
+              k_mg_block<T><<<batch, MG_BLOCK_THREADS, g->mg_smem, g->stream>>>(
+                  P, g->ctl, bin, bin_odd, bout));
     for (int l = lc - 1; l >= 0; --l) {
         T* y = l == 0 ? dst : mb.Yl[l];
         NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
@@ -436,26 +493,35 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* dst, int par) {
 
 // Preconditioned BiCGStab iterations on every state whose status is ST_ITER,
 // until none is.  zero_start: the solve started from x = 0 (FP32 inner).
+// One preconditioned BiCGStab iteration on every state still iterating: the
+// same launch sequence for every iteration (the ping-pong parity is read from
+// each state's control block), so it can also be captured as a loop body.
+template <typename T>
+ns_status mg_iteration(ns_grid* g, int batch, double tol2, int zero_start) {
+    const Lev& L0 = g->plan.lev[0];
+    MgBuf<T> mb = mgbuf<T>(g);
+    const dim3 grid(L0.ctas, batch), blk = block_dim();
+    mg_apply<T, SRC_P>(g, batch, mb, mb.P[0], mb.P[1], mb.Y);
+    NS_LAUNCH(g, NS_K_MG_LAP_V, 0,
+              k_mg_lapdot_v<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
+    mg_apply<T, SRC_S>(g, batch, mb, mb.S, nullptr, mb.Z);
+    NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
+              k_mg_lapdot_t<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
+    NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
+              k_mg_update<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, tol2,
+                                                           g->maxit, zero_start));
+    NS_CUDA(cudaGetLastError());
+    return NS_OK;
+}
+
 template <typename T>
 ns_status run_mg(ns_grid* g, int batch, double rtol, int zero_start, int* max_iters,
                  double* max_rel) {
     const Lev& L0 = g->plan.lev[0];
-    MgBuf<T> mb = mgbuf<T>(g);
-    const dim3 grid(L0.ctas, batch), blk = block_dim();
     const double tol2 = rtol * rtol;
     int next_poll = std::max(1, g->iter_hint);
     for (int it = 1;; ++it) {
-        const int par = it & 1;
-        mg_apply<T, SRC_P>(g, batch, mb, mb.P[par], mb.Y, par);
-        NS_LAUNCH(g, NS_K_MG_LAP_V, 0,
-                  k_mg_lapdot_v<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, par));
-        mg_apply<T, SRC_S>(g, batch, mb, mb.S, mb.Z, par);
-        NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
-                  k_mg_lapdot_t<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
-        NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
-                  k_mg_update<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, tol2,
-                                                               g->maxit, zero_start));
-        NS_CUDA(cudaGetLastError());
+        NS_TRY(mg_iteration<T>(g, batch, tol2, zero_start));
         if (it >= next_poll) {
             NS_TRY(poll_ctl(g, batch));
             bool any = false;
@@ -499,7 +565,116 @@ ns_status run_mg(ns_grid* g, int batch, double rtol, int zero_start, int* max_it
     return st;
 }
 
-ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const double* p_prev) {
+// ---------------------------------------------------------------------------
+// graph-resident solve: the same kernels, with the host's loops replaced by
+// conditional while nodes whose conditions k_loop_cond sets on the device
+// ---------------------------------------------------------------------------
+
+ns_status capture_graph_of(cudaStream_t st, cudaGraph_t* graph, const cudaGraphNode_t** deps,
+                           size_t* nd) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NS_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, graph, deps, nullptr, nd));
+    if (cs != cudaStreamCaptureStatusActive)
+        return fail(NS_ERR_CUDA, "graph capture: stream is not capturing");
+    return NS_OK;
+}
+
+ns_status make_handle(cudaStream_t st, cudaGraphConditionalHandle* h) {
+    cudaGraph_t gr;
+    const cudaGraphNode_t* deps;
+    size_t nd;
+    NS_TRY(capture_graph_of(st, &gr, &deps, &nd));
+    NS_CUDA(cudaGraphConditionalHandleCreate(h, gr, 0u, 0u));
+    return NS_OK;
+}
+
+ns_status loop_cond(ns_grid* g, int batch, cudaGraphConditionalHandle h, int mode, int cap) {
+    k_loop_cond<<<1, 32, 0, g->stream>>>(g->ctl, batch, g->loopc, h, mode, (unsigned)cap);
+    g->cap_launches += 1;
+    NS_CUDA(cudaGetLastError());
+    return NS_OK;
+}
+
+// Appends a while node (condition h) to the capture on g->stream and
+// captures its body, launched by body() with g->stream = bst.
+template <typename F>
+ns_status add_while(ns_grid* g, cudaStream_t bst, cudaGraphConditionalHandle h, F&& body) {
+    const cudaStream_t st = g->stream;
+    cudaGraph_t gr;
+    const cudaGraphNode_t* deps;
+    size_t nd;
+    NS_TRY(capture_graph_of(st, &gr, &deps, &nd));
+    cudaGraphNodeParams prm{};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    NS_CUDA(cudaGraphAddNode(&node, gr, deps, nullptr, nd, &prm));
+    NS_CUDA(cudaStreamBeginCaptureToGraph(bst, prm.conditional.phGraph_out[0], nullptr, nullptr,
+                                          0, cudaStreamCaptureModeRelaxed));
+    g->stream = bst;
+    const ns_status sb = body();
+    g->stream = st;
+    cudaGraph_t out;
+    const cudaError_t e = cudaStreamEndCapture(bst, &out);
+    NS_TRY(sb);
+    if (e != cudaSuccess)
+        return fail(NS_ERR_CUDA, std::string("graph capture of a loop body: ") +
+                                     cudaGetErrorString(e));
+    NS_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies));
+    return NS_OK;
+}
+
+ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
+    const Lev& L0 = g->plan.lev[0];
+    const dim3 grid(L0.ctas, batch), blk = block_dim();
+    const int cap_inner = g->maxit + 2;
+    const int cap_refine = (g->maxit + 2) * (kMaxOuter + 2);
+    if (!g->fp32) {
+        MgBuf<double> mb = mgbuf<double>(g);
+        const double tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, 0,
+                  k_mg_init_warm<double><<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->part_mg,
+                      tol2, g->maxit));
+        NS_CUDA(cudaGetLastError());
+        cudaGraphConditionalHandle h;
+        NS_TRY(make_handle(g->stream, &h));
+        NS_TRY(loop_cond(g, batch, h, LC_FP64_START, cap_inner));
+        return add_while(g, g->body_stream[0], h, [&]() -> ns_status {
+            NS_TRY(mg_iteration<double>(g, batch, tol2, 0));
+            return loop_cond(g, batch, h, LC_FP64_ITER, cap_inner);
+        });
+    }
+    MgBuf<float> mb = mgbuf<float>(g);
+    const double otol2 = g->d.refine_rtol * g->d.refine_rtol;
+    const double itol2 = g->inner_rtol * g->inner_rtol;
+    NS_LAUNCH(g, NS_K_SOLVE_INIT, 0,
+              k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
+                  L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->p64[0], g->r64,
+                  g->part_mg, otol2, itol2, g->maxit));
+    NS_CUDA(cudaGetLastError());
+    // one loop: an inner iteration, then the outer correction of every state
+    // whose inner solve has ended (k_loop_cond explains why this matches the
+    // host's nested loops state by state)
+    cudaGraphConditionalHandle h;
+    NS_TRY(make_handle(g->stream, &h));
+    NS_TRY(loop_cond(g, batch, h, LC_REFINE_START, cap_refine));
+    return add_while(g, g->body_stream[0], h, [&]() -> ns_status {
+        NS_TRY(mg_iteration<float>(g, batch, itol2, 1));
+        NS_LAUNCH(g, NS_K_REFINE, 0,
+                  k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->p64[0], g->r64, g->part_mg, otol2, itol2, g->maxit,
+                      kMaxOuter, 1));
+        NS_CUDA(cudaGetLastError());
+        return loop_cond(g, batch, h, LC_REFINE_ITER, cap_refine);
+    });
+}
+
+ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
+    if (g->capturing) return solve_pressure_mg_graph(g, batch, p_in);
     const Lev& L0 = g->plan.lev[0];
     const dim3 grid(L0.ctas, batch), blk = block_dim();
     int max_iters = 0;
@@ -509,7 +684,7 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const dou
         const double tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
         NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
                   k_mg_init_warm<double><<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, p_prev,
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in,
                       g->part_mg, tol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         NS_TRY(run_mg<double>(g, batch, g->d.poisson_rtol, 0, &max_iters, &max_rel));
@@ -519,7 +694,7 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const dou
         const double itol2 = g->inner_rtol * g->inner_rtol;
         NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
                   k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, p_prev, g->p64[0],
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->p64[0],
                       g->r64, g->part_mg, otol2, itol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         for (int m = 0;; ++m) {
@@ -533,7 +708,7 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const dou
             NS_LAUNCH(g, NS_K_REFINE, L0.cells * batch,
                       k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
                           L0, mb, g->ctl, g->p64[0], g->r64, g->part_mg, otol2, itol2, g->maxit,
-                          kMaxOuter));
+                          kMaxOuter, 0));
             NS_CUDA(cudaGetLastError());
         }
         for (int s = 0; s < batch; ++s) {
@@ -559,9 +734,8 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in, const dou
 // sums in g->part_div; warm start p_in (double, device).  Result: the solution
 // buffer of each state (FP64: kv x; FP32+refine: p64[p_final]) and its sum in
 // SliceCtl.sx.
-ns_status solve_pressure(ns_grid* g, int batch, const double* p_in,
-                         const double* p_prev = nullptr) {
-    if (g->mg) return solve_pressure_mg(g, batch, p_in, p_prev);
+ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
+    if (g->mg) return solve_pressure_mg(g, batch, p_in);
     const Geo& G = g->geo;
     const dim3 grid(G.ctas, batch);
     int max_iters = 0;
@@ -671,15 +845,15 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
                       with_u ? w : nullptr, g->b, g->part_div, 1.0 / dt));
         NS_CUDA(cudaGetLastError());
         // multigrid path: from the second step of a call the solve starts from
-        // 2 p^n - p^(n-1); the correction keeps p^n for that
+        // 2 p^n - p^(n-1), which the previous correction wrote into p_prev
         const bool extrap = g->mg && n > 0;
-        NS_TRY(solve_pressure(g, B, p, extrap ? g->p_prev : nullptr));
+        NS_TRY(solve_pressure(g, B, extrap ? g->p_prev : p));
         NS_LAUNCH(g, NS_K_CORRECT, cells,
                   k_correct<T, INCR><<<gface, block_dim(), 0, g->stream>>>(
                       G, g->ctl, fu, fv, fw, u, v, w, x0, x1, p, dt,
                       g->mg && n + 1 < nsteps ? g->p_prev : nullptr));
         NS_CUDA(cudaGetLastError());
-        g->stats.steps += B;
+        if (!g->capturing) g->stats.steps += B;
     }
     return NS_OK;
 }
@@ -756,6 +930,145 @@ ns_status parareal_update(ns_grid* g, const void* const fy[4], const void* const
     return NS_OK;
 }
 
+// One Parareal iteration with the fine sweep in chunks of `chunk` slices on
+// this grid's stream (this thread) and the serial coarse chain with the
+// update of Eq. 6 on the companion grid's stream (a second host thread).
+// The chain takes slice n once the chunk holding n has been swept, and
+// writes y_{n+1} only after the chunk holding n+1 has copied its inputs, so
+// the chain of chunk c overlaps the sweep of chunk c+1.  Every state is
+// computed by the same kernels as in the unchunked iteration (reductions do
+// not depend on the batch), so the result is bit-identical.
+template <typename T>
+ns_status parareal_iteration_chunked(ns_grid* g, ns_state slices, int N, int S, int M,
+                                     double dt, int chunk, double* defect) {
+    const Geo& G = g->geo;
+    const int C = (N + chunk - 1) / chunk;
+    if (!g->chain) {
+        ns_grid_desc d = g->d;
+        d.batch = 1;
+        d.parareal_chunk = -1;
+        d.solid_mask = g->mask_host.empty() ? nullptr : g->mask_host.data();
+        int lo = 0, hi = 0;
+        NS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        NS_CUDA(cudaStreamCreateWithPriority(&g->chain_stream, cudaStreamNonBlocking, hi));
+        NS_TRY(ns_create_grid(&d, g->chain_stream, &g->chain));
+    }
+    if ((int)g->pipe_ev.size() < 2 * C + 2) {
+        while ((int)g->pipe_ev.size() < 2 * C + 2) {
+            cudaEvent_t e;
+            NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            g->pipe_ev.push_back(e);
+        }
+    }
+    ns_grid* h = g->chain;
+    cudaEvent_t* ev_copied = g->pipe_ev.data();
+    cudaEvent_t* ev_swept = g->pipe_ev.data() + C;
+    cudaEvent_t ev_start = g->pipe_ev[2 * C], ev_end = g->pipe_ev[2 * C + 1];
+    void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
+    const double dtc = dt * S / M;
+    // the chain's own coarse state buffer lives in this grid's pr_g
+    ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
+    NS_CUDA(cudaEventRecord(ev_start, g->stream));
+    const ns_stats chain0 = h->stats;
+
+    std::mutex mu;
+    std::condition_variable cv;
+    int copied = -1, swept = -1;  // last chunk whose event is recorded
+    bool abort = false;
+    ns_status st_chain = NS_OK;
+    std::string err_chain;
+    auto wait_for = [&](const int& what, int c) {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return what >= c || abort; });
+        return !abort;
+    };
+    auto post = [&](int& what, int c) {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            what = c;
+        }
+        cv.notify_all();
+    };
+    std::thread chain_thread([&]() {
+        auto run = [&]() -> ns_status {
+            NS_CUDA(cudaStreamWaitEvent(h->stream, ev_start, 0));
+            NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
+            for (int c = 0; c < C; ++c) {
+                if (!wait_for(swept, c)) return NS_OK;
+                NS_CUDA(cudaStreamWaitEvent(h->stream, ev_swept[c], 0));
+                if (c + 1 < C) {
+                    if (!wait_for(copied, c + 1)) return NS_OK;
+                    NS_CUDA(cudaStreamWaitEvent(h->stream, ev_copied[c + 1], 0));
+                }
+                const int n1 = std::min(N, (c + 1) * chunk);
+                for (int n = c * chunk; n < n1; ++n) {
+                    NS_TRY(copy_states<T>(h, g->pr_g, ys, 0, n, 1));
+                    NS_TRY(step_impl<T>(h, gs, dtc, M));
+                    NS_TRY(parareal_update<T>(h, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
+                }
+            }
+            NS_CUDA(cudaMemcpyAsync(h->h_defect, h->d_defect, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, h->stream));
+            NS_CUDA(cudaEventRecord(ev_end, h->stream));
+            return sync_stream(h);
+        };
+        st_chain = run();
+        if (st_chain != NS_OK) {
+            err_chain = g_last_error;
+            std::lock_guard<std::mutex> lk(mu);
+            abort = true;
+        }
+        cv.notify_all();
+    });
+    ns_status st = NS_OK;
+    for (int c = 0; c < C && st == NS_OK; ++c) {
+        const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (abort) break;
+        }
+        st = copy_states<T>(g, g->pr_f, ys, n0, n0, m);
+        if (st == NS_OK && cudaEventRecord(ev_copied[c], g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "chunked Parareal: event record failed");
+        if (st != NS_OK) break;
+        post(copied, c);
+        ns_state fb{(char*)g->pr_f[0] + (size_t)n0 * G.cnt[0] * sizeof(T),
+                    (char*)g->pr_f[1] + (size_t)n0 * G.cnt[1] * sizeof(T),
+                    (char*)g->pr_f[2] + (size_t)n0 * G.cnt[2] * sizeof(T),
+                    (char*)g->pr_f[3] + (size_t)n0 * G.cnt[3] * sizeof(double), m};
+        st = step_impl<T>(g, fb, dt, S);
+        if (st == NS_OK && cudaEventRecord(ev_swept[c], g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "chunked Parareal: event record failed");
+        if (st != NS_OK) break;
+        post(swept, c);
+    }
+    if (st != NS_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        abort = true;
+    }
+    cv.notify_all();
+    const std::string err_fine = g_last_error;
+    chain_thread.join();
+    // the slices are written by the chain: later work on this stream waits for it
+    if (st == NS_OK && st_chain == NS_OK) {
+        NS_CUDA(cudaStreamWaitEvent(g->stream, ev_end, 0));
+        NS_TRY(sync_stream(g));
+    } else {
+        cudaStreamSynchronize(h->stream);
+        cudaStreamSynchronize(g->stream);
+    }
+    // the chain's counters count as this grid's
+    g->stats.launches += h->stats.launches - chain0.launches;
+    g->stats.steps += h->stats.steps - chain0.steps;
+    g->stats.solves += h->stats.solves - chain0.solves;
+    g->stats.krylov_iters += h->stats.krylov_iters - chain0.krylov_iters;
+    g->stats.refine_steps += h->stats.refine_steps - chain0.refine_steps;
+    if (st != NS_OK) return fail(st, err_fine);
+    if (st_chain != NS_OK) return fail(st_chain, err_chain);
+    std::memcpy(defect, h->h_defect, sizeof(double));
+    return NS_OK;
+}
+
 template <typename T>
 ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, int M,
                         double dt, int kmax, double tol, int resume, int* k_done,
@@ -792,24 +1105,29 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
         }
     }
     g->pr_valid = false;
+    const int chunk = g->d.parareal_chunk > 0 ? g->d.parareal_chunk : 0;
     int k = 0;
     for (; k < kmax; ++k) {
-        // F(y^k_n) for all n in one batched sweep
-        NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
-        ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
-        NS_TRY(step_impl<T>(g, fb, dt, S));
-        NS_CUDA(cudaMemsetAsync(g->d_defect, 0, sizeof(unsigned long long), g->stream));
-        // serial coarse sweep with the update of Eq. 6
-        for (int n = 0; n < N; ++n) {
-            NS_TRY(copy_states<T>(g, g->pr_g, ys, 0, n, 1));
-            NS_TRY(step_impl<T>(g, gs, dtc, M));
-            NS_TRY(parareal_update<T>(g, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
-        }
-        NS_CUDA(cudaMemcpyAsync(g->h_defect, g->d_defect, sizeof(unsigned long long),
-                                cudaMemcpyDeviceToHost, g->stream));
-        NS_TRY(sync_stream(g));
         double dk;
-        std::memcpy(&dk, g->h_defect, sizeof(double));
+        if (chunk > 0 && chunk < N) {
+            NS_TRY(parareal_iteration_chunked<T>(g, slices, N, S, M, dt, chunk, &dk));
+        } else {
+            // F(y^k_n) for all n in one batched sweep
+            NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
+            ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
+            NS_TRY(step_impl<T>(g, fb, dt, S));
+            NS_CUDA(cudaMemsetAsync(g->d_defect, 0, sizeof(unsigned long long), g->stream));
+            // serial coarse sweep with the update of Eq. 6
+            for (int n = 0; n < N; ++n) {
+                NS_TRY(copy_states<T>(g, g->pr_g, ys, 0, n, 1));
+                NS_TRY(step_impl<T>(g, gs, dtc, M));
+                NS_TRY(parareal_update<T>(g, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
+            }
+            NS_CUDA(cudaMemcpyAsync(g->h_defect, g->d_defect, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, g->stream));
+            NS_TRY(sync_stream(g));
+            std::memcpy(&dk, g->h_defect, sizeof(double));
+        }
         if (defects) defects[k] = dk;
         if (!std::isfinite(dk)) {
             if (k_done) *k_done = k + 1;
@@ -1004,6 +1322,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     int n_solid = 0;
     if (d.solid_mask) {
         const long long nc = (long long)d.nx * d.ny * d.nz;
+        g->mask_host.assign(d.solid_mask, d.solid_mask + nc);
         for (long long q = 0; q < nc; ++q) n_solid += d.solid_mask[q] != 0;
         if (n_solid == nc) {
             delete g;
@@ -1037,8 +1356,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     A((void**)&g->part_r, nparts * 3 * sizeof(double));
     A((void**)&g->ctl, sizeof(SliceCtl) * B);
     if (d.solid_mask && st == NS_OK) {
-        // obstacles: a device copy of the cell mask; the multigrid hierarchy
-        // has no coarse masks, so the solves use plain BiCGStab
+        // obstacles: a device copy of the cell mask
         void* m = nullptr;
         A(&m, ncell);
         if (st == NS_OK &&
@@ -1047,12 +1365,22 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         g->geo.solid = (const uint8_t*)m;
         g->geo.n_fluid = (int)(ncell - n_solid);
     }
-    if (d.preconditioner == NS_PC_MULTIGRID && !d.solid_mask) {
-        // levels at or below this size run in one CTA per state; FP64 keeps
-        // that CTA's share small (one SM's FP64 rate is low)
+    if (d.preconditioner == NS_PC_MULTIGRID && st == NS_OK) {
+        // levels at or below this size run in one CTA per state: kept small,
+        // since one SM does that work (its shared memory stays under 8 KB)
         const char* env = std::getenv("NS_MG_BLOCK_CELLS");
-        const int block_cells = env ? std::max(8, std::atoi(env)) : (g->fp32 ? 4096 : 512);
-        g->mg = setup_mg(g, block_cells, ev);
+        const int block_cells = env ? std::max(8, std::atoi(env)) : 512;
+        g->mg = setup_mg(g, block_cells, ev, d.solid_mask != nullptr);
+        if (g->mg && d.solid_mask) {
+            // solid cells enter the finest level through its face codes
+            const std::vector<uint8_t> code = face_codes(g->geo, d.solid_mask);
+            void* fc = nullptr;
+            A(&fc, ncell);
+            if (st == NS_OK &&
+                cudaMemcpy(fc, code.data(), ncell, cudaMemcpyHostToDevice) != cudaSuccess)
+                st = fail(NS_ERR_CUDA, "ns_create_grid: face-code copy failed");
+            g->plan.lev[0].fcode = (const uint8_t*)fc;
+        }
     }
     if (g->mg) {
         for (int q = 0; q < 3; ++q) A(&g->mg_vec[q], ncell * ev * B);
@@ -1061,6 +1389,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
             A(&g->mg_Y[l], (size_t)g->plan.lev[l].cells * ev * B);
         }
         A((void**)&g->counter, sizeof(unsigned int) * B);
+        A((void**)&g->loopc, sizeof(LoopCount));
         A((void**)&g->p_prev, ncell * sizeof(double) * B);
         if (g->fp32) A((void**)&g->r64, ncell * sizeof(double) * B);
         A((void**)&g->part_mg, nparts * 4 * sizeof(double));
@@ -1083,6 +1412,9 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
                 st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
         if (st == NS_OK &&
             cudaMemsetAsync(g->ctl, 0, sizeof(SliceCtl) * B, g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        if (st == NS_OK && g->loopc &&
+            cudaMemsetAsync(g->loopc, 0, sizeof(LoopCount), g->stream) != cudaSuccess)
             st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
         if (st == NS_OK) {
             const int ps = 3 * PS_N * (int)sizeof(double);
@@ -1127,6 +1459,10 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
 ns_status ns_destroy_grid(ns_grid* grid) {
     if (!grid) return NS_OK;
     cudaStreamSynchronize(grid->stream);
+    if (grid->chain) ns_destroy_grid(grid->chain);
+    if (grid->chain_stream) cudaStreamDestroy(grid->chain_stream);
+    for (cudaEvent_t e : grid->pipe_ev) cudaEventDestroy(e);
+    grid->pipe_ev.clear();
     free_all(grid);
     delete grid;
     return NS_OK;
@@ -1310,6 +1646,203 @@ ns_status ns_get_stats(const ns_grid* grid, ns_stats* out) {
 ns_status ns_reset_stats(ns_grid* grid) {
     if (!grid) return fail(NS_ERR_ARG, "ns_reset_stats: null argument");
     grid->stats = ns_stats{};
+    return NS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of fine steps (several grids as concurrent branches)
+// ---------------------------------------------------------------------------
+
+struct ns_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t origin = nullptr;
+    std::vector<ns_grid*> grids;
+    std::vector<int> batch, nsteps;
+    std::vector<cudaStream_t> streams;  // 3 per branch: top level, outer body, inner body
+    std::vector<cudaEvent_t> events;
+    std::vector<LoopCount> seen_loops;  // device loop totals at the last check
+    std::vector<std::vector<SliceCtl>> seen_ctl;
+    long long launched = 0;             // graph launches since the last check
+};
+
+namespace {
+
+// Kernels one preconditioned iteration launches (mg_apply twice + 3).
+long long mg_iteration_launches(const ns_grid* g) {
+    const int lc = g->plan.lc;
+    const long long apply = 1 + lc + std::max(lc - 1, 0) + 1 + lc;
+    return 2 * apply + 3;
+}
+
+void graph_free(ns_graph* gr) {
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    for (cudaEvent_t e : gr->events) cudaEventDestroy(e);
+    for (cudaStream_t s : gr->streams) cudaStreamDestroy(s);
+    if (gr->origin) cudaStreamDestroy(gr->origin);
+    delete gr;
+}
+
+}  // namespace
+
+ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const double* dts,
+                          const int* nsteps, int n, ns_graph** out) {
+    if (!out) return fail(NS_ERR_ARG, "ns_graph_create: null output");
+    *out = nullptr;
+    if (!grids || !states || !dts || !nsteps || n < 1)
+        return fail(NS_ERR_ARG, "ns_graph_create: null array or n < 1");
+    for (int i = 0; i < n; ++i) {
+        ns_grid* g = grids[i];
+        if (!g) return fail(NS_ERR_ARG, "ns_graph_create: null grid");
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == g)
+                return fail(NS_ERR_ARG, "ns_graph_create: a grid appears in two branches");
+        if (!g->mg)
+            return fail(NS_ERR_ARG,
+                        "ns_graph_create: graph-resident solves need the multigrid "
+                        "preconditioner (branch " + std::to_string(i) + ")");
+        NS_TRY(check_state(g, states[i], "ns_graph_create"));
+        if (!(dts[i] > 0.0) || !std::isfinite(dts[i]) || nsteps[i] < 1)
+            return fail(NS_ERR_ARG, "ns_graph_create: dt must be positive and nsteps >= 1");
+    }
+    ns_graph* gr = new (std::nothrow) ns_graph();
+    if (!gr) return fail(NS_ERR_OOM, "ns_graph_create: out of host memory");
+    auto bail = [&](ns_status st) {
+        graph_free(gr);
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&gr->origin, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream creation failed"));
+    for (int i = 0; i < 3 * n; ++i) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream creation failed"));
+        gr->streams.push_back(s);
+    }
+    for (int i = 0; i < n + 1; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(NS_ERR_CUDA, "ns_graph_create: event creation failed"));
+        gr->events.push_back(e);
+    }
+    // the branches must see the states as the caller's streams left them
+    for (int i = 0; i < n; ++i)
+        if (cudaStreamSynchronize(grids[i]->stream) != cudaSuccess)
+            return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream synchronisation failed"));
+    if (cudaStreamBeginCapture(gr->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return bail(fail(NS_ERR_CUDA, "ns_graph_create: cudaStreamBeginCapture failed"));
+    ns_status st = NS_OK;
+    if (cudaEventRecord(gr->events[n], gr->origin) != cudaSuccess)
+        st = fail(NS_ERR_CUDA, "ns_graph_create: fork event failed");
+    for (int i = 0; i < n && st == NS_OK; ++i) {
+        ns_grid* g = grids[i];
+        cudaStream_t top = gr->streams[3 * i];
+        if (cudaStreamWaitEvent(top, gr->events[n], 0) != cudaSuccess) {
+            st = fail(NS_ERR_CUDA, "ns_graph_create: fork wait failed");
+            break;
+        }
+        const cudaStream_t saved = g->stream;
+        const bool prof_active = g->prof.active;
+        g->stream = top;
+        g->body_stream[0] = gr->streams[3 * i + 1];
+        g->body_stream[1] = gr->streams[3 * i + 2];
+        g->capturing = true;
+        st = g->fp32 ? step_impl<float>(g, states[i], dts[i], nsteps[i])
+                     : step_impl<double>(g, states[i], dts[i], nsteps[i]);
+        g->capturing = false;
+        g->prof.active = prof_active;
+        g->stream = saved;
+        g->body_stream[0] = g->body_stream[1] = nullptr;
+        if (st == NS_OK && (cudaEventRecord(gr->events[i], top) != cudaSuccess ||
+                            cudaStreamWaitEvent(gr->origin, gr->events[i], 0) != cudaSuccess))
+            st = fail(NS_ERR_CUDA, "ns_graph_create: join failed");
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(gr->origin, &graph);
+    gr->graph = graph;
+    if (st != NS_OK) return bail(st);
+    if (e != cudaSuccess)
+        return bail(fail(NS_ERR_CUDA, std::string("ns_graph_create: cudaStreamEndCapture: ") +
+                                          cudaGetErrorString(e)));
+    const cudaError_t ei = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+    if (ei != cudaSuccess)
+        return bail(fail(NS_ERR_CUDA, std::string("ns_graph_create: cudaGraphInstantiate: ") +
+                                          cudaGetErrorString(ei)));
+    for (int i = 0; i < n; ++i) {
+        ns_grid* g = grids[i];
+        gr->grids.push_back(g);
+        gr->batch.push_back(states[i].batch);
+        gr->nsteps.push_back(nsteps[i]);
+        LoopCount lc{};
+        std::vector<SliceCtl> ctl(states[i].batch);
+        if (cudaMemcpy(&lc, g->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ctl.data(), g->ctl, sizeof(SliceCtl) * ctl.size(),
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            return bail(fail(NS_ERR_CUDA, "ns_graph_create: reading the control blocks failed"));
+        gr->seen_loops.push_back(lc);
+        gr->seen_ctl.push_back(ctl);
+    }
+    *out = gr;
+    return NS_OK;
+}
+
+ns_status ns_graph_launch(ns_graph* gr, void* cuda_stream) {
+    if (!gr || !gr->exec) return fail(NS_ERR_ARG, "ns_graph_launch: null graph");
+    NS_CUDA(cudaGraphLaunch(gr->exec, (cudaStream_t)cuda_stream));
+    gr->launched += 1;
+    return NS_OK;
+}
+
+ns_status ns_graph_check(ns_graph* gr, void* cuda_stream) {
+    if (!gr) return fail(NS_ERR_ARG, "ns_graph_check: null graph");
+    NS_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+    ns_status result = NS_OK;
+    for (size_t i = 0; i < gr->grids.size(); ++i) {
+        ns_grid* g = gr->grids[i];
+        const int B = gr->batch[i];
+        LoopCount lc{};
+        std::vector<SliceCtl> ctl(B);
+        NS_CUDA(cudaMemcpy(&lc, g->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
+        NS_CUDA(cudaMemcpy(ctl.data(), g->ctl, sizeof(SliceCtl) * B, cudaMemcpyDeviceToHost));
+        const LoopCount& l0 = gr->seen_loops[i];
+        const long long bodies = (long long)(lc.inner_total - l0.inner_total);
+        const long long steps = gr->launched * gr->nsteps[i];
+        g->stats.steps += steps * B;
+        // per step: predict, divergence, solve start, loop condition, correction;
+        // per loop body: one iteration, (FP32) the outer correction, the condition
+        g->stats.launches +=
+            steps * 5 + bodies * (mg_iteration_launches(g) + (g->fp32 ? 2 : 1));
+        for (int s = 0; s < B; ++s) {
+            const SliceCtl& a = ctl[s];
+            const SliceCtl& b = gr->seen_ctl[i][s];
+            g->stats.solves += a.total_solves - b.total_solves;
+            g->stats.krylov_iters += a.total_iters - b.total_iters;
+            g->stats.refine_steps += a.total_outer - b.total_outer;
+            if (a.fail && result == NS_OK) {
+                result = fail(a.fail & 2 ? NS_ERR_NONFINITE : NS_ERR_NOT_CONVERGED,
+                              "ns_graph_check: a pressure solve of branch " + std::to_string(i) +
+                                  ", state " + std::to_string(s) +
+                                  (a.fail & 2 ? " met a non-finite residual"
+                                              : " did not reach its tolerance"));
+            }
+            if (a.fail) {
+                const int zero = 0;
+                NS_CUDA(cudaMemcpy(&g->ctl[s].fail, &zero, sizeof(int), cudaMemcpyHostToDevice));
+                ctl[s].fail = 0;
+            }
+        }
+        gr->seen_loops[i] = lc;
+        gr->seen_ctl[i] = ctl;
+    }
+    gr->launched = 0;
+    return result;
+}
+
+ns_status ns_graph_destroy(ns_graph* gr) {
+    if (!gr) return NS_OK;
+    if (gr->origin) cudaStreamSynchronize(gr->origin);
+    graph_free(gr);
     return NS_OK;
 }
 

@@ -31,10 +31,12 @@ struct SliceCtl {
     int o_status;      // OS_*: FP32+refine outer loop
     int o_steps;       // outer corrections applied
     int p_final;       // FP32+refine: p64 buffer holding the result
-    int pad;
+    int fail;          // graph-resident solves: sticky bits, 1 not converged, 2 non-finite
     double o_bb, o_rr;
     long long total_iters;  // Krylov iterations accumulated over solves
     double beta;       // multigrid path: beta of the next iteration
+    long long total_outer;  // graph-resident solves: refinement steps accumulated
+    long long total_solves; // graph-resident solves: solves finished
 };
 
 template <typename T>
@@ -771,9 +773,11 @@ __global__ void __launch_bounds__(NTHREADS)
         }
         if (p_out && i < g.n[0] && j < g.n[1] && k < g.n[2]) {
             const long long id = cindex(g, i, j, k);
-            // p_keep (optional) receives the pressure being replaced
-            if (p_keep) p_keep[s * g.cnt[3] + id] = p_out[s * g.cnt[3] + id];
-            p_out[s * g.cnt[3] + id] = cell_solid(g, i, j, k) ? 0.0 : x[id] - mean;
+            const double pn = cell_solid(g, i, j, k) ? 0.0 : x[id] - mean;
+            // p_keep (optional) receives the next solve's warm start, the
+            // linear extrapolation 2 p^(n+1) - p^n
+            if (p_keep) p_keep[s * g.cnt[3] + id] = 2.0 * pn - p_out[s * g.cnt[3] + id];
+            p_out[s * g.cnt[3] + id] = pn;
         }
     }
 }

@@ -1,0 +1,127 @@
+"""CUDA graphs of fine steps with device-resident solver loops.
+
+A graph launch must reproduce the stream path bit for bit (the same kernels
+in the same order, the loops ended by the same device decisions), for
+several grids of different shapes and Reynolds numbers captured as
+concurrent branches, and report solver failures after the fact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_06149_gb300 import Grid, NSError, StepGraph, inputs
+from paper_1705_06149_gb300 import _native as N
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": 1e-10, "fp32_refine": 1e-5}
+
+# (dims, bc, Re, batch): one cubic wall cavity, one anisotropic periodic box,
+# one with solid boxes
+CASES = [((16, 16, 16), ("wall",) * 3, 1000.0, 2),
+         ((24, 16, 8), ("periodic", "wall", "wall"), 300.0, 1),
+         ((20, 18, 16), ("wall",) * 3, 500.0, 1)]
+
+
+def make(prec, k, solid=None):
+    dims, bc, re, batch = CASES[k]
+    g = Grid(*dims, re=re, bc=bc, precision=prec, batch=batch, solid=solid)
+    inits = [inputs.random_state(*dims, seed=70 + 10 * k + s, sigma=0.2, bc=bc, solid=solid)
+             for s in range(batch)]
+    return g, inits
+
+
+def stack(g, inits):
+    return g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_graph_reproduces_the_stream_path_bit_for_bit(prec):
+    _, solid = inputs.obstacle_boxes(CASES[2][0], seed=1, count=2, edge=(0.15, 0.3))
+    branches, refs = [], []
+    dts, nsteps = [1e-3, 2e-3, 1e-3], [3, 2, 4]
+    for k in range(3):
+        g, inits = make(prec, k, solid if k == 2 else None)
+        a = stack(g, inits)
+        b = stack(g, inits)
+        branches.append((g, a, dts[k], nsteps[k]))
+        refs.append((g, b, inits))
+    graph = StepGraph(branches)
+    for _ in range(2):
+        graph.launch()
+    graph.check()
+    for k, (g, b, inits) in enumerate(refs):
+        g.step_fine(b, dts[k], nsteps[k])
+        g.step_fine(b, dts[k], nsteps[k])
+        for c in range(4):
+            assert torch.equal(branches[k][1].fields()[c], b.fields()[c]), (k, c)
+    graph.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_graph_counts_steps_solves_and_iterations(prec):
+    g, inits = make(prec, 0)
+    a, b = stack(g, inits), stack(g, inits)
+    graph = StepGraph([(g, a, 1e-3, 3)])
+    g.reset_stats()
+    graph.launch()
+    graph.check()
+    s_graph = g.stats()
+    g.reset_stats()
+    g.step_fine(b, 1e-3, 3)
+    s_host = g.stats()
+    for key in ("steps", "solves", "krylov_iters", "refine_steps"):
+        assert s_graph[key] == s_host[key], (key, s_graph, s_host)
+    assert s_graph["launches"] > 0
+    graph.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_graph_matches_the_oracle(prec):
+    dims, bc, re, _ = CASES[1]
+    init = inputs.random_state(*dims, seed=5, sigma=0.2, bc=bc)
+    og = oracle.Grid(*dims, re=re, bc=bc, rtol=1e-13)
+    want = oracle.copy_state(init)
+    og.step(want, 2e-3, 5)
+    g = Grid(*dims, re=re, bc=bc, precision=prec, batch=1, poisson_rtol=1e-13)
+    st = g.state_from(init)
+    graph = StepGraph([(g, st, 2e-3, 5)])
+    graph.launch()
+    graph.check()
+    got = [a[0] for a in st.numpy()]
+    vg = np.concatenate([np.ravel(got[c]) for c in range(3)])
+    vw = np.concatenate([np.ravel(want[c]) for c in range(3)])
+    assert np.linalg.norm(vg - vw) <= TOL[prec] * np.linalg.norm(vw)
+    assert np.linalg.norm(got[3] - want[3]) <= TOL[prec] * np.linalg.norm(want[3])
+    graph.close()
+
+
+def test_graph_reports_a_solve_that_hits_its_iteration_limit():
+    dims = (16, 16, 16)
+    g = Grid(*dims, re=100.0, batch=1, poisson_rtol=1e-30, poisson_maxit=3)
+    st = g.state_from(inputs.random_state(*dims, seed=9, sigma=0.2))
+    graph = StepGraph([(g, st, 1e-3, 2)])
+    graph.launch()
+    with pytest.raises(NSError) as e:
+        graph.check()
+    assert e.value.status == N.NS_ERR_NOT_CONVERGED
+    # the failure flags are cleared by the check; the graph stays usable
+    graph.launch()
+    with pytest.raises(NSError):
+        graph.check()
+    graph.close()
+
+
+def test_graph_rejects_bad_branches():
+    g = Grid(16, 16, 16, batch=1)
+    st = g.zeros(1)
+    with pytest.raises(NSError) as e:
+        StepGraph([(g, st, 1e-3, 1), (g, g.zeros(1), 1e-3, 1)])
+    assert e.value.status == N.NS_ERR_ARG
+    gp = Grid(16, 16, 16, batch=1, preconditioner="none")
+    with pytest.raises(NSError) as e:
+        StepGraph([(gp, gp.zeros(1), 1e-3, 1)])
+    assert e.value.status == N.NS_ERR_ARG
+    with pytest.raises(NSError):
+        StepGraph([(g, st, -1.0, 1)])

@@ -46,14 +46,16 @@ def test_predictor_with_solids_matches_oracle(dims, bc, prec):
         assert err <= tol, (c, err)
 
 
+@pytest.mark.parametrize("pc", ["multigrid", "none"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
-def test_steps_with_solids_match_oracle(prec):
+def test_steps_with_solids_match_oracle(prec, pc):
     dims = (20, 18, 16)
     solid = masked_case(dims, seed=7)
-    og = oracle.Grid(*dims, re=100.0, solid=solid)
+    og = oracle.Grid(*dims, re=100.0, solid=solid, rtol=1e-13)
     B = 2
     inits = [inputs.random_state(*dims, seed=30 + s, sigma=0.2, solid=solid) for s in range(B)]
-    g = Grid(*dims, re=100.0, precision=prec, solid=solid, batch=B)
+    g = Grid(*dims, re=100.0, precision=prec, solid=solid, batch=B, preconditioner=pc,
+             poisson_rtol=1e-13)
     st = g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
     g.step_fine(st, 1e-3, 4)
     got = st.numpy()
@@ -79,8 +81,34 @@ def test_parareal_with_solids_and_a_defect_tolerance():
     for n in range(5):
         close([a[n] for a in got], y_ref[n], 1e-10, f"slice {n}")
     for a, b in zip(defects, d_ref):
-        assert abs(a - b) <= 1e-3 * b + 1e-14
+        # late defects sit at the pressure solves' tolerance (~1e-10): their
+        # agreement is absolute, not relative
+        assert abs(a - b) <= 1e-3 * b + 1e-11
     # a tolerance between the second and third defects stops after three
     tol = 0.5 * (d_ref[1] + d_ref[2])
     k2, d2 = g.parareal(g.zeros(1), g.zeros(5), 4, 10, 2, 1e-3, kmax=4, tol=tol)
     assert k2 == 3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_multigrid_with_solids_keeps_the_iteration_count_low(prec):
+    """The V-cycle with solid cells on its finest level still preconditions:
+    a few iterations per solve on the 32^3 cavity with 8 boxes, where plain
+    BiCGStab needs tens; both give the oracle's steps."""
+    dims = (32, 32, 32)
+    _, solid = inputs.obstacle_boxes(dims, seed=0, count=8)
+    init = inputs.random_state(*dims, seed=40, sigma=0.2, solid=solid)
+    og = oracle.Grid(*dims, re=1000.0, solid=solid, rtol=1e-13)
+    want = oracle.copy_state(init)
+    og.step(want, 5e-4, 3)
+    iters = {}
+    for pc in ("multigrid", "none"):
+        g = Grid(*dims, re=1000.0, precision=prec, solid=solid, batch=1, preconditioner=pc,
+                 poisson_rtol=1e-13)
+        st = g.state_from(init)
+        g.step_fine(st, 5e-4, 3)
+        close([a[0] for a in st.numpy()], want, TOL[prec], pc)
+        s = g.stats()
+        iters[pc] = s["krylov_iters"] / s["solves"]
+    assert iters["multigrid"] <= 25, iters
+    assert iters["none"] >= 3 * iters["multigrid"], iters

@@ -110,11 +110,13 @@ def test_fine_steps_match_oracle(dims, bc, prec, pc):
     B = 3
     inits = [inputs.random_state(*dims, seed=20 + s, sigma=0.2, bc=bc) for s in range(B)]
     # The pressure error of a solve stopped at relative residual rtol is
-    # bounded by cond(L) * rtol (a few hundred here), so both sides solve to
-    # 1e-13 for a 1e-10 pressure comparison.
-    og = oracle.Grid(*dims, re=100.0, bc=bc, rtol=1e-13)
+    # bounded by cond(L) * rtol (a few hundred on these grids), so both sides
+    # solve to 1e-13 for a 1e-10 pressure comparison.  On 2x2x2, cond(L) is 3
+    # and the residual's rounding floor (|p| >> |b| h^2) lies above 1e-13.
+    rtol = 1e-12 if min(dims) <= 2 else 1e-13
+    og = oracle.Grid(*dims, re=100.0, bc=bc, rtol=rtol)
     g = Grid(*dims, re=100.0, bc=bc, precision=prec, batch=B, preconditioner=pc,
-             poisson_rtol=1e-13)
+             poisson_rtol=rtol)
     st = g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
     g.step_fine(st, dt, steps)
     got = st.numpy()
@@ -288,3 +290,26 @@ def test_iteration_limit_is_reported(prec, pc):
     # the grid stays usable afterwards
     g2 = Grid(16, 16, 16, precision=prec, batch=1)
     g2.step_fine(g2.zeros(1), 1e-3, 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_chunked_parareal_is_bit_identical(prec):
+    """The fine sweep in chunks, each chunk's coarse chain overlapped with the
+    next chunk's sweep on a second stream, computes exactly the unchunked
+    iteration: same slices bit for bit, same defects."""
+    runs = {}
+    for chunk in (0, 4, 8):
+        g = Grid(16, 16, 16, re=400.0, precision=prec, batch=16, parareal_chunk=chunk)
+        u0 = g.state_from(inputs.random_state(16, 16, 16, seed=11, sigma=0.2))
+        g.project(u0)
+        slices = g.zeros(17)
+        k1, d1 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=1)
+        k2, d2 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=1, resume=True)
+        runs[chunk] = (slices, d1 + d2, g.stats())
+    ref, dref, sref = runs[0]
+    for chunk in (4, 8):
+        got, d, s = runs[chunk]
+        assert d == dref, (chunk, d, dref)
+        for c in range(4):
+            assert torch.equal(got.fields()[c], ref.fields()[c]), (chunk, c)
+        assert s["steps"] == sref["steps"] and s["solves"] == sref["solves"]
