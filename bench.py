@@ -106,7 +106,7 @@ def parse():
                          "adjoint: gradient of the 64^3 cavity's kinetic energy after 500 "
                          "steps; obstacles: Parareal on the 128^3 cavity with 8 boxes; mixed: "
                          "16 slices of a 256^3 cavity and 24 cavities of mixed sizes and "
-                         "Reynolds numbers, 20 fine steps per CUDA graph launch")
+                         "Reynolds numbers, 20 fine steps of every grid per call")
     return ap.parse_args()
 
 
@@ -513,12 +513,13 @@ def run_kernels_only(args):
 
 def run_coarse_only(args):
     """The serial coarse chain alone (the G sweep of one Parareal iteration,
-    without the update kernels), for profilers: `steps` repetitions."""
+    without the update kernels), for profilers: `steps` repetitions, on a
+    batch-1 grid tiled like Parareal's coarse grid (2 cells per thread in z)."""
     import torch
     from paper_1705_06149_gb300 import Grid
     init = initial_field_gpu(args.precision)
-    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=N_SLICES,
-             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=1,
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol, tile_z=2)
     st = g.state_from(init)
     g.project(st)
     dtc = DT_FINE * FINE_STEPS / COARSE_STEPS
@@ -617,60 +618,83 @@ def run_obstacles(args):
 def run_mixed(args):
     """A mixed batch: 16 states of a 256^3 cavity (Re 1000) and 24 independent
     cavities with (nx, ny, nz) drawn from {32, 48, 64, 96} and Re ~ U[100,
-    2000] (seed 0), all from rest, dt = 5e-4.  One CUDA graph holds 20 fine
-    steps of every grid as concurrent branches; `steps` graph launches are
-    timed after `warmup` ones, against the same steps issued grid by grid on
-    the stream path."""
+    2000] (seed 0), all from rest, dt = 5e-4.  `steps` timed calls (after
+    `warmup`) of ns_step_fine_many, 20 fine steps of every grid per call, the
+    grids on streams and host threads of their own; against the same work
+    issued grid by grid, as one CUDA graph with a branch per grid, and the
+    256^3 grid's 20 steps alone on the stream path and as a graph."""
     import torch
-    from paper_1705_06149_gb300 import Grid, StepGraph, inputs
-    dt, per_launch = 5e-4, 20
+    from paper_1705_06149_gb300 import Grid, StepGraph, inputs, step_fine_many
+    dt, per_call = 5e-4, 20
     dims, res = inputs.mixed_batch_sizes(24, seed=0)
     specs = [((256, 256, 256), 1000.0, 16)] + [(d, r, 1) for d, r in zip(dims, res)]
-    grids, states = [], []
+    from paper_1705_06149_gb300.autotune import seed_order
+    grids, states, tiles = [], [], []
     for d, re, b in specs:
-        g = Grid(*d, re=re, precision=args.precision, batch=b, inner_rtol=args.inner_rtol)
+        tz = seed_order(*d, b)[0][0]  # the autotuner's seeded tile height
+        g = Grid(*d, re=re, precision=args.precision, batch=b, inner_rtol=args.inner_rtol,
+                 tile_z=tz)
         grids.append(g)
         states.append(g.zeros(b))
-    cell_steps = per_launch * sum(b * d[0] * d[1] * d[2] for d, _, b in specs)
-    t0 = time.perf_counter()
-    graph = StepGraph([(g, s, dt, per_launch) for g, s in zip(grids, states)])
-    t_capture = time.perf_counter() - t0
+        tiles.append(tz)
+    cells = [b * d[0] * d[1] * d[2] for d, _, b in specs]
+    cell_steps = per_call * sum(cells)
+    branches = [(g, s, dt, per_call) for g, s in zip(grids, states)]
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
     for _ in range(args.warmup):
-        graph.launch()
-    graph.check()
+        step_fine_many(branches)
     for g in grids:
         g.reset_stats()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.launch()
-    e1.record(stream)
-    graph.check()
-    ms_graph = e0.elapsed_time(e1) / args.steps
+    ms_many = timed(lambda: step_fine_many(branches), args.steps)
     st = [g.stats() for g in grids]
-    # the same work on the stream path, grid after grid
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for g, s in zip(grids, states):
-        g.step_fine(s, dt, per_launch)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_stream = e0.elapsed_time(e1)
+
+    def sequential():
+        for g, s in zip(grids, states):
+            g.step_fine(s, dt, per_call)
+    ms_seq = timed(sequential, 1)
+    # the same 20 steps of every grid as one CUDA graph (a branch per grid)
+    graph = StepGraph(branches)
+    graph.launch()
+    graph.check()
+    ms_graph = timed(graph.launch, args.steps)
+    graph.check()
+    graph.close()
+    # the 256^3 grid alone: stream path against one CUDA graph of its 20 steps
+    ms_big_stream = timed(lambda: grids[0].step_fine(states[0], dt, per_call), 1)
+    graph = StepGraph([branches[0]])
+    graph.launch()
+    graph.check()
+    ms_big_graph = timed(graph.launch, 1)
+    graph.check()
+    graph.close()
     iters = sum(x["krylov_iters"] for x in st) / max(1, sum(x["solves"] for x in st))
     print(json.dumps({"mode": "mixed", "precision": args.precision,
                       "workload": "256^3 cavity x 16 states (Re 1000) + 24 cavities, sizes "
                       "from {32,48,64,96}^3, Re ~ U[100,2000] (seed 0), from rest, dt 5e-4, "
-                      "20 fine steps per graph launch",
+                      "20 fine steps of every grid per call",
                       "metric": "fine cell-steps/s over the whole mixed batch",
-                      "value": cell_steps / (ms_graph / 1e3), "unit": UNIT,
-                      "ms_per_graph_launch": ms_graph, "ms_stream_path": ms_stream,
-                      "stream_path_value": cell_steps / (ms_stream / 1e3),
-                      "capture_s": t_capture, "branches": len(grids),
-                      "krylov_iters_per_solve": iters,
-                      "shapes": [list(d) for d, _, _ in specs]}), flush=True)
-    graph.close()
+                      "value": cell_steps / (ms_many / 1e3), "unit": UNIT,
+                      "ms_per_call": ms_many, "ms_grid_by_grid": ms_seq,
+                      "grid_by_grid_value": cell_steps / (ms_seq / 1e3),
+                      "ms_per_graph_launch": ms_graph,
+                      "graph_value": cell_steps / (ms_graph / 1e3),
+                      "big_grid": {"cells": cells[0], "ms_stream": ms_big_stream,
+                                   "ms_graph": ms_big_graph,
+                                   "graph_value": per_call * cells[0] / (ms_big_graph / 1e3)},
+                      "grids": len(grids), "krylov_iters_per_solve": iters,
+                      "shapes": [list(d) for d, _, _ in specs], "tile_z": tiles}),
+          flush=True)
     for g in grids:
         g.close()
     return 0

@@ -262,6 +262,19 @@ ns_status ns_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
                                    double *p, void *cuda_stream, int *iters);
 
 /* Message of the last failure on the calling host thread ("" if none). */
+/* Advances several independent grids at once: for each i < n exactly what
+ * ns_step_fine(grids[i], states[i], dts[i], nsteps[i]) computes.  Each grid
+ * runs on a stream of its own (ordered after, and joined back into, the
+ * grid's stream) driven by a host thread of its own, so the grids' kernels
+ * overlap on the GPU and a grid waiting for its convergence flags holds no
+ * other.  This serves many independent cavities of different sizes and
+ * Reynolds numbers (one grid per shape; Section 3's workloads as a mixed
+ * batch).  The grids must be distinct.  Returns when every grid's work has
+ * been issued and its solves have converged; the first failing grid (by
+ * index) is reported. */
+ns_status ns_step_fine_many(ns_grid *const *grids, const ns_state *states, const double *dts,
+                            const int *nsteps, int n);
+
 /* ---- CUDA graphs of fine steps ------------------------------------------
  * ns_graph_create captures, for each i < n, nsteps[i] fine steps of grids[i]
  * on states[i] with time step dts[i] -- exactly what
@@ -271,9 +284,9 @@ ns_status ns_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
  * FP32+refine outer corrections are conditional while nodes whose conditions
  * the solver's own decision kernels set on the device (each loop is also
  * capped at its iteration limit + 2), so a launch makes no host round trip.
- * This serves many independent cavities of different sizes and Reynolds
- * numbers in one launch (one grid per shape, Section 3's workloads as a mixed
- * batch) and launch-bound small grids.
+ * This serves launch-bound small grids, repeated step sequences and many
+ * independent cavities in one launch (one grid per shape, Section 3's
+ * workloads as a mixed batch).
  *   grids    n distinct grids, each created with NS_PC_MULTIGRID on a grid it
  *            can coarsen (else NS_ERR_ARG); a grid may sit in one branch only
  *   states   n caller-owned device states; their pointers are baked into the

@@ -21,7 +21,7 @@ EXPORTS = ("ns_create_grid", "ns_destroy_grid", "ns_set_stream", "ns_step_fine",
            "ns_step_coarse", "ns_project", "ns_predict", "ns_poisson_solve",
            "ns_parareal_iterate", "ns_adjoint", "ns_get_stats", "ns_reset_stats",
            "ns_profile_enable", "ns_profile_read", "ns_poisson_solve_noalloc",
-           "ns_set_lid_speed", "ns_graph_create", "ns_graph_launch", "ns_graph_check",
+           "ns_set_lid_speed", "ns_step_fine_many", "ns_graph_create", "ns_graph_launch", "ns_graph_check",
            "ns_graph_destroy", "ns_last_error")
 
 KERNEL_KINDS = ("predict", "divergence", "solve_init", "krylov_A", "krylov_B", "krylov_C",
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = False):
             "ns_reset_stats": [vp],
             "ns_profile_enable": [vp, ctypes.c_int, ctypes.c_int],
             "ns_profile_read": [vp, ctypes.POINTER(KernelTime), ctypes.c_int],
+            "ns_step_fine_many": [vp, vp, dp, ip, ctypes.c_int],
             "ns_graph_create": [vp, vp, dp, ip, ctypes.c_int, gpp],
             "ns_graph_launch": [vp, vp],
             "ns_graph_check": [vp, vp],

@@ -276,6 +276,23 @@ class Grid:
                 for i, k in enumerate(N.KERNEL_KINDS)}
 
 
+def step_fine_many(branches):
+    """Advance several grids at once: for each (grid, state, dt, nsteps), what
+    grid.step_fine(state, dt, nsteps) computes, every grid on a stream and host
+    thread of its own so their kernels overlap."""
+    lib = N.load()
+    grids = [b[0] for b in branches]
+    for g, b in zip(grids, branches):
+        g._sync_stream()
+        g._check(b[1], "step_fine_many")
+    n = len(branches)
+    N.check(lib.ns_step_fine_many((ctypes.c_void_p * n)(*[g._h.value for g in grids]),
+                                  (N.StateC * n)(*[b[1]._c() for b in branches]),
+                                  (ctypes.c_double * n)(*[float(b[2]) for b in branches]),
+                                  (ctypes.c_int * n)(*[int(b[3]) for b in branches]), n),
+            "ns_step_fine_many")
+
+
 class StepGraph:
     """A CUDA graph of fine steps of several grids, one concurrent branch per
     (grid, state, dt, nsteps): each launch advances every state exactly as

@@ -109,9 +109,8 @@ struct ns_grid {
     cudaStream_t body_stream[2] = {nullptr, nullptr};
     LoopCount* loopc = nullptr;
     long long cap_launches = 0;  // kernels captured so far
-    // chunked Parareal: a batch-1 companion grid (same description, so the
-    // same kernels, tiling and reduction order) runs the coarse chain on its
-    // own stream while this grid sweeps the next chunk
+    // Parareal's coarse propagator: a batch-1 companion grid (this grid's
+    // description, tiled for one state) on its own stream (ensure_chain)
     std::vector<uint8_t> mask_host;             // copy of the solid mask, for the companion
     ns_grid* chain = nullptr;
     cudaStream_t chain_stream = nullptr;
@@ -276,9 +275,11 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
         P.lc = std::max(P.lc, 1);
     }
     size_t smem = 0;
-    for (int m = P.lc; m < P.nlev; ++m) smem += 3 * (size_t)P.lev[m].cells * elem;
+    for (int m = P.lc; m < P.nlev; ++m) smem += 2 * (size_t)P.lev[m].cells * elem;
     g->mg_smem = smem;
-    P.block_ok = smem <= 200 * 1024 ? 1 : 0;
+    // the one-CTA levels: at most MG_BLOCK_PER_THREAD cells per thread, and
+    // shared memory within 48 KB
+    P.block_ok = P.lev[P.lc].cells <= MG_BLOCK_MAX_CELLS && smem <= 48 * 1024 ? 1 : 0;
     return P.block_ok != 0;
 }
 
@@ -627,6 +628,44 @@ ns_status add_while(ns_grid* g, cudaStream_t bst, cudaGraphConditionalHandle h, 
     return NS_OK;
 }
 
+// Captures the launches fn() issues on g->stream into an executable graph:
+// the capture runs on `top`, the solver loops' bodies on `body`.
+template <typename F>
+ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
+                       cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
+    *graph_out = nullptr;
+    *exec_out = nullptr;
+    NS_CUDA(cudaStreamBeginCapture(top, cudaStreamCaptureModeRelaxed));
+    const cudaStream_t saved = g->stream;
+    const bool prof_active = g->prof.active;
+    g->stream = top;
+    g->body_stream[0] = body;
+    g->capturing = true;
+    const ns_status st = fn();
+    g->capturing = false;
+    g->prof.active = prof_active;
+    g->stream = saved;
+    g->body_stream[0] = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(top, &graph);
+    if (st != NS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess)
+        return fail(NS_ERR_CUDA, std::string("graph capture: cudaStreamEndCapture: ") +
+                                     cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(exec_out, graph, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(NS_ERR_CUDA, std::string("graph capture: cudaGraphInstantiate: ") +
+                                     cudaGetErrorString(ei));
+    }
+    *graph_out = graph;
+    return NS_OK;
+}
+
+
 ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
     const Lev& L0 = g->plan.lev[0];
     const dim3 grid(L0.ctas, batch), blk = block_dim();
@@ -702,8 +741,10 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
             bool any = false;
             for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].o_status == OS_REFINE;
             if (!any || m > kMaxOuter + 1) break;
+            // an inner solve that stops at its iteration limit still improves
+            // the outer residual; any other failure ends the solve
             ns_status st = run_mg<float>(g, batch, g->inner_rtol, 1, &max_iters, nullptr);
-            if (st == NS_ERR_NONFINITE) return st;
+            if (st != NS_OK && st != NS_ERR_NOT_CONVERGED) return st;
             g_last_error.clear();
             NS_LAUNCH(g, NS_K_REFINE, L0.cells * batch,
                       k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
@@ -930,6 +971,105 @@ ns_status parareal_update(ns_grid* g, const void* const fy[4], const void* const
     return NS_OK;
 }
 
+// Kernels one preconditioned iteration launches (mg_apply twice + 3).
+long long mg_iteration_launches(const ns_grid* g) {
+    const int lc = g->plan.lc;
+    const long long apply = 1 + lc + std::max(lc - 1, 0) + 1 + lc;
+    return 2 * apply + 3;
+}
+
+// After graph launches of `steps` fine steps per state of a batch-B grid have
+// completed: adds the work the device counters show since `seen_*` to the
+// grid's ns_stats (plus extra_launches kernels outside the steps) and reports
+// (then clears) a failed solve.
+ns_status account_graph(ns_grid* g, int B, long long steps, long long extra_launches,
+                        LoopCount& seen_lc, SliceCtl* seen_ctl, const std::string& what) {
+    LoopCount lc{};
+    std::vector<SliceCtl> ctl(B);
+    NS_CUDA(cudaMemcpy(&lc, g->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
+    NS_CUDA(cudaMemcpy(ctl.data(), g->ctl, sizeof(SliceCtl) * B, cudaMemcpyDeviceToHost));
+    const long long bodies = (long long)(lc.inner_total - seen_lc.inner_total);
+    g->stats.steps += steps * B;
+    // per step: predict, divergence, solve start, loop condition, correction;
+    // per loop body: one iteration, (FP32) the outer correction, the condition
+    g->stats.launches += steps * 5 + bodies * (mg_iteration_launches(g) + (g->fp32 ? 2 : 1)) +
+                         extra_launches;
+    ns_status result = NS_OK;
+    for (int s = 0; s < B; ++s) {
+        const SliceCtl& a = ctl[s];
+        const SliceCtl& b = seen_ctl[s];
+        g->stats.solves += a.total_solves - b.total_solves;
+        g->stats.krylov_iters += a.total_iters - b.total_iters;
+        g->stats.refine_steps += a.total_outer - b.total_outer;
+        if (a.fail && result == NS_OK)
+            result = fail(a.fail & 2 ? NS_ERR_NONFINITE : NS_ERR_NOT_CONVERGED,
+                          what + ": a pressure solve of state " + std::to_string(s) +
+                              (a.fail & 2 ? " met a non-finite residual"
+                                          : " did not reach its tolerance"));
+        if (a.fail) {
+            const int zero = 0;
+            NS_CUDA(cudaMemcpy(&g->ctl[s].fail, &zero, sizeof(int), cudaMemcpyHostToDevice));
+            ctl[s].fail = 0;
+        }
+        seen_ctl[s] = ctl[s];
+    }
+    seen_lc = lc;
+    return result;
+}
+
+// The coarse propagator's grid: a batch-1 companion with this grid's
+// description, tiled for one state (2 cells per thread along z: four times
+// the CTAs of the batched sweep's tiling), on its own high-priority stream.
+// Every coarse evaluation of Parareal runs on it, so G_new and G_old of equal
+// inputs are bit-identical.
+ns_status ensure_chain(ns_grid* g) {
+    if (g->chain) return NS_OK;
+    ns_grid_desc d = g->d;
+    d.batch = 1;
+    d.parareal_chunk = 0;
+    d.tile_z = 2;
+    d.solid_mask = g->mask_host.empty() ? nullptr : g->mask_host.data();
+    int lo = 0, hi = 0;
+    NS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    NS_CUDA(cudaStreamCreateWithPriority(&g->chain_stream, cudaStreamNonBlocking, hi));
+    NS_TRY(ns_create_grid(&d, g->chain_stream, &g->chain));
+    if (g->pipe_ev.size() < 2) {
+        for (int q = 0; q < 2; ++q) {
+            cudaEvent_t e;
+            NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            g->pipe_ev.push_back(e);
+        }
+    }
+    return NS_OK;
+}
+
+// Adds the companion's counters since `before` to this grid's.
+void merge_chain_stats(ns_grid* g, const ns_stats& before) {
+    const ns_stats& a = g->chain->stats;
+    g->stats.launches += a.launches - before.launches;
+    g->stats.steps += a.steps - before.steps;
+    g->stats.solves += a.solves - before.solves;
+    g->stats.krylov_iters += a.krylov_iters - before.krylov_iters;
+    g->stats.refine_steps += a.refine_steps - before.refine_steps;
+}
+
+// Work on the companion's stream ordered after everything issued so far on
+// this grid's stream (ev[0]); afterwards this grid's stream waits for it (ev[1]).
+template <typename F>
+ns_status on_chain(ns_grid* g, F&& fn) {
+    ns_grid* h = g->chain;
+    cudaEvent_t e0 = g->pipe_ev[0], e1 = g->pipe_ev[1];
+    NS_CUDA(cudaEventRecord(e0, g->stream));
+    NS_CUDA(cudaStreamWaitEvent(h->stream, e0, 0));
+    const ns_stats before = h->stats;
+    const ns_status st = fn(h);
+    merge_chain_stats(g, before);
+    NS_TRY(st);
+    NS_CUDA(cudaEventRecord(e1, h->stream));
+    NS_CUDA(cudaStreamWaitEvent(g->stream, e1, 0));
+    return NS_OK;
+}
+
 // One Parareal iteration with the fine sweep in chunks of `chunk` slices on
 // this grid's stream (this thread) and the serial coarse chain with the
 // update of Eq. 6 on the companion grid's stream (a second host thread).
@@ -937,33 +1077,23 @@ ns_status parareal_update(ns_grid* g, const void* const fy[4], const void* const
 // writes y_{n+1} only after the chunk holding n+1 has copied its inputs, so
 // the chain of chunk c overlaps the sweep of chunk c+1.  Every state is
 // computed by the same kernels as in the unchunked iteration (reductions do
-// not depend on the batch), so the result is bit-identical.
+// not depend on the batch, and the chain runs on the same companion), so the
+// result is bit-identical.
 template <typename T>
 ns_status parareal_iteration_chunked(ns_grid* g, ns_state slices, int N, int S, int M,
                                      double dt, int chunk, double* defect) {
     const Geo& G = g->geo;
     const int C = (N + chunk - 1) / chunk;
-    if (!g->chain) {
-        ns_grid_desc d = g->d;
-        d.batch = 1;
-        d.parareal_chunk = -1;
-        d.solid_mask = g->mask_host.empty() ? nullptr : g->mask_host.data();
-        int lo = 0, hi = 0;
-        NS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        NS_CUDA(cudaStreamCreateWithPriority(&g->chain_stream, cudaStreamNonBlocking, hi));
-        NS_TRY(ns_create_grid(&d, g->chain_stream, &g->chain));
-    }
-    if ((int)g->pipe_ev.size() < 2 * C + 2) {
-        while ((int)g->pipe_ev.size() < 2 * C + 2) {
-            cudaEvent_t e;
-            NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            g->pipe_ev.push_back(e);
-        }
+    NS_TRY(ensure_chain(g));
+    while ((int)g->pipe_ev.size() < 2 * C + 4) {
+        cudaEvent_t e;
+        NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g->pipe_ev.push_back(e);
     }
     ns_grid* h = g->chain;
-    cudaEvent_t* ev_copied = g->pipe_ev.data();
-    cudaEvent_t* ev_swept = g->pipe_ev.data() + C;
-    cudaEvent_t ev_start = g->pipe_ev[2 * C], ev_end = g->pipe_ev[2 * C + 1];
+    cudaEvent_t* ev_copied = g->pipe_ev.data() + 2;
+    cudaEvent_t* ev_swept = g->pipe_ev.data() + 2 + C;
+    cudaEvent_t ev_start = g->pipe_ev[2 * C + 2], ev_end = g->pipe_ev[2 * C + 3];
     void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
     const double dtc = dt * S / M;
     // the chain's own coarse state buffer lives in this grid's pr_g
@@ -1058,11 +1188,7 @@ ns_status parareal_iteration_chunked(ns_grid* g, ns_state slices, int N, int S, 
         cudaStreamSynchronize(g->stream);
     }
     // the chain's counters count as this grid's
-    g->stats.launches += h->stats.launches - chain0.launches;
-    g->stats.steps += h->stats.steps - chain0.steps;
-    g->stats.solves += h->stats.solves - chain0.solves;
-    g->stats.krylov_iters += h->stats.krylov_iters - chain0.krylov_iters;
-    g->stats.refine_steps += h->stats.refine_steps - chain0.refine_steps;
+    merge_chain_stats(g, chain0);
     if (st != NS_OK) return fail(st, err_fine);
     if (st_chain != NS_OK) return fail(st_chain, err_chain);
     std::memcpy(defect, h->h_defect, sizeof(double));
@@ -1093,16 +1219,21 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
             return fail(NS_ERR_ARG, "ns_parareal_iterate: resume=1 without stored coarse values "
                                     "for these slices");
     } else {
-        NS_TRY(copy_states<T>(g, ys, u0s, 0, 0, 1));
-        for (int n = 0; n < N; ++n) {
-            NS_TRY(copy_states<T>(g, ys, ys, n + 1, n, 1));
-            ns_state one{(char*)slices.u + (size_t)(n + 1) * G.cnt[0] * sizeof(T),
-                         (char*)slices.v + (size_t)(n + 1) * G.cnt[1] * sizeof(T),
-                         (char*)slices.w + (size_t)(n + 1) * G.cnt[2] * sizeof(T),
-                         (char*)slices.p + (size_t)(n + 1) * G.cnt[3] * sizeof(double), 1};
-            NS_TRY(step_impl<T>(g, one, dtc, M));
-            NS_TRY(copy_states<T>(g, g->pr_gold, ys, n, n + 1, 1));
-        }
+        // iteration 0: the serial coarse sweep y_{n+1} = G(y_n)
+        NS_TRY(ensure_chain(g));
+        NS_TRY(on_chain(g, [&](ns_grid* h) -> ns_status {
+            NS_TRY(copy_states<T>(h, ys, u0s, 0, 0, 1));
+            for (int n = 0; n < N; ++n) {
+                NS_TRY(copy_states<T>(h, ys, ys, n + 1, n, 1));
+                ns_state one{(char*)slices.u + (size_t)(n + 1) * G.cnt[0] * sizeof(T),
+                             (char*)slices.v + (size_t)(n + 1) * G.cnt[1] * sizeof(T),
+                             (char*)slices.w + (size_t)(n + 1) * G.cnt[2] * sizeof(T),
+                             (char*)slices.p + (size_t)(n + 1) * G.cnt[3] * sizeof(double), 1};
+                NS_TRY(step_impl<T>(h, one, dtc, M));
+                NS_TRY(copy_states<T>(h, g->pr_gold, ys, n, n + 1, 1));
+            }
+            return NS_OK;
+        }));
     }
     g->pr_valid = false;
     const int chunk = g->d.parareal_chunk > 0 ? g->d.parareal_chunk : 0;
@@ -1116,17 +1247,24 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
             NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
             ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
             NS_TRY(step_impl<T>(g, fb, dt, S));
-            NS_CUDA(cudaMemsetAsync(g->d_defect, 0, sizeof(unsigned long long), g->stream));
-            // serial coarse sweep with the update of Eq. 6
-            for (int n = 0; n < N; ++n) {
-                NS_TRY(copy_states<T>(g, g->pr_g, ys, 0, n, 1));
-                NS_TRY(step_impl<T>(g, gs, dtc, M));
-                NS_TRY(parareal_update<T>(g, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
-            }
-            NS_CUDA(cudaMemcpyAsync(g->h_defect, g->d_defect, sizeof(unsigned long long),
-                                    cudaMemcpyDeviceToHost, g->stream));
+            // serial coarse sweep with the update of Eq. 6, on the companion
+            auto chain = [&](ns_grid* h) -> ns_status {
+                NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
+                for (int n = 0; n < N; ++n) {
+                    NS_TRY(copy_states<T>(h, g->pr_g, ys, 0, n, 1));
+                    NS_TRY(step_impl<T>(h, gs, dtc, M));
+                    NS_TRY(parareal_update<T>(h, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
+                }
+                return NS_OK;
+            };
+            NS_TRY(on_chain(g, [&](ns_grid* h) -> ns_status {
+                NS_TRY(chain(h));
+                NS_CUDA(cudaMemcpyAsync(h->h_defect, h->d_defect, sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, h->stream));
+                return NS_OK;
+            }));
             NS_TRY(sync_stream(g));
-            std::memcpy(&dk, g->h_defect, sizeof(double));
+            std::memcpy(&dk, g->chain->h_defect, sizeof(double));
         }
         if (defects) defects[k] = dk;
         if (!std::isfinite(dk)) {
@@ -1366,10 +1504,11 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         g->geo.n_fluid = (int)(ncell - n_solid);
     }
     if (d.preconditioner == NS_PC_MULTIGRID && st == NS_OK) {
-        // levels at or below this size run in one CTA per state: kept small,
-        // since one SM does that work (its shared memory stays under 8 KB)
+        // levels at or below this size run in one CTA per state (FP32: up to
+        // 16^3, 37 KB of shared memory; FP64 keeps that one SM's share small,
+        // its FP64 rate being low)
         const char* env = std::getenv("NS_MG_BLOCK_CELLS");
-        const int block_cells = env ? std::max(8, std::atoi(env)) : 512;
+        const int block_cells = env ? std::max(8, std::atoi(env)) : (g->fp32 ? 4096 : 512);
         g->mg = setup_mg(g, block_cells, ev, d.solid_mask != nullptr);
         if (g->mg && d.solid_mask) {
             // solid cells enter the finest level through its face codes
@@ -1433,16 +1572,9 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
             for (int q = 0; q < 3 && st == NS_OK; ++q)
                 if (cudaMemsetAsync(g->mg_vec[q], 0, ncell * ev * B, g->stream) != cudaSuccess)
                     st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
-            const cudaError_t e1 = g->fp32
-                ? cudaFuncSetAttribute(k_mg_block<float>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)g->mg_smem)
-                : cudaFuncSetAttribute(k_mg_block<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)g->mg_smem);
-            if (st == NS_OK && e1 != cudaSuccess)
-                st = fail(NS_ERR_CUDA, std::string("ns_create_grid: shared memory attribute: ") +
-                                           cudaGetErrorString(e1));
+            // k_mg_block's shared memory stays within the default 48 KB
+            // (setup_mg): no function attribute, which is process-wide and
+            // would be overwritten by every grid created later
         }
         if (st == NS_OK && cudaStreamSynchronize(g->stream) != cudaSuccess)
             st = fail(NS_ERR_CUDA, "ns_create_grid: stream synchronize failed");
@@ -1649,18 +1781,73 @@ ns_status ns_reset_stats(ns_grid* grid) {
     return NS_OK;
 }
 
+ns_status ns_step_fine_many(ns_grid* const* grids, const ns_state* states, const double* dts,
+                            const int* nsteps, int n) {
+    if (!grids || !states || !dts || !nsteps || n < 1)
+        return fail(NS_ERR_ARG, "ns_step_fine_many: null array or n < 1");
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i]) return fail(NS_ERR_ARG, "ns_step_fine_many: null grid");
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == grids[i])
+                return fail(NS_ERR_ARG, "ns_step_fine_many: a grid appears twice");
+    }
+    std::vector<cudaStream_t> own(n, nullptr);
+    std::vector<cudaStream_t> saved(n, nullptr);
+    std::vector<cudaEvent_t> ev(2 * n, nullptr);
+    ns_status st = NS_OK;
+    for (int i = 0; i < n && st == NS_OK; ++i) {
+        if (cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev[2 * i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev[2 * i + 1], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ev[2 * i], grids[i]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(own[i], ev[2 * i], 0) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, "ns_step_fine_many: stream setup failed");
+    }
+    std::vector<ns_status> res(n, NS_OK);
+    std::vector<std::string> msg(n);
+    if (st == NS_OK) {
+        std::vector<std::thread> threads;
+        for (int i = 0; i < n; ++i) {
+            saved[i] = grids[i]->stream;
+            grids[i]->stream = own[i];
+        }
+        for (int i = 0; i < n; ++i)
+            threads.emplace_back([&, i]() {
+                res[i] = step_any(grids[i], states[i], dts[i], nsteps[i], "ns_step_fine_many");
+                if (res[i] != NS_OK) msg[i] = g_last_error;
+            });
+        for (auto& t : threads) t.join();
+        for (int i = 0; i < n; ++i) {
+            grids[i]->stream = saved[i];
+            if (cudaEventRecord(ev[2 * i + 1], own[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(saved[i], ev[2 * i + 1], 0) != cudaSuccess)
+                if (st == NS_OK) st = fail(NS_ERR_CUDA, "ns_step_fine_many: join failed");
+        }
+    }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s2 : own)
+        if (s2) cudaStreamDestroy(s2);
+    if (st != NS_OK) return st;
+    for (int i = 0; i < n; ++i)
+        if (res[i] != NS_OK)
+            return fail(res[i], msg[i] + " (grid " + std::to_string(i) + ")");
+    return NS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // CUDA graphs of fine steps (several grids as concurrent branches)
 // ---------------------------------------------------------------------------
 
 struct ns_graph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaStream_t origin = nullptr;
+    // one executable graph per branch, each on its own stream: a launch forks
+    // the branches from the caller's stream and joins them back
+    std::vector<cudaGraph_t> graphs;
+    std::vector<cudaGraphExec_t> execs;
     std::vector<ns_grid*> grids;
     std::vector<int> batch, nsteps;
-    std::vector<cudaStream_t> streams;  // 3 per branch: top level, outer body, inner body
-    std::vector<cudaEvent_t> events;
+    std::vector<cudaStream_t> streams;  // 2 per branch: top level, loop bodies
+    std::vector<cudaEvent_t> events;    // per branch: done; last: fork
     std::vector<LoopCount> seen_loops;  // device loop totals at the last check
     std::vector<std::vector<SliceCtl>> seen_ctl;
     long long launched = 0;             // graph launches since the last check
@@ -1668,19 +1855,11 @@ struct ns_graph {
 
 namespace {
 
-// Kernels one preconditioned iteration launches (mg_apply twice + 3).
-long long mg_iteration_launches(const ns_grid* g) {
-    const int lc = g->plan.lc;
-    const long long apply = 1 + lc + std::max(lc - 1, 0) + 1 + lc;
-    return 2 * apply + 3;
-}
-
 void graph_free(ns_graph* gr) {
-    if (gr->exec) cudaGraphExecDestroy(gr->exec);
-    if (gr->graph) cudaGraphDestroy(gr->graph);
+    for (cudaGraphExec_t e : gr->execs) cudaGraphExecDestroy(e);
+    for (cudaGraph_t g : gr->graphs) cudaGraphDestroy(g);
     for (cudaEvent_t e : gr->events) cudaEventDestroy(e);
     for (cudaStream_t s : gr->streams) cudaStreamDestroy(s);
-    if (gr->origin) cudaStreamDestroy(gr->origin);
     delete gr;
 }
 
@@ -1712,9 +1891,7 @@ ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const d
         graph_free(gr);
         return st;
     };
-    if (cudaStreamCreateWithFlags(&gr->origin, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream creation failed"));
-    for (int i = 0; i < 3 * n; ++i) {
+    for (int i = 0; i < 2 * n; ++i) {
         cudaStream_t s;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
             return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream creation failed"));
@@ -1730,47 +1907,20 @@ ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const d
     for (int i = 0; i < n; ++i)
         if (cudaStreamSynchronize(grids[i]->stream) != cudaSuccess)
             return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream synchronisation failed"));
-    if (cudaStreamBeginCapture(gr->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess)
-        return bail(fail(NS_ERR_CUDA, "ns_graph_create: cudaStreamBeginCapture failed"));
-    ns_status st = NS_OK;
-    if (cudaEventRecord(gr->events[n], gr->origin) != cudaSuccess)
-        st = fail(NS_ERR_CUDA, "ns_graph_create: fork event failed");
-    for (int i = 0; i < n && st == NS_OK; ++i) {
-        ns_grid* g = grids[i];
-        cudaStream_t top = gr->streams[3 * i];
-        if (cudaStreamWaitEvent(top, gr->events[n], 0) != cudaSuccess) {
-            st = fail(NS_ERR_CUDA, "ns_graph_create: fork wait failed");
-            break;
-        }
-        const cudaStream_t saved = g->stream;
-        const bool prof_active = g->prof.active;
-        g->stream = top;
-        g->body_stream[0] = gr->streams[3 * i + 1];
-        g->body_stream[1] = gr->streams[3 * i + 2];
-        g->capturing = true;
-        st = g->fp32 ? step_impl<float>(g, states[i], dts[i], nsteps[i])
-                     : step_impl<double>(g, states[i], dts[i], nsteps[i]);
-        g->capturing = false;
-        g->prof.active = prof_active;
-        g->stream = saved;
-        g->body_stream[0] = g->body_stream[1] = nullptr;
-        if (st == NS_OK && (cudaEventRecord(gr->events[i], top) != cudaSuccess ||
-                            cudaStreamWaitEvent(gr->origin, gr->events[i], 0) != cudaSuccess))
-            st = fail(NS_ERR_CUDA, "ns_graph_create: join failed");
-    }
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(gr->origin, &graph);
-    gr->graph = graph;
-    if (st != NS_OK) return bail(st);
-    if (e != cudaSuccess)
-        return bail(fail(NS_ERR_CUDA, std::string("ns_graph_create: cudaStreamEndCapture: ") +
-                                          cudaGetErrorString(e)));
-    const cudaError_t ei = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
-    if (ei != cudaSuccess)
-        return bail(fail(NS_ERR_CUDA, std::string("ns_graph_create: cudaGraphInstantiate: ") +
-                                          cudaGetErrorString(ei)));
     for (int i = 0; i < n; ++i) {
         ns_grid* g = grids[i];
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        const ns_status st = capture_exec(
+            g, gr->streams[2 * i], gr->streams[2 * i + 1],
+            [&]() -> ns_status {
+                return g->fp32 ? step_impl<float>(g, states[i], dts[i], nsteps[i])
+                               : step_impl<double>(g, states[i], dts[i], nsteps[i]);
+            },
+            &graph, &exec);
+        if (st != NS_OK) return bail(st);
+        gr->graphs.push_back(graph);
+        gr->execs.push_back(exec);
         gr->grids.push_back(g);
         gr->batch.push_back(states[i].batch);
         gr->nsteps.push_back(nsteps[i]);
@@ -1788,8 +1938,17 @@ ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const d
 }
 
 ns_status ns_graph_launch(ns_graph* gr, void* cuda_stream) {
-    if (!gr || !gr->exec) return fail(NS_ERR_ARG, "ns_graph_launch: null graph");
-    NS_CUDA(cudaGraphLaunch(gr->exec, (cudaStream_t)cuda_stream));
+    if (!gr || gr->execs.empty()) return fail(NS_ERR_ARG, "ns_graph_launch: null graph");
+    const cudaStream_t cs = (cudaStream_t)cuda_stream;
+    const size_t n = gr->execs.size();
+    NS_CUDA(cudaEventRecord(gr->events[n], cs));
+    for (size_t i = 0; i < n; ++i) {
+        const cudaStream_t bs = gr->streams[2 * i];
+        NS_CUDA(cudaStreamWaitEvent(bs, gr->events[n], 0));
+        NS_CUDA(cudaGraphLaunch(gr->execs[i], bs));
+        NS_CUDA(cudaEventRecord(gr->events[i], bs));
+    }
+    for (size_t i = 0; i < n; ++i) NS_CUDA(cudaStreamWaitEvent(cs, gr->events[i], 0));
     gr->launched += 1;
     return NS_OK;
 }
@@ -1798,50 +1957,23 @@ ns_status ns_graph_check(ns_graph* gr, void* cuda_stream) {
     if (!gr) return fail(NS_ERR_ARG, "ns_graph_check: null graph");
     NS_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
     ns_status result = NS_OK;
+    std::string msg;
     for (size_t i = 0; i < gr->grids.size(); ++i) {
-        ns_grid* g = gr->grids[i];
-        const int B = gr->batch[i];
-        LoopCount lc{};
-        std::vector<SliceCtl> ctl(B);
-        NS_CUDA(cudaMemcpy(&lc, g->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
-        NS_CUDA(cudaMemcpy(ctl.data(), g->ctl, sizeof(SliceCtl) * B, cudaMemcpyDeviceToHost));
-        const LoopCount& l0 = gr->seen_loops[i];
-        const long long bodies = (long long)(lc.inner_total - l0.inner_total);
-        const long long steps = gr->launched * gr->nsteps[i];
-        g->stats.steps += steps * B;
-        // per step: predict, divergence, solve start, loop condition, correction;
-        // per loop body: one iteration, (FP32) the outer correction, the condition
-        g->stats.launches +=
-            steps * 5 + bodies * (mg_iteration_launches(g) + (g->fp32 ? 2 : 1));
-        for (int s = 0; s < B; ++s) {
-            const SliceCtl& a = ctl[s];
-            const SliceCtl& b = gr->seen_ctl[i][s];
-            g->stats.solves += a.total_solves - b.total_solves;
-            g->stats.krylov_iters += a.total_iters - b.total_iters;
-            g->stats.refine_steps += a.total_outer - b.total_outer;
-            if (a.fail && result == NS_OK) {
-                result = fail(a.fail & 2 ? NS_ERR_NONFINITE : NS_ERR_NOT_CONVERGED,
-                              "ns_graph_check: a pressure solve of branch " + std::to_string(i) +
-                                  ", state " + std::to_string(s) +
-                                  (a.fail & 2 ? " met a non-finite residual"
-                                              : " did not reach its tolerance"));
-            }
-            if (a.fail) {
-                const int zero = 0;
-                NS_CUDA(cudaMemcpy(&g->ctl[s].fail, &zero, sizeof(int), cudaMemcpyHostToDevice));
-                ctl[s].fail = 0;
-            }
+        const ns_status st = account_graph(
+            gr->grids[i], gr->batch[i], gr->launched * gr->nsteps[i], 0, gr->seen_loops[i],
+            gr->seen_ctl[i].data(), "ns_graph_check: branch " + std::to_string(i));
+        if (st != NS_OK && result == NS_OK) {
+            result = st;
+            msg = g_last_error;
         }
-        gr->seen_loops[i] = lc;
-        gr->seen_ctl[i] = ctl;
     }
     gr->launched = 0;
-    return result;
+    return result == NS_OK ? NS_OK : fail(result, msg);
 }
 
 ns_status ns_graph_destroy(ns_graph* gr) {
     if (!gr) return NS_OK;
-    if (gr->origin) cudaStreamSynchronize(gr->origin);
+    for (cudaStream_t s : gr->streams) cudaStreamSynchronize(s);
     graph_free(gr);
     return NS_OK;
 }

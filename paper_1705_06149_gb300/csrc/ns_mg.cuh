@@ -553,9 +553,24 @@ __device__ __forceinline__ T lap_smem(const Lev& L, const T* a, int i, int j, in
     return lap_lev(L, v, i, j, k, a[lindex(L, i, j, k)]);
 }
 
+// Cells per thread the one-CTA levels may hold (MG_BLOCK_THREADS threads).
+constexpr int MG_BLOCK_PER_THREAD = 4;
+constexpr int MG_BLOCK_MAX_CELLS = MG_BLOCK_THREADS * MG_BLOCK_PER_THREAD;
+
+// (i, j, k) of linear index q on a level (32-bit: the one-CTA levels are small).
+__device__ __forceinline__ void lev_ijk(const Lev& L, unsigned q, int& i, int& j, int& k) {
+    const unsigned nx = (unsigned)L.n[0], nxy = nx * (unsigned)L.n[1];
+    k = (int)(q / nxy);
+    const unsigned r = q - (unsigned)k * nxy;
+    j = (int)(r / nx);
+    i = (int)(r - (unsigned)j * nx);
+}
+
 // V(2,0) cycle on levels plan.lc .. nlev-1 for the right side `in` (global,
 // level lc); writes the result to `out` (global, level lc).  Shared memory per
-// level m: b_m, y_m, t_m.
+// level m: the right side b_m and the iterate y_m; a Jacobi sweep that reads
+// neighbours of y_m stages its results in registers (at most
+// MG_BLOCK_PER_THREAD cells per thread) and writes them back after a barrier.
 template <typename T>
 __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     k_mg_block(MgPlan plan, SliceCtl* __restrict__ ctl, const T* __restrict__ in_even,
@@ -569,45 +584,63 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     const int lc = plan.lc, nl = plan.nlev;
     T* bq[MG_MAX_LEVELS];
     T* yq[MG_MAX_LEVELS];
-    T* tq[MG_MAX_LEVELS];
     {
         long long o = 0;
         for (int m = lc; m < nl; ++m) {
             const long long n = plan.lev[m].cells;
             bq[m] = sm + o;
             yq[m] = sm + o + n;
-            tq[m] = sm + o + 2 * n;
-            o += 3 * n;
+            o += 2 * n;
         }
     }
-    const int t = threadIdx.x;
+    const unsigned t = threadIdx.x, nt = blockDim.x;
     const T w = T(MG_OMEGA);
+    // w / diagonal at a cell
+    auto wdiag = [&](const Lev& L, int i, int j, int k) -> T {
+        return -neg_over<T>(w, diag_at<T>(L, i, j, k));
+    };
+    // one Jacobi sweep y <- y + w (b - L y) / d over a level, in place
+    auto sweep = [&](int m) {
+        const Lev& L = plan.lev[m];
+        const unsigned cells = (unsigned)L.cells;
+        T nv[MG_BLOCK_PER_THREAD];
+#pragma unroll
+        for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
+            const unsigned q = t + c * nt;
+            if (q < cells) {
+                int i, j, k;
+                lev_ijk(L, q, i, j, k);
+                nv[c] = yq[m][q] + wdiag(L, i, j, k) * (bq[m][q] - lap_smem(L, yq[m], i, j, k));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
+            const unsigned q = t + c * nt;
+            if (q < cells) yq[m][q] = nv[c];
+        }
+        __syncthreads();
+    };
     {
         const Lev& L = plan.lev[lc];
         const T* __restrict__ src = in + s * L.cells;
-        for (long long q = t; q < L.cells; q += blockDim.x) bq[lc][q] = src[q];
+        for (unsigned q = t; q < (unsigned)L.cells; q += nt) bq[lc][q] = src[q];
     }
     __syncthreads();
     // down: two Jacobi sweeps from zero, restrict the residual
     for (int m = lc; m < nl - 1; ++m) {
         const Lev& L = plan.lev[m];
         const Lev& Lc = plan.lev[m + 1];
-        for (long long q = t; q < L.cells; q += blockDim.x) {
-            const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
-                      k = int(q / ((long long)L.n[0] * L.n[1]));
-            tq[m][q] = w * bq[m][q] / diag_at<T>(L, i, j, k);
+        for (unsigned q = t; q < (unsigned)L.cells; q += nt) {
+            int i, j, k;
+            lev_ijk(L, q, i, j, k);
+            yq[m][q] = wdiag(L, i, j, k) * bq[m][q];
         }
         __syncthreads();
-        for (long long q = t; q < L.cells; q += blockDim.x) {
-            const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
-                      k = int(q / ((long long)L.n[0] * L.n[1]));
-            yq[m][q] = tq[m][q] + w * (bq[m][q] - lap_smem(L, tq[m], i, j, k)) /
-                                      diag_at<T>(L, i, j, k);
-        }
-        __syncthreads();
-        for (long long q = t; q < Lc.cells; q += blockDim.x) {
-            const int I = int(q % Lc.n[0]), J = int((q / Lc.n[0]) % Lc.n[1]),
-                      K = int(q / ((long long)Lc.n[0] * Lc.n[1]));
+        sweep(m);
+        for (unsigned q = t; q < (unsigned)Lc.cells; q += nt) {
+            int I, J, K;
+            lev_ijk(Lc, q, I, J, K);
             T acc = T(0);
             for (int dz = 0; dz < 2; ++dz)
                 for (int dy = 0; dy < 2; ++dy)
@@ -620,38 +653,24 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
         }
         __syncthreads();
     }
-    // coarsest level: Jacobi sweeps from zero (ping-pong y / t)
+    // coarsest level: Jacobi sweeps from zero
     {
         const int m = nl - 1;
         const Lev& L = plan.lev[m];
-        for (long long q = t; q < L.cells; q += blockDim.x) yq[m][q] = T(0);
+        for (unsigned q = t; q < (unsigned)L.cells; q += nt) yq[m][q] = T(0);
         __syncthreads();
-        T* a = yq[m];  // ping-pong pair: not restrict-qualified
-        T* b = tq[m];
-        // enough sweeps for the coarsest level's size (an even count, so the
-        // result ends in yq[m]); a 2^3 level needs few
+        // enough sweeps for the coarsest level's size; a 2^3 level needs few
         const int nmax = max(L.n[0], max(L.n[1], L.n[2]));
         const int sweeps = min(MG_COARSEST_SWEEPS, 4 * ((nmax + 1) / 2) * 2);
-        for (int sweep = 0; sweep < sweeps; ++sweep) {
-            for (long long q = t; q < L.cells; q += blockDim.x) {
-                const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
-                          k = int(q / ((long long)L.n[0] * L.n[1]));
-                b[q] = a[q] + w * (bq[m][q] - lap_smem(L, a, i, j, k)) / diag_at<T>(L, i, j, k);
-            }
-            __syncthreads();
-            T* tmp = a;
-            a = b;
-            b = tmp;
-        }
-        // an even number of sweeps: the result is back in yq[m]
+        for (int q = 0; q < sweeps; ++q) sweep(m);
     }
     // up: add the prolonged coarse correction
     for (int m = nl - 2; m >= lc; --m) {
         const Lev& L = plan.lev[m];
         const Lev& Lc = plan.lev[m + 1];
-        for (long long q = t; q < L.cells; q += blockDim.x) {
-            const int i = int(q % L.n[0]), j = int((q / L.n[0]) % L.n[1]),
-                      k = int(q / ((long long)L.n[0] * L.n[1]));
+        for (unsigned q = t; q < (unsigned)L.cells; q += nt) {
+            int i, j, k;
+            lev_ijk(L, q, i, j, k);
             yq[m][q] += prolong_at(Lc, yq[m + 1], i, j, k);
         }
         __syncthreads();
@@ -659,7 +678,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     {
         const Lev& L = plan.lev[lc];
         T* __restrict__ dst = out + s * L.cells;
-        for (long long q = t; q < L.cells; q += blockDim.x) dst[q] = yq[lc][q];
+        for (unsigned q = t; q < (unsigned)L.cells; q += nt) dst[q] = yq[lc][q];
     }
 }
 

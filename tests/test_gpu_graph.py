@@ -125,3 +125,39 @@ def test_graph_rejects_bad_branches():
     assert e.value.status == N.NS_ERR_ARG
     with pytest.raises(NSError):
         StepGraph([(g, st, -1.0, 1)])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_step_fine_many_reproduces_the_stream_path(prec):
+    """Several grids of different shapes and Reynolds numbers advanced at once
+    (a stream and host thread per grid) give what each grid's own calls give."""
+    from paper_1705_06149_gb300 import step_fine_many
+    _, solid = inputs.obstacle_boxes(CASES[2][0], seed=1, count=2, edge=(0.15, 0.3))
+    branches, refs = [], []
+    dts, nsteps = [1e-3, 2e-3, 1e-3], [3, 2, 4]
+    for k in range(3):
+        g, inits = make(prec, k, solid if k == 2 else None)
+        branches.append((g, stack(g, inits), dts[k], nsteps[k]))
+        refs.append(stack(g, inits))
+    step_fine_many(branches)
+    step_fine_many(branches)
+    for k, (g, a, dt, n) in enumerate(branches):
+        g.step_fine(refs[k], dt, n)
+        g.step_fine(refs[k], dt, n)
+        for c in range(4):
+            assert torch.equal(a.fields()[c], refs[k].fields()[c]), (k, c)
+
+
+def test_step_fine_many_reports_the_failing_grid():
+    from paper_1705_06149_gb300 import step_fine_many
+    good = Grid(16, 16, 16, batch=1)
+    bad = Grid(16, 16, 16, batch=1, poisson_rtol=1e-30, poisson_maxit=3)
+    init = inputs.random_state(16, 16, 16, seed=9, sigma=0.2)
+    with pytest.raises(NSError) as e:
+        step_fine_many([(good, good.state_from(init), 1e-3, 2),
+                        (bad, bad.state_from(init), 1e-3, 2)])
+    assert e.value.status == N.NS_ERR_NOT_CONVERGED
+    assert "grid 1" in str(e.value)
+    with pytest.raises(NSError) as e:
+        step_fine_many([(good, good.zeros(1), 1e-3, 1), (good, good.zeros(1), 1e-3, 1)])
+    assert e.value.status == N.NS_ERR_ARG
