@@ -115,6 +115,17 @@ struct ns_grid {
     ns_grid* chain = nullptr;
     cudaStream_t chain_stream = nullptr;
     std::vector<cudaEvent_t> pipe_ev;
+    // the coarse chain of an iteration as one CUDA graph on the companion
+    // (rebuilt when the slices, their count, the coarse steps or buffers change)
+    cudaStream_t chain_cap[2] = {nullptr, nullptr};
+    cudaGraph_t chain_graph = nullptr;
+    cudaGraphExec_t chain_exec = nullptr;
+    const void* chain_key_ys = nullptr;
+    const void* chain_key_f = nullptr;
+    int chain_key_n = 0, chain_key_m = 0;
+    double chain_key_dt = 0.0;
+    LoopCount chain_seen_lc{};
+    SliceCtl chain_seen_ctl{};
     std::vector<void*> allocs;
 };
 
@@ -1070,6 +1081,33 @@ ns_status on_chain(ns_grid* g, F&& fn) {
     return NS_OK;
 }
 
+// Captures (or reuses) the coarse chain of an iteration -- build() issues it
+// on the companion -- as one executable graph.
+template <typename F>
+ns_status ensure_chain_graph(ns_grid* g, const void* ys, int N, int M, double dtc, F&& build) {
+    if (g->chain_exec && g->chain_key_ys == ys && g->chain_key_f == g->pr_f[0] &&
+        g->chain_key_n == N && g->chain_key_m == M && g->chain_key_dt == dtc)
+        return NS_OK;
+    if (g->chain_exec) cudaGraphExecDestroy(g->chain_exec);
+    if (g->chain_graph) cudaGraphDestroy(g->chain_graph);
+    g->chain_exec = nullptr;
+    g->chain_graph = nullptr;
+    for (cudaStream_t& cs : g->chain_cap)
+        if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    ns_grid* h = g->chain;
+    NS_CUDA(cudaStreamSynchronize(h->stream));
+    NS_TRY(capture_exec(h, g->chain_cap[0], g->chain_cap[1], build, &g->chain_graph,
+                        &g->chain_exec));
+    g->chain_key_ys = ys;
+    g->chain_key_f = g->pr_f[0];
+    g->chain_key_n = N;
+    g->chain_key_m = M;
+    g->chain_key_dt = dtc;
+    NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
+    NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
+    return NS_OK;
+}
+
 // One Parareal iteration with the fine sweep in chunks of `chunk` slices on
 // this grid's stream (this thread) and the serial coarse chain with the
 // update of Eq. 6 on the companion grid's stream (a second host thread).
@@ -1258,7 +1296,18 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
                 return NS_OK;
             };
             NS_TRY(on_chain(g, [&](ns_grid* h) -> ns_status {
-                NS_TRY(chain(h));
+                if (!h->mg) {
+                    NS_TRY(chain(h));
+                } else {
+                    // the whole chain is one graph launch: its solver loops
+                    // run on the device, with no host round trip per solve
+                    NS_TRY(ensure_chain_graph(g, slices.u, N, M, dtc, [&]() { return chain(h); }));
+                    NS_CUDA(cudaGraphLaunch(g->chain_exec, h->stream));
+                    NS_CUDA(cudaStreamSynchronize(h->stream));
+                    // N x M coarse steps, plus the 4 update kernels per slice
+                    NS_TRY(account_graph(h, 1, (long long)N * M, 4LL * N, g->chain_seen_lc,
+                                         &g->chain_seen_ctl, "ns_parareal_iterate"));
+                }
                 NS_CUDA(cudaMemcpyAsync(h->h_defect, h->d_defect, sizeof(unsigned long long),
                                         cudaMemcpyDeviceToHost, h->stream));
                 return NS_OK;
@@ -1591,6 +1640,10 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
 ns_status ns_destroy_grid(ns_grid* grid) {
     if (!grid) return NS_OK;
     cudaStreamSynchronize(grid->stream);
+    if (grid->chain_exec) cudaGraphExecDestroy(grid->chain_exec);
+    if (grid->chain_graph) cudaGraphDestroy(grid->chain_graph);
+    for (cudaStream_t cs : grid->chain_cap)
+        if (cs) cudaStreamDestroy(cs);
     if (grid->chain) ns_destroy_grid(grid->chain);
     if (grid->chain_stream) cudaStreamDestroy(grid->chain_stream);
     for (cudaEvent_t e : grid->pipe_ev) cudaEventDestroy(e);
