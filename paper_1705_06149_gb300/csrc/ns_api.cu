@@ -245,6 +245,9 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
         L.by = ceil_div(L.n[1], TY);
         L.bz = ceil_div(L.n[2], L.tz);
         L.ctas = L.bx * L.by * L.bz;
+        L.rbx = ceil_div(L.n[0], 16);
+        L.rby = ceil_div(L.n[1], 8);
+        L.rctas = L.rbx * L.rby * L.bz;
     };
     Lev L0{};
     for (int a = 0; a < 3; ++a) {
@@ -481,7 +484,7 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
         const T* bsrc_odd = l == 0 ? src_odd : nullptr;
         const T* ysrc = l == 0 ? dst : mb.Yl[l];
         NS_LAUNCH(g, l == 0 ? NS_K_MG_RESTRICT0 : NS_K_MG_COARSE, 0,
-                  k_mg_restrict<T><<<dim3(P.lev[l].ctas, batch), blk, 0, g->stream>>>(
+                  k_mg_restrict<T><<<dim3(P.lev[l].rctas, batch), blk, 0, g->stream>>>(
                       P.lev[l], P.lev[l + 1], g->ctl, bsrc, bsrc_odd, ysrc, mb.B[l + 1]));
         if (l + 1 < lc)
             NS_LAUNCH(g, NS_K_MG_COARSE, 0,

@@ -47,6 +47,7 @@ struct Lev {
     float lih2[3];  // ih2 - fih2 (the FP32 remainder: fih2 + lih2 = ih2 to ~2^-48)
     long long cells;
     int tz, bx, by, bz, ctas;
+    int rbx, rby, rctas;   // restriction tiling: 16 x 8 cells per CTA plane
 };
 
 template <typename T> __device__ __forceinline__ T lw(const Lev& L, int d);
@@ -406,10 +407,24 @@ __global__ void __launch_bounds__(NTHREADS)
     axis_nbr(j, L.n[1], L.bc[1], jl, jh, act);
     const T dxc = diag_axis<T>(L, 0, i), dxl = diag_axis<T>(L, 0, il), dxh = diag_axis<T>(L, 0, ih_);
     const T dyc = diag_axis<T>(L, 1, j), dyl = diag_axis<T>(L, 1, jl), dyh = diag_axis<T>(L, 1, jh);
+    // weights w / d where the cell and both z neighbours are interior in z
+    // (the same expressions as the general case, evaluated once)
+    const T dz2 = T(2) * lw<T>(L, 2);
+    const T icI = neg_over<T>(w, dxc + dyc + dz2);
+    const T icxhI = neg_over<T>(w, dxh + dyc + dz2), icxlI = neg_over<T>(w, dxl + dyc + dz2);
+    const T icyhI = neg_over<T>(w, dxc + dyh + dz2), icylI = neg_over<T>(w, dxc + dyl + dz2);
+    // the source at the z neighbour below and at the cell, carried along the
+    // march (each value is computed once per thread, as the neighbours' are)
+    const bool roll = PRE && L.fcode == nullptr;
+    T zlo = T(0), zc = T(0);
     for (int k = k0; k < k1; ++k) {
         const Nbr nb = make_nbr(L, i, j, k);
         const int id = nb.c;
-        const T bc = srcq(id);
+        if (roll && k == k0) {
+            zlo = srcq(nb.lo[2]);
+            zc = srcq(id);
+        }
+        const T bc = roll ? zc : srcq(id);
         if (MODE == SRC_P) {
             pn[id] = bc;
             if (restart && !first) rh[id] = r[id];
@@ -431,21 +446,37 @@ __global__ void __launch_bounds__(NTHREADS)
                               lw<T>(L, 2);
             y[id] = y0c + ic * (bc - lap);
         } else if (PRE) {
-            int kl, kh;
-            axis_nbr(k, L.n[2], L.bc[2], kl, kh, act);
-            const T dzc = diag_axis<T>(L, 2, k), dzl = diag_axis<T>(L, 2, kl),
-                    dzh = diag_axis<T>(L, 2, kh);
+            const T zhi = srcq(nb.hi[2]);
             // y0 = w b / d at the cell and its neighbours (d = -(dx + dy + dz))
-            const T ic = neg_over<T>(w, dxc + dyc + dzc);
+            T ic, icxh, icxl, icyh, icyl, iczh, iczl;
+            if (L.bc[2] == BC_PERIODIC || (k >= 2 && k + 2 < L.n[2])) {
+                ic = icI;
+                icxh = icxhI;
+                icxl = icxlI;
+                icyh = icyhI;
+                icyl = icylI;
+                iczh = iczl = icI;
+            } else {
+                int kl, kh;
+                axis_nbr(k, L.n[2], L.bc[2], kl, kh, act);
+                const T dzc = diag_axis<T>(L, 2, k), dzl = diag_axis<T>(L, 2, kl),
+                        dzh = diag_axis<T>(L, 2, kh);
+                ic = neg_over<T>(w, dxc + dyc + dzc);
+                icxh = neg_over<T>(w, dxh + dyc + dzc);
+                icxl = neg_over<T>(w, dxl + dyc + dzc);
+                icyh = neg_over<T>(w, dxc + dyh + dzc);
+                icyl = neg_over<T>(w, dxc + dyl + dzc);
+                iczh = neg_over<T>(w, dxc + dyc + dzh);
+                iczl = neg_over<T>(w, dxc + dyc + dzl);
+            }
             const T y0c = ic * bc;
             const T lap =
-                (neg_over<T>(w, dxh + dyc + dzc) * srcq(nb.hi[0]) +
-                 neg_over<T>(w, dxl + dyc + dzc) * srcq(nb.lo[0]) - T(2) * y0c) * lw<T>(L, 0) +
-                (neg_over<T>(w, dxc + dyh + dzc) * srcq(nb.hi[1]) +
-                 neg_over<T>(w, dxc + dyl + dzc) * srcq(nb.lo[1]) - T(2) * y0c) * lw<T>(L, 1) +
-                (neg_over<T>(w, dxc + dyc + dzh) * srcq(nb.hi[2]) +
-                 neg_over<T>(w, dxc + dyc + dzl) * srcq(nb.lo[2]) - T(2) * y0c) * lw<T>(L, 2);
+                (icxh * srcq(nb.hi[0]) + icxl * srcq(nb.lo[0]) - T(2) * y0c) * lw<T>(L, 0) +
+                (icyh * srcq(nb.hi[1]) + icyl * srcq(nb.lo[1]) - T(2) * y0c) * lw<T>(L, 1) +
+                (iczh * zhi + iczl * zlo - T(2) * y0c) * lw<T>(L, 2);
             y[id] = y0c + ic * (bc - lap);
+            zlo = bc;
+            zc = zhi;
         }
     }
 }
@@ -464,9 +495,17 @@ __global__ void __launch_bounds__(NTHREADS)
         (bsrc_odd != nullptr && iter_parity(ctl + s) ? bsrc_odd : bsrc) + s * L.cells;
     const T* __restrict__ y = ysrc + s * L.cells;
     T* __restrict__ bc = bdst + s * Lc.cells;
-    __shared__ T row[TY][TX / 2];
-    int i, j, k0;
-    lev_origin(L, blockIdx.x, i, j, k0);
+    // a warp covers 16 x 2 cells: the x pair of a child octet is lanes
+    // (l, l^1), the y pair lanes (l, l^16), the z pair two steps of the march,
+    // so the octet sums need no shared memory (sizes are even on every level
+    // that is restricted, and tiles start at even indices)
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int tx = blockIdx.x % L.rbx;
+    const int rest = blockIdx.x / L.rbx;
+    const int ty = rest % L.rby;
+    const int i = tx * 16 + (lane & 15);
+    const int j = ty * 8 + warp * 2 + (lane >> 4);
+    const int k0 = (rest / L.rby) * L.tz;
     const bool in = i < L.n[0] && j < L.n[1];
     const int k1 = min(k0 + L.tz, L.n[2]);
     auto yq = [&](int q) -> T { return y[q]; };
@@ -477,15 +516,11 @@ __global__ void __launch_bounds__(NTHREADS)
             const Nbr nb = make_nbr(L, i, j, k);
             res = b[nb.c] - lap_nbr(L, nb, yq, y[nb.c]);
         }
-        res += __shfl_xor_sync(0xffffffffu, res, 1);  // x pair
-        if ((threadIdx.x & 1) == 0) row[threadIdx.y][threadIdx.x >> 1] = res;
-        __syncthreads();
-        if ((threadIdx.x & 1) == 0 && (threadIdx.y & 1) == 0)
-            accz += row[threadIdx.y][threadIdx.x >> 1] + row[threadIdx.y + 1][threadIdx.x >> 1];
-        __syncthreads();
+        res += __shfl_xor_sync(0xffffffffu, res, 1);   // x pair
+        res += __shfl_xor_sync(0xffffffffu, res, 16);  // y pair
+        accz += res;
         if ((k & 1) == 1) {  // z pair complete
-            if (in && (threadIdx.x & 1) == 0 && (threadIdx.y & 1) == 0)
-                bc[lindex(Lc, i >> 1, j >> 1, k >> 1)] = accz * T(0.125);
+            if (in && (lane & 17) == 0) bc[lindex(Lc, i >> 1, j >> 1, k >> 1)] = accz * T(0.125);
             accz = T(0);
         }
     }
