@@ -64,13 +64,15 @@ WORDS_MG = {"krylov_A": 5, "mg_restrict0": 2.125, "mg_prolong0": 2.125, "mg_lap_
 WORDS_PLAIN = {"krylov_A": 6, "krylov_B": 3, "krylov_C": 8}
 
 # Bytes per cell per launch of the step and refinement kernels, FP32+refine
-# path (velocities and increments FP32, pressure and residual FP64):
-#   predict     u, v, w -> dt*RHS increments:            3*4 + 3*4
-#   divergence  increments -> b (FP64):                   3*4 + 8
-#   correct     u, increments, p64, p -> u, p, p_keep:    3*4 + 3*4 + 8 + 8 + 3*4 + 8 + 8
-#   solve_init  b, p, p_prev -> b, p64, r64, r, r_hat:    3*8 + 3*8 + 2*4
-#   refine      p64, r64, e -> p64, r64, r, r_hat:        2*8 + 4 + 2*8 + 2*4
-BYTES_STEP_FP32 = {"predict": 24, "divergence": 20, "correct": 68, "solve_init": 56,
+# multigrid path (velocities and increments FP32; b and the caller's p FP64;
+# the iterate p, residual r, warm start w and last pressure q float-float,
+# 8 bytes each):
+#   predict     u, v, w -> dt*RHS increments:             3*4 + 3*4
+#   divergence  increments -> b (FP64):                    3*4 + 8
+#   correct     u, increments, p, q -> u, p (FP64), w, q:  3*4 + 3*4 + 8 + 8 + 3*4 + 8 + 8 + 8
+#   solve_init  b, w -> p, r, r32, r_hat:                   8 + 8 + 8 + 8 + 2*4
+#   refine      p, r, e -> p, r, r32, r_hat:                8 + 8 + 4 + 8 + 8 + 2*4
+BYTES_STEP_FP32 = {"predict": 24, "divergence": 20, "correct": 76, "solve_init": 40,
                    "refine": 44}
 
 
@@ -78,8 +80,8 @@ KERNEL_NAMES = {"krylov_A": "k_mg_src<SRC_P> / k_bicg_A", "krylov_B": "k_mg_src<
                 "krylov_C": "k_mg_update / k_bicg_C", "mg_lap_v": "k_mg_lapdot_v",
                 "mg_lap_t": "k_mg_lapdot_t", "mg_restrict0": "k_mg_restrict (finest)",
                 "mg_prolong0": "k_mg_prolong (finest)", "predict": "k_predict_tile",
-                "divergence": "k_divergence", "correct": "k_correct",
-                "solve_init": "k_mg_refine_init", "refine": "k_mg_refine_update"}
+                "divergence": "k_divergence", "correct": "k_correct_ff",
+                "solve_init": "k_mg_refine_init_ff", "refine": "k_mg_refine_update_ff"}
 
 
 def parse():

@@ -70,6 +70,8 @@ typedef struct {
     double refine_rtol;      /* FP32_REFINE: outer FP64 relative residual target     */
     double inner_rtol;       /* FP32_REFINE: inner FP32 relative residual per outer
                                 step (<= 0: 1e-4)                                    */
+    int refine_maxit;        /* FP32_REFINE: outer corrections per solve before
+                                NS_ERR_NOT_CONVERGED (<= 0: 40)                      */
     int batch;               /* capacity: largest batch one call may advance (>= 1)  */
     int preconditioner;      /* ns_preconditioner: BiCGStab as in Section 2 without
                                 (NS_PC_NONE) or with one multigrid V-cycle as right

@@ -42,7 +42,8 @@ class GridDesc(ctypes.Structure):
                 ("bc", ctypes.c_int * 3), ("solid_mask", ctypes.c_void_p),
                 ("precision", ctypes.c_int), ("poisson_rtol", ctypes.c_double),
                 ("poisson_maxit", ctypes.c_int), ("refine_rtol", ctypes.c_double),
-                ("inner_rtol", ctypes.c_double), ("batch", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
+                ("batch", ctypes.c_int),
                 ("preconditioner", ctypes.c_int), ("tile_z", ctypes.c_int),
                 ("parareal_chunk", ctypes.c_int)]
 

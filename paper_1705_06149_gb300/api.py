@@ -69,7 +69,7 @@ class Grid:
                  poisson_rtol: float = 1e-12, poisson_maxit: int = 0,
                  refine_rtol: float = 1e-10, inner_rtol: float = 1e-4, batch: int = 1,
                  preconditioner: str = "multigrid", solid: Optional[np.ndarray] = None,
-                 tile_z: int = 0, parareal_chunk: int = 0,
+                 tile_z: int = 0, parareal_chunk: int = 0, refine_maxit: int = 0,
                  device: Optional[torch.device] = None):
         self.lib = N.load()
         self.device = torch.device(device) if device is not None else torch.device(
@@ -98,6 +98,7 @@ class Grid:
         desc.inner_rtol = inner_rtol
         desc.batch = batch
         desc.preconditioner = {"none": N.NS_PC_NONE, "multigrid": N.NS_PC_MULTIGRID}[preconditioner]
+        desc.refine_maxit = refine_maxit
         desc.tile_z = tile_z
         desc.parareal_chunk = parareal_chunk
         self.preconditioner = preconditioner

@@ -44,7 +44,7 @@ ns_status fail(ns_status st, const std::string& msg) {
         if (s_ != NS_OK) return s_;          \
     } while (0)
 
-constexpr int kMaxOuter = 40;
+constexpr int kMaxOuterDefault = 40;
 
 }  // namespace
 
@@ -55,6 +55,7 @@ struct ns_grid {
     int cap = 0;
     bool fp32 = false;
     int maxit = 0;
+    int max_outer = kMaxOuterDefault;  // FP32+refine: outer corrections per solve
     double inner_rtol = 1e-4;
     // workspace, [cap][...]
     void* fs[3] = {nullptr, nullptr, nullptr};  // F* (element type of the precision)
@@ -70,7 +71,9 @@ struct ns_grid {
     void* mg_Y[MG_MAX_LEVELS] = {};             // level iterates, levels 1..lc
     unsigned int* counter = nullptr;            // per state: CTAs arrived
     double* p_prev = nullptr;                   // 2 p^n - p^(n-1): the next solve's warm start
-    double* r64 = nullptr;                      // FP32+refine: FP64 outer residual
+    double* r64 = nullptr;                      // FP32+refine, plain solver: FP64 outer residual
+    float* ffb[8] = {};                         // FP32+refine, multigrid: the float-float
+                                                // iterate, residual, warm start, last p
     double* part_mg = nullptr;                  // [cap][ctas][4]
     double* part_div = nullptr;
     double* part_a = nullptr;
@@ -126,6 +129,10 @@ struct ns_grid {
     double chain_key_dt = 0.0;
     LoopCount chain_seen_lc{};
     SliceCtl chain_seen_ctl{};
+    // the chain of each chunk of the chunked schedule as a graph of its own
+    std::vector<cudaGraph_t> chunk_graph;
+    std::vector<cudaGraphExec_t> chunk_exec;
+    int chunk_key = 0;
     std::vector<void*> allocs;
 };
 
@@ -462,6 +469,38 @@ MgBuf<T> mgbuf(const ns_grid* g) {
     return m;
 }
 
+FFBuf ffbuf(const ns_grid* g) {
+    FFBuf f;
+    f.p_hi = g->ffb[0];
+    f.p_lo = g->ffb[1];
+    f.r_hi = g->ffb[2];
+    f.r_lo = g->ffb[3];
+    f.w_hi = g->ffb[4];
+    f.w_lo = g->ffb[5];
+    f.q_hi = g->ffb[6];
+    f.q_lo = g->ffb[7];
+    return f;
+}
+
+// Start of an FP32+refine multigrid solve: from the FP64 pressure p_in, or
+// (p_in null) from the extrapolated warm start the last correction wrote.
+void launch_refine_init_ff(ns_grid* g, int batch, const double* p_in, double otol2,
+                           double itol2) {
+    const Lev& L0 = g->plan.lev[0];
+    const dim3 grid(L0.ctas, batch), blk = block_dim();
+    MgBuf<float> mb = mgbuf<float>(g);
+    if (p_in)
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
+                  k_mg_refine_init_ff<true><<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, ffbuf(g),
+                      g->part_mg, otol2, itol2, g->maxit));
+    else
+        NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
+                  k_mg_refine_init_ff<false><<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, nullptr, ffbuf(g),
+                      g->part_mg, otol2, itol2, g->maxit));
+}
+
 // One application of the V-cycle to the level-0 vector the source kernel of
 // the given mode writes (src, or for SRC_P the parity's one of src / src_odd),
 // result in `dst`.
@@ -684,14 +723,14 @@ ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
     const Lev& L0 = g->plan.lev[0];
     const dim3 grid(L0.ctas, batch), blk = block_dim();
     const int cap_inner = g->maxit + 2;
-    const int cap_refine = (g->maxit + 2) * (kMaxOuter + 2);
+    const int cap_refine = (g->maxit + 2) * (g->max_outer + 2);
     if (!g->fp32) {
         MgBuf<double> mb = mgbuf<double>(g);
         const double tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
         NS_LAUNCH(g, NS_K_SOLVE_INIT, 0,
                   k_mg_init_warm<double><<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->part_mg,
-                      tol2, g->maxit));
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b,
+                      p_in ? p_in : g->p_prev, g->part_mg, tol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         cudaGraphConditionalHandle h;
         NS_TRY(make_handle(g->stream, &h));
@@ -704,10 +743,7 @@ ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
     MgBuf<float> mb = mgbuf<float>(g);
     const double otol2 = g->d.refine_rtol * g->d.refine_rtol;
     const double itol2 = g->inner_rtol * g->inner_rtol;
-    NS_LAUNCH(g, NS_K_SOLVE_INIT, 0,
-              k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
-                  L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->p64[0], g->r64,
-                  g->part_mg, otol2, itol2, g->maxit));
+    launch_refine_init_ff(g, batch, p_in, otol2, itol2);
     NS_CUDA(cudaGetLastError());
     // one loop: an inner iteration, then the outer correction of every state
     // whose inner solve has ended (k_loop_cond explains why this matches the
@@ -718,9 +754,9 @@ ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
     return add_while(g, g->body_stream[0], h, [&]() -> ns_status {
         NS_TRY(mg_iteration<float>(g, batch, itol2, 1));
         NS_LAUNCH(g, NS_K_REFINE, 0,
-                  k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->p64[0], g->r64, g->part_mg, otol2, itol2, g->maxit,
-                      kMaxOuter, 1));
+                  k_mg_refine_update_ff<<<grid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, ffbuf(g), g->part_mg, otol2, itol2, g->maxit, g->max_outer,
+                      1));
         NS_CUDA(cudaGetLastError());
         return loop_cond(g, batch, h, LC_REFINE_ITER, cap_refine);
     });
@@ -737,33 +773,30 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
         const double tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
         NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
                   k_mg_init_warm<double><<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in,
-                      g->part_mg, tol2, g->maxit));
+                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b,
+                      p_in ? p_in : g->p_prev, g->part_mg, tol2, g->maxit));
         NS_CUDA(cudaGetLastError());
         NS_TRY(run_mg<double>(g, batch, g->d.poisson_rtol, 0, &max_iters, &max_rel));
     } else {
         MgBuf<float> mb = mgbuf<float>(g);
         const double otol2 = g->d.refine_rtol * g->d.refine_rtol;
         const double itol2 = g->inner_rtol * g->inner_rtol;
-        NS_LAUNCH(g, NS_K_SOLVE_INIT, L0.cells * batch,
-                  k_mg_refine_init<<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, g->part_div, g->geo.n_fluid, g->b, p_in, g->p64[0],
-                      g->r64, g->part_mg, otol2, itol2, g->maxit));
+        launch_refine_init_ff(g, batch, p_in, otol2, itol2);
         NS_CUDA(cudaGetLastError());
         for (int m = 0;; ++m) {
             NS_TRY(poll_ctl(g, batch));
             bool any = false;
             for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].o_status == OS_REFINE;
-            if (!any || m > kMaxOuter + 1) break;
+            if (!any || m > g->max_outer + 1) break;
             // an inner solve that stops at its iteration limit still improves
             // the outer residual; any other failure ends the solve
             ns_status st = run_mg<float>(g, batch, g->inner_rtol, 1, &max_iters, nullptr);
             if (st != NS_OK && st != NS_ERR_NOT_CONVERGED) return st;
             g_last_error.clear();
             NS_LAUNCH(g, NS_K_REFINE, L0.cells * batch,
-                      k_mg_refine_update<<<grid, blk, 0, g->stream>>>(
-                          L0, mb, g->ctl, g->p64[0], g->r64, g->part_mg, otol2, itol2, g->maxit,
-                          kMaxOuter, 0));
+                      k_mg_refine_update_ff<<<grid, blk, 0, g->stream>>>(
+                          L0, mb, g->ctl, ffbuf(g), g->part_mg, otol2, itol2, g->maxit,
+                          g->max_outer, 0));
             NS_CUDA(cudaGetLastError());
         }
         for (int s = 0; s < batch; ++s) {
@@ -814,16 +847,16 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
         for (;; ++m) {
             NS_LAUNCH(g, NS_K_INNER_INIT, G.cnt[3] * batch,
                       k_inner_init<<<grid, block_dim(), 0, g->stream>>>(
-                          G, kb, g->ctl, g->part_r, g->part_c, tol2, m, kMaxOuter));
+                          G, kb, g->ctl, g->part_r, g->part_c, tol2, m, g->max_outer));
             NS_CUDA(cudaGetLastError());
             NS_TRY(poll_ctl(g, batch));
             bool any = false;
             for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].o_status == OS_REFINE;
             if (!any) break;
+            // a stalled inner solve still improves p (the outer test decides);
+            // any other failure ends the solve
             ns_status st = run_krylov<float>(g, batch, g->inner_rtol, &max_iters, nullptr);
-            if (st == NS_ERR_NONFINITE) return st;
-            // a stalled inner solve still improves p; the outer test decides
-            (void)st;
+            if (st != NS_OK && st != NS_ERR_NOT_CONVERGED) return st;
             g_last_error.clear();
             NS_LAUNCH(g, NS_K_REFINE, G.cnt[3] * batch,
                       k_refine_update<<<grid, block_dim(), 0, g->stream>>>(
@@ -900,13 +933,20 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
                       with_u ? w : nullptr, g->b, g->part_div, 1.0 / dt));
         NS_CUDA(cudaGetLastError());
         // multigrid path: from the second step of a call the solve starts from
-        // 2 p^n - p^(n-1), which the previous correction wrote into p_prev
+        // 2 p^n - p^(n-1), which the previous correction wrote (null p_in)
         const bool extrap = g->mg && n > 0;
-        NS_TRY(solve_pressure(g, B, extrap ? g->p_prev : p));
-        NS_LAUNCH(g, NS_K_CORRECT, cells,
-                  k_correct<T, INCR><<<gface, block_dim(), 0, g->stream>>>(
-                      G, g->ctl, fu, fv, fw, u, v, w, x0, x1, p, dt,
-                      g->mg && n + 1 < nsteps ? g->p_prev : nullptr));
+        NS_TRY(solve_pressure(g, B, extrap ? nullptr : p));
+        const bool keep = g->mg && n + 1 < nsteps;
+        if (INCR && g->mg)
+            NS_LAUNCH(g, NS_K_CORRECT, cells,
+                      k_correct_ff<INCR><<<gface, block_dim(), 0, g->stream>>>(
+                          G, g->ctl, (const float*)fu, (const float*)fv, (const float*)fw,
+                          (float*)u, (float*)v, (float*)w, ffbuf(g), p, dt, keep ? 1 : 0));
+        else
+            NS_LAUNCH(g, NS_K_CORRECT, cells,
+                      k_correct<T, INCR><<<gface, block_dim(), 0, g->stream>>>(
+                          G, g->ctl, fu, fv, fw, u, v, w, x0, x1, p, dt,
+                          keep ? g->p_prev : nullptr));
         NS_CUDA(cudaGetLastError());
         if (!g->capturing) g->stats.steps += B;
     }
@@ -941,9 +981,15 @@ ns_status project_impl(ns_grid* g, const ns_state& io) {
     NS_TRY(solve_pressure(g, B, g->p64[1]));
     const double* x0 = g->fp32 ? g->p64[0] : (const double*)g->kv[0];
     const double* x1 = g->fp32 ? g->p64[1] : (const double*)g->kv[0];
-    NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
-              k_correct<T, false><<<gface, block_dim(), 0, g->stream>>>(
-                  G, g->ctl, u, v, w, u, v, w, x0, x1, nullptr, 1.0));
+    if (g->fp32 && g->mg)
+        NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
+                  k_correct_ff<false><<<gface, block_dim(), 0, g->stream>>>(
+                      G, g->ctl, (const float*)u, (const float*)v, (const float*)w, (float*)u,
+                      (float*)v, (float*)w, ffbuf(g), nullptr, 1.0, 0));
+    else
+        NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
+                  k_correct<T, false><<<gface, block_dim(), 0, g->stream>>>(
+                      G, g->ctl, u, v, w, u, v, w, x0, x1, nullptr, 1.0));
     NS_CUDA(cudaGetLastError());
     return NS_OK;
 }
@@ -1108,6 +1154,102 @@ ns_status ensure_chain_graph(ns_grid* g, const void* ys, int N, int M, double dt
     g->chain_key_dt = dtc;
     NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
     NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
+    return NS_OK;
+}
+
+// One chunked iteration with every chunk's chain a graph launch: the copies
+// of all slices first, then per chunk its sweep (this thread, polling the
+// solves) and its chain (a graph on the companion's stream, after the
+// chunk's sweep), so the chain of chunk c runs while chunk c+1 is swept.  The
+// chain of chunk c writes y_{n+1} of the next chunk's first slice, which the
+// up-front copy has already taken.
+template <typename T>
+ns_status parareal_iteration_chunked_graphs(ns_grid* g, ns_state slices, int N, int S, int M,
+                                            double dt, int chunk, double* defect) {
+    const Geo& G = g->geo;
+    const int C = (N + chunk - 1) / chunk;
+    ns_grid* h = g->chain;
+    void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
+    const double dtc = dt * S / M;
+    ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
+    const bool same = (int)g->chunk_exec.size() == C && g->chunk_key == chunk &&
+                      g->chain_key_ys == ys[0] && g->chain_key_f == g->pr_f[0] &&
+                      g->chain_key_n == N && g->chain_key_m == M && g->chain_key_dt == dtc;
+    if (!same) {
+        for (cudaGraphExec_t e : g->chunk_exec) cudaGraphExecDestroy(e);
+        for (cudaGraph_t c : g->chunk_graph) cudaGraphDestroy(c);
+        g->chunk_exec.clear();
+        g->chunk_graph.clear();
+        // the whole-chain graph shares the key fields: drop it too
+        if (g->chain_exec) cudaGraphExecDestroy(g->chain_exec);
+        if (g->chain_graph) cudaGraphDestroy(g->chain_graph);
+        g->chain_exec = nullptr;
+        g->chain_graph = nullptr;
+        for (cudaStream_t& cs : g->chain_cap)
+            if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        NS_CUDA(cudaStreamSynchronize(h->stream));
+        for (int c = 0; c < C; ++c) {
+            cudaGraph_t gr;
+            cudaGraphExec_t ex;
+            const int n1 = std::min(N, (c + 1) * chunk);
+            NS_TRY(capture_exec(
+                h, g->chain_cap[0], g->chain_cap[1],
+                [&]() -> ns_status {
+                    for (int n = c * chunk; n < n1; ++n) {
+                        NS_TRY(copy_states<T>(h, g->pr_g, ys, 0, n, 1));
+                        NS_TRY(step_impl<T>(h, gs, dtc, M));
+                        NS_TRY(parareal_update<T>(h, g->pr_f, g->pr_g, g->pr_gold, ys, n, n,
+                                                  n + 1));
+                    }
+                    return NS_OK;
+                },
+                &gr, &ex));
+            g->chunk_graph.push_back(gr);
+            g->chunk_exec.push_back(ex);
+        }
+        g->chunk_key = chunk;
+        g->chain_key_ys = ys[0];
+        g->chain_key_f = g->pr_f[0];
+        g->chain_key_n = N;
+        g->chain_key_m = M;
+        g->chain_key_dt = dtc;
+        NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount),
+                           cudaMemcpyDeviceToHost));
+        NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
+    }
+    while ((int)g->pipe_ev.size() < C + 2) {
+        cudaEvent_t e;
+        NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g->pipe_ev.push_back(e);
+    }
+    cudaEvent_t ev_start = g->pipe_ev[0], ev_end = g->pipe_ev[1];
+    cudaEvent_t* ev_swept = g->pipe_ev.data() + 2;
+    NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
+    NS_CUDA(cudaEventRecord(ev_start, g->stream));
+    NS_CUDA(cudaStreamWaitEvent(h->stream, ev_start, 0));
+    NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
+    for (int c = 0; c < C; ++c) {
+        const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
+        ns_state fb{(char*)g->pr_f[0] + (size_t)n0 * G.cnt[0] * sizeof(T),
+                    (char*)g->pr_f[1] + (size_t)n0 * G.cnt[1] * sizeof(T),
+                    (char*)g->pr_f[2] + (size_t)n0 * G.cnt[2] * sizeof(T),
+                    (char*)g->pr_f[3] + (size_t)n0 * G.cnt[3] * sizeof(double), m};
+        NS_TRY(step_impl<T>(g, fb, dt, S));
+        NS_CUDA(cudaEventRecord(ev_swept[c], g->stream));
+        NS_CUDA(cudaStreamWaitEvent(h->stream, ev_swept[c], 0));
+        NS_CUDA(cudaGraphLaunch(g->chunk_exec[c], h->stream));
+    }
+    NS_CUDA(cudaMemcpyAsync(h->h_defect, h->d_defect, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, h->stream));
+    NS_CUDA(cudaEventRecord(ev_end, h->stream));
+    NS_CUDA(cudaStreamWaitEvent(g->stream, ev_end, 0));
+    NS_TRY(sync_stream(g));
+    const ns_stats chain0 = h->stats;
+    const ns_status st = account_graph(h, 1, (long long)N * M, 4LL * N, g->chain_seen_lc,
+                                       &g->chain_seen_ctl, "ns_parareal_iterate");
+    merge_chain_stats(g, chain0);
+    NS_TRY(st);
+    std::memcpy(defect, h->h_defect, sizeof(double));
     return NS_OK;
 }
 
@@ -1282,7 +1424,11 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
     for (; k < kmax; ++k) {
         double dk;
         if (chunk > 0 && chunk < N) {
-            NS_TRY(parareal_iteration_chunked<T>(g, slices, N, S, M, dt, chunk, &dk));
+            NS_TRY(ensure_chain(g));
+            if (g->chain->mg)
+                NS_TRY(parareal_iteration_chunked_graphs<T>(g, slices, N, S, M, dt, chunk, &dk));
+            else
+                NS_TRY(parareal_iteration_chunked<T>(g, slices, N, S, M, dt, chunk, &dk));
         } else {
             // F(y^k_n) for all n in one batched sweep
             NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
@@ -1524,6 +1670,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     g->fp32 = d.precision == NS_FP32_REFINE;
     g->maxit = d.poisson_maxit > 0 ? d.poisson_maxit : 20 * std::max(d.nx, std::max(d.ny, d.nz));
     g->inner_rtol = d.inner_rtol > 0 ? d.inner_rtol : 1e-4;
+    g->max_outer = d.refine_maxit > 0 ? d.refine_maxit : kMaxOuterDefault;
     setup_geo(g);
     const Geo& G = g->geo;
     const size_t B = (size_t)g->cap;
@@ -1582,7 +1729,8 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         A((void**)&g->counter, sizeof(unsigned int) * B);
         A((void**)&g->loopc, sizeof(LoopCount));
         A((void**)&g->p_prev, ncell * sizeof(double) * B);
-        if (g->fp32) A((void**)&g->r64, ncell * sizeof(double) * B);
+        if (g->fp32)
+            for (int q = 0; q < 8; ++q) A((void**)&g->ffb[q], ncell * sizeof(float) * B);
         A((void**)&g->part_mg, nparts * 4 * sizeof(double));
     }
     A((void**)&g->d_defect, sizeof(unsigned long long));
@@ -1645,6 +1793,8 @@ ns_status ns_destroy_grid(ns_grid* grid) {
     cudaStreamSynchronize(grid->stream);
     if (grid->chain_exec) cudaGraphExecDestroy(grid->chain_exec);
     if (grid->chain_graph) cudaGraphDestroy(grid->chain_graph);
+    for (cudaGraphExec_t e : grid->chunk_exec) cudaGraphExecDestroy(e);
+    for (cudaGraph_t c : grid->chunk_graph) cudaGraphDestroy(c);
     for (cudaStream_t cs : grid->chain_cap)
         if (cs) cudaStreamDestroy(cs);
     if (grid->chain) ns_destroy_grid(grid->chain);
@@ -1725,7 +1875,13 @@ ns_status ns_poisson_solve(ns_grid* grid, const double* b, double* p, int batch,
     // the face part pointed at the (unused) F* buffers
     const double* x0 = grid->fp32 ? grid->p64[0] : (const double*)grid->kv[0];
     const double* x1 = grid->fp32 ? grid->p64[1] : (const double*)grid->kv[0];
-    if (grid->fp32)
+    if (grid->fp32 && grid->mg)
+        NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
+                  k_correct_ff<false><<<gface, block_dim(), 0, grid->stream>>>(
+                      G, grid->ctl, (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2],
+                      (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2], ffbuf(grid),
+                      p, 0.0, 0));
+    else if (grid->fp32)
         NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
                   k_correct<float, false><<<gface, block_dim(), 0, grid->stream>>>(
                       G, grid->ctl, (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2],

@@ -37,6 +37,7 @@ struct SliceCtl {
     double beta;       // multigrid path: beta of the next iteration
     long long total_outer;  // graph-resident solves: refinement steps accumulated
     long long total_solves; // graph-resident solves: solves finished
+    double o_scale;    // FP32+refine: power of two the inner solve's right side carries
 };
 
 template <typename T>
@@ -745,6 +746,7 @@ __global__ void __launch_bounds__(NTHREADS)
     const double mean = c->sx / g.n_fluid;
     const T* f3[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
     T* o3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
+    const double dtih[3] = {dt * g.ih[0], dt * g.ih[1], dt * g.ih[2]};
     int i, j, k0;
     tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
     const int k1 = min(k0 + g.tz, g.n[2] + 1);
@@ -760,14 +762,14 @@ __global__ void __launch_bounds__(NTHREADS)
                 } else {
                     int lo[3] = {i, j, k};
                     lo[d] = q[d] == 0 ? g.n[d] - 1 : q[d] - 1;
-                    const double gp =
-                        (x[cindex(g, i, j, k)] - x[cindex(g, lo[0], lo[1], lo[2])]) * g.ih[d];
-                    // the pressure difference is taken in FP64; in the increment
-                    // form u + (increment - dt G p) is rounded once
+                    // dt (G p) in FP64 (dt / h folded into one factor); in the
+                    // increment form u + (increment - dt G p) is rounded once
+                    const double dgp =
+                        (x[cindex(g, i, j, k)] - x[cindex(g, lo[0], lo[1], lo[2])]) * dtih[d];
                     if (INCR)
-                        o3[d][id] = o3[d][id] + (f3[d][id] - T(dt * gp));
+                        o3[d][id] = o3[d][id] + (f3[d][id] - T(dgp));
                     else
-                        o3[d][id] = f3[d][id] - T(dt * gp);
+                        o3[d][id] = f3[d][id] - T(dgp);
                 }
             }
         }

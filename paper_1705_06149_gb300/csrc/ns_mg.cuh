@@ -62,7 +62,6 @@ template <> __device__ __forceinline__ double lw<double>(const Lev& L, int d) { 
 struct Nbr {
     int c;
     int lo[3], hi[3];
-    int act[3];  // active faces per axis (0, 1 or 2)
 };
 
 __device__ __forceinline__ void axis_nbr(int x, int n, int bc, int& lo, int& hi, int& act) {
@@ -77,23 +76,39 @@ __device__ __forceinline__ void axis_nbr(int x, int n, int bc, int& lo, int& hi,
     }
 }
 
-__device__ __forceinline__ Nbr make_nbr(const Lev& L, int i, int j, int k) {
-    Nbr b;
+// The x and y parts of a thread's neighbours, fixed along its march in z:
+// the column's base index and the offsets to its x / y neighbours.
+struct NbrXY {
+    int base;
+    int xl, xh, yl, yh;
+};
+
+__device__ __forceinline__ NbrXY make_nbr_xy(const Lev& L, int i, int j) {
+    NbrXY q;
     int lo, hi, act;
-    const int sy = L.n[0], sz = L.n[0] * L.n[1];
-    b.c = k * sz + j * sy + i;
+    const int sy = L.n[0];
+    q.base = j * sy + i;
     axis_nbr(i, L.n[0], L.bc[0], lo, hi, act);
-    b.lo[0] = b.c - i + lo;
-    b.hi[0] = b.c - i + hi;
-    b.act[0] = act;
+    q.xl = lo - i;
+    q.xh = hi - i;
     axis_nbr(j, L.n[1], L.bc[1], lo, hi, act);
-    b.lo[1] = b.c + (lo - j) * sy;
-    b.hi[1] = b.c + (hi - j) * sy;
-    b.act[1] = act;
+    q.yl = (lo - j) * sy;
+    q.yh = (hi - j) * sy;
+    return q;
+}
+
+__device__ __forceinline__ Nbr nbr_at(const Lev& L, const NbrXY& q, int k) {
+    Nbr b;
+    const int sz = L.n[0] * L.n[1];
+    b.c = k * sz + q.base;
+    b.lo[0] = b.c + q.xl;
+    b.hi[0] = b.c + q.xh;
+    b.lo[1] = b.c + q.yl;
+    b.hi[1] = b.c + q.yh;
+    int lo, hi, act;
     axis_nbr(k, L.n[2], L.bc[2], lo, hi, act);
     b.lo[2] = b.c + (lo - k) * sz;
     b.hi[2] = b.c + (hi - k) * sz;
-    b.act[2] = act;
     if (L.fcode != nullptr) {
         // faces into solid cells (and every face of a solid cell) are dropped:
         // the neighbour is clamped to the cell itself, as at a wall
@@ -102,10 +117,13 @@ __device__ __forceinline__ Nbr make_nbr(const Lev& L, int i, int j, int k) {
         for (int a = 0; a < 3; ++a) {
             if (!(m & (1u << (2 * a)))) b.lo[a] = b.c;
             if (!(m & (2u << (2 * a)))) b.hi[a] = b.c;
-            b.act[a] = __popc((m >> (2 * a)) & 3u);
         }
     }
     return b;
+}
+
+__device__ __forceinline__ Nbr make_nbr(const Lev& L, int i, int j, int k) {
+    return nbr_at(L, make_nbr_xy(L, i, j), k);
 }
 
 // Cell is fluid (always true without solid cells).
@@ -130,10 +148,37 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// L e at a cell, as a double, for FP32 e: per axis the second difference
+// A float-float number hi + lo (|lo| <= ulp(hi) / 2 after normalisation):
+// about 48 significant bits on the FP32 pipe.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_norm(float s, float e) {  // |s| >= |e|
+    const float h = s + e;
+    return FF{h, e - (h - s)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return ff_norm(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    return ff_norm(s, e + a.lo);
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_from_double(double d) {
+    const float h = float(d);
+    return FF{h, float(d - double(h))};
+}
+__device__ __forceinline__ double ff_to_double(FF a) { return double(a.hi) + double(a.lo); }
+
+// L e at a cell in float-float for FP32 e: per axis the second difference
 // e_hi + e_lo - 2 e_c in float-float (exact), times the float-float weight
-// (fih2 + lih2), summed in float-float; only the final combination is FP64.
-__device__ __forceinline__ double lap_ff(const Lev& L, const Nbr& nb, const float* e, float ec) {
+// (fih2 + lih2), summed in float-float.
+__device__ __forceinline__ FF lap_ff_pair(const Lev& L, const Nbr& nb, const float* e, float ec) {
     float acc_hi = 0.0f, acc_lo = 0.0f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -150,7 +195,8 @@ __device__ __forceinline__ double lap_ff(const Lev& L, const Nbr& nb, const floa
         acc_hi = s_hi;
         acc_lo += s_err + p_lo;
     }
-    return double(acc_hi) + double(acc_lo);
+    const float h = acc_hi + acc_lo;
+    return FF{h, acc_lo - (h - acc_hi)};
 }
 
 // -w / d in the preconditioner (deterministic; the V-cycle only has to be a
@@ -417,8 +463,9 @@ __global__ void __launch_bounds__(NTHREADS)
     // march (each value is computed once per thread, as the neighbours' are)
     const bool roll = PRE && L.fcode == nullptr;
     T zlo = T(0), zc = T(0);
+    const NbrXY xy = make_nbr_xy(L, i, j);
     for (int k = k0; k < k1; ++k) {
-        const Nbr nb = make_nbr(L, i, j, k);
+        const Nbr nb = nbr_at(L, xy, k);
         const int id = nb.c;
         if (roll && k == k0) {
             zlo = srcq(nb.lo[2]);
@@ -510,10 +557,11 @@ __global__ void __launch_bounds__(NTHREADS)
     const int k1 = min(k0 + L.tz, L.n[2]);
     auto yq = [&](int q) -> T { return y[q]; };
     T accz = T(0);
+    const NbrXY xy = make_nbr_xy(L, i, j);
     for (int k = k0; k < k1; ++k) {
         T res = T(0);
         if (in) {
-            const Nbr nb = make_nbr(L, i, j, k);
+            const Nbr nb = nbr_at(L, xy, k);
             res = b[nb.c] - lap_nbr(L, nb, yq, y[nb.c]);
         }
         res += __shfl_xor_sync(0xffffffffu, res, 1);   // x pair
@@ -739,8 +787,9 @@ __global__ void __launch_bounds__(NTHREADS)
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         auto yq = [&](int q) -> T { return y[q]; };
+        const NbrXY xy = make_nbr_xy(L, i, j);
         for (int k = k0; k < k1; ++k) {
-            const Nbr nb = make_nbr(L, i, j, k);
+            const Nbr nb = nbr_at(L, xy, k);
             const int id = nb.c;
             const T lv = lap_nbr(L, nb, yq, y[id]);
             v[id] = lv;
@@ -771,8 +820,9 @@ __global__ void __launch_bounds__(NTHREADS)
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         auto zq = [&](int q) -> T { return z[q]; };
+        const NbrXY xy = make_nbr_xy(L, i, j);
         for (int k = k0; k < k1; ++k) {
-            const Nbr nb = make_nbr(L, i, j, k);
+            const Nbr nb = nbr_at(L, xy, k);
             const int id = nb.c;
             const T tv = lap_nbr(L, nb, zq, z[id]);
             t[id] = tv;
@@ -889,8 +939,9 @@ __global__ void __launch_bounds__(NTHREADS)
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         auto xq = [&](int q) -> T { return xs[q]; };
+        const NbrXY xy = make_nbr_xy(L, i, j);
         for (int k = k0; k < k1; ++k) {
-            const Nbr nb = make_nbr(L, i, j, k);
+            const Nbr nb = nbr_at(L, xy, k);
             const int id = nb.c;
             const T bv = lev_fluid(L, id) ? b[id] - mean : T(0);
             const T xc = xq(id);
@@ -918,65 +969,119 @@ __global__ void __launch_bounds__(NTHREADS)
 }
 
 // ---------------------------------------------------------------------------
-// FP32 inner iterations inside FP64 iterative refinement
+// FP32 inner iterations inside float-float iterative refinement: the pressure
+// iterate p, the outer residual r and the warm starts are held as hi + lo
+// FP32 pairs (about 48 significant bits), so the refinement runs on the FP32
+// pipe -- GB300's FP64 rate is a small fraction of its FP32 rate.  The outer
+// target (relative residual 1e-10) and the FP64 pressure the caller receives
+// are unaffected by the 48-bit precision.
 // ---------------------------------------------------------------------------
 
-// Start from the warm start p (p^n, or the extrapolated 2 p^n - p^(n-1) the
-// previous correction wrote): b <- b - mean(b); p64 = p; r64 = b - L p (FP64); r = float(r64);
-// r_hat = r (r64 itself is not stored).  The last CTA tests the outer residual and starts the inner
-// solve (from e = 0) where it is not yet small enough.
+// Sum of squares of FP32 values accumulated in FP32 without losing the tiny
+// ones: values below 2^-60 are squared after scaling by 2^64 into a second
+// sum (so squares down to about 1e-76 count), combined in FP64.
+struct SqAcc {
+    float big = 0.0f, small = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        if (fabsf(x) >= 0x1p-60f) {
+            big = fmaf(x, x, big);
+        } else {
+            const float y = x * 0x1p64f;
+            small = fmaf(y, y, small);
+        }
+    }
+    __device__ __forceinline__ double total() const {
+        return double(big) + double(small) * 0x1p-128;
+    }
+};
+
+// Power of two that brings a residual of squared norm rr over `cells` cells to
+// an RMS of order one (1 for a zero residual): the inner FP32 solve works on
+// the scaled residual, so its dot products neither underflow nor overflow
+// however far the refinement has driven the residual down.
+__device__ __forceinline__ double pow2_scale(double rr, long long cells) {
+    if (!(rr > 0.0) || !isfinite(rr)) return 1.0;
+    const int e = ilogb(sqrt(rr / double(cells)));
+    return ldexp(1.0, -max(-100, min(100, e)));
+}
+
+struct FFBuf {
+    float *p_hi, *p_lo;   // the iterate
+    float *r_hi, *r_lo;   // the outer residual b - L p
+    float *w_hi, *w_lo;   // the next solve's warm start 2 p^n - p^(n-1)
+    float *q_hi, *q_lo;   // the last gauged pressure p^n
+};
+
+// Start: b <- b - mean(b); p = the warm start (FROM64: the FP64 pressure p_in,
+// which also becomes q; else w); r = b - L p; r32 = r_hat = r.hi.  The last
+// CTA tests the outer residual and starts the inner solve (from e = 0) where
+// it is not yet small enough.
+template <bool FROM64>
 __global__ void __launch_bounds__(NTHREADS)
-    k_mg_refine_init(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
-                     const double* __restrict__ part_b, int nfluid, double* __restrict__ bvec,
-                     const double* __restrict__ p_in, double* __restrict__ p64, double* __restrict__ r64,
-                     double* __restrict__ part, double otol2,
-                     double itol2, int maxit) {
+    k_mg_refine_init_ff(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
+                        const double* __restrict__ part_b, int nfluid,
+                        const double* __restrict__ bvec, const double* __restrict__ p_in,
+                        FFBuf f, double* __restrict__ part, double otol2, double itol2,
+                        int maxit) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     double sb[1];
     reduce_partials<1>(part_b + s * L.ctas, L.ctas, sb);
     const double mean = sb[0] / nfluid;
     const long long off = s * L.cells;
-    double* __restrict__ b = bvec + off;
-    const double* __restrict__ ps = p_in + off;
-    double* __restrict__ pd = p64 + off;
-    double* __restrict__ rd = r64 + off;
+    const double* __restrict__ b = bvec + off;
+    const double* __restrict__ ps = FROM64 ? p_in + off : nullptr;
     float* __restrict__ r = mb.r + off;
     float* __restrict__ rh = mb.rhat + off;
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    float a3 = 0.0f;
+    SqAcc arr, abb;
+    FF sp{0.0f, 0.0f};
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto pq = [&](int q) -> double { return ps[q]; };
+        const NbrXY xy = make_nbr_xy(L, i, j);
         for (int k = k0; k < k1; ++k) {
-            const Nbr nb = make_nbr(L, i, j, k);
+            const Nbr nb = nbr_at(L, xy, k);
             const int id = nb.c;
-            const double bv = lev_fluid(L, id) ? b[id] - mean : 0.0;
-            const double pc = pq(id);
-            const double rv = bv - lap_nbr(L, nb, pq, pc);
-            const float rf = float(rv);
-            b[id] = bv;
-            pd[id] = pc;
-            rd[id] = rv;
-            r[id] = rf;
-            rh[id] = rf;
-            a0 += rv * rv;
-            a1 += bv * bv;
-            a2 += pc;
-            a3 += rf * rf;
+            const bool fl = lev_fluid(L, id);
+            const double bv = fl ? b[id] - mean : 0.0;
+            FF p0, res;
+            if (FROM64) {
+                auto pq = [&](int q) -> double { return ps[q]; };
+                const double pc = ps[id];
+                res = ff_from_double(bv - lap_nbr(L, nb, pq, pc));
+                p0 = ff_from_double(pc);
+                f.q_hi[off + id] = p0.hi;
+                f.q_lo[off + id] = p0.lo;
+            } else {
+                const float* __restrict__ wh = f.w_hi + off;
+                const float* __restrict__ wl = f.w_lo + off;
+                p0 = FF{wh[id], wl[id]};
+                auto lq = [&](int q) -> float { return wl[q]; };
+                const FF lp = ff_add_f(lap_ff_pair(L, nb, wh, p0.hi), lap_nbr(L, nb, lq, p0.lo));
+                res = ff_add(ff_from_double(bv), ff_neg(lp));
+            }
+            f.p_hi[off + id] = p0.hi;
+            f.p_lo[off + id] = p0.lo;
+            f.r_hi[off + id] = res.hi;
+            f.r_lo[off + id] = res.lo;
+            r[id] = res.hi;
+            rh[id] = res.hi;
+            arr.add(res.hi);
+            abb.add(float(bv));
+            sp = ff_add(sp, p0);
         }
     }
-    double acc[4] = {a0, a1, a2, double(a3)};
-    double tot[4];
-    if (partials_and_arrive<4>(acc, part + s * L.ctas * 4, mb.counter + s, L.ctas, tot) &&
+    double acc[3] = {arr.total(), abb.total(), ff_to_double(sp)};
+    double tot[3];
+    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
         tid_flat() == 0) {
         c->o_bb = tot[1];
         c->o_rr = tot[0];
         c->o_steps = 0;
         c->p_final = 0;
         c->sx = tot[2];
+        c->o_scale = 1.0;
         if (!isfinite(tot[0])) {
             c->o_status = OS_NONFINITE;
             c->status = ST_IDLE;
@@ -986,23 +1091,21 @@ __global__ void __launch_bounds__(NTHREADS)
         } else {
             c->o_status = OS_REFINE;
             c->it_cur = 0;
-            c->bb = tot[3];
+            c->bb = tot[0];
             c->omega = 1.0;
             c->alpha = 1.0;
-            bicg_decide(c, tot[3], tot[3], 0.0, itol2, maxit);
+            bicg_decide(c, tot[0], tot[0], 0.0, itol2, maxit);
         }
     }
 }
 
-// Outer correction: p += e (FP64, in place); r64 -= L e, with L e of the FP32
-// correction evaluated exactly in float-float (lap_ff) and the residual kept
-// in FP64; r = float(r64); r_hat = r.  The last CTA tests the outer residual
-// and restarts the inner solve, or stops (converged / out of outer steps).
+// Outer correction: p += e; r -= L e (L e of the FP32 correction in
+// float-float); r32 = r_hat = r.hi.  The last CTA tests the outer residual and
+// restarts the inner solve, or stops (converged / out of outer steps).
 __global__ void __launch_bounds__(NTHREADS)
-    k_mg_refine_update(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl,
-                       double* __restrict__ p64, double* __restrict__ r64,
-                       double* __restrict__ part, double otol2, double itol2, int maxit,
-                       int max_outer, int skip_iterating) {
+    k_mg_refine_update_ff(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl, FFBuf f,
+                          double* __restrict__ part, double otol2, double itol2, int maxit,
+                          int max_outer, int skip_iterating) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->o_status != OS_REFINE) return;
@@ -1010,36 +1113,44 @@ __global__ void __launch_bounds__(NTHREADS)
     if (skip_iterating && c->status == ST_ITER) return;
     const bool bad = c->status == ST_NONFINITE;
     const long long off = s * L.cells;
-    double* __restrict__ pd = p64 + off;
-    double* __restrict__ rd = r64 + off;
     const float* __restrict__ e = mb.x + off;
     float* __restrict__ r = mb.r + off;
     float* __restrict__ rh = mb.rhat + off;
+    // e carries the scale of the inner solve's right side; the next right
+    // side is scaled by the previous residual's norm (all CTAs read both
+    // before the last one updates them)
+    const float unscale = float(1.0 / c->o_scale);
+    const double sc_next = pow2_scale(c->o_rr, L.cells);
+    const float fsc = float(sc_next);
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
-    double a0 = 0.0, a1 = 0.0;
-    float a2 = 0.0f;
+    SqAcc arr;
+    FF sp{0.0f, 0.0f};
     if (!bad && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
+        const NbrXY xy = make_nbr_xy(L, i, j);
         for (int k = k0; k < k1; ++k) {
-            const Nbr nb = make_nbr(L, i, j, k);
+            const Nbr nb = nbr_at(L, xy, k);
             const int id = nb.c;
+            const long long q = off + id;
             const float ec = e[id];
-            const double pc = pd[id] + double(ec);
-            const double rv = rd[id] - lap_ff(L, nb, e, ec);
-            const float rf = float(rv);
-            pd[id] = pc;
-            rd[id] = rv;
-            r[id] = rf;
-            rh[id] = rf;
-            a0 += rv * rv;
-            a1 += pc;
-            a2 += rf * rf;
+            const FF le = lap_ff_pair(L, nb, e, ec);
+            const FF pn = ff_add_f(FF{f.p_hi[q], f.p_lo[q]}, ec * unscale);
+            const FF rn =
+                ff_add(FF{f.r_hi[q], f.r_lo[q]}, FF{-le.hi * unscale, -le.lo * unscale});
+            f.p_hi[q] = pn.hi;
+            f.p_lo[q] = pn.lo;
+            f.r_hi[q] = rn.hi;
+            f.r_lo[q] = rn.lo;
+            r[id] = rn.hi * fsc;
+            rh[id] = rn.hi * fsc;
+            arr.add(rn.hi);
+            sp = ff_add(sp, pn);
         }
     }
-    double acc[3] = {a0, a1, double(a2)};
-    double tot[3];
-    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+    double acc[2] = {arr.total(), ff_to_double(sp)};
+    double tot[2];
+    if (partials_and_arrive<2>(acc, part + s * L.ctas * 2, mb.counter + s, L.ctas, tot) &&
         tid_flat() == 0) {
         c->o_steps += 1;
         c->o_rr = tot[0];
@@ -1055,11 +1166,71 @@ __global__ void __launch_bounds__(NTHREADS)
             c->o_status = OS_FAIL;
             c->status = ST_IDLE;
         } else {
+            const double rr = tot[0] * sc_next * sc_next;  // of the scaled right side
+            c->o_scale = sc_next;
             c->it_cur = 0;
-            c->bb = tot[2];
+            c->bb = rr;
             c->omega = 1.0;
             c->alpha = 1.0;
-            bicg_decide(c, tot[2], tot[2], 0.0, itol2, maxit);
+            bicg_decide(c, rr, rr, 0.0, itol2, maxit);
+        }
+    }
+}
+
+// Velocity correction u += increment - dt G p (INCR) or u = F* - dt G p, with
+// p = the float-float iterate: the difference of neighbouring values taken
+// in float from both parts.  Cells: p_out = p - mean (FP64); with keep, the
+// next warm start w = 2 (p - mean) - q and q = p - mean (float-float).
+template <bool INCR>
+__global__ void __launch_bounds__(NTHREADS)
+    k_correct_ff(Geo g, const SliceCtl* __restrict__ ctl, const float* fu, const float* fv,
+                 const float* fw, float* u, float* v, float* w, FFBuf f,
+                 double* __restrict__ p_out, double dt, int keep) {
+    const long long s = blockIdx.y;
+    const SliceCtl* c = ctl + s;
+    const long long off = s * g.cnt[3];
+    const float* __restrict__ ph = f.p_hi + off;
+    const float* __restrict__ pl = f.p_lo + off;
+    const FF mean = ff_from_double(c->sx / g.n_fluid);
+    const float* f3[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
+    float* o3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
+    const float dtih[3] = {float(dt * g.ih[0]), float(dt * g.ih[1]), float(dt * g.ih[2])};
+    int i, j, k0;
+    tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
+    const int k1 = min(k0 + g.tz, g.n[2] + 1);
+    for (int k = k0; k < k1; ++k) {
+        const int q3[3] = {i, j, k};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (i < g.ext[d][0] && j < g.ext[d][1] && k < g.ext[d][2]) {
+                const long long id = vindex(g, d, i, j, k);
+                if (!face_active_dev(g, d, q3)) {
+                    o3[d][id] = 0.0f;
+                } else {
+                    int lo[3] = {i, j, k};
+                    lo[d] = q3[d] == 0 ? g.n[d] - 1 : q3[d] - 1;
+                    const int a = cindex(g, i, j, k), b = cindex(g, lo[0], lo[1], lo[2]);
+                    const float dgp = ((ph[a] - ph[b]) + (pl[a] - pl[b])) * dtih[d];
+                    if (INCR)
+                        o3[d][id] = o3[d][id] + (f3[d][id] - dgp);
+                    else
+                        o3[d][id] = f3[d][id] - dgp;
+                }
+            }
+        }
+        if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+            const int id = cindex(g, i, j, k);
+            const bool sol = cell_solid(g, i, j, k);
+            const FF pg = sol ? FF{0.0f, 0.0f} : ff_add(FF{ph[id], pl[id]}, ff_neg(mean));
+            if (p_out) p_out[off + id] = ff_to_double(pg);
+            if (keep) {
+                const FF q{f.q_hi[off + id], f.q_lo[off + id]};
+                const FF wn = ff_add(FF{2.0f * pg.hi, 2.0f * pg.lo}, ff_neg(q));
+                f.w_hi[off + id] = wn.hi;
+                f.w_lo[off + id] = wn.lo;
+                f.q_hi[off + id] = pg.hi;
+                f.q_lo[off + id] = pg.lo;
+            }
         }
     }
 }

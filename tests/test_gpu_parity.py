@@ -280,9 +280,10 @@ def test_nonfinite_input_is_reported():
 @pytest.mark.parametrize("pc", PCS)
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
 def test_iteration_limit_is_reported(prec, pc):
-    # one Krylov iteration per solve and a tolerance no solve can reach
+    # one Krylov iteration per solve (and, with refinement, one outer
+    # correction): no solve reaches its tolerance
     g = Grid(16, 16, 16, precision=prec, poisson_maxit=1, batch=1, preconditioner=pc,
-             poisson_rtol=1e-30, refine_rtol=1e-30)
+             poisson_rtol=1e-30, refine_rtol=1e-10, refine_maxit=1)
     st = g.zeros(1)
     with pytest.raises(NSError) as e:
         g.step_fine(st, 1e-3, 1)
@@ -292,14 +293,17 @@ def test_iteration_limit_is_reported(prec, pc):
     g2.step_fine(g2.zeros(1), 1e-3, 1)
 
 
+@pytest.mark.parametrize("pc", PCS)
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
-def test_chunked_parareal_is_bit_identical(prec):
+def test_chunked_parareal_is_bit_identical(prec, pc):
     """The fine sweep in chunks, each chunk's coarse chain overlapped with the
-    next chunk's sweep on a second stream, computes exactly the unchunked
-    iteration: same slices bit for bit, same defects."""
+    next chunk's sweep on a second stream (graph launches with the multigrid
+    solver, a second host thread with plain BiCGStab), computes exactly the
+    unchunked iteration: same slices bit for bit, same defects."""
     runs = {}
     for chunk in (0, 4, 8):
-        g = Grid(16, 16, 16, re=400.0, precision=prec, batch=16, parareal_chunk=chunk)
+        g = Grid(16, 16, 16, re=400.0, precision=prec, batch=16, parareal_chunk=chunk,
+                 preconditioner=pc)
         u0 = g.state_from(inputs.random_state(16, 16, 16, seed=11, sigma=0.2))
         g.project(u0)
         slices = g.zeros(17)
