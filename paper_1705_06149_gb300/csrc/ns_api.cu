@@ -469,6 +469,11 @@ MgBuf<T> mgbuf(const ns_grid* g) {
     return m;
 }
 
+// dt / h per axis, for the float-float correction
+float3 dt_ih(const Geo& G, double dt) {
+    return make_float3(float(dt * G.ih[0]), float(dt * G.ih[1]), float(dt * G.ih[2]));
+}
+
 FFBuf ffbuf(const ns_grid* g) {
     FFBuf f;
     f.p_hi = g->ffb[0];
@@ -755,8 +760,8 @@ ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
         NS_TRY(mg_iteration<float>(g, batch, itol2, 1));
         NS_LAUNCH(g, NS_K_REFINE, 0,
                   k_mg_refine_update_ff<<<grid, blk, 0, g->stream>>>(
-                      L0, mb, g->ctl, ffbuf(g), g->part_mg, otol2, itol2, g->maxit, g->max_outer,
-                      1));
+                      L0, mb, g->ctl, ffbuf(g), g->geo.n_fluid, g->part_mg, otol2, itol2,
+                      g->maxit, g->max_outer, 1));
         NS_CUDA(cudaGetLastError());
         return loop_cond(g, batch, h, LC_REFINE_ITER, cap_refine);
     });
@@ -795,8 +800,8 @@ ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
             g_last_error.clear();
             NS_LAUNCH(g, NS_K_REFINE, L0.cells * batch,
                       k_mg_refine_update_ff<<<grid, blk, 0, g->stream>>>(
-                          L0, mb, g->ctl, ffbuf(g), g->part_mg, otol2, itol2, g->maxit,
-                          g->max_outer, 0));
+                          L0, mb, g->ctl, ffbuf(g), g->geo.n_fluid, g->part_mg, otol2, itol2,
+                          g->maxit, g->max_outer, 0));
             NS_CUDA(cudaGetLastError());
         }
         for (int s = 0; s < batch; ++s) {
@@ -941,7 +946,8 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
             NS_LAUNCH(g, NS_K_CORRECT, cells,
                       k_correct_ff<INCR><<<gface, block_dim(), 0, g->stream>>>(
                           G, g->ctl, (const float*)fu, (const float*)fv, (const float*)fw,
-                          (float*)u, (float*)v, (float*)w, ffbuf(g), p, dt, keep ? 1 : 0));
+                          (float*)u, (float*)v, (float*)w, ffbuf(g), p, dt_ih(G, dt),
+                          keep ? 1 : 0));
         else
             NS_LAUNCH(g, NS_K_CORRECT, cells,
                       k_correct<T, INCR><<<gface, block_dim(), 0, g->stream>>>(
@@ -985,7 +991,7 @@ ns_status project_impl(ns_grid* g, const ns_state& io) {
         NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
                   k_correct_ff<false><<<gface, block_dim(), 0, g->stream>>>(
                       G, g->ctl, (const float*)u, (const float*)v, (const float*)w, (float*)u,
-                      (float*)v, (float*)w, ffbuf(g), nullptr, 1.0, 0));
+                      (float*)v, (float*)w, ffbuf(g), nullptr, dt_ih(G, 1.0), 0));
     else
         NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
                   k_correct<T, false><<<gface, block_dim(), 0, g->stream>>>(
@@ -1731,7 +1737,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         A((void**)&g->p_prev, ncell * sizeof(double) * B);
         if (g->fp32)
             for (int q = 0; q < 8; ++q) A((void**)&g->ffb[q], ncell * sizeof(float) * B);
-        A((void**)&g->part_mg, nparts * 4 * sizeof(double));
+        A((void**)&g->part_mg, nparts * 6 * sizeof(double));
     }
     A((void**)&g->d_defect, sizeof(unsigned long long));
     if (st == NS_OK) {
@@ -1880,7 +1886,7 @@ ns_status ns_poisson_solve(ns_grid* grid, const double* b, double* p, int batch,
                   k_correct_ff<false><<<gface, block_dim(), 0, grid->stream>>>(
                       G, grid->ctl, (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2],
                       (float*)grid->fs[0], (float*)grid->fs[1], (float*)grid->fs[2], ffbuf(grid),
-                      p, 0.0, 0));
+                      p, dt_ih(G, 0.0), 0));
     else if (grid->fp32)
         NS_LAUNCH(grid, NS_K_CORRECT, G.cnt[3] * batch,
                   k_correct<float, false><<<gface, block_dim(), 0, grid->stream>>>(

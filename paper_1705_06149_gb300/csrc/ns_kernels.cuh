@@ -38,6 +38,10 @@ struct SliceCtl {
     long long total_outer;  // graph-resident solves: refinement steps accumulated
     long long total_solves; // graph-resident solves: solves finished
     double o_scale;    // FP32+refine: power of two the inner solve's right side carries
+    float o_funs;      // FP32+refine: 1 / that scale, for the next outer correction
+    float o_fsc;       // FP32+refine: the scale the next correction gives its right side
+    float mean_hi, mean_lo;  // FP32+refine: the fluid mean of the iterate, float-float
+    float rmean_hi, rmean_lo;  // FP32+refine: the fluid mean of the outer residual
 };
 
 template <typename T>
@@ -83,71 +87,104 @@ __global__ void __launch_bounds__(PT_THREADS)
     // stage: positions (i0-2 .. i0+PT_X+1) etc. of every component
     const bool inner = i0 >= PH && j0 >= PH && k0 >= PH && i0 + PT_X + PH <= g.n[0] &&
                        j0 + PT_Y + PH <= g.n[1] && k0 + PT_Z + PH <= g.n[2];
+    // Each thread stages fixed positions of the (x, y) plane of the tile for
+    // every z: the plane part of the index and the x / y range test are
+    // computed once, each element then costs an add, a compare and a load.
+    constexpr int PLANE = PS_X * PS_Y;
+    constexpr int PER = (PLANE + PT_THREADS - 1) / PT_THREADS;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        for (int r = t; r < PS_N; r += PT_THREADS) {
-            const int x = r % PS_X, y = (r / PS_X) % PS_Y, z = r / (PS_X * PS_Y);
-            const int gi = i0 - PH + x, gj = j0 - PH + y, gk = k0 - PH + z;
-            T val;
-            if (inner) {
-                val = vel3[c][vindex(g, c, gi, gj, gk)];
-            } else {
-                // only positions up to two beyond the domain are ever read
-                const bool near = gi >= -PH && gj >= -PH && gk >= -PH &&
-                                  gi < g.ext[c][0] + PH && gj < g.ext[c][1] + PH &&
-                                  gk < g.ext[c][2] + PH;
-                val = near ? vel(g, c, vel3[c], gi, gj, gk) : T(0);
+    for (int h = 0; h < PER; ++h) {
+        const int pq = t + h * PT_THREADS;
+        if (pq >= PLANE) break;
+        const int x = pq % PS_X, y = pq / PS_X;
+        const int gi = i0 - PH + x, gj = j0 - PH + y;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int e0 = g.ext[c][0], e1 = g.ext[c][1], e2 = g.ext[c][2];
+            const bool xy_in = inner || (gi >= 0 && gj >= 0 && gi < e0 && gj < e1);
+            const bool xy_near = gi >= -PH && gj >= -PH && gi < e0 + PH && gj < e1 + PH;
+            const long long plane = (long long)e1 * e0;
+            const T* __restrict__ a = vel3[c] + (long long)gj * e0 + gi;
+            T* dst = sm + c * PS_N + pq;
+            for (int z = 0; z < PS_Z; ++z) {
+                const int gk = k0 - PH + z;
+                T val;
+                if (xy_in && (inner || (gk >= 0 && gk < e2))) {
+                    // a stored value (wall-normal boundary faces are stored as 0)
+                    val = a[gk * plane];
+                } else {
+                    // a ghost value; only positions up to two beyond the
+                    // domain are ever read
+                    val = (xy_near && gk >= -PH && gk < e2 + PH)
+                              ? vel(g, c, vel3[c], gi, gj, gk)
+                              : T(0);
+                }
+                dst[z * PLANE] = val;
             }
-            sm[c * PS_N + r] = val;
         }
     }
     __syncthreads();
     const T tdt = T(dt), inv_re = g_inv_re<T>(g);
     constexpr int strd[3] = {1, PS_X, PS_X * PS_Y};
+    // Each thread owns the column (x, y) = (lane, warp) of the tile and marches
+    // its PT_Z cells in z.  A face flux is evaluated once: the flux entering
+    // cell x across its low x face is the one lane x-1 computed for its high
+    // face (a shuffle), and the low z face flux is the high one of the cell
+    // below (carried along the march); only y fluxes are evaluated on both
+    // faces.  The operands are the same values either way, so the fluxes are
+    // identical to evaluating every face from both sides.
+    const int x = t % PT_X, y = t / PT_X;
+    const unsigned lane = t & 31u;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-    for (int r = t; r < PT_X * PT_Y * PT_Z; r += PT_THREADS) {
-        const int x = r % PT_X, y = (r / PT_X) % PT_Y, z = r / (PT_X * PT_Y);
-        const int f[3] = {i0 + x, j0 + y, k0 + z};
-        if (f[0] >= g.n[0] || f[1] >= g.n[1] || f[2] >= g.n[2]) continue;
-        const long long id = vindex(g, c, f[0], f[1], f[2]);
-        // the high wall face of the last cell along c is inactive: zero it
-        if (g.bc[c] != BC_PERIODIC && f[c] == g.n[c] - 1) {
-            int h3[3] = {f[0], f[1], f[2]};
-            h3[c] += 1;
-            out[c][vindex(g, c, h3[0], h3[1], h3[2])] = T(0);
-        }
-        const bool active = g.bc[c] == BC_PERIODIC || f[c] > 0;
-        if (!active) {
-            out[c][id] = T(0);
-            continue;
-        }
+    for (int c = 0; c < 3; ++c) {
         const T* sc = sm + c * PS_N;
-        const int o = ((z + PH) * PS_Y + (y + PH)) * PS_X + (x + PH);
-        T conv = T(0), diff = T(0);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
+        const int sc_c = strd[c];
+        // transport velocity at the high face of direction d of the cell at o
+        auto up_at = [&](int d, int o) -> T {
             const int sd = strd[d];
-            const T a0 = sc[o - 2 * sd], a1 = sc[o - sd], a2 = sc[o], a3 = sc[o + sd],
-                    a4 = sc[o + 2 * sd];
-            T up, um;
-            if (d == c) {
-                up = T(0.5) * (a2 + a3);
-                um = T(0.5) * (a1 + a2);
-            } else {
-                // component d at (c-index f_c - 1 and f_c) x (d-index f_d + 1 and f_d)
-                const T* sdc = sm + d * PS_N;
-                const int sc_c = strd[c];
-                up = T(0.5) * (sdc[o - sc_c + sd] + sdc[o + sd]);
-                um = T(0.5) * (sdc[o - sc_c] + sdc[o]);
+            if (d == c) return T(0.5) * (sc[o] + sc[o + sd]);
+            const T* sdc = sm + d * PS_N;
+            return T(0.5) * (sdc[o - sc_c + sd] + sdc[o + sd]);
+        };
+        T fz_lo = T(0);
+        for (int z = 0; z < PT_Z; ++z) {
+            const int o = ((z + PH) * PS_Y + (y + PH)) * PS_X + (x + PH);
+            T conv = T(0), diff = T(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int sd = strd[d];
+                const T a0 = sc[o - 2 * sd], a1 = sc[o - sd], a2 = sc[o], a3 = sc[o + sd],
+                        a4 = sc[o + 2 * sd];
+                const T fp = smart_flux_sel(up_at(d, o), a1, a2, a3, a4);
+                T fm;
+                if (d == 0) {
+                    fm = __shfl_up_sync(0xffffffffu, fp, 1);
+                    if (lane == 0) fm = smart_flux_sel(up_at(0, o - 1), a0, a1, a2, a3);
+                } else if (d == 1 || z == 0) {
+                    fm = smart_flux_sel(up_at(d, o - sd), a0, a1, a2, a3);
+                } else {
+                    fm = fz_lo;
+                }
+                if (d == 2) fz_lo = fp;
+                conv += (fp - fm) * g_ih<T>(g, d);
+                diff += (a3 - T(2) * a2 + a1) * g_ih2<T>(g, d);
             }
-            const T fp = smart_flux_sel(up, a1, a2, a3, a4);
-            const T fm = smart_flux_sel(um, a0, a1, a2, a3);
-            conv += (fp - fm) * g_ih<T>(g, d);
-            diff += (a3 - T(2) * a2 + a1) * g_ih2<T>(g, d);
+            const int f[3] = {i0 + x, j0 + y, k0 + z};
+            if (f[0] >= g.n[0] || f[1] >= g.n[1] || f[2] >= g.n[2]) continue;
+            const long long id = vindex(g, c, f[0], f[1], f[2]);
+            // the high wall face of the last cell along c is inactive: zero it
+            if (g.bc[c] != BC_PERIODIC && f[c] == g.n[c] - 1) {
+                int h3[3] = {f[0], f[1], f[2]};
+                h3[c] += 1;
+                out[c][vindex(g, c, h3[0], h3[1], h3[2])] = T(0);
+            }
+            if (!(g.bc[c] == BC_PERIODIC || f[c] > 0)) {
+                out[c][id] = T(0);
+                continue;
+            }
+            const T incr = tdt * (inv_re * diff - conv);
+            out[c][id] = INCR ? incr : sc[o] + incr;
         }
-        const T incr = tdt * (inv_re * diff - conv);
-        out[c][id] = INCR ? incr : sc[o] + incr;
     }
 }
 

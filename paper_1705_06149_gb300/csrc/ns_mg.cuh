@@ -1005,6 +1005,31 @@ __device__ __forceinline__ double pow2_scale(double rr, long long cells) {
     return ldexp(1.0, -max(-100, min(100, e)));
 }
 
+// CTA partials of NF FP32 sums (warp trees in FP32) and NX float-float sums
+// (converted to FP64 per thread, FP64 trees), FP64 across warps and CTAs;
+// returns whether this CTA arrived last, which then holds the state's totals
+// (the float-float ones last) in thread 0.
+template <int NF, int NX>
+__device__ __forceinline__ bool partials_arrive_ff(float (&v)[NF], const FF (&x)[NX],
+                                                   double* part_state, unsigned int* counter,
+                                                   int ctas, double (&total)[NF + NX]) {
+    constexpr int NV = NF + NX;
+    double bf[NF], bx[NX], dx[NX];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) dx[q] = ff_to_double(x[q]);
+    block_sum_mixed<float, NF>(v, bf);
+    block_sum_mixed<double, NX>(dx, bx);
+    if (tid_flat() == 0) {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) part_state[(long long)blockIdx.x * NV + q] = bf[q];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) part_state[(long long)blockIdx.x * NV + NF + q] = bx[q];
+    }
+    if (!arrive_last(counter, ctas)) return false;
+    sum_partials_l2<NV>(part_state, ctas, total);
+    return true;
+}
+
 struct FFBuf {
     float *p_hi, *p_lo;   // the iterate
     float *r_hi, *r_lo;   // the outer residual b - L p
@@ -1036,7 +1061,7 @@ __global__ void __launch_bounds__(NTHREADS)
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     SqAcc arr, abb;
-    FF sp{0.0f, 0.0f};
+    FF sp{0.0f, 0.0f}, sr{0.0f, 0.0f};
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         const NbrXY xy = make_nbr_xy(L, i, j);
@@ -1070,18 +1095,29 @@ __global__ void __launch_bounds__(NTHREADS)
             arr.add(res.hi);
             abb.add(float(bv));
             sp = ff_add(sp, p0);
+            sr = ff_add(sr, res);
         }
     }
-    double acc[3] = {arr.total(), abb.total(), ff_to_double(sp)};
-    double tot[3];
-    if (partials_and_arrive<3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+    float acc[4] = {arr.big, arr.small, abb.big, abb.small};
+    const FF ffs[2] = {sp, sr};
+    double t6[6];
+    if (partials_arrive_ff<4, 2>(acc, ffs, part + s * L.ctas * 6, mb.counter + s, L.ctas, t6) &&
         tid_flat() == 0) {
+        const double tot[3] = {t6[0] + t6[1] * 0x1p-128, t6[2] + t6[3] * 0x1p-128, t6[4]};
+        const FF rmean = ff_from_double(t6[5] / nfluid);
+        c->rmean_hi = rmean.hi;
+        c->rmean_lo = rmean.lo;
         c->o_bb = tot[1];
         c->o_rr = tot[0];
         c->o_steps = 0;
         c->p_final = 0;
         c->sx = tot[2];
         c->o_scale = 1.0;
+        c->o_funs = 1.0f;
+        c->o_fsc = float(pow2_scale(tot[0], L.cells));
+        const FF mean = ff_from_double(tot[2] / nfluid);
+        c->mean_hi = mean.hi;
+        c->mean_lo = mean.lo;
         if (!isfinite(tot[0])) {
             c->o_status = OS_NONFINITE;
             c->status = ST_IDLE;
@@ -1104,8 +1140,8 @@ __global__ void __launch_bounds__(NTHREADS)
 // restarts the inner solve, or stops (converged / out of outer steps).
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_refine_update_ff(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl, FFBuf f,
-                          double* __restrict__ part, double otol2, double itol2, int maxit,
-                          int max_outer, int skip_iterating) {
+                          int nfluid, double* __restrict__ part, double otol2, double itol2,
+                          int maxit, int max_outer, int skip_iterating) {
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->o_status != OS_REFINE) return;
@@ -1119,13 +1155,17 @@ __global__ void __launch_bounds__(NTHREADS)
     // e carries the scale of the inner solve's right side; the next right
     // side is scaled by the previous residual's norm (all CTAs read both
     // before the last one updates them)
-    const float unscale = float(1.0 / c->o_scale);
-    const double sc_next = pow2_scale(c->o_rr, L.cells);
-    const float fsc = float(sc_next);
+    const float unscale = c->o_funs;
+    const float fsc = c->o_fsc;
+    // the previous residual's fluid mean, taken out of the new one: the
+    // residual of the singular (Neumann / periodic) problem must stay in the
+    // range of L, or its rounding-made mean, which no correction can remove,
+    // becomes the inner solve's floor once the residual is small
+    const FF neg_rmean{-c->rmean_hi, -c->rmean_lo};
     int i, j, k0;
     lev_origin(L, blockIdx.x, i, j, k0);
     SqAcc arr;
-    FF sp{0.0f, 0.0f};
+    FF sp{0.0f, 0.0f}, sr{0.0f, 0.0f};
     if (!bad && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         const NbrXY xy = make_nbr_xy(L, i, j);
@@ -1136,8 +1176,8 @@ __global__ void __launch_bounds__(NTHREADS)
             const float ec = e[id];
             const FF le = lap_ff_pair(L, nb, e, ec);
             const FF pn = ff_add_f(FF{f.p_hi[q], f.p_lo[q]}, ec * unscale);
-            const FF rn =
-                ff_add(FF{f.r_hi[q], f.r_lo[q]}, FF{-le.hi * unscale, -le.lo * unscale});
+            FF rn = ff_add(FF{f.r_hi[q], f.r_lo[q]}, FF{-le.hi * unscale, -le.lo * unscale});
+            if (lev_fluid(L, id)) rn = ff_add(rn, neg_rmean);
             f.p_hi[q] = pn.hi;
             f.p_lo[q] = pn.lo;
             f.r_hi[q] = rn.hi;
@@ -1146,16 +1186,28 @@ __global__ void __launch_bounds__(NTHREADS)
             rh[id] = rn.hi * fsc;
             arr.add(rn.hi);
             sp = ff_add(sp, pn);
+            sr = ff_add(sr, rn);
         }
     }
-    double acc[2] = {arr.total(), ff_to_double(sp)};
-    double tot[2];
-    if (partials_and_arrive<2>(acc, part + s * L.ctas * 2, mb.counter + s, L.ctas, tot) &&
+    float acc[2] = {arr.big, arr.small};
+    const FF ffs[2] = {sp, sr};
+    double t4[4];
+    if (partials_arrive_ff<2, 2>(acc, ffs, part + s * L.ctas * 4, mb.counter + s, L.ctas, t4) &&
         tid_flat() == 0) {
+        const double tot[2] = {t4[0] + t4[1] * 0x1p-128, t4[2]};
+        const FF rmean = ff_from_double(t4[3] / nfluid);
+        c->rmean_hi = rmean.hi;
+        c->rmean_lo = rmean.lo;
+        const double sc_next = double(fsc);
         c->o_steps += 1;
         c->o_rr = tot[0];
         c->sx = tot[1];
         c->p_final = 0;
+        c->o_funs = 1.0f / fsc;
+        c->o_fsc = float(pow2_scale(tot[0], L.cells));
+        const FF mean = ff_from_double(tot[1] / nfluid);
+        c->mean_hi = mean.hi;
+        c->mean_lo = mean.lo;
         if (bad || !isfinite(tot[0])) {
             c->o_status = OS_NONFINITE;
             c->status = ST_IDLE;
@@ -1179,22 +1231,23 @@ __global__ void __launch_bounds__(NTHREADS)
 
 // Velocity correction u += increment - dt G p (INCR) or u = F* - dt G p, with
 // p = the float-float iterate: the difference of neighbouring values taken
-// in float from both parts.  Cells: p_out = p - mean (FP64); with keep, the
+// in float from both parts, times dt_ih = dt / h per axis.  Cells: p_out =
+// p - mean (FP64; the mean the last refinement kernel left); with keep, the
 // next warm start w = 2 (p - mean) - q and q = p - mean (float-float).
 template <bool INCR>
 __global__ void __launch_bounds__(NTHREADS)
     k_correct_ff(Geo g, const SliceCtl* __restrict__ ctl, const float* fu, const float* fv,
                  const float* fw, float* u, float* v, float* w, FFBuf f,
-                 double* __restrict__ p_out, double dt, int keep) {
+                 double* __restrict__ p_out, float3 dt_ih, int keep) {
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     const long long off = s * g.cnt[3];
     const float* __restrict__ ph = f.p_hi + off;
     const float* __restrict__ pl = f.p_lo + off;
-    const FF mean = ff_from_double(c->sx / g.n_fluid);
+    const FF mean{c->mean_hi, c->mean_lo};
     const float* f3[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
     float* o3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
-    const float dtih[3] = {float(dt * g.ih[0]), float(dt * g.ih[1]), float(dt * g.ih[2])};
+    const float dtih[3] = {dt_ih.x, dt_ih.y, dt_ih.z};
     int i, j, k0;
     tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
     const int k1 = min(k0 + g.tz, g.n[2] + 1);
