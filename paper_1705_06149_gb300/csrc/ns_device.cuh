@@ -76,33 +76,33 @@ __device__ __forceinline__ long long cindex(const Geo& g, int i, int j, int k) {
 //   tangential, wall          2*u_wall - mirror (u_wall = u_lid for u on y = ly);
 //   tangential, slip          +mirror.
 template <typename T>
+__device__ __forceinline__ void ghost_axis(const Geo& g, int c, int d, int& x, T& sign, T& add) {
+    const int e = g.ext[c][d];
+    if (x >= 0 && x < e) return;
+    const int n = g.n[d];
+    if (g.bc[d] == BC_PERIODIC) {
+        x = x < 0 ? x + e : x - e;
+    } else if (d == c) {
+        x = x < 0 ? -x : 2 * n - x;
+        sign = -sign;
+    } else {
+        const bool hi = x >= e;
+        x = hi ? 2 * n - 1 - x : -x - 1;
+        if (g.bc[d] == BC_WALL) {
+            sign = -sign;
+            if (c == 0 && d == 1 && hi) add = T(2.0 * g.u_lid);
+        }
+    }
+}
+
+template <typename T>
 __device__ __forceinline__ T vel(const Geo& g, int c, const T* __restrict__ a, int i, int j,
                                  int k) {
     int q[3] = {i, j, k};
     T sign = T(1);
     T add = T(0);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int e = g.ext[c][d];
-        int x = q[d];
-        if (x < 0 || x >= e) {
-            const int n = g.n[d];
-            if (g.bc[d] == BC_PERIODIC) {
-                x = x < 0 ? x + e : x - e;
-            } else if (d == c) {
-                x = x < 0 ? -x : 2 * n - x;
-                sign = -sign;
-            } else {
-                const bool hi = x >= e;
-                x = hi ? 2 * n - 1 - x : -x - 1;
-                if (g.bc[d] == BC_WALL) {
-                    sign = -sign;
-                    if (c == 0 && d == 1 && hi) add = T(2.0 * g.u_lid);
-                }
-            }
-            q[d] = x;
-        }
-    }
+    for (int d = 0; d < 3; ++d) ghost_axis(g, c, d, q[d], sign, add);
     return add + sign * a[vindex(g, c, q[0], q[1], q[2])];
 }
 

@@ -84,40 +84,54 @@ __global__ void __launch_bounds__(PT_THREADS)
     const int j0 = ((cta / tbx) % tby) * PT_Y;
     const int k0 = (cta / (tbx * tby)) * PT_Z;
     const int t = threadIdx.x;
-    // stage: positions (i0-2 .. i0+PT_X+1) etc. of every component
-    const bool inner = i0 >= PH && j0 >= PH && k0 >= PH && i0 + PT_X + PH <= g.n[0] &&
-                       j0 + PT_Y + PH <= g.n[1] && k0 + PT_Z + PH <= g.n[2];
-    // Each thread stages fixed positions of the (x, y) plane of the tile for
-    // every z: the plane part of the index and the x / y range test are
-    // computed once, each element then costs an add, a compare and a load.
+    // Stage positions (i0-2 .. i0+PT_X+1) etc. of every component, ghost
+    // values applied (the rules act on each axis separately).  The z part of
+    // the rules is the same for the whole CTA and the x / y part is fixed per
+    // plane position, so each is evaluated once; every element then costs a
+    // load and at most a multiply-add.
     constexpr int PLANE = PS_X * PS_Y;
     constexpr int PER = (PLANE + PT_THREADS - 1) / PT_THREADS;
 #pragma unroll
-    for (int h = 0; h < PER; ++h) {
-        const int pq = t + h * PT_THREADS;
-        if (pq >= PLANE) break;
-        const int x = pq % PS_X, y = pq / PS_X;
-        const int gi = i0 - PH + x, gj = j0 - PH + y;
+    for (int c = 0; c < 3; ++c) {
+        const int e0 = g.ext[c][0], e1 = g.ext[c][1], e2 = g.ext[c][2];
+        const long long plane = (long long)e1 * e0;
+        long long zoff[PS_Z];
+        T zsign[PS_Z];
+        bool zghost[PS_Z], znear[PS_Z];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int e0 = g.ext[c][0], e1 = g.ext[c][1], e2 = g.ext[c][2];
-            const bool xy_in = inner || (gi >= 0 && gj >= 0 && gi < e0 && gj < e1);
+        for (int z = 0; z < PS_Z; ++z) {
+            const int gk = k0 - PH + z;
+            int qk = gk;
+            T sg = T(1), ad = T(0);
+            ghost_axis(g, c, 2, qk, sg, ad);
+            zoff[z] = qk * plane;
+            zsign[z] = sg;
+            zghost[z] = gk < 0 || gk >= e2;
+            znear[z] = gk >= -PH && gk < e2 + PH;
+        }
+#pragma unroll
+        for (int h = 0; h < PER; ++h) {
+            const int pq = t + h * PT_THREADS;
+            if (pq >= PLANE) break;
+            const int x = pq % PS_X, y = pq / PS_X;
+            const int gi = i0 - PH + x, gj = j0 - PH + y;
+            int qi = gi, qj = gj;
+            T sxy = T(1), add = T(0);
+            ghost_axis(g, c, 0, qi, sxy, add);
+            ghost_axis(g, c, 1, qj, sxy, add);
+            const bool xy_ghost = gi < 0 || gj < 0 || gi >= e0 || gj >= e1;
+            // only positions up to two beyond the stored range are ever read
             const bool xy_near = gi >= -PH && gj >= -PH && gi < e0 + PH && gj < e1 + PH;
-            const long long plane = (long long)e1 * e0;
-            const T* __restrict__ a = vel3[c] + (long long)gj * e0 + gi;
+            const T* __restrict__ a = vel3[c] + (long long)qj * e0 + qi;
             T* dst = sm + c * PS_N + pq;
+#pragma unroll
             for (int z = 0; z < PS_Z; ++z) {
-                const int gk = k0 - PH + z;
-                T val;
-                if (xy_in && (inner || (gk >= 0 && gk < e2))) {
-                    // a stored value (wall-normal boundary faces are stored as 0)
-                    val = a[gk * plane];
-                } else {
-                    // a ghost value; only positions up to two beyond the
-                    // domain are ever read
-                    val = (xy_near && gk >= -PH && gk < e2 + PH)
-                              ? vel(g, c, vel3[c], gi, gj, gk)
-                              : T(0);
+                T val = T(0);
+                if (xy_near && znear[z]) {
+                    const T st = a[zoff[z]];
+                    // stored values as they are (wall-normal boundary faces
+                    // are stored as 0); ghosts = add + sign * mirror
+                    val = (xy_ghost || zghost[z]) ? add + (sxy * zsign[z]) * st : st;
                 }
                 dst[z * PLANE] = val;
             }
