@@ -131,12 +131,41 @@ __device__ __forceinline__ bool lev_fluid(const Lev& L, int id) {
     return L.fcode == nullptr || (L.fcode[id] & FC_FLUID) != 0;
 }
 
+// The Laplacian from the cell value and its six neighbour values (x high,
+// x low, y high, y low, z high, z low).
+template <typename T>
+__device__ __forceinline__ T lap7(const Lev& L, T xh, T xl, T yh, T yl, T zh, T zl, T vc) {
+    const T two = T(2);
+    return (xh + xl - two * vc) * lw<T>(L, 0) + (yh + yl - two * vc) * lw<T>(L, 1) +
+           (zh + zl - two * vc) * lw<T>(L, 2);
+}
+
 template <typename T, typename F>
 __device__ __forceinline__ T lap_nbr(const Lev& L, const Nbr& b, const F& val, T vc) {
-    const T two = T(2);
-    return (val(b.hi[0]) + val(b.lo[0]) - two * vc) * lw<T>(L, 0) +
-           (val(b.hi[1]) + val(b.lo[1]) - two * vc) * lw<T>(L, 1) +
-           (val(b.hi[2]) + val(b.lo[2]) - two * vc) * lw<T>(L, 2);
+    return lap7<T>(L, val(b.hi[0]), val(b.lo[0]), val(b.hi[1]), val(b.lo[1]), val(b.hi[2]),
+                   val(b.lo[2]), vc);
+}
+
+// The 7-point values of a cell in registers: a thread's march in z loads a
+// batch of MG_ZB cells before it computes any of them, so every load of the
+// batch is in flight at once (the cells' arithmetic and the order of the
+// per-thread sums along z are those of the plain march).
+constexpr int MG_ZB = 4;
+
+template <typename T>
+struct Vals7 {
+    T c, xh, xl, yh, yl, zh, zl;
+};
+
+template <typename T>
+__device__ __forceinline__ Vals7<T> load7(const Nbr& b, const T* __restrict__ a) {
+    return Vals7<T>{a[b.c], a[b.hi[0]], a[b.lo[0]], a[b.hi[1]], a[b.lo[1]], a[b.hi[2]],
+                    a[b.lo[2]]};
+}
+
+template <typename T>
+__device__ __forceinline__ T lap_vals(const Lev& L, const Vals7<T>& v) {
+    return lap7<T>(L, v.xh, v.xl, v.yh, v.yl, v.zh, v.zl, v.c);
 }
 
 // Error-free transformations of FP32 arithmetic (Knuth's TwoSum; the exact
@@ -178,12 +207,13 @@ __device__ __forceinline__ double ff_to_double(FF a) { return double(a.hi) + dou
 // L e at a cell in float-float for FP32 e: per axis the second difference
 // e_hi + e_lo - 2 e_c in float-float (exact), times the float-float weight
 // (fih2 + lih2), summed in float-float.
-__device__ __forceinline__ FF lap_ff_pair(const Lev& L, const Nbr& nb, const float* e, float ec) {
+__device__ __forceinline__ FF lap_ff6(const Lev& L, const float (&eh)[3], const float (&el)[3],
+                                     float ec) {
     float acc_hi = 0.0f, acc_lo = 0.0f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         float t_hi, t_lo, u_hi, u_err;
-        two_sum(e[nb.hi[d]], e[nb.lo[d]], t_hi, t_lo);
+        two_sum(eh[d], el[d], t_hi, t_lo);
         two_sum(t_hi, -2.0f * ec, u_hi, u_err);
         const float u_lo = t_lo + u_err;
         const float w_hi = L.fih2[d], w_lo = L.lih2[d];
@@ -197,6 +227,20 @@ __device__ __forceinline__ FF lap_ff_pair(const Lev& L, const Nbr& nb, const flo
     }
     const float h = acc_hi + acc_lo;
     return FF{h, acc_lo - (h - acc_hi)};
+}
+
+// The same at a cell from its stencil neighbours' indices (values from e).
+__device__ __forceinline__ FF lap_ff_pair(const Lev& L, const Nbr& nb, const float* e, float ec) {
+    const float eh[3] = {e[nb.hi[0]], e[nb.hi[1]], e[nb.hi[2]]};
+    const float el[3] = {e[nb.lo[0]], e[nb.lo[1]], e[nb.lo[2]]};
+    return lap_ff6(L, eh, el, ec);
+}
+
+// The same from a cell's 7-point values.
+__device__ __forceinline__ FF lap_ff_vals(const Lev& L, const Vals7<float>& v) {
+    const float eh[3] = {v.xh, v.yh, v.zh};
+    const float el[3] = {v.xl, v.yl, v.zl};
+    return lap_ff6(L, eh, el, v.c);
 }
 
 // -w / d in the preconditioner (deterministic; the V-cycle only has to be a
@@ -555,21 +599,35 @@ __global__ void __launch_bounds__(NTHREADS)
     const int k0 = (rest / L.rby) * L.tz;
     const bool in = i < L.n[0] && j < L.n[1];
     const int k1 = min(k0 + L.tz, L.n[2]);
-    auto yq = [&](int q) -> T { return y[q]; };
     T accz = T(0);
     const NbrXY xy = make_nbr_xy(L, i, j);
-    for (int k = k0; k < k1; ++k) {
-        T res = T(0);
-        if (in) {
-            const Nbr nb = nbr_at(L, xy, k);
-            res = b[nb.c] - lap_nbr(L, nb, yq, y[nb.c]);
+    for (int kb = k0; kb < k1; kb += MG_ZB) {
+        // the batch's loads first, then its residuals and octet sums
+        Vals7<T> yv[MG_ZB];
+        T bv[MG_ZB];
+#pragma unroll
+        for (int q = 0; q < MG_ZB; ++q) {
+            if (in && kb + q < k1) {
+                const Nbr nb = nbr_at(L, xy, kb + q);
+                yv[q] = load7<T>(nb, y);
+                bv[q] = b[nb.c];
+            }
         }
-        res += __shfl_xor_sync(0xffffffffu, res, 1);   // x pair
-        res += __shfl_xor_sync(0xffffffffu, res, 16);  // y pair
-        accz += res;
-        if ((k & 1) == 1) {  // z pair complete
-            if (in && (lane & 17) == 0) bc[lindex(Lc, i >> 1, j >> 1, k >> 1)] = accz * T(0.125);
-            accz = T(0);
+#pragma unroll
+        for (int q = 0; q < MG_ZB; ++q) {
+            const int k = kb + q;
+            if (k < k1) {  // the same for the whole CTA
+                T res = T(0);
+                if (in) res = bv[q] - lap_vals<T>(L, yv[q]);
+                res += __shfl_xor_sync(0xffffffffu, res, 1);   // x pair
+                res += __shfl_xor_sync(0xffffffffu, res, 16);  // y pair
+                accz += res;
+                if ((k & 1) == 1) {  // z pair complete
+                    if (in && (lane & 17) == 0)
+                        bc[lindex(Lc, i >> 1, j >> 1, k >> 1)] = accz * T(0.125);
+                    accz = T(0);
+                }
+            }
         }
     }
 }
@@ -620,9 +678,57 @@ __global__ void __launch_bounds__(NTHREADS)
     lev_origin(L, blockIdx.x, i, j, k0);
     if (i >= L.n[0] || j >= L.n[1]) return;
     const int k1 = min(k0 + L.tz, L.n[2]);
-    for (int k = k0; k < k1; ++k) {
-        const int id = lindex(L, i, j, k);
-        if (lev_fluid(L, id)) y[id] += prolong_at(Lc, e, i, j, k);
+    const int plane = L.n[0] * L.n[1];
+    const int base = lindex(L, i, j, 0);
+    // the x / y part of the trilinear weights is fixed for the thread's
+    // column: bil(K) is the bilinear value of coarse plane K at the column,
+    // the same expression prolong_at evaluates for each of its two planes
+    int x0, x1, y0, y1;
+    T wx, wy;
+    tri_axis<T>(i, Lc.n[0], Lc.bc[0], x0, x1, wx);
+    tri_axis<T>(j, Lc.n[1], Lc.bc[1], y0, y1, wy);
+    const T ax = T(1) - wx, ay = T(1) - wy;
+    const int cx = Lc.n[0], cplane = Lc.n[0] * Lc.n[1];
+    const int o00 = y0 * cx + x0, o10 = y0 * cx + x1, o01 = y1 * cx + x0, o11 = y1 * cx + x1;
+    auto bil = [&](int K) -> T {
+        const T* __restrict__ pl = e + K * cplane;
+        return ay * (ax * pl[o00] + wx * pl[o10]) + wy * (ax * pl[o01] + wx * pl[o11]);
+    };
+    // Fine cells 2K and 2K+1 lie in coarse cell K; along z the first takes
+    // its second plane below K, the second above K (tri_axis: the cell itself
+    // at a wall, wrapped when periodic).  Marching K upwards, the planes below
+    // and at K are the previous pair's planes at and above: each plane is
+    // interpolated once.  Tiles start at even k and levels that are
+    // prolonged to have an even nz = 2 Lc.n[2].
+    const T wz = T(0.25), az = T(1) - wz;
+    const int nzc = Lc.n[2];
+    const bool per = Lc.bc[2] == BC_PERIODIC;
+    const int Ks = k0 >> 1;
+    T bm = bil(Ks > 0 ? Ks - 1 : (per ? nzc - 1 : Ks));
+    T bc = bil(Ks);
+    constexpr int CH = 2 * MG_ZB;
+    for (int kb = k0; kb < k1; kb += CH) {
+        // the chunk's y values first, then the planes and the stores
+        T yv[CH];
+        bool fl[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int k = kb + q;
+            fl[q] = k < k1 && lev_fluid(L, base + k * plane);
+            if (fl[q]) yv[q] = y[base + k * plane];
+        }
+#pragma unroll
+        for (int q = 0; q < CH; q += 2) {
+            const int k = kb + q;
+            if (k < k1) {
+                const int K = k >> 1;
+                const T bp = bil(K + 1 < nzc ? K + 1 : (per ? 0 : K));
+                if (fl[q]) y[base + k * plane] = yv[q] + (az * bc + wz * bm);
+                if (fl[q + 1]) y[base + (k + 1) * plane] = yv[q + 1] + (az * bc + wz * bp);
+                bm = bc;
+                bc = bp;
+            }
+        }
     }
 }
 
@@ -786,14 +892,27 @@ __global__ void __launch_bounds__(NTHREADS)
     T acc_t = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto yq = [&](int q) -> T { return y[q]; };
         const NbrXY xy = make_nbr_xy(L, i, j);
-        for (int k = k0; k < k1; ++k) {
-            const Nbr nb = nbr_at(L, xy, k);
-            const int id = nb.c;
-            const T lv = lap_nbr(L, nb, yq, y[id]);
-            v[id] = lv;
-            acc_t += rh[id] * lv;
+        const int plane = L.n[0] * L.n[1];
+        for (int kb = k0; kb < k1; kb += MG_ZB) {
+            Vals7<T> yv[MG_ZB];
+            T rq[MG_ZB];
+#pragma unroll
+            for (int q = 0; q < MG_ZB; ++q) {
+                if (kb + q < k1) {
+                    const Nbr nb = nbr_at(L, xy, kb + q);
+                    yv[q] = load7<T>(nb, y);
+                    rq[q] = rh[nb.c];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MG_ZB; ++q) {
+                if (kb + q < k1) {
+                    const T lv = lap_vals<T>(L, yv[q]);
+                    v[(kb + q) * plane + xy.base] = lv;
+                    acc_t += rq[q] * lv;
+                }
+            }
         }
     }
     T acc[1] = {acc_t};
@@ -819,15 +938,28 @@ __global__ void __launch_bounds__(NTHREADS)
     T ts = T(0), tt = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        auto zq = [&](int q) -> T { return z[q]; };
         const NbrXY xy = make_nbr_xy(L, i, j);
-        for (int k = k0; k < k1; ++k) {
-            const Nbr nb = nbr_at(L, xy, k);
-            const int id = nb.c;
-            const T tv = lap_nbr(L, nb, zq, z[id]);
-            t[id] = tv;
-            ts += tv * sv[id];
-            tt += tv * tv;
+        const int plane = L.n[0] * L.n[1];
+        for (int kb = k0; kb < k1; kb += MG_ZB) {
+            Vals7<T> zv[MG_ZB];
+            T sq[MG_ZB];
+#pragma unroll
+            for (int q = 0; q < MG_ZB; ++q) {
+                if (kb + q < k1) {
+                    const Nbr nb = nbr_at(L, xy, kb + q);
+                    zv[q] = load7<T>(nb, z);
+                    sq[q] = sv[nb.c];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MG_ZB; ++q) {
+                if (kb + q < k1) {
+                    const T tv = lap_vals<T>(L, zv[q]);
+                    t[(kb + q) * plane + xy.base] = tv;
+                    ts += tv * sq[q];
+                    tt += tv * tv;
+                }
+            }
         }
     }
     T acc[2] = {ts, tt};
@@ -892,15 +1024,35 @@ __global__ void __launch_bounds__(NTHREADS)
     T a0 = T(0), a1 = T(0), a2 = T(0);
     if (i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
-        for (int k = k0; k < k1; ++k) {
-            const int id = lindex(L, i, j, k);
-            const T xv = (fresh ? T(0) : x[id]) + (ta * y[id] + tw * z[id]);
-            const T rv = sv[id] - tw * t[id];
-            x[id] = xv;
-            r[id] = rv;
-            a0 += rh[id] * rv;
-            a1 += rv * rv;
-            a2 += xv;
+        const int plane = L.n[0] * L.n[1];
+        const int base = lindex(L, i, j, 0);
+        for (int kb = k0; kb < k1; kb += MG_ZB) {
+            T xo[MG_ZB], yv[MG_ZB], zv[MG_ZB], sq[MG_ZB], tq[MG_ZB], rq[MG_ZB];
+#pragma unroll
+            for (int q = 0; q < MG_ZB; ++q) {
+                if (kb + q < k1) {
+                    const int id = base + (kb + q) * plane;
+                    xo[q] = fresh ? T(0) : x[id];
+                    yv[q] = y[id];
+                    zv[q] = z[id];
+                    sq[q] = sv[id];
+                    tq[q] = t[id];
+                    rq[q] = rh[id];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MG_ZB; ++q) {
+                if (kb + q < k1) {
+                    const int id = base + (kb + q) * plane;
+                    const T xv = xo[q] + (ta * yv[q] + tw * zv[q]);
+                    const T rv = sq[q] - tw * tq[q];
+                    x[id] = xv;
+                    r[id] = rv;
+                    a0 += rq[q] * rv;
+                    a1 += rv * rv;
+                    a2 += xv;
+                }
+            }
         }
     }
     T acc[3] = {a0, a1, a2};
@@ -1169,24 +1321,45 @@ __global__ void __launch_bounds__(NTHREADS)
     if (!bad && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         const NbrXY xy = make_nbr_xy(L, i, j);
-        for (int k = k0; k < k1; ++k) {
-            const Nbr nb = nbr_at(L, xy, k);
-            const int id = nb.c;
-            const long long q = off + id;
-            const float ec = e[id];
-            const FF le = lap_ff_pair(L, nb, e, ec);
-            const FF pn = ff_add_f(FF{f.p_hi[q], f.p_lo[q]}, ec * unscale);
-            FF rn = ff_add(FF{f.r_hi[q], f.r_lo[q]}, FF{-le.hi * unscale, -le.lo * unscale});
-            if (lev_fluid(L, id)) rn = ff_add(rn, neg_rmean);
-            f.p_hi[q] = pn.hi;
-            f.p_lo[q] = pn.lo;
-            f.r_hi[q] = rn.hi;
-            f.r_lo[q] = rn.lo;
-            r[id] = rn.hi * fsc;
-            rh[id] = rn.hi * fsc;
-            arr.add(rn.hi);
-            sp = ff_add(sp, pn);
-            sr = ff_add(sr, rn);
+        const int plane = L.n[0] * L.n[1];
+        for (int kb = k0; kb < k1; kb += MG_ZB) {
+            // the batch's loads first (e on the 7 points, the float-float
+            // iterate and residual), then its arithmetic and stores
+            Vals7<float> ev[MG_ZB];
+            FF po[MG_ZB], ro[MG_ZB];
+            bool fl[MG_ZB];
+#pragma unroll
+            for (int u = 0; u < MG_ZB; ++u) {
+                if (kb + u < k1) {
+                    const Nbr nb = nbr_at(L, xy, kb + u);
+                    const long long q = off + nb.c;
+                    ev[u] = load7<float>(nb, e);
+                    po[u] = FF{f.p_hi[q], f.p_lo[q]};
+                    ro[u] = FF{f.r_hi[q], f.r_lo[q]};
+                    fl[u] = lev_fluid(L, nb.c);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < MG_ZB; ++u) {
+                if (kb + u < k1) {
+                    const int id = (kb + u) * plane + xy.base;
+                    const long long q = off + id;
+                    const float ec = ev[u].c;
+                    const FF le = lap_ff_vals(L, ev[u]);
+                    const FF pn = ff_add_f(po[u], ec * unscale);
+                    FF rn = ff_add(ro[u], FF{-le.hi * unscale, -le.lo * unscale});
+                    if (fl[u]) rn = ff_add(rn, neg_rmean);
+                    f.p_hi[q] = pn.hi;
+                    f.p_lo[q] = pn.lo;
+                    f.r_hi[q] = rn.hi;
+                    f.r_lo[q] = rn.lo;
+                    r[id] = rn.hi * fsc;
+                    rh[id] = rn.hi * fsc;
+                    arr.add(rn.hi);
+                    sp = ff_add(sp, pn);
+                    sr = ff_add(sr, rn);
+                }
+            }
         }
     }
     float acc[2] = {arr.big, arr.small};
