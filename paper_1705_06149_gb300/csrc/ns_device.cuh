@@ -262,12 +262,27 @@ template <int NV>
 __device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ctas,
                                                 double (&out)[NV]) {
     __shared__ double bc[NV];
+    // each thread sums the CTAs t, t + NTHREADS, ... in that order, loading a
+    // batch of them before adding so that the batch's reads overlap
+    constexpr int UB = NV <= 3 ? 4 : 2;
     double v[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = 0.0;
-    for (int c = tid_flat(); c < ctas; c += NTHREADS) {
+    for (int c0 = tid_flat(); c0 < ctas; c0 += UB * NTHREADS) {
+        double buf[UB][NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] += part[(long long)c * NV + q];
+        for (int u = 0; u < UB; ++u) {
+            const int c = c0 + u * NTHREADS;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) buf[u][q] = c < ctas ? part[(long long)c * NV + q] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            if (c0 + u * NTHREADS < ctas) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) v[q] += buf[u][q];
+            }
+        }
     }
     block_sum<NV>(v);
     if (tid_flat() == 0) {

@@ -315,32 +315,6 @@ __device__ __forceinline__ T diag_at(const Lev& L, int i, int j, int k) {
     return d;
 }
 
-// The same Laplacian as lap_cell, on a multigrid level.
-template <typename T, typename F>
-__device__ __forceinline__ T lap_lev(const Lev& L, const F& val, int i, int j, int k, T vc) {
-    T s = T(0);
-    const int c[3] = {i, j, k};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int n = L.n[d];
-        const T w = lw<T>(L, d);
-        int hi[3] = {c[0], c[1], c[2]};
-        int lo[3] = {c[0], c[1], c[2]};
-        if (L.bc[d] == BC_PERIODIC) {
-            hi[d] = c[d] + 1 == n ? 0 : c[d] + 1;
-            lo[d] = c[d] == 0 ? n - 1 : c[d] - 1;
-            s += (val(hi[0], hi[1], hi[2]) - vc) * w;
-            s -= (vc - val(lo[0], lo[1], lo[2])) * w;
-        } else {
-            hi[d] = c[d] + 1;
-            lo[d] = c[d] - 1;
-            if (hi[d] < n) s += (val(hi[0], hi[1], hi[2]) - vc) * w;
-            if (lo[d] >= 0) s -= (vc - val(lo[0], lo[1], lo[2])) * w;
-        }
-    }
-    return s;
-}
-
 __device__ __forceinline__ void lev_origin(const Lev& L, int cta, int& i, int& j, int& k0) {
     int tx = cta % L.bx;
     int r = cta / L.bx;
@@ -368,14 +342,31 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, int ctas) {
 }
 
 // Fixed-order sum of [ctas][NV] partials, read through L2, in the last CTA.
+// Each thread sums the CTAs t, t + NTHREADS, ... in that order; it loads a
+// batch of them before adding, so the reads of the batch overlap (the last
+// CTA's reduction is on the critical path of every solver phase).
 template <int NV>
 __device__ __forceinline__ void sum_partials_l2(const double* part, int ctas, double (&out)[NV]) {
+    constexpr int UB = NV <= 3 ? 4 : 2;
     double v[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = 0.0;
-    for (int c = tid_flat(); c < ctas; c += NTHREADS) {
+    for (int c0 = tid_flat(); c0 < ctas; c0 += UB * NTHREADS) {
+        double buf[UB][NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] += __ldcg(part + (long long)c * NV + q);
+        for (int u = 0; u < UB; ++u) {
+            const int c = c0 + u * NTHREADS;
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+                buf[u][q] = c < ctas ? __ldcg(part + (long long)c * NV + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            if (c0 + u * NTHREADS < ctas) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) v[q] += buf[u][q];
+            }
+        }
     }
     block_sum<NV>(v);
 #pragma unroll
@@ -736,12 +727,6 @@ __global__ void __launch_bounds__(NTHREADS)
 // the small levels in one CTA per state (shared memory)
 // ---------------------------------------------------------------------------
 
-template <typename T>
-__device__ __forceinline__ T lap_smem(const Lev& L, const T* a, int i, int j, int k) {
-    auto v = [&](int x, int y, int z) { return a[lindex(L, x, y, z)]; };
-    return lap_lev(L, v, i, j, k, a[lindex(L, i, j, k)]);
-}
-
 // Cells per thread the one-CTA levels may hold (MG_BLOCK_THREADS threads).
 constexpr int MG_BLOCK_PER_THREAD = 4;
 constexpr int MG_BLOCK_MAX_CELLS = MG_BLOCK_THREADS * MG_BLOCK_PER_THREAD;
@@ -755,11 +740,47 @@ __device__ __forceinline__ void lev_ijk(const Lev& L, unsigned q, int& i, int& j
     i = (int)(r - (unsigned)j * nx);
 }
 
+// A cell of a one-CTA level as one thread holds it across the phases of a
+// level: its coordinates packed 10 bits per axis (every extent of a one-CTA
+// level is at most 1024) and its Jacobi weight w / diag.
+__device__ __forceinline__ int blk_pack(int i, int j, int k) { return i | (j << 10) | (k << 20); }
+
+template <typename T>
+__device__ __forceinline__ T blk_wd(const Lev& L, int pk, T w) {
+    return -neg_over<T>(w, diag_at<T>(L, pk & 1023, (pk >> 10) & 1023, pk >> 20));
+}
+
+// The Neumann Laplacian of a one-CTA level at the packed cell pk (linear
+// index q): per axis the high and the low face term, the neighbour wrapped
+// across a periodic seam and clamped to the cell itself across a wall (that
+// face term is then exactly 0: the wall face drops out of L).
+template <typename T>
+__device__ __forceinline__ T blk_lap(const Lev& L, int pk, int q, const T* a) {
+    const int c[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+    const int st[3] = {1, L.n[0], L.n[0] * L.n[1]};
+    const T vc = a[q];
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int n = L.n[d];
+        const bool per = L.bc[d] == BC_PERIODIC;
+        const int lo = c[d] > 0 ? -st[d] : (per ? (n - 1) * st[d] : 0);
+        const int hi = c[d] + 1 < n ? st[d] : (per ? -(n - 1) * st[d] : 0);
+        const T w = lw<T>(L, d);
+        s += (a[q + hi] - vc) * w;
+        s -= (vc - a[q + lo]) * w;
+    }
+    return s;
+}
+
 // V(2,0) cycle on levels plan.lc .. nlev-1 for the right side `in` (global,
 // level lc); writes the result to `out` (global, level lc).  Shared memory per
-// level m: the right side b_m and the iterate y_m; a Jacobi sweep that reads
-// neighbours of y_m stages its results in registers (at most
-// MG_BLOCK_PER_THREAD cells per thread) and writes them back after a barrier.
+// level m: the right side b_m and the iterate y_m.  Thread t holds the cells
+// t + c * blockDim.x (c < MG_BLOCK_PER_THREAD) of a level; their coordinates
+// and Jacobi weights are computed once per level visit and kept in registers.
+// A Jacobi sweep stages its results in registers and writes them back after a
+// barrier; the residual b - L y replaces b (a V(2,0) cycle does not need b
+// again) and the restriction is the mean of its 8 children.
 template <typename T>
 __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     k_mg_block(MgPlan plan, SliceCtl* __restrict__ ctl, const T* __restrict__ in_even,
@@ -784,23 +805,33 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     }
     const unsigned t = threadIdx.x, nt = blockDim.x;
     const T w = T(MG_OMEGA);
-    // w / diagonal at a cell
-    auto wdiag = [&](const Lev& L, int i, int j, int k) -> T {
-        return -neg_over<T>(w, diag_at<T>(L, i, j, k));
-    };
-    // one Jacobi sweep y <- y + w (b - L y) / d over a level, in place
-    auto sweep = [&](int m) {
+    // the thread's cells of level m: packed coordinates and Jacobi weights
+    int pk[MG_BLOCK_PER_THREAD];
+    T wd[MG_BLOCK_PER_THREAD];
+    auto cells_of = [&](int m) {
         const Lev& L = plan.lev[m];
-        const unsigned cells = (unsigned)L.cells;
+#pragma unroll
+        for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
+            const unsigned q = t + c * nt;
+            pk[c] = 0;
+            wd[c] = T(0);
+            if (q < (unsigned)L.cells) {
+                int i, j, k;
+                lev_ijk(L, q, i, j, k);
+                pk[c] = blk_pack(i, j, k);
+                wd[c] = blk_wd<T>(L, pk[c], w);
+            }
+        }
+    };
+    // one Jacobi sweep y <- y + w (b - L y) / d over level m, in place
+    auto sweep = [&](int m) {
+        const unsigned cells = (unsigned)plan.lev[m].cells;
         T nv[MG_BLOCK_PER_THREAD];
 #pragma unroll
         for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
             const unsigned q = t + c * nt;
-            if (q < cells) {
-                int i, j, k;
-                lev_ijk(L, q, i, j, k);
-                nv[c] = yq[m][q] + wdiag(L, i, j, k) * (bq[m][q] - lap_smem(L, yq[m], i, j, k));
-            }
+            if (q < cells)
+                nv[c] = yq[m][q] + wd[c] * (bq[m][q] - blk_lap<T>(plan.lev[m], pk[c], (int)q, yq[m]));
         }
         __syncthreads();
 #pragma unroll
@@ -816,28 +847,33 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
         for (unsigned q = t; q < (unsigned)L.cells; q += nt) bq[lc][q] = src[q];
     }
     __syncthreads();
-    // down: two Jacobi sweeps from zero, restrict the residual
+    // down: two Jacobi sweeps from zero, the residual, its restriction
     for (int m = lc; m < nl - 1; ++m) {
         const Lev& L = plan.lev[m];
         const Lev& Lc = plan.lev[m + 1];
-        for (unsigned q = t; q < (unsigned)L.cells; q += nt) {
-            int i, j, k;
-            lev_ijk(L, q, i, j, k);
-            yq[m][q] = wdiag(L, i, j, k) * bq[m][q];
+        const unsigned cells = (unsigned)L.cells;
+        cells_of(m);
+#pragma unroll
+        for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
+            const unsigned q = t + c * nt;
+            if (q < cells) yq[m][q] = wd[c] * bq[m][q];
         }
         __syncthreads();
         sweep(m);
+#pragma unroll
+        for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
+            const unsigned q = t + c * nt;
+            if (q < cells) bq[m][q] = bq[m][q] - blk_lap<T>(L, pk[c], (int)q, yq[m]);
+        }
+        __syncthreads();
         for (unsigned q = t; q < (unsigned)Lc.cells; q += nt) {
             int I, J, K;
             lev_ijk(Lc, q, I, J, K);
             T acc = T(0);
             for (int dz = 0; dz < 2; ++dz)
                 for (int dy = 0; dy < 2; ++dy)
-                    for (int dx = 0; dx < 2; ++dx) {
-                        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                        const int f = lindex(L, i, j, k);
-                        acc += bq[m][f] - lap_smem(L, yq[m], i, j, k);
-                    }
+                    for (int dx = 0; dx < 2; ++dx)
+                        acc += bq[m][lindex(L, 2 * I + dx, 2 * J + dy, 2 * K + dz)];
             bq[m + 1][q] = acc * T(0.125);
         }
         __syncthreads();
@@ -846,6 +882,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     {
         const int m = nl - 1;
         const Lev& L = plan.lev[m];
+        cells_of(m);
         for (unsigned q = t; q < (unsigned)L.cells; q += nt) yq[m][q] = T(0);
         __syncthreads();
         // enough sweeps for the coarsest level's size; a 2^3 level needs few
