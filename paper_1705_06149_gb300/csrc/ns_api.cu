@@ -252,7 +252,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
         L.by = ceil_div(L.n[1], TY);
         L.bz = ceil_div(L.n[2], L.tz);
         L.ctas = L.bx * L.by * L.bz;
-        L.rbx = ceil_div(L.n[0], 16);
+        L.rbx = ceil_div(L.n[0], 32);
         L.rby = ceil_div(L.n[1], 8);
         L.rctas = L.rbx * L.rby * L.bz;
     };

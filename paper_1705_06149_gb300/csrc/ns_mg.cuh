@@ -47,7 +47,7 @@ struct Lev {
     float lih2[3];  // ih2 - fih2 (the FP32 remainder: fih2 + lih2 = ih2 to ~2^-48)
     long long cells;
     int tz, bx, by, bz, ctas;
-    int rbx, rby, rctas;   // restriction tiling: 16 x 8 cells per CTA plane
+    int rbx, rby, rctas;   // restriction tiling: 32 x 8 cells per CTA plane
 };
 
 template <typename T> __device__ __forceinline__ T lw(const Lev& L, int d);
@@ -563,6 +563,19 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
+// Two consecutive values at an even index as one vector load (the arrays of
+// every level that is restricted have even rows, planes and states).
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+template <typename T>
+__device__ __forceinline__ void load_pair(const T* __restrict__ p, T& a, T& b) {
+    const typename Pair2<T>::type v = *reinterpret_cast<const typename Pair2<T>::type*>(p);
+    a = v.x;
+    b = v.y;
+}
+
 // Residual b - L y on level l, restricted (mean of the 8 children) to level l+1.
 // b is bsrc, or with bsrc_odd given the one of the pair (bsrc, bsrc_odd) that
 // the iteration's parity selects.
@@ -577,44 +590,72 @@ __global__ void __launch_bounds__(NTHREADS)
         (bsrc_odd != nullptr && iter_parity(ctl + s) ? bsrc_odd : bsrc) + s * L.cells;
     const T* __restrict__ y = ysrc + s * L.cells;
     T* __restrict__ bc = bdst + s * Lc.cells;
-    // a warp covers 16 x 2 cells: the x pair of a child octet is lanes
-    // (l, l^1), the y pair lanes (l, l^16), the z pair two steps of the march,
-    // so the octet sums need no shared memory (sizes are even on every level
-    // that is restricted, and tiles start at even indices)
+    // A thread holds the x pair (i, i+1) of a child octet, a warp 16 pairs of
+    // two rows: the y pair of an octet is lanes (l, l^16), the z pair two
+    // steps of the march, so the octet sums need no shared memory (sizes are
+    // even on every level that is restricted, and tiles start at even indices)
     const int lane = threadIdx.x, warp = threadIdx.y;
     const int tx = blockIdx.x % L.rbx;
     const int rest = blockIdx.x / L.rbx;
     const int ty = rest % L.rby;
-    const int i = tx * 16 + (lane & 15);
+    const int i = tx * 32 + 2 * (lane & 15);
     const int j = ty * 8 + warp * 2 + (lane >> 4);
     const int k0 = (rest / L.rby) * L.tz;
     const bool in = i < L.n[0] && j < L.n[1];
     const int k1 = min(k0 + L.tz, L.n[2]);
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+    // neighbour offsets from cell i: its low x neighbour, the high x
+    // neighbour of cell i+1 (its own low neighbour is i, the high one of i is
+    // i+1), and the rows below / above (clamped at walls, wrapped when periodic)
+    int lo, hi, act, xlo_i, xhi_i1, jl, jh;
+    axis_nbr(i, nx, L.bc[0], xlo_i, hi, act);
+    axis_nbr(i + 1, nx, L.bc[0], lo, xhi_i1, act);
+    axis_nbr(j, L.n[1], L.bc[1], jl, jh, act);
+    const int ox_lo = xlo_i - i, ox_hi = xhi_i1 - i;
+    const int oy_lo = (jl - j) * nx, oy_hi = (jh - j) * nx;
+    const bool masked = L.fcode != nullptr;
+    const NbrXY xy0 = make_nbr_xy(L, i, j);
+    const NbrXY xy1 = make_nbr_xy(L, i + 1, j);
     T accz = T(0);
-    const NbrXY xy = make_nbr_xy(L, i, j);
-    for (int kb = k0; kb < k1; kb += MG_ZB) {
-        // the batch's loads first, then its residuals and octet sums
-        Vals7<T> yv[MG_ZB];
-        T bv[MG_ZB];
+    for (int kb = k0; kb < k1; kb += 2) {
+        // the z pair's loads first, then its residuals and octet sums
+        T r0[2], r1[2];
 #pragma unroll
-        for (int q = 0; q < MG_ZB; ++q) {
-            if (in && kb + q < k1) {
-                const Nbr nb = nbr_at(L, xy, kb + q);
-                yv[q] = load7<T>(nb, y);
-                bv[q] = b[nb.c];
+        for (int q = 0; q < 2; ++q) {
+            r0[q] = T(0);
+            r1[q] = T(0);
+            const int k = kb + q;
+            if (!in || k >= k1) continue;
+            if (masked) {
+                // solid cells: per-cell stencil arms from the face codes
+                const Nbr n0 = nbr_at(L, xy0, k), n1 = nbr_at(L, xy1, k);
+                r0[q] = b[n0.c] - lap_vals<T>(L, load7<T>(n0, y));
+                r1[q] = b[n1.c] - lap_vals<T>(L, load7<T>(n1, y));
+            } else {
+                int kl, kh;
+                axis_nbr(k, L.n[2], L.bc[2], kl, kh, act);
+                const int c = k * nxy + j * nx + i;
+                T y0, y1, yl0, yl1, yh0, yh1, zl0, zl1, zh0, zh1, b0, b1;
+                load_pair<T>(y + c, y0, y1);
+                load_pair<T>(y + c + oy_lo, yl0, yl1);
+                load_pair<T>(y + c + oy_hi, yh0, yh1);
+                load_pair<T>(y + c + (kl - k) * nxy, zl0, zl1);
+                load_pair<T>(y + c + (kh - k) * nxy, zh0, zh1);
+                load_pair<T>(b + c, b0, b1);
+                const T xl0 = y[c + ox_lo], xh1 = y[c + ox_hi];
+                r0[q] = b0 - lap7<T>(L, y1, xl0, yh0, yl0, zh0, zl0, y0);
+                r1[q] = b1 - lap7<T>(L, xh1, y0, yh1, yl1, zh1, zl1, y1);
             }
         }
 #pragma unroll
-        for (int q = 0; q < MG_ZB; ++q) {
+        for (int q = 0; q < 2; ++q) {
             const int k = kb + q;
             if (k < k1) {  // the same for the whole CTA
-                T res = T(0);
-                if (in) res = bv[q] - lap_vals<T>(L, yv[q]);
-                res += __shfl_xor_sync(0xffffffffu, res, 1);   // x pair
+                T res = r0[q] + r1[q];                         // x pair
                 res += __shfl_xor_sync(0xffffffffu, res, 16);  // y pair
                 accz += res;
                 if ((k & 1) == 1) {  // z pair complete
-                    if (in && (lane & 17) == 0)
+                    if (in && lane < 16)
                         bc[lindex(Lc, i >> 1, j >> 1, k >> 1)] = accz * T(0.125);
                     accz = T(0);
                 }
