@@ -515,7 +515,14 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
     const int lc = P.lc;
     const dim3 blk = block_dim();
     const Lev& L0 = P.lev[0];
-    if (lc > 0)
+    if (lc > 0 && L0.fcode == nullptr && L0.n[0] % 2 == 0) {
+        // x pairs per thread (no solid cells, even nx)
+        const int pbx = ceil_div(L0.n[0], 64);
+        NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
+                  (k_mg_src_pair<T, MODE>
+                   <<<dim3(pbx * L0.by * L0.bz, batch), blk, 0, g->stream>>>(L0, mb, g->ctl, dst,
+                                                                               pbx)));
+    } else if (lc > 0)
         NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
                   (k_mg_src<T, MODE, true><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
                       L0, mb, g->ctl, nullptr, dst)));

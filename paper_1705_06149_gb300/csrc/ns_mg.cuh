@@ -438,6 +438,19 @@ __device__ __forceinline__ bool partials_and_arrive(double (&acc)[NV], double* p
 // level-0 sources and the pre-smoothing of a level
 // ---------------------------------------------------------------------------
 
+// Two consecutive values at an even index as one vector load (the arrays of
+// every level that is restricted have even rows, planes and states).
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+template <typename T>
+__device__ __forceinline__ void load_pair(const T* __restrict__ p, T& a, T& b) {
+    const typename Pair2<T>::type v = *reinterpret_cast<const typename Pair2<T>::type*>(p);
+    a = v.x;
+    b = v.y;
+}
+
 enum { SRC_P = 0, SRC_S = 1, SRC_ARR = 2 };
 
 // Parity of the iteration in progress (1 for the first): selects the
@@ -563,17 +576,163 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
-// Two consecutive values at an even index as one vector load (the arrays of
-// every level that is restricted have even rows, planes and states).
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
-
-template <typename T>
-__device__ __forceinline__ void load_pair(const T* __restrict__ p, T& a, T& b) {
-    const typename Pair2<T>::type v = *reinterpret_cast<const typename Pair2<T>::type*>(p);
-    a = v.x;
-    b = v.y;
+// The same as k_mg_src<T, MODE, true> (MODE SRC_P or SRC_S) on a level without
+// solid cells and with an even nx, a thread holding the x pair (i, i+1): the
+// source values of the pair, of the rows beside it and of the plane above are
+// evaluated once per pair from paired vector loads, those of the pair's x
+// neighbours i-1 and i+2 singly, and the plane below and the pair itself are
+// carried along the march.  Every cell's arithmetic is that of k_mg_src.
+// Tiling: 32 x 4 threads cover 64 x 4 cells of a plane; pbx = ceil(nx / 64).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_src_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
+                  int pbx) {
+    const long long s = blockIdx.y;
+    const SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const int par = iter_parity(c);
+    const long long off = s * L.cells;
+    const T* __restrict__ r = mb.r + off;
+    T* __restrict__ rh = mb.rhat + off;
+    const T* __restrict__ po = mb.P[par ^ 1] + off;
+    const T* __restrict__ vo = mb.V[par ^ 1] + off;
+    T* __restrict__ pn = mb.P[par] + off;
+    const T* __restrict__ vn = mb.V[par] + off;
+    T* __restrict__ sv = mb.S + off;
+    T* __restrict__ y = ydst + off;
+    const bool restart = c->restart != 0;
+    const bool first = c->it_cur == 0;
+    const T tb = T(c->beta), tw = T(c->omega), ta = T(c->alpha);
+    auto src1 = [&](int q) -> T {
+        if (MODE == SRC_P) return restart ? r[q] : r[q] + tb * (po[q] - tw * vo[q]);
+        return r[q] - ta * vn[q];
+    };
+    auto src2 = [&](int q, T& a, T& b) {
+        T r0, r1;
+        load_pair<T>(r + q, r0, r1);
+        if (MODE == SRC_P) {
+            if (restart) {
+                a = r0;
+                b = r1;
+            } else {
+                T p0, p1, v0, v1;
+                load_pair<T>(po + q, p0, p1);
+                load_pair<T>(vo + q, v0, v1);
+                a = r0 + tb * (p0 - tw * v0);
+                b = r1 + tb * (p1 - tw * v1);
+            }
+        } else {
+            T v0, v1;
+            load_pair<T>(vn + q, v0, v1);
+            a = r0 - ta * v0;
+            b = r1 - ta * v1;
+        }
+    };
+    const int cta = blockIdx.x;
+    const int tx = cta % pbx;
+    const int rest = cta / pbx;
+    const int i = tx * 64 + 2 * (int)threadIdx.x;
+    const int j = (rest % L.by) * TY + (int)threadIdx.y;
+    const int k0 = (rest / L.by) * L.tz;
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+    if (i >= nx || j >= L.n[1]) return;
+    const int k1 = min(k0 + L.tz, L.n[2]);
+    const T w = T(MG_OMEGA);
+    // x neighbours of the two cells, the rows beside them, and the separable
+    // diagonal parts (as k_mg_src evaluates them for each cell)
+    int ila, iha, ilb, ihb, jl, jh, act;
+    axis_nbr(i, nx, L.bc[0], ila, iha, act);
+    axis_nbr(i + 1, nx, L.bc[0], ilb, ihb, act);
+    axis_nbr(j, L.n[1], L.bc[1], jl, jh, act);
+    const int ox_lo = ila - i, ox_hi = ihb - i;  // from cell i: x-low of i, x-high of i+1
+    const int oy_lo = (jl - j) * nx, oy_hi = (jh - j) * nx;
+    const T dxa = diag_axis<T>(L, 0, i), dxla = diag_axis<T>(L, 0, ila), dxha = diag_axis<T>(L, 0, iha);
+    const T dxb = diag_axis<T>(L, 0, i + 1), dxlb = diag_axis<T>(L, 0, ilb),
+            dxhb = diag_axis<T>(L, 0, ihb);
+    const T dyc = diag_axis<T>(L, 1, j), dyl = diag_axis<T>(L, 1, jl), dyh = diag_axis<T>(L, 1, jh);
+    const T dz2 = T(2) * lw<T>(L, 2);
+    const T icIa = neg_over<T>(w, dxa + dyc + dz2), icIb = neg_over<T>(w, dxb + dyc + dz2);
+    const T icxhIa = neg_over<T>(w, dxha + dyc + dz2), icxlIa = neg_over<T>(w, dxla + dyc + dz2);
+    const T icxhIb = neg_over<T>(w, dxhb + dyc + dz2), icxlIb = neg_over<T>(w, dxlb + dyc + dz2);
+    const T icyhIa = neg_over<T>(w, dxa + dyh + dz2), icylIa = neg_over<T>(w, dxa + dyl + dz2);
+    const T icyhIb = neg_over<T>(w, dxb + dyh + dz2), icylIb = neg_over<T>(w, dxb + dyl + dz2);
+    const T w0 = lw<T>(L, 0), w1 = lw<T>(L, 1), w2 = lw<T>(L, 2);
+    // the source at the plane below and at the pair, carried along the march
+    T zla, zlb, bca, bcb;
+    {
+        int kl, kh;
+        axis_nbr(k0, L.n[2], L.bc[2], kl, kh, act);
+        const int cq = k0 * nxy + j * nx + i;
+        src2(cq + (kl - k0) * nxy, zla, zlb);
+        src2(cq, bca, bcb);
+    }
+    for (int k = k0; k < k1; ++k) {
+        int kl, kh;
+        axis_nbr(k, L.n[2], L.bc[2], kl, kh, act);
+        const int cq = k * nxy + j * nx + i;
+        T zha, zhb, yla, ylb, yha, yhb;
+        src2(cq + (kh - k) * nxy, zha, zhb);
+        src2(cq + oy_lo, yla, ylb);
+        src2(cq + oy_hi, yha, yhb);
+        const T sxl = src1(cq + ox_lo), sxh = src1(cq + ox_hi);
+        if (MODE == SRC_P) {
+            reinterpret_cast<typename Pair2<T>::type*>(pn + cq)[0] = {bca, bcb};
+            if (restart && !first) {
+                T r0, r1;
+                load_pair<T>(r + cq, r0, r1);
+                reinterpret_cast<typename Pair2<T>::type*>(rh + cq)[0] = {r0, r1};
+            }
+        }
+        if (MODE == SRC_S) reinterpret_cast<typename Pair2<T>::type*>(sv + cq)[0] = {bca, bcb};
+        T ica, icxha, icxla, icyha, icyla, iczha, iczla;
+        T icb, icxhb, icxlb, icyhb, icylb, iczhb, iczlb;
+        if (L.bc[2] == BC_PERIODIC || (k >= 2 && k + 2 < L.n[2])) {
+            ica = icIa;
+            icxha = icxhIa;
+            icxla = icxlIa;
+            icyha = icyhIa;
+            icyla = icylIa;
+            iczha = iczla = icIa;
+            icb = icIb;
+            icxhb = icxhIb;
+            icxlb = icxlIb;
+            icyhb = icyhIb;
+            icylb = icylIb;
+            iczhb = iczlb = icIb;
+        } else {
+            const T dzc = diag_axis<T>(L, 2, k), dzl = diag_axis<T>(L, 2, kl),
+                    dzh = diag_axis<T>(L, 2, kh);
+            ica = neg_over<T>(w, dxa + dyc + dzc);
+            icxha = neg_over<T>(w, dxha + dyc + dzc);
+            icxla = neg_over<T>(w, dxla + dyc + dzc);
+            icyha = neg_over<T>(w, dxa + dyh + dzc);
+            icyla = neg_over<T>(w, dxa + dyl + dzc);
+            iczha = neg_over<T>(w, dxa + dyc + dzh);
+            iczla = neg_over<T>(w, dxa + dyc + dzl);
+            icb = neg_over<T>(w, dxb + dyc + dzc);
+            icxhb = neg_over<T>(w, dxhb + dyc + dzc);
+            icxlb = neg_over<T>(w, dxlb + dyc + dzc);
+            icyhb = neg_over<T>(w, dxb + dyh + dzc);
+            icylb = neg_over<T>(w, dxb + dyl + dzc);
+            iczhb = neg_over<T>(w, dxb + dyc + dzh);
+            iczlb = neg_over<T>(w, dxb + dyc + dzl);
+        }
+        // cell i: x-high neighbour i+1 (bcb), x-low i-1 (sxl); cell i+1:
+        // x-high i+2 (sxh), x-low i (bca)
+        const T y0a = ica * bca, y0b = icb * bcb;
+        const T lapa = (icxha * bcb + icxla * sxl - T(2) * y0a) * w0 +
+                       (icyha * yha + icyla * yla - T(2) * y0a) * w1 +
+                       (iczha * zha + iczla * zla - T(2) * y0a) * w2;
+        const T lapb = (icxhb * sxh + icxlb * bca - T(2) * y0b) * w0 +
+                       (icyhb * yhb + icylb * ylb - T(2) * y0b) * w1 +
+                       (iczhb * zhb + iczlb * zlb - T(2) * y0b) * w2;
+        reinterpret_cast<typename Pair2<T>::type*>(y + cq)[0] = {y0a + ica * (bca - lapa),
+                                                                 y0b + icb * (bcb - lapb)};
+        zla = bca;
+        zlb = bcb;
+        bca = zha;
+        bcb = zhb;
+    }
 }
 
 // Residual b - L y on level l, restricted (mean of the 8 children) to level l+1.
