@@ -551,9 +551,20 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
                   P, g->ctl, bin, bin_odd, bout));
     for (int l = lc - 1; l >= 0; --l) {
         T* y = l == 0 ? dst : mb.Yl[l];
-        NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
-                  k_mg_prolong<T><<<dim3(P.lev[l].ctas, batch), blk, 0, g->stream>>>(
-                      P.lev[l], P.lev[l + 1], g->ctl, y, mb.Yl[l + 1]));
+        const Lev& L = P.lev[l];
+        if (L.fcode == nullptr) {
+            // x pairs per thread (no solid cells; nx is even on every level
+            // prolonged to)
+            const int pbx = ceil_div(L.n[0], 64);
+            NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
+                      k_mg_prolong_pair<T><<<dim3(pbx * L.by * L.bz, batch), blk, 0,
+                                             g->stream>>>(L, P.lev[l + 1], g->ctl, y,
+                                                          mb.Yl[l + 1], pbx));
+        } else {
+            NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
+                      k_mg_prolong<T><<<dim3(L.ctas, batch), blk, 0, g->stream>>>(
+                          L, P.lev[l + 1], g->ctl, y, mb.Yl[l + 1]));
+        }
     }
 }
 
@@ -567,12 +578,27 @@ ns_status mg_iteration(ns_grid* g, int batch, double tol2, int zero_start) {
     const Lev& L0 = g->plan.lev[0];
     MgBuf<T> mb = mgbuf<T>(g);
     const dim3 grid(L0.ctas, batch), blk = block_dim();
+    // x pairs per thread where the level has no solid cells and an even nx
+    const bool pair = L0.fcode == nullptr && L0.n[0] % 2 == 0;
+    const int pbx = ceil_div(L0.n[0], 64);
+    const int pctas = pbx * L0.by * L0.bz;
+    const dim3 pgrid(pctas, batch);
     mg_apply<T, SRC_P>(g, batch, mb, mb.P[0], mb.P[1], mb.Y);
-    NS_LAUNCH(g, NS_K_MG_LAP_V, 0,
-              k_mg_lapdot_v<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
+    if (pair)
+        NS_LAUNCH(g, NS_K_MG_LAP_V, 0,
+                  (k_mg_lapdot_pair<T, 0><<<pgrid, blk, 0, g->stream>>>(L0, mb, g->ctl,
+                                                                       g->part_mg, pbx, pctas)));
+    else
+        NS_LAUNCH(g, NS_K_MG_LAP_V, 0,
+                  k_mg_lapdot_v<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
     mg_apply<T, SRC_S>(g, batch, mb, mb.S, nullptr, mb.Z);
-    NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
-              k_mg_lapdot_t<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
+    if (pair)
+        NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
+                  (k_mg_lapdot_pair<T, 1><<<pgrid, blk, 0, g->stream>>>(L0, mb, g->ctl,
+                                                                       g->part_mg, pbx, pctas)));
+    else
+        NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
+                  k_mg_lapdot_t<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
     NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
               k_mg_update<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, tol2,
                                                            g->maxit, zero_start));

@@ -923,6 +923,71 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
+// k_mg_prolong on a level without solid cells, a thread holding the x pair
+// (i, i+1) (nx is even on every level prolonged to): both cells lie in coarse
+// column i/2 and take their second x column on opposite sides, so a coarse
+// plane costs six loads for the pair; the pair's y values move as one vector.
+// Each cell's arithmetic is that of k_mg_prolong.  Tiling as k_mg_src_pair.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_prolong_pair(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
+                      const T* __restrict__ ecoarse, int pbx) {
+    const long long s = blockIdx.y;
+    if (ctl[s].status != ST_ITER) return;
+    T* __restrict__ y = ydst + s * L.cells;
+    const T* __restrict__ e = ecoarse + s * Lc.cells;
+    const int cta = blockIdx.x;
+    const int tx = cta % pbx;
+    const int rest = cta / pbx;
+    const int i = tx * 64 + 2 * (int)threadIdx.x;
+    const int j = (rest % L.by) * TY + (int)threadIdx.y;
+    const int k0 = (rest / L.by) * L.tz;
+    if (i >= L.n[0] || j >= L.n[1]) return;
+    const int k1 = min(k0 + L.tz, L.n[2]);
+    const int plane = L.n[0] * L.n[1];
+    const int base = lindex(L, i, j, 0);
+    int x0, x1a, x1b, y0, y1, xdup;
+    T wxa, wxb, wy;
+    tri_axis<T>(i, Lc.n[0], Lc.bc[0], x0, x1a, wxa);
+    tri_axis<T>(i + 1, Lc.n[0], Lc.bc[0], xdup, x1b, wxb);
+    tri_axis<T>(j, Lc.n[1], Lc.bc[1], y0, y1, wy);
+    const T axa = T(1) - wxa, axb = T(1) - wxb, ay = T(1) - wy;
+    const int cx = Lc.n[0], cplane = Lc.n[0] * Lc.n[1];
+    const int r0 = y0 * cx, r1 = y1 * cx;
+    // bilinear values of coarse plane K at the two columns
+    auto bil = [&](int K, T& va, T& vb) {
+        const T* __restrict__ pl = e + K * cplane;
+        const T e00 = pl[r0 + x0], e01 = pl[r1 + x0];
+        const T ea0 = pl[r0 + x1a], ea1 = pl[r1 + x1a];
+        const T eb0 = pl[r0 + x1b], eb1 = pl[r1 + x1b];
+        va = ay * (axa * e00 + wxa * ea0) + wy * (axa * e01 + wxa * ea1);
+        vb = ay * (axb * e00 + wxb * eb0) + wy * (axb * e01 + wxb * eb1);
+    };
+    const T wz = T(0.25), az = T(1) - wz;
+    const int nzc = Lc.n[2];
+    const bool per = Lc.bc[2] == BC_PERIODIC;
+    const int Ks = k0 >> 1;
+    T bma, bmb, bca, bcb;
+    bil(Ks > 0 ? Ks - 1 : (per ? nzc - 1 : Ks), bma, bmb);
+    bil(Ks, bca, bcb);
+    for (int k = k0; k < k1; k += 2) {
+        const int K = k >> 1;
+        T ya0, yb0, ya1 = T(0), yb1 = T(0), bpa, bpb;
+        load_pair<T>(y + base + k * plane, ya0, yb0);
+        if (k + 1 < k1) load_pair<T>(y + base + (k + 1) * plane, ya1, yb1);
+        bil(K + 1 < nzc ? K + 1 : (per ? 0 : K), bpa, bpb);
+        reinterpret_cast<typename Pair2<T>::type*>(y + base + k * plane)[0] = {
+            ya0 + (az * bca + wz * bma), yb0 + (az * bcb + wz * bmb)};
+        if (k + 1 < k1)
+            reinterpret_cast<typename Pair2<T>::type*>(y + base + (k + 1) * plane)[0] = {
+                ya1 + (az * bca + wz * bpa), yb1 + (az * bcb + wz * bpb)};
+        bma = bca;
+        bmb = bcb;
+        bca = bpa;
+        bcb = bpb;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the small levels in one CTA per state (shared memory)
 // ---------------------------------------------------------------------------
@@ -1204,6 +1269,102 @@ __global__ void __launch_bounds__(NTHREADS)
     if (partials_arrive<T, 2>(acc, part + s * L.ctas * 2, mb.counter + s, L.ctas, tot) &&
         tid_flat() == 0)
         c->omega = tot[1] != 0.0 ? tot[0] / tot[1] : 0.0;
+}
+
+// k_mg_lapdot_v (WHICH 0: v = L y, (r_hat, v); the last CTA sets alpha) and
+// k_mg_lapdot_t (WHICH 1: t = L z, (t, s), (t, t); the last CTA sets omega)
+// on a level without solid cells and with an even nx, a thread holding the x
+// pair (i, i+1): the pair, its rows beside and its plane above from paired
+// loads, its x neighbours singly, the plane below and the pair itself carried
+// along the march.  Each cell's Laplacian is that of lap_nbr.  Tiling as
+// k_mg_src_pair (ctas = pbx * by * bz CTAs per state reduce their partials).
+template <typename T, int WHICH>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_lapdot_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
+                     int pbx, int ctas) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const long long off = s * L.cells;
+    const T* __restrict__ a;   // the operand: y or z
+    const T* __restrict__ d;   // r_hat or s
+    T* __restrict__ o;         // v or t
+    if (WHICH == 0) {
+        const int par = iter_parity(c);
+        a = mb.Y + off;
+        d = mb.rhat + off;
+        o = mb.V[par] + off;
+    } else {
+        a = mb.Z + off;
+        d = mb.S + off;
+        o = mb.Tt + off;
+    }
+    const int cta = blockIdx.x;
+    const int tx = cta % pbx;
+    const int rest = cta / pbx;
+    const int i = tx * 64 + 2 * (int)threadIdx.x;
+    const int j = (rest % L.by) * TY + (int)threadIdx.y;
+    const int k0 = (rest / L.by) * L.tz;
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+    T acc0 = T(0), acc1 = T(0);
+    if (i < nx && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        int ila, iha, ilb, ihb, jl, jh, act;
+        axis_nbr(i, nx, L.bc[0], ila, iha, act);
+        axis_nbr(i + 1, nx, L.bc[0], ilb, ihb, act);
+        axis_nbr(j, L.n[1], L.bc[1], jl, jh, act);
+        const int ox_lo = ila - i, ox_hi = ihb - i;
+        const int oy_lo = (jl - j) * nx, oy_hi = (jh - j) * nx;
+        T zla, zlb, ca, cb;
+        {
+            int kl, kh;
+            axis_nbr(k0, L.n[2], L.bc[2], kl, kh, act);
+            const int cq = k0 * nxy + j * nx + i;
+            load_pair<T>(a + cq + (kl - k0) * nxy, zla, zlb);
+            load_pair<T>(a + cq, ca, cb);
+        }
+        for (int k = k0; k < k1; ++k) {
+            int kl, kh;
+            axis_nbr(k, L.n[2], L.bc[2], kl, kh, act);
+            const int cq = k * nxy + j * nx + i;
+            T zha, zhb, yla, ylb, yha, yhb, da, db;
+            load_pair<T>(a + cq + (kh - k) * nxy, zha, zhb);
+            load_pair<T>(a + cq + oy_lo, yla, ylb);
+            load_pair<T>(a + cq + oy_hi, yha, yhb);
+            load_pair<T>(d + cq, da, db);
+            const T xla = a[cq + ox_lo], xhb = a[cq + ox_hi];
+            // cell i: x-high i+1 (cb), x-low i-1; cell i+1: x-high i+2, x-low i (ca)
+            const T la = lap7<T>(L, cb, xla, yha, yla, zha, zla, ca);
+            const T lb = lap7<T>(L, xhb, ca, yhb, ylb, zhb, zlb, cb);
+            reinterpret_cast<typename Pair2<T>::type*>(o + cq)[0] = {la, lb};
+            if (WHICH == 0) {
+                acc0 += da * la;
+                acc0 += db * lb;
+            } else {
+                acc0 += la * da;
+                acc1 += la * la;
+                acc0 += lb * db;
+                acc1 += lb * lb;
+            }
+            zla = ca;
+            zlb = cb;
+            ca = zha;
+            cb = zhb;
+        }
+    }
+    if (WHICH == 0) {
+        T acc[1] = {acc0};
+        double tot[1];
+        if (partials_arrive<T, 1>(acc, part + s * ctas, mb.counter + s, ctas, tot) &&
+            tid_flat() == 0)
+            c->alpha = c->rho[0] / tot[0];
+    } else {
+        T acc[2] = {acc0, acc1};
+        double tot[2];
+        if (partials_arrive<T, 2>(acc, part + s * ctas * 2, mb.counter + s, ctas, tot) &&
+            tid_flat() == 0)
+            c->omega = tot[1] != 0.0 ? tot[0] / tot[1] : 0.0;
+    }
 }
 
 // Decision after an iteration (or after a start), in the last CTA:
