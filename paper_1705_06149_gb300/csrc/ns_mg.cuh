@@ -857,6 +857,24 @@ __device__ __forceinline__ T prolong_at(const Lev& Lc, const T* e, int i, int j,
     return az * lo + wz * hi;
 }
 
+// prolong_at with the coarse neighbours as offsets from the coarse cell (the
+// same eight values in the same expression).
+template <typename T>
+__device__ __forceinline__ T prolong_off(const Lev& Lc, const T* e, int i, int j, int k) {
+    int x0, x1, y0, y1, z0, z1;
+    T wx, wy, wz;
+    tri_axis<T>(i, Lc.n[0], Lc.bc[0], x0, x1, wx);
+    tri_axis<T>(j, Lc.n[1], Lc.bc[1], y0, y1, wy);
+    tri_axis<T>(k, Lc.n[2], Lc.bc[2], z0, z1, wz);
+    const T ax = T(1) - wx, ay = T(1) - wy, az = T(1) - wz;
+    const int cx = Lc.n[0], cxy = Lc.n[0] * Lc.n[1];
+    const T* p = e + (z0 * Lc.n[1] + y0) * cx + x0;
+    const int ox = x1 - x0, oy = (y1 - y0) * cx, oz = (z1 - z0) * cxy;
+    const T lo = ay * (ax * p[0] + wx * p[ox]) + wy * (ax * p[oy] + wx * p[oy + ox]);
+    const T hi = ay * (ax * p[oz] + wx * p[oz + ox]) + wy * (ax * p[oz + oy] + wx * p[oz + oy + ox]);
+    return az * lo + wz * hi;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_prolong(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
@@ -996,13 +1014,27 @@ __global__ void __launch_bounds__(NTHREADS)
 constexpr int MG_BLOCK_PER_THREAD = 4;
 constexpr int MG_BLOCK_MAX_CELLS = MG_BLOCK_THREADS * MG_BLOCK_PER_THREAD;
 
-// (i, j, k) of linear index q on a level (32-bit: the one-CTA levels are small).
-__device__ __forceinline__ void lev_ijk(const Lev& L, unsigned q, int& i, int& j, int& k) {
-    const unsigned nx = (unsigned)L.n[0], nxy = nx * (unsigned)L.n[1];
-    k = (int)(q / nxy);
-    const unsigned r = q - (unsigned)k * nxy;
-    j = (int)(r / nx);
-    i = (int)(r - (unsigned)j * nx);
+// (i, j, k) of linear index q on a one-CTA level.  The two divisions are
+// floor((q + 1/2) * fl(1/d)) in FP32 with the correctly rounded reciprocal
+// rd = fl(1/d) of the divisor d (nx, then nx * ny): with x = (q + 1/2) / d the
+// product is within x 2^-23 <= 2^-11 / d of x (q < 4096 gives x d < 4096),
+// while x lies at least 1/(2d) from an integer, so the truncation is exactly
+// floor(q / d) for every q < 4096 and d <= 4096 (also checked exhaustively).
+struct LevRcp {
+    float rx, rxy;  // fl(1 / nx), fl(1 / (nx ny))
+};
+
+__device__ __forceinline__ LevRcp lev_rcp(const Lev& L) {
+    return LevRcp{__frcp_rn(float(L.n[0])), __frcp_rn(float(L.n[0] * L.n[1]))};
+}
+
+__device__ __forceinline__ void lev_ijk(const Lev& L, const LevRcp& rc, unsigned q, int& i,
+                                        int& j, int& k) {
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+    k = (int)((float(q) + 0.5f) * rc.rxy);
+    const int r = (int)q - k * nxy;
+    j = (int)((float(r) + 0.5f) * rc.rx);
+    i = r - j * nx;
 }
 
 // A cell of a one-CTA level as one thread holds it across the phases of a
@@ -1075,6 +1107,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     T wd[MG_BLOCK_PER_THREAD];
     auto cells_of = [&](int m) {
         const Lev& L = plan.lev[m];
+        const LevRcp rc = lev_rcp(L);
 #pragma unroll
         for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
             const unsigned q = t + c * nt;
@@ -1082,7 +1115,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
             wd[c] = T(0);
             if (q < (unsigned)L.cells) {
                 int i, j, k;
-                lev_ijk(L, q, i, j, k);
+                lev_ijk(L, rc, q, i, j, k);
                 pk[c] = blk_pack(i, j, k);
                 wd[c] = blk_wd<T>(L, pk[c], w);
             }
@@ -1131,9 +1164,10 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
             if (q < cells) bq[m][q] = bq[m][q] - blk_lap<T>(L, pk[c], (int)q, yq[m]);
         }
         __syncthreads();
+        const LevRcp rcc = lev_rcp(Lc);
         for (unsigned q = t; q < (unsigned)Lc.cells; q += nt) {
             int I, J, K;
-            lev_ijk(Lc, q, I, J, K);
+            lev_ijk(Lc, rcc, q, I, J, K);
             T acc = T(0);
             for (int dz = 0; dz < 2; ++dz)
                 for (int dy = 0; dy < 2; ++dy)
@@ -1159,10 +1193,11 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     for (int m = nl - 2; m >= lc; --m) {
         const Lev& L = plan.lev[m];
         const Lev& Lc = plan.lev[m + 1];
+        const LevRcp rc = lev_rcp(L);
         for (unsigned q = t; q < (unsigned)L.cells; q += nt) {
             int i, j, k;
-            lev_ijk(L, q, i, j, k);
-            yq[m][q] += prolong_at(Lc, yq[m + 1], i, j, k);
+            lev_ijk(L, rc, q, i, j, k);
+            yq[m][q] += prolong_off(Lc, yq[m + 1], i, j, k);
         }
         __syncthreads();
     }
