@@ -1182,12 +1182,52 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
         const int m = nl - 1;
         const Lev& L = plan.lev[m];
         cells_of(m);
-        for (unsigned q = t; q < (unsigned)L.cells; q += nt) yq[m][q] = T(0);
-        __syncthreads();
         // enough sweeps for the coarsest level's size; a 2^3 level needs few
         const int nmax = max(L.n[0], max(L.n[1], L.n[2]));
         const int sweeps = min(MG_COARSEST_SWEEPS, 4 * ((nmax + 1) / 2) * 2);
-        for (int q = 0; q < sweeps; ++q) sweep(m);
+        if (L.cells <= 32) {
+            // at most 32 cells: warp 0 alone, lane t holding cell t; the
+            // neighbours' iterates come by register shuffles, so the sweeps
+            // need no barrier (the same face terms as blk_lap, in its order)
+            if (t < 32u) {
+                const bool own = t < (unsigned)L.cells;
+                const int c3[3] = {pk[0] & 1023, (pk[0] >> 10) & 1023, pk[0] >> 20};
+                const int st[3] = {1, L.n[0], L.n[0] * L.n[1]};
+                int lo[3], hi[3];  // the neighbours' lanes
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const int n = L.n[d];
+                    const bool per = L.bc[d] == BC_PERIODIC;
+                    lo[d] = (int)t;
+                    hi[d] = (int)t;
+                    if (own) {
+                        lo[d] += c3[d] > 0 ? -st[d] : (per ? (n - 1) * st[d] : 0);
+                        hi[d] += c3[d] + 1 < n ? st[d] : (per ? -(n - 1) * st[d] : 0);
+                    }
+                }
+                const T bv = own ? bq[m][t] : T(0);
+                T y = T(0);
+                for (int q = 0; q < sweeps; ++q) {
+                    const T vc = y;
+                    T sl = T(0);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const T vh = __shfl_sync(0xffffffffu, vc, hi[d]);
+                        const T vl = __shfl_sync(0xffffffffu, vc, lo[d]);
+                        const T wgt = lw<T>(L, d);
+                        sl += (vh - vc) * wgt;
+                        sl -= (vc - vl) * wgt;
+                    }
+                    y = vc + wd[0] * (bv - sl);
+                }
+                if (own) yq[m][t] = y;
+            }
+            __syncthreads();
+        } else {
+            for (unsigned q = t; q < (unsigned)L.cells; q += nt) yq[m][q] = T(0);
+            __syncthreads();
+            for (int q = 0; q < sweeps; ++q) sweep(m);
+        }
     }
     // up: add the prolonged coarse correction
     for (int m = nl - 2; m >= lc; --m) {
