@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--parareal-chunk", type=int, default=0,
                     help="slices per fine-sweep chunk overlapped with the coarse chain "
                          "(0: one sweep over all slices, then the chain)")
-    ap.add_argument("--inner-rtol", type=float, default=1e-4,
+    ap.add_argument("--inner-rtol", type=float, default=3e-4,
                     help="FP32+refine: relative residual of each inner FP32 solve")
     ap.add_argument("--mode", choices=["bench", "kernels", "coarse", "adjoint", "obstacles",
                                        "mixed"],

@@ -69,7 +69,7 @@ typedef struct {
     int poisson_maxit;       /* iteration limit per Krylov solve (<= 0: 20*max(n))   */
     double refine_rtol;      /* FP32_REFINE: outer FP64 relative residual target     */
     double inner_rtol;       /* FP32_REFINE: inner FP32 relative residual per outer
-                                step (<= 0: 1e-4)                                    */
+                                step (<= 0: 3e-4)                                    */
     int refine_maxit;        /* FP32_REFINE: outer corrections per solve before
                                 NS_ERR_NOT_CONVERGED (<= 0: 40)                      */
     int batch;               /* capacity: largest batch one call may advance (>= 1)  */

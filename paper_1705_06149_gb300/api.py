@@ -67,7 +67,7 @@ class Grid:
                  lz: float = 1.0, re: float = 100.0, u_lid: float = 1.0,
                  bc: Sequence[str] = ("wall", "wall", "wall"), precision: str = "fp64",
                  poisson_rtol: float = 1e-12, poisson_maxit: int = 0,
-                 refine_rtol: float = 1e-10, inner_rtol: float = 1e-4, batch: int = 1,
+                 refine_rtol: float = 1e-10, inner_rtol: float = 3e-4, batch: int = 1,
                  preconditioner: str = "multigrid", solid: Optional[np.ndarray] = None,
                  tile_z: int = 0, parareal_chunk: int = 0, refine_maxit: int = 0,
                  device: Optional[torch.device] = None):

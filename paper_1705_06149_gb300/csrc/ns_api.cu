@@ -56,7 +56,7 @@ struct ns_grid {
     bool fp32 = false;
     int maxit = 0;
     int max_outer = kMaxOuterDefault;  // FP32+refine: outer corrections per solve
-    double inner_rtol = 1e-4;
+    double inner_rtol = 3e-4;
     // workspace, [cap][...]
     void* fs[3] = {nullptr, nullptr, nullptr};  // F* (element type of the precision)
     double* b = nullptr;                        // right side of the pressure equation
@@ -1708,7 +1708,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     g->cap = d.batch;
     g->fp32 = d.precision == NS_FP32_REFINE;
     g->maxit = d.poisson_maxit > 0 ? d.poisson_maxit : 20 * std::max(d.nx, std::max(d.ny, d.nz));
-    g->inner_rtol = d.inner_rtol > 0 ? d.inner_rtol : 1e-4;
+    g->inner_rtol = d.inner_rtol > 0 ? d.inner_rtol : 3e-4;
     g->max_outer = d.refine_maxit > 0 ? d.refine_maxit : kMaxOuterDefault;
     setup_geo(g);
     const Geo& G = g->geo;
