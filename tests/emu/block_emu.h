@@ -1,0 +1,55 @@
+// Host emulation of one CTA of the one-CTA multigrid kernel (test support).
+//
+// The kernel's source, taken verbatim from csrc/ns_mg.cuh by the test, is
+// compiled as host C++ with the CUDA keywords below: every thread of the CTA
+// is a std::thread, __syncthreads() is a barrier over all of them, and a warp
+// shuffle is an exchange through a per-warp buffer between two barriers over
+// the warp's 32 threads.  Shared memory is one heap block of exactly the size
+// the library requests, so AddressSanitizer reports any access outside it.
+#pragma once
+#include <algorithm>
+#include <barrier>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+using std::max;
+using std::min;
+
+#define __device__
+#define __global__
+#define __forceinline__ inline
+#define __launch_bounds__(x)
+#define __restrict__
+#define __align__(x)
+
+struct EmuDim3 {
+    unsigned x = 0, y = 0, z = 0;
+};
+thread_local EmuDim3 threadIdx, blockIdx;
+EmuDim3 blockDim, gridDim;
+
+std::barrier<>* emu_cta_barrier;
+std::barrier<>* emu_warp_barrier[32];
+unsigned char* emu_smem;
+
+inline void __syncthreads() { emu_cta_barrier->arrive_and_wait(); }
+
+template <typename T>
+inline T __shfl_sync(unsigned, T v, int src) {
+    static T buf[32][32];
+    const int lane = (int)threadIdx.x % 32, w = (int)threadIdx.x / 32;
+    buf[w][lane] = v;
+    emu_warp_barrier[w]->arrive_and_wait();
+    const T r = buf[w][src];
+    emu_warp_barrier[w]->arrive_and_wait();
+    return r;
+}
+
+// IEEE single-precision reciprocal, rounded to nearest (as __frcp_rn)
+inline float __frcp_rn(float x) { return 1.0f / x; }
+inline float __fdividef(float a, float b) { return a / b; }
