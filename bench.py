@@ -78,7 +78,7 @@ BYTES_STEP_FP32 = {"predict": 24, "divergence": 20, "correct": 76, "solve_init":
 
 KERNEL_NAMES = {"krylov_A": "k_mg_src_pair<SRC_P> / k_mg_src<SRC_P> / k_bicg_A",
                 "krylov_B": "k_mg_src_pair<SRC_S> / k_mg_src<SRC_S> / k_bicg_B",
-                "krylov_C": "k_mg_update / k_bicg_C", "mg_lap_v": "k_mg_lapdot_pair<0> / k_mg_lapdot_v",
+                "krylov_C": "k_mg_update_pair / k_mg_update / k_bicg_C", "mg_lap_v": "k_mg_lapdot_pair<0> / k_mg_lapdot_v",
                 "mg_lap_t": "k_mg_lapdot_pair<1> / k_mg_lapdot_t",
                 "mg_restrict0": "k_mg_restrict (finest)",
                 "mg_prolong0": "k_mg_prolong_pair / k_mg_prolong (finest)", "predict": "k_predict_tile",

@@ -520,8 +520,8 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
         const int pbx = ceil_div(L0.n[0], 64);
         NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
                   (k_mg_src_pair<T, MODE>
-                   <<<dim3(pbx * L0.by * L0.bz, batch), blk, 0, g->stream>>>(L0, mb, g->ctl, dst,
-                                                                               pbx)));
+                   <<<dim3(pbx * L0.by * L0.bz, batch), blk, 0, g->stream>>>(
+                       L0, mb, g->ctl, nullptr, dst, pbx)));
     } else if (lc > 0)
         NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
                   (k_mg_src<T, MODE, true><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
@@ -537,11 +537,22 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
         NS_LAUNCH(g, l == 0 ? NS_K_MG_RESTRICT0 : NS_K_MG_COARSE, 0,
                   k_mg_restrict<T><<<dim3(P.lev[l].rctas, batch), blk, 0, g->stream>>>(
                       P.lev[l], P.lev[l + 1], g->ctl, bsrc, bsrc_odd, ysrc, mb.B[l + 1]));
-        if (l + 1 < lc)
-            NS_LAUNCH(g, NS_K_MG_COARSE, 0,
-                      (k_mg_src<T, SRC_ARR, true>
-                       <<<dim3(P.lev[l + 1].ctas, batch), blk, 0, g->stream>>>(
-                           P.lev[l + 1], mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1])));
+        if (l + 1 < lc) {
+            const Lev& Ls = P.lev[l + 1];
+            if (Ls.fcode == nullptr && Ls.n[0] % 2 == 0) {
+                // x pairs per thread (a level that is restricted has an even nx)
+                const int pbx = ceil_div(Ls.n[0], 64);
+                NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+                          (k_mg_src_pair<T, SRC_ARR>
+                           <<<dim3(pbx * Ls.by * Ls.bz, batch), blk, 0, g->stream>>>(
+                               Ls, mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1], pbx)));
+            } else {
+                NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+                          (k_mg_src<T, SRC_ARR, true>
+                           <<<dim3(Ls.ctas, batch), blk, 0, g->stream>>>(
+                               Ls, mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1])));
+            }
+        }
     }
     T* bin = lc == 0 ? src : mb.B[lc];
     T* bin_odd = lc == 0 ? src_odd : nullptr;
@@ -599,9 +610,14 @@ ns_status mg_iteration(ns_grid* g, int batch, double tol2, int zero_start) {
     else
         NS_LAUNCH(g, NS_K_MG_LAP_T, 0,
                   k_mg_lapdot_t<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg));
-    NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
-              k_mg_update<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, tol2,
-                                                           g->maxit, zero_start));
+    if (pair)
+        NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
+                  (k_mg_update_pair<T><<<pgrid, blk, 0, g->stream>>>(
+                      L0, mb, g->ctl, g->part_mg, tol2, g->maxit, zero_start, pbx, pctas)));
+    else
+        NS_LAUNCH(g, NS_K_KRYLOV_C, 0,
+                  k_mg_update<T><<<grid, blk, 0, g->stream>>>(L0, mb, g->ctl, g->part_mg, tol2,
+                                                               g->maxit, zero_start));
     NS_CUDA(cudaGetLastError());
     return NS_OK;
 }

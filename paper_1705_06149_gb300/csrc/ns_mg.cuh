@@ -576,8 +576,8 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
-// The same as k_mg_src<T, MODE, true> (MODE SRC_P or SRC_S) on a level without
-// solid cells and with an even nx, a thread holding the x pair (i, i+1): the
+// The same as k_mg_src<T, MODE, true> on a level without solid cells and with
+// an even nx, a thread holding the x pair (i, i+1): the
 // source values of the pair, of the rows beside it and of the plane above are
 // evaluated once per pair from paired vector loads, those of the pair's x
 // neighbours i-1 and i+2 singly, and the plane below and the pair itself are
@@ -585,8 +585,8 @@ __global__ void __launch_bounds__(NTHREADS)
 // Tiling: 32 x 4 threads cover 64 x 4 cells of a plane; pbx = ceil(nx / 64).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(NTHREADS)
-    k_mg_src_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
-                  int pbx) {
+    k_mg_src_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, const T* __restrict__ barr,
+                  T* __restrict__ ydst, int pbx) {
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -600,14 +600,20 @@ __global__ void __launch_bounds__(NTHREADS)
     const T* __restrict__ vn = mb.V[par] + off;
     T* __restrict__ sv = mb.S + off;
     T* __restrict__ y = ydst + off;
+    const T* __restrict__ ba = MODE == SRC_ARR ? barr + off : nullptr;
     const bool restart = c->restart != 0;
     const bool first = c->it_cur == 0;
     const T tb = T(c->beta), tw = T(c->omega), ta = T(c->alpha);
     auto src1 = [&](int q) -> T {
+        if (MODE == SRC_ARR) return ba[q];
         if (MODE == SRC_P) return restart ? r[q] : r[q] + tb * (po[q] - tw * vo[q]);
         return r[q] - ta * vn[q];
     };
     auto src2 = [&](int q, T& a, T& b) {
+        if (MODE == SRC_ARR) {
+            load_pair<T>(ba + q, a, b);
+            return;
+        }
         T r0, r1;
         load_pair<T>(r + q, r0, r1);
         if (MODE == SRC_P) {
@@ -1531,6 +1537,89 @@ __global__ void __launch_bounds__(NTHREADS)
     T acc[3] = {a0, a1, a2};
     double tot[3];
     if (partials_arrive<T, 3>(acc, part + s * L.ctas * 3, mb.counter + s, L.ctas, tot) &&
+        tid_flat() == 0) {
+        c->it_cur += 1;
+        c->total_iters += 1;
+        bicg_decide(c, tot[0], tot[1], tot[2], tol2, maxit);
+    }
+}
+
+// k_mg_update on a level without solid cells and with an even nx, a thread
+// holding the x pair (i, i+1): the six vectors and the two results move as
+// paired vector loads and stores, two z steps of loads in flight before their
+// arithmetic.  Each cell's arithmetic is that of k_mg_update; the per-thread
+// sums take the pair's cells in x order.  Tiling as k_mg_src_pair (ctas =
+// pbx * by * bz CTAs per state reduce their partials).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_mg_update_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
+                     double tol2, int maxit, int zero_start, int pbx, int ctas) {
+    const long long s = blockIdx.y;
+    SliceCtl* c = ctl + s;
+    if (c->status != ST_ITER) return;
+    const long long off = s * L.cells;
+    T* __restrict__ x = mb.x + off;
+    T* __restrict__ r = mb.r + off;
+    const T* __restrict__ rh = mb.rhat + off;
+    const T* __restrict__ y = mb.Y + off;
+    const T* __restrict__ z = mb.Z + off;
+    const T* __restrict__ sv = mb.S + off;
+    const T* __restrict__ t = mb.Tt + off;
+    const T ta = T(c->alpha), tw = T(c->omega);
+    const bool fresh = zero_start && c->it_cur == 0;
+    const int cta = blockIdx.x;
+    const int tx = cta % pbx;
+    const int rest = cta / pbx;
+    const int i = tx * 64 + 2 * (int)threadIdx.x;
+    const int j = (rest % L.by) * TY + (int)threadIdx.y;
+    const int k0 = (rest / L.by) * L.tz;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    if (i < L.n[0] && j < L.n[1]) {
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        const int plane = L.n[0] * L.n[1];
+        const int base = lindex(L, i, j, 0);
+        constexpr int ZB = 2;
+        for (int kb = k0; kb < k1; kb += ZB) {
+            T xo[ZB][2], yv[ZB][2], zv[ZB][2], sq[ZB][2], tq[ZB][2], rq[ZB][2];
+#pragma unroll
+            for (int q = 0; q < ZB; ++q) {
+                if (kb + q < k1) {
+                    const int id = base + (kb + q) * plane;
+                    if (fresh) {
+                        xo[q][0] = T(0);
+                        xo[q][1] = T(0);
+                    } else {
+                        load_pair<T>(x + id, xo[q][0], xo[q][1]);
+                    }
+                    load_pair<T>(y + id, yv[q][0], yv[q][1]);
+                    load_pair<T>(z + id, zv[q][0], zv[q][1]);
+                    load_pair<T>(sv + id, sq[q][0], sq[q][1]);
+                    load_pair<T>(t + id, tq[q][0], tq[q][1]);
+                    load_pair<T>(rh + id, rq[q][0], rq[q][1]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < ZB; ++q) {
+                if (kb + q < k1) {
+                    const int id = base + (kb + q) * plane;
+                    T xv[2], rv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        xv[h] = xo[q][h] + (ta * yv[q][h] + tw * zv[q][h]);
+                        rv[h] = sq[q][h] - tw * tq[q][h];
+                        a0 += rq[q][h] * rv[h];
+                        a1 += rv[h] * rv[h];
+                        a2 += xv[h];
+                    }
+                    reinterpret_cast<typename Pair2<T>::type*>(x + id)[0] = {xv[0], xv[1]};
+                    reinterpret_cast<typename Pair2<T>::type*>(r + id)[0] = {rv[0], rv[1]};
+                }
+            }
+        }
+    }
+    T acc[3] = {a0, a1, a2};
+    double tot[3];
+    if (partials_arrive<T, 3>(acc, part + s * ctas * 3, mb.counter + s, ctas, tot) &&
         tid_flat() == 0) {
         c->it_cur += 1;
         c->total_iters += 1;
