@@ -8,6 +8,7 @@
 // the library requests, so AddressSanitizer reports any access outside it.
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <barrier>
 #include <cmath>
 #include <cstdint>
@@ -53,3 +54,32 @@ inline T __shfl_sync(unsigned, T v, int src) {
 // IEEE single-precision reciprocal, rounded to nearest (as __frcp_rn)
 inline float __frcp_rn(float x) { return 1.0f / x; }
 inline float __fdividef(float a, float b) { return a / b; }
+
+// --- further device primitives used by the grid-wide multigrid kernels ------
+// (CTAs of a grid run one after another, so "global" atomics and fences only
+// need to be ordinary operations; a CTA's static shared arrays are the
+// function-local statics that __shared__ becomes)
+#define __shared__ static
+struct float2 {
+    float x, y;
+};
+struct double2 {
+    double x, y;
+};
+template <typename T>
+inline T __shfl_xor_sync(unsigned, T v, int mask) {
+    static T buf[32][32];
+    const int lane = (int)(threadIdx.y * 32 + threadIdx.x) % 32;
+    const int w = (int)(threadIdx.y * 32 + threadIdx.x) / 32;
+    buf[w][lane] = v;
+    emu_warp_barrier[w]->arrive_and_wait();
+    const T r = buf[w][lane ^ mask];
+    emu_warp_barrier[w]->arrive_and_wait();
+    return r;
+}
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+template <typename T>
+inline T __ldcg(const T* p) { return *p; }
+inline int __popc(unsigned x) { return __builtin_popcount(x); }
+using std::isfinite;
+inline unsigned atomicAdd(unsigned* p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
