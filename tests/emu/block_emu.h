@@ -83,3 +83,14 @@ inline T __ldcg(const T* p) { return *p; }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
 using std::isfinite;
 inline unsigned atomicAdd(unsigned* p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+template <typename T>
+inline T __shfl_up_sync(unsigned, T v, int delta) {
+    static T buf[32][32];
+    const int t = (int)(threadIdx.y * 32 + threadIdx.x);
+    const int lane = t % 32, w = t / 32;
+    buf[w][lane] = v;
+    emu_warp_barrier[w]->arrive_and_wait();
+    const T r = lane >= delta ? buf[w][lane - delta] : v;
+    emu_warp_barrier[w]->arrive_and_wait();
+    return r;
+}
