@@ -94,3 +94,15 @@ inline T __shfl_up_sync(unsigned, T v, int delta) {
     emu_warp_barrier[w]->arrive_and_wait();
     return r;
 }
+inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v) {
+    unsigned long long old = *p;
+    while (old < v && !__atomic_compare_exchange_n(p, &old, v, false, __ATOMIC_SEQ_CST,
+                                                   __ATOMIC_SEQ_CST)) {
+    }
+    return old;
+}
+inline long long __double_as_longlong(double x) {
+    long long r;
+    std::memcpy(&r, &x, sizeof r);
+    return r;
+}
