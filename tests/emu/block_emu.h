@@ -106,3 +106,6 @@ inline long long __double_as_longlong(double x) {
     std::memcpy(&r, &x, sizeof r);
     return r;
 }
+struct float3 {
+    float x, y, z;
+};
