@@ -76,7 +76,11 @@ typedef struct {
     int preconditioner;      /* ns_preconditioner: BiCGStab as in Section 2 without
                                 (NS_PC_NONE) or with one multigrid V-cycle as right
                                 preconditioner (NS_PC_MULTIGRID; falls back to
-                                NS_PC_NONE on grids it cannot coarsen far enough) */
+                                NS_PC_NONE on grids it cannot coarsen far enough).
+                                The levels with at most 4096 cells (FP32_REFINE;
+                                512 in FP64) run in one CTA per state; the
+                                environment variable NS_MG_BLOCK_CELLS, read at
+                                ns_create_grid, overrides that size (>= 8).     */
     int tile_z;              /* cells each thread marches along z in the stencil and
                                 solver kernels: an even number >= 2 (clamped to nz);
                                 0: 8.  Results depend on it at rounding level (it
