@@ -1,0 +1,74 @@
+// Driver of the host emulation of the adjoint right side (test support):
+// k_adj_rhs, out += (dR/du)^T mu and dlid += (dR/du_lid)^T mu for one state,
+// FP64, every CTA as host threads (its atomics as real atomic additions).
+//
+// usage: adj_emu nx ny nz bcx bcy bcz re u_lid in.bin out.bin
+//   in.bin: u, v, w, then mu_u, mu_v, mu_w (FP64); out.bin: the three adjoint
+//   right sides, then dlid.
+
+#include <functional>
+
+static void launch(int gx, const std::function<void()>& body) {
+    for (int bx = 0; bx < gx; ++bx) {
+        std::barrier<> bar(NTHREADS);
+        emu_cta_barrier = &bar;
+        for (int w = 0; w < NWARPS; ++w) emu_warp_barrier[w] = new std::barrier<>(32);
+        std::vector<std::thread> th;
+        for (int t = 0; t < NTHREADS; ++t)
+            th.emplace_back([&, t, bx]() {
+                threadIdx.x = (unsigned)(t % TX);
+                threadIdx.y = (unsigned)(t / TX);
+                blockIdx.x = (unsigned)bx;
+                blockIdx.y = 0;
+                body();
+                emu_warp_barrier[t / 32]->arrive_and_drop();
+                bar.arrive_and_drop();
+            });
+        for (auto& x : th) x.join();
+        for (int w = 0; w < NWARPS; ++w) delete emu_warp_barrier[w];
+    }
+}
+
+int main(int argc, char** argv) {
+    if (argc != 11) return 1;
+    Geo G{};
+    for (int a = 0; a < 3; ++a) {
+        G.n[a] = atoi(argv[1 + a]);
+        G.bc[a] = atoi(argv[4 + a]);
+        G.h[a] = 1.0 / G.n[a];
+        G.ih[a] = 1.0 / G.h[a];
+        G.ih2[a] = 1.0 / (G.h[a] * G.h[a]);
+    }
+    G.inv_re = 1.0 / atof(argv[7]);
+    G.u_lid = atof(argv[8]);
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a)
+            G.ext[c][a] = G.n[a] + ((c == a && G.bc[a] != BC_PERIODIC) ? 1 : 0);
+    for (int c = 0; c < 3; ++c) G.cnt[c] = (long long)G.ext[c][0] * G.ext[c][1] * G.ext[c][2];
+    G.cnt[3] = (long long)G.n[0] * G.n[1] * G.n[2];
+    G.tz = std::min(8, G.n[2]);
+    G.fbx = (G.n[0] + 1 + TX - 1) / TX;
+    G.fby = (G.n[1] + 1 + TY - 1) / TY;
+    G.fbz = (G.n[2] + 1 + G.tz - 1) / G.tz;
+    G.fctas = G.fbx * G.fby * G.fbz;
+    const long long nv = G.cnt[0] + G.cnt[1] + G.cnt[2];
+    std::vector<double> in(2 * nv);
+    FILE* f = fopen(argv[9], "rb");
+    if (!f || fread(in.data(), 8, in.size(), f) != in.size()) return 3;
+    fclose(f);
+    const double* u = in.data();
+    const double* mu = in.data() + nv;
+    std::vector<double> out(nv, 0.0);
+    double dlid = 0.0;
+    launch(G.fctas, [&] {
+        k_adj_rhs(G, u, u + G.cnt[0], u + G.cnt[0] + G.cnt[1], mu, mu + G.cnt[0],
+                  mu + G.cnt[0] + G.cnt[1], out.data(), out.data() + G.cnt[0],
+                  out.data() + G.cnt[0] + G.cnt[1], &dlid);
+    });
+    f = fopen(argv[10], "wb");
+    if (!f) return 5;
+    fwrite(out.data(), 8, out.size(), f);
+    fwrite(&dlid, 8, 1, f);
+    fclose(f);
+    return 0;
+}

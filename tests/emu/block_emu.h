@@ -109,3 +109,6 @@ inline long long __double_as_longlong(double x) {
 struct float3 {
     float x, y, z;
 };
+inline double atomicAdd(double* p, double v) {
+    return std::atomic_ref<double>(*p).fetch_add(v);
+}
