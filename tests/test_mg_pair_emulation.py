@@ -74,9 +74,9 @@ def pair_emulator(tmp_path_factory):
 
 
 CASES = [
-    ((64, 16, 8), (WALL,) * 3, 8),              # two 64-wide x tiles of pairs
-    ((32, 12, 6), (PERIODIC, WALL, SLIP), 4),   # periodic seam in x, ragged z tile
-    ((80, 8, 10), (WALL, PERIODIC, PERIODIC), 4),  # ragged x tile (80 = 64 + 16)
+    ((64, 8, 8), (WALL,) * 3, 8),               # a full 64-wide x tile of pairs
+    ((32, 6, 6), (PERIODIC, WALL, SLIP), 4),    # periodic seam in x, ragged y and z tiles
+    ((80, 4, 6), (WALL, PERIODIC, PERIODIC), 4),  # ragged x tile (80 = 64 + 16)
     ((16, 10, 4), (PERIODIC, PERIODIC, WALL), 2),  # ragged y tile (10 = 4 + 4 + 2)
 ]
 
