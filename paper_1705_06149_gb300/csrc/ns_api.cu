@@ -897,6 +897,10 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
                                                                      g->part_r));
         NS_CUDA(cudaGetLastError());
         const double tol2 = g->d.refine_rtol * g->d.refine_rtol;
+        // outer corrections per state: one for every outer step that finds the
+        // state still refining (SliceCtl.o_steps holds the index of the last
+        // inner solve started, one less than the corrections applied)
+        std::vector<int> corrections(batch, 0);
         int m = 0;
         for (;; ++m) {
             NS_LAUNCH(g, NS_K_INNER_INIT, G.cnt[3] * batch,
@@ -905,7 +909,11 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
             NS_CUDA(cudaGetLastError());
             NS_TRY(poll_ctl(g, batch));
             bool any = false;
-            for (int s = 0; s < batch; ++s) any |= g->h_ctl[s].o_status == OS_REFINE;
+            for (int s = 0; s < batch; ++s) {
+                const bool refining = g->h_ctl[s].o_status == OS_REFINE;
+                any |= refining;
+                corrections[s] += refining ? 1 : 0;
+            }
             if (!any) break;
             // a stalled inner solve still improves p (the outer test decides);
             // any other failure ends the solve
@@ -922,7 +930,7 @@ ns_status solve_pressure(ns_grid* g, int batch, const double* p_in) {
             const SliceCtl& c = g->h_ctl[s];
             const double rel = c.o_bb > 0 ? std::sqrt(c.o_rr / c.o_bb) : std::sqrt(c.o_rr);
             max_rel = std::max(max_rel, rel);
-            g->stats.refine_steps += c.o_steps;
+            g->stats.refine_steps += corrections[s];
             if (c.o_status == OS_NONFINITE)
                 return fail(NS_ERR_NONFINITE, "non-finite residual in the pressure solve");
             if (c.o_status != OS_DONE)
