@@ -89,7 +89,7 @@ CASES = [
 KMAX = 4
 
 
-def _run(exe, d, dims, bc, solid, b, x0, rtol, inner_rtol, refine_rtol, kmax):
+def _start(exe, d, dims, bc, solid, b, x0, rtol, inner_rtol, refine_rtol, kmax):
     nx, ny, nz = dims
     tag = f"{os.getpid()}_{nx}_{ny}_{nz}_{int(solid is not None)}_{kmax}"
     fin, fsol, fout = d / f"in_{tag}.bin", d / f"solid_{tag}.bin", d / f"out_{tag}.bin"
@@ -100,14 +100,39 @@ def _run(exe, d, dims, bc, solid, b, x0, rtol, inner_rtol, refine_rtol, kmax):
     args = [exe, *map(str, dims), *(str(BC[x]) for x in bc), repr(rtol), str(maxit),
             repr(inner_rtol), repr(refine_rtol), "40", str(kmax), str(fin),
             str(fsol) if solid is not None else "-", str(fout)]
-    r = subprocess.run(args, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0, (r.returncode, r.stderr[-3000:])
+    proc = subprocess.Popen(args, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+    return proc, fout, maxit
+
+
+def _finish(run):
+    proc, fout, maxit = run
+    so, se = proc.communicate(timeout=600)
+    assert proc.returncode == 0, (proc.returncode, se[-3000:])
     val = {}
-    for line in r.stdout.split("\n"):
+    for line in so.split("\n"):
         if line.strip():
             k, v = line.split()
             val[k] = float(v)
     return val, open(fout, "rb").read(), maxit
+
+
+WHOLE = ((8, 4, 4), ("wall",) * 3)  # one CTA: a solve is hundreds of launches
+WHOLE_TOL = (1e-6, 3e-4, 1e-6)      # FP64 rtol, inner rtol, outer rtol
+
+
+@pytest.fixture(scope="module")
+def krylov_runs(krylov_emulator):
+    """Every case at once: each run waits mostly on its threads' barriers, so
+    they overlap well on the host's cores."""
+    exe, d = krylov_emulator
+    runs = {}
+    for dims, bc, masked in CASES:
+        _, solid, _, b, x0 = _inputs(dims, masked)
+        runs[(dims, bc, masked)] = _start(exe, d, dims, bc, solid, b, x0, 1e-30, 1e-30, 1e-30,
+                                          KMAX)
+    _, _, _, b, x0 = _inputs(WHOLE[0], False)
+    runs["whole"] = _start(exe, d, WHOLE[0], WHOLE[1], None, b, x0, *WHOLE_TOL, 0)
+    return {k: _finish(v) for k, v in runs.items()}
 
 
 def _inputs(dims, masked):
@@ -153,11 +178,10 @@ def _bicgstab(L, b, x, iters):
 
 
 @pytest.mark.parametrize("dims,bc,masked", CASES)
-def test_bicgstab_iterations_match_definition(krylov_emulator, dims, bc, masked):
-    exe, d = krylov_emulator
+def test_bicgstab_iterations_match_definition(krylov_runs, dims, bc, masked):
     shape, solid, fluid, b, x0 = _inputs(dims, masked)
     og = oracle.Grid(*dims, bc=bc, solid=solid)
-    val, raw, _ = _run(exe, d, dims, bc, solid, b, x0, 1e-30, 1e-30, 1e-30, KMAX)
+    val, raw, _ = krylov_runs[(dims, bc, masked)]
     C = b.size
     off = 0
 
@@ -194,13 +218,12 @@ def test_bicgstab_iterations_match_definition(krylov_emulator, dims, bc, masked)
     assert np.all(np.abs(r32 - rw) <= 2.0 ** -24 * np.abs(rw) + 1e-12 * np.max(np.abs(rw)))
 
 
-def test_whole_solves_match_oracle(krylov_emulator):
-    exe, d = krylov_emulator
-    dims, bc = (8, 4, 4), ("wall",) * 3  # one CTA: a solve is hundreds of launches
-    rtol, inner_rtol, refine_rtol = 1e-6, 3e-4, 1e-6
-    shape, solid, fluid, b, x0 = _inputs(dims, False)
+def test_whole_solves_match_oracle(krylov_runs):
+    dims, bc = WHOLE
+    rtol, _, refine_rtol = WHOLE_TOL
+    shape, _, _, b, x0 = _inputs(dims, False)
     og = oracle.Grid(*dims, bc=bc)
-    val, raw, maxit = _run(exe, d, dims, bc, None, b, x0, rtol, inner_rtol, refine_rtol, 0)
+    val, raw, maxit = krylov_runs["whole"]
     out = np.frombuffer(raw, dtype=np.float64)
     C = b.size
     x, p, pref = (out[q * C:(q + 1) * C].reshape(shape) for q in range(3))

@@ -85,13 +85,27 @@ EXACT = ("src0_y", "src0_p", "src0_p1", "src0_s", "src0_rhat", "src1_y", "src1_p
          "upd_r", "upd0_x", "upd0_r", "prolong_y")
 
 
+@pytest.fixture(scope="module")
+def pair_runs(pair_emulator):
+    """All cases at once: each run waits mostly on its threads' barriers, so
+    they overlap well on the host's cores."""
+    procs = {case: subprocess.Popen([pair_emulator, *map(str, case[0]), *map(str, case[1]),
+                                     str(case[2])], stdout=subprocess.PIPE,
+                                    stderr=subprocess.PIPE, text=True)
+             for case in CASES}
+    out = {}
+    for case, pr in procs.items():
+        so, se = pr.communicate(timeout=600)
+        out[case] = (pr.returncode, so, se)
+    return out
+
+
 @pytest.mark.parametrize("n,bc,tz", CASES)
-def test_pair_kernels_match_cell_kernels(pair_emulator, n, bc, tz):
-    r = subprocess.run([pair_emulator, *map(str, n), *map(str, bc), str(tz)],
-                       capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0, (r.returncode, r.stderr[-3000:])
+def test_pair_kernels_match_cell_kernels(pair_runs, n, bc, tz):
+    rc, stdout, stderr = pair_runs[(n, bc, tz)]
+    assert rc == 0, (rc, stderr[-3000:])
     res = {}
-    for line in r.stdout.split("\n"):
+    for line in stdout.split("\n"):
         if line.strip():
             name, diff, scale = line.split()
             res.setdefault(name, []).append((float(diff), float(scale)))

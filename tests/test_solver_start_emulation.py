@@ -97,9 +97,7 @@ def _close(got, want, rel=1e-13):
     return float(np.max(np.abs(got - want))) <= rel * scale
 
 
-@pytest.mark.parametrize("dims,bc,masked", CASES)
-def test_solver_start_kernels_match_oracle(start_emulator, dims, bc, masked):
-    exe, d = start_emulator
+def _inputs(dims, masked):
     nx, ny, nz = dims
     shape = (nz, ny, nx)
     solid = None
@@ -107,29 +105,52 @@ def test_solver_start_kernels_match_oracle(start_emulator, dims, bc, masked):
         _, solid = inputs.obstacle_boxes(dims, seed=21, count=3, edge=(0.15, 0.3))
         assert solid.any()
     fluid = np.ones(shape, bool) if solid is None else solid == 0
-    og = oracle.Grid(*dims, bc=bc, solid=solid)
     rng = np.random.default_rng(nx * ny + nz)
     b = np.where(fluid, 1.0 + rng.normal(size=shape), 0.0)  # a nonzero mean to remove
     x0 = np.where(fluid, rng.normal(size=shape), 0.0)
     p = rng.normal(size=shape)                               # solid cells to be zeroed
     pold = np.where(fluid, rng.normal(size=shape), 0.0)
     e = np.where(fluid, 1e-3 * rng.normal(size=shape), 0.0).astype(np.float32)
-    tag = f"{os.getpid()}_{nx}_{ny}_{nz}_{int(masked)}"
-    fin, fsol, fout = d / f"in_{tag}.bin", d / f"solid_{tag}.bin", d / f"out_{tag}.bin"
-    with open(fin, "wb") as f:
-        for a in (b, x0, p, pold):
-            a.astype(np.float64).tofile(f)
-        e.tofile(f)
-    if masked:
-        with open(fsol, "wb") as f:
-            np.ascontiguousarray(solid, dtype=np.uint8).tofile(f)
-            _codes(solid, bc).tofile(f)
-    args = [exe, *map(str, dims), *(str(BC[x]) for x in bc), str(fin),
-            str(fsol) if masked else "-", str(fout)]
-    r = subprocess.run(args, capture_output=True, text=True, timeout=300)
-    assert r.returncode == 0, (r.returncode, r.stderr[-3000:])
+    return shape, solid, fluid, b, x0, p, pold, e
+
+
+@pytest.fixture(scope="module")
+def start_runs(start_emulator):
+    """Every case at once: each run waits mostly on its threads' barriers, so
+    they overlap well on the host's cores."""
+    exe, d = start_emulator
+    procs = {}
+    for dims, bc, masked in CASES:
+        _, solid, _, b, x0, p, pold, e = _inputs(dims, masked)
+        tag = f"{os.getpid()}_{'_'.join(map(str, dims))}_{int(masked)}"
+        fin, fsol, fout = d / f"in_{tag}.bin", d / f"solid_{tag}.bin", d / f"out_{tag}.bin"
+        with open(fin, "wb") as f:
+            for a in (b, x0, p, pold):
+                a.astype(np.float64).tofile(f)
+            e.tofile(f)
+        if masked:
+            with open(fsol, "wb") as f:
+                np.ascontiguousarray(solid, dtype=np.uint8).tofile(f)
+                _codes(solid, bc).tofile(f)
+        args = [exe, *map(str, dims), *(str(BC[x]) for x in bc), str(fin),
+                str(fsol) if masked else "-", str(fout)]
+        procs[(dims, bc, masked)] = (subprocess.Popen(args, stdout=subprocess.PIPE,
+                                                      stderr=subprocess.PIPE, text=True), fout)
+    out = {}
+    for case, (pr, fout) in procs.items():
+        so, se = pr.communicate(timeout=300)
+        out[case] = (pr.returncode, so, se, fout)
+    return out
+
+
+@pytest.mark.parametrize("dims,bc,masked", CASES)
+def test_solver_start_kernels_match_oracle(start_runs, dims, bc, masked):
+    shape, solid, fluid, b, x0, p, pold, e = _inputs(dims, masked)
+    og = oracle.Grid(*dims, bc=bc, solid=solid)
+    rc, stdout, stderr, fout = start_runs[(dims, bc, masked)]
+    assert rc == 0, (rc, stderr[-3000:])
     val = {}
-    for line in r.stdout.split("\n"):
+    for line in stdout.split("\n"):
         if line.strip():
             k, v = line.split()
             val[k] = float(v)
