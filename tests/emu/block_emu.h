@@ -112,3 +112,14 @@ struct float3 {
 inline double atomicAdd(double* p, double v) {
     return std::atomic_ref<double>(*p).fetch_add(v);
 }
+inline bool __any_sync(unsigned, bool v) {
+    static bool buf[32][32];
+    const int t = (int)(threadIdx.y * 32 + threadIdx.x);
+    const int lane = t % 32, w = t / 32;
+    buf[w][lane] = v;
+    emu_warp_barrier[w]->arrive_and_wait();
+    bool r = false;
+    for (int q = 0; q < 32; ++q) r = r || buf[w][q];
+    emu_warp_barrier[w]->arrive_and_wait();
+    return r;
+}
