@@ -103,7 +103,7 @@ def parse():
     ap.add_argument("--inner-rtol", type=float, default=3e-4,
                     help="FP32+refine: relative residual of each inner FP32 solve")
     ap.add_argument("--mode", choices=["bench", "kernels", "coarse", "adjoint", "obstacles",
-                                       "mixed"],
+                                       "mixed", "peaks"],
                     default="bench",
                     help="kernels: only `steps` batched fine steps of the 32-slice sweep; "
                          "coarse: only the serial coarse chain (32 slices x 5 coarse steps, "
@@ -111,7 +111,9 @@ def parse():
                          "adjoint: gradient of the 64^3 cavity's kinetic energy after 500 "
                          "steps; obstacles: Parareal on the 128^3 cavity with 8 boxes; mixed: "
                          "16 slices of a 256^3 cavity and 24 cavities of mixed sizes and "
-                         "Reynolds numbers, 20 fine steps of every grid per call")
+                         "Reynolds numbers, 20 fine steps of every grid per call; peaks: "
+                         "the FP32 and FP64 FMA throughput of this GPU (best of `steps` "
+                         "probe launches after `warmup`)")
     return ap.parse_args()
 
 
@@ -260,14 +262,15 @@ def initial_field_oracle():
 def oracle_sample(o64, start, nslices: int):
     """Time one fine step of nslices copies of the start state, advanced in
     parallel over the host cores after one untimed warm step (so that the
-    pressure solve starts warm as it does inside the sweep)."""
+    pressure solve starts warm as it does inside the sweep).  Returns the
+    rate, the timed seconds and the state after the two steps."""
     import oracle
     states = [oracle.copy_state(start) for _ in range(nslices)]
     o64.run_batch(states, DT_FINE, 1)
     t0 = time.perf_counter()
     o64.run_batch(states, DT_FINE, 1)
     dt = time.perf_counter() - t0
-    return nslices * N_CELLS ** 3 / dt, dt
+    return nslices * N_CELLS ** 3 / dt, dt, states[0]
 
 
 def cpu_cores() -> int:
@@ -287,7 +290,7 @@ def run_reference(args, world, rank, pg):
         oracle_sample(o64, start, nsl)
     rates, times = [], []
     for _ in range(args.steps):
-        r, t = oracle_sample(o64, start, nsl)
+        r, t, _ = oracle_sample(o64, start, nsl)
         rates.append(r)
         times.append(t)
     value = float(np.mean(rates))
@@ -338,6 +341,41 @@ def traffic_for(kernel: str):
     return k.get("dram_bytes_per_cell")
 
 
+def state_errors(got, want):
+    """Relative L2 errors of a GPU state against the oracle's: per field, of
+    the velocity field (u, v, w together) and of the pressure."""
+    out = {}
+    for c, name in enumerate("uvwp"):
+        a = np.asarray(got[c], dtype=np.float64).ravel()
+        b = np.asarray(want[c], dtype=np.float64).ravel()
+        out[name] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    a = np.concatenate([np.asarray(got[c], dtype=np.float64).ravel() for c in range(3)])
+    b = np.concatenate([np.asarray(want[c], dtype=np.float64).ravel() for c in range(3)])
+    out["velocity"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out["pressure"] = out["p"]
+    return out
+
+
+def gpu_error_vs_oracle(g, start, ref, steps: int):
+    """`steps` fine steps of two copies of the oracle's FP64 start state on
+    grid g (a batched call), compared with the oracle's result `ref`."""
+    import torch
+    st = g.state_from([np.stack([a, a]) for a in start])
+    g.step_fine(st, DT_FINE, steps)
+    torch.cuda.synchronize()
+    got = st.numpy()
+    return state_errors([got[c][1] for c in range(4)], ref)
+
+
+def run_parareal_iterations(g, u0, slices, n: int):
+    defects = []
+    for _ in range(n):
+        _, d = g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=1,
+                          resume=True)
+        defects += d
+    return defects
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     from paper_1705_06149_gb300 import Grid
@@ -355,12 +393,10 @@ def run_ours(args, world, rank, local, pg):
     g.project(u0)
     slices = g.zeros(N_SLICES + 1)
     g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=0)
-    for _ in range(args.warmup):
-        g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=1, resume=True)
+    run_parareal_iterations(g, u0, slices, args.warmup)
     torch.cuda.synchronize()
 
-    # ---- timed region --------------------------------------------------------
-    g.profile(True, min_batch=2)  # the fine sweep (chunks of 8 slices), not batch-1 calls
+    # ---- timed region: Parareal iterations, no per-launch timing --------------
     launches0 = g.stats()["launches"]
     krylov0 = g.stats()["krylov_iters"]
     clocks = ClockSampler(local)
@@ -371,88 +407,121 @@ def run_ours(args, world, rank, local, pg):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    defects = []
-    for _ in range(args.steps):
-        _, d = g.parareal(u0, slices, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE, kmax=1,
-                          resume=True)
-        defects += d
+    defects = run_parareal_iterations(g, u0, slices, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(pg, dev)
     clock_rec = clocks.stop()
     ms_total = e0.elapsed_time(e1)
-    prof = g.profile_read()
-    g.profile(False)
     st = g.stats()
     launches = st["launches"] - launches0
+    iters_per_step = (st["krylov_iters"] - krylov0) / max(1, args.steps)
     cell_steps = N_SLICES * FINE_STEPS * N_CELLS ** 3
     value, ms_step = job_value(ms_total / args.steps, world, cell_steps, pg, dev)
 
-    # ---- roofline of the dominant kernel (live CUDA-event timing) -------------
+    # ---- profiled pass: the same iterations with every batched launch of the
+    # fine sweep bracketed by CUDA events on the grid's stream (the coarse
+    # chain is one graph launch and is not split) ------------------------------
+    g.profile(True, min_batch=2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    run_parareal_iterations(g, u0, slices, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_profiled = e0.elapsed_time(e1) / args.steps
+    prof = g.profile_read()
+    g.profile(False)
+
+    # ---- roofline: dominant kernel and the whole sweep -----------------------
     esz = 4 if prec == "fp32_refine" else 8
     words = WORDS_MG if args.preconditioner == "multigrid" else WORDS_PLAIN
     peak = float(peaks["hbm_gbs"])
-    per_kernel = {}
     bpc = {k: wpc * esz for k, wpc in words.items()}
     if prec == "fp32_refine" and args.preconditioner == "multigrid":
         bpc.update(BYTES_STEP_FP32)
+    # the coarser levels count words moved (cell_units are words there)
+    bpc.update({"mg_coarse": esz, "mg_block": esz})
+    per_kernel = {}
     for k, b in bpc.items():
         kp = prof[k]
         if kp["ms"] <= 0 or kp["launches"] == 0:
             continue
         bytes_alg = kp["cell_units"] * b
         per_kernel[k] = {"achieved_gbs": bytes_alg / (kp["ms"] / 1e3) / 1e9,
+                         "frac": bytes_alg / (kp["ms"] / 1e3) / 1e9 / peak,
                          "ms_per_step": kp["ms"] / args.steps,
                          "avg_launch_us": 1e3 * kp["ms"] / kp["launches"],
-                         "launches": kp["launches"]}
-    kern = max(per_kernel, key=lambda k: per_kernel[k]["ms_per_step"])
+                         "launches": kp["launches"],
+                         "bytes_per_step": bytes_alg / args.steps}
+    # the dominant single kernel (mg_coarse is several kernels of the coarser
+    # levels, mg_block the one-CTA levels: reported, not picked)
+    single = {k: v for k, v in per_kernel.items() if k not in ("mg_coarse", "mg_block")}
+    kern = max(single, key=lambda k: single[k]["ms_per_step"])
     kp = prof[kern]
     achieved = per_kernel[kern]["achieved_gbs"]
     traffic = traffic_for(kern)
     per_launch_units = kp["cell_units"] / max(kp["launches"], 1)
+    sweep_ms = sum(v["ms"] for v in prof.values()) / args.steps
+    modelled_ms = sum(v["ms_per_step"] for v in per_kernel.values())
+    sweep_bytes = sum(v["bytes_per_step"] for v in per_kernel.values())
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[kern], "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": per_launch_units * bpc[kern],
                 "avg_launch_us": 1e3 * kp["ms"] / max(kp["launches"], 1),
                 "traffic": (traffic * per_launch_units) if traffic else None,
+                "timing": "separate profiled pass of the same iterations (CUDA events "
+                          "around every batched launch); the headline pass is unprofiled",
+                "sweep_frac": (sweep_bytes / (modelled_ms / 1e3) / 1e9 / peak)
+                if modelled_ms > 0 else None,
+                "sweep_kernel_ms_per_step": sweep_ms,
+                "sweep_modelled_ms_per_step": modelled_ms,
+                "sweep_algorithmic_gb_per_step": sweep_bytes / 1e9,
+                "sweep_frac_of_iteration": (sweep_bytes / (ms_step / 1e3) / 1e9 / peak),
                 "solver_kernels": per_kernel}
-    fine_kernel_ms = sum(v["ms"] for v in prof.values()) / args.steps
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
                for k, v in prof.items() if v["launches"]}
-    iters_per_cell_step = (st["krylov_iters"] - krylov0) / max(1, args.steps)
 
     # ---- end to end through the public API with host buffers ------------------
     host = slices.to("cpu")
     host = type(host)(*[t.pin_memory() for t in host.fields()])
-    e2e_steps = max(1, min(2, args.steps))
     barrier(pg, dev)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = d2h = 0
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         _, _, bi, bo = g.parareal_host(u0, host, N_SLICES, FINE_STEPS, COARSE_STEPS, DT_FINE,
                                        kmax=1, resume=True, slices_dev=slices)
         h2d, d2h = bi, bo
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, pg, dev)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, pg, dev)
     e2e = {"value": world * cell_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
-    # ---- comparators: FP64 batched and plain per-slice FP64 ------------------
-    comparators = None
-    if not args.no_comparators and rank == 0:
-        comparators = fp64_comparators(init)
-
+    # ---- CPU oracle: timing sample, and the reference the GPU paths' errors
+    # are measured against (the oracle's own start state, 2 fine steps) -------
     cpu = None
-    if not args.no_cpu_baseline and rank == 0:
+    errors = None
+    comparators = None
+    if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         o64, start = initial_field_oracle()
         cores = cpu_cores()
-        rate, secs = oracle_sample(o64, start, max(1, cores))
+        rate, secs, ref2 = oracle_sample(o64, start, max(1, cores))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{max(1, cores)} copies of the 64^3 start state, 1 fine step each "
                          f"after 1 warm step ({secs:.1f} s timed), OpenMP over copies"}
+        errors = gpu_error_vs_oracle(g, start, ref2, 2)
+        errors["sample"] = ("2 fine steps (dt 5e-4) of the oracle's 64^3 start state, two "
+                            "copies in one batched call; relative L2 against the FP64 oracle")
+        if not args.no_comparators:
+            comparators = fp64_comparators(init, start, ref2)
+    elif rank == 0 and not args.no_comparators:
+        comparators = fp64_comparators(init, None, None)
+    if comparators is not None:
+        comparators["ratio_fp32_refine_to_fp64_per_slice"] = (
+            value / comparators["fp64_per_slice"]["value"])
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -469,6 +538,10 @@ def run_ours(args, world, rank, local, pg):
                                 "chunk overlapped with the next chunk's sweep"
                                 % args.parareal_chunk)
                    if args.parareal_chunk > 0 else "fine sweep over all slices, then the chain",
+                   "timed": "consecutive Parareal iterations (resume) after the coarse sweep "
+                            "and the warm-up iterations; the per-iteration cost does not "
+                            "depend on the iteration index (every fine and coarse solve starts "
+                            "from its own warm start)",
                    "l2": "working set > L2 (no flush needed): ~%.0f MB of Krylov vectors"
                          % (N_SLICES * N_CELLS ** 3 * esz * 8 / 1e6)},
         "roofline": roofline,
@@ -476,10 +549,12 @@ def run_ours(args, world, rank, local, pg):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clock_rec,
-        "fine_sweep": {"kernel_ms_per_step": fine_kernel_ms,
-                       "cell_steps_per_s_kernels": cell_steps / (fine_kernel_ms / 1e3)
-                       if fine_kernel_ms > 0 else None,
-                       "krylov_iters_per_step_all_solves": iters_per_cell_step,
+        "error_vs_oracle": errors,
+        "fine_sweep": {"kernel_ms_per_step": sweep_ms,
+                       "cell_steps_per_s_kernels": cell_steps / (sweep_ms / 1e3)
+                       if sweep_ms > 0 else None,
+                       "profiled_pass_ms_per_step": ms_profiled,
+                       "krylov_iters_per_step_all_solves": iters_per_step,
                        "kernels": kernels},
         "defects": defects,
         "comparators": comparators,
@@ -708,37 +783,100 @@ def run_mixed(args):
     return 0
 
 
-def fp64_comparators(init):
-    """Rates of the FP64 batched sweep and of the plain per-slice FP64 path (one
-    slice per call), each over a bounded sample of the same workload."""
+def run_peaks(args):
+    """FP32 and FP64 fused multiply-add throughput (libns_peaks.so): the
+    arithmetic ceilings for kernels that HBM does not bind.  Best of `steps`
+    launches after `warmup`, with the SM clocks sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_1705_06149_gb300 import build as nb
+    nb.build()
+    lib = ctypes.CDLL(nb.PEAKS_LIB)
+    lib.nsp_fma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_double)]
+    torch.cuda.set_device(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {"mode": "peaks", "sms": sms}
+    clocks = ClockSampler(0)
+    clocks.start()
+    # 8 CTAs of 256 threads per SM (2048 threads: every warp slot)
+    for name, fp64, iters in (("fp32", 0, 200000), ("fp64", 1, 4000)):
+        best = 0.0
+        ms = ctypes.c_float(0)
+        fl = ctypes.c_double(0)
+        for rep in range(args.warmup + args.steps):
+            rc = lib.nsp_fma_probe(fp64, 8 * sms, iters, ctypes.c_void_p(stream),
+                                   ctypes.byref(ms), ctypes.byref(fl))
+            if rc != 0:
+                raise RuntimeError(f"nsp_fma_probe failed with CUDA error {rc}")
+            if rep >= args.warmup:
+                best = max(best, fl.value / (ms.value / 1e3) / 1e12)
+        out[f"{name}_tflops"] = best
+        out[f"{name}_ms_per_launch"] = ms.value
+    out["clocks"] = clocks.stop()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def fp64_comparators(init, start, ref):
+    """Rates of the FP64 batched sweep and of the per-slice FP64 paths (one
+    slice per call, with the multigrid preconditioner and with plain
+    BiCGStab), each over a bounded sample of the same workload after a
+    warm-up, every solve to the relative residual 1e-10 that the FP32+refine
+    path's FP64 refinement reaches; with start/ref given (the oracle's start
+    state and its 2-step result), each path's error against the oracle."""
     import torch
     from paper_1705_06149_gb300 import Grid
     out = {}
-    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision="fp64", batch=N_SLICES)
+    rtol, steps = 1e-10, 8
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision="fp64", batch=N_SLICES,
+             poisson_rtol=rtol)
     st = g.state_from(init)
     g.project(st)
     batch = g.state_from([t.expand((N_SLICES,) + tuple(t.shape[1:])).cpu().numpy()
                           for t in st.fields()])
     g.step_fine(batch, DT_FINE, 2)  # warm
-    torch.cuda.synchronize()
-    steps = 4
-    t0 = time.perf_counter()
-    g.step_fine(batch, DT_FINE, steps)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+    it0 = g.stats()["krylov_iters"]
+    t = timed(lambda: g.step_fine(batch, DT_FINE, steps))
     out["fp64_batched"] = {"value": N_SLICES * steps * N_CELLS ** 3 / t, "unit": UNIT,
-                           "sample": f"{N_SLICES} slices x {steps} fine steps"}
-    nsl = 4
-    one = [batch.slice(s).clone() for s in range(nsl)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in range(nsl):
-        g.step_fine(one[s], DT_FINE, steps)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    out["fp64_per_slice"] = {"value": nsl * steps * N_CELLS ** 3 / t, "unit": UNIT,
-                             "sample": f"{nsl} slices x {steps} fine steps, one slice per call"}
+                           "sample": f"{N_SLICES} slices x {steps} fine steps in one call "
+                                     f"(after 2 warm steps), Poisson rtol {rtol:g}",
+                           "krylov_iters_per_solve": (g.stats()["krylov_iters"] - it0)
+                           / (N_SLICES * steps)}
+    if start is not None:
+        out["fp64_batched"]["error_vs_oracle"] = gpu_error_vs_oracle(g, start, ref, 2)
+    slices = [batch.slice(s).clone() for s in range(8)]
     g.close()
+    for name, pc in (("fp64_per_slice", "multigrid"), ("fp64_per_slice_plain", "none")):
+        g1 = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision="fp64", batch=2,
+                  poisson_rtol=rtol, preconditioner=pc)
+        one = [s.clone() for s in slices]
+        g1.step_fine(one[0].clone(), DT_FINE, 2)  # warm
+        it0 = g1.stats()["krylov_iters"]
+
+        def per_slice():
+            for s in one:
+                g1.step_fine(s, DT_FINE, steps)
+        t = timed(per_slice)
+        out[name] = {"value": len(one) * steps * N_CELLS ** 3 / t, "unit": UNIT,
+                     "sample": f"{len(one)} slices x {steps} fine steps, one slice per call, "
+                               f"{'multigrid-preconditioned' if pc == 'multigrid' else 'plain'} "
+                               f"BiCGStab, Poisson rtol {rtol:g}",
+                     "krylov_iters_per_solve": (g1.stats()["krylov_iters"] - it0)
+                     / (len(one) * steps)}
+        if start is not None:
+            out[name]["error_vs_oracle"] = gpu_error_vs_oracle(g1, start, ref, 2)
+        g1.close()
     return out
 
 
@@ -755,6 +893,8 @@ def main():
         rc = run_obstacles(args)
     elif args.mode == "mixed":
         rc = run_mixed(args)
+    elif args.mode == "peaks":
+        rc = run_peaks(args)
     elif args.impl == "reference":
         rc = run_reference(args, world, rank, pg)
     else:

@@ -23,6 +23,9 @@
  * - No C++ exception crosses the ABI.  On a non-OK status the contents of
  *   output buffers are unspecified; ns_last_error() describes the failure.
  * - A grid object must not be used by two host threads at once.
+ * - A grid belongs to the CUDA device that was current when it was created;
+ *   every call (and every host thread a call starts) makes that device
+ *   current for its duration and restores the caller's device on return.
  */
 #ifndef NS_H
 #define NS_H
@@ -189,7 +192,12 @@ ns_status ns_parareal_iterate(ns_grid *grid, ns_state u0, ns_state slices, int n
 ns_status ns_adjoint(ns_grid *grid, ns_state u0, double dt, int nsteps, int ckpt_every,
                      double *J, ns_state grad_u0, double *dJ_dulid);
 
-/* Sets the lid speed u_lid of the grid (for derivative checks in u_lid). */
+/* Sets the lid speed u_lid of the grid (for derivative checks in u_lid).
+ * It reaches every later call, including the coarse propagator of
+ * ns_parareal_iterate.  The coarse values a Parareal call stored for a
+ * resume belong to the old lid and are dropped (resume = 1 then fails with
+ * NS_ERR_ARG), and launches of graphs that ns_graph_create captured from
+ * this grid before the change fail with NS_ERR_ARG. */
 ns_status ns_set_lid_speed(ns_grid *grid, double u_lid);
 
 ns_status ns_get_stats(const ns_grid *grid, ns_stats *out);
@@ -213,9 +221,11 @@ typedef enum {
     NS_K_MG_LAP_T = 11,    /* multigrid path: t = L z, (t,s), (t,t)            */
     NS_K_MG_RESTRICT0 = 12,/* multigrid: finest-level residual, restricted     */
     NS_K_MG_PROLONG0 = 13, /* multigrid: finest-level trilinear correction     */
-    NS_K_MG_COARSE = 14,   /* multigrid: every coarser level, incl. the one-CTA levels */
-    NS_K_ADJOINT = 15,     /* adjoint: (dR/du)^T mu scatter, terminal and update kernels */
-    NS_K_KINDS = 16
+    NS_K_MG_COARSE = 14,   /* multigrid: the grid-level kernels of the coarser levels
+                              (smoothing, restriction, prolongation)              */
+    NS_K_ADJOINT = 15,     /* adjoint: (dR/du)^T mu, terminal and update kernels */
+    NS_K_MG_BLOCK = 16,    /* multigrid: the one-CTA levels (one CTA per state)   */
+    NS_K_KINDS = 17
 } ns_kernel_kind;
 
 typedef struct {
@@ -223,7 +233,11 @@ typedef struct {
     long long launches;    /* timed launches                                         */
     long long cell_units;  /* cells processed by them: for the Krylov phases the sum
                               over states of (iterations x cells), elsewhere
-                              (states x cells) per launch                          */
+                              (states x cells) per launch; for NS_K_MG_COARSE and
+                              NS_K_MG_BLOCK the values (words) the launches read
+                              and write by the algorithmic model: 2 per cell for
+                              smoothing and for the one-CTA levels' input and
+                              output, 2 + 1/8 for restriction and prolongation */
 } ns_kernel_time;
 
 /* Turns per-launch timing on (on != 0) or off.  While on, every launch made by
@@ -255,8 +269,10 @@ ns_status ns_profile_read(ns_grid *grid, ns_kernel_time *out, int n);
  *     NS_NOALLOC_MAX_CELLS cells are rejected with NS_ERR_ARG.
  *   - No cudaMalloc, cudaFree or other allocating routine is called.  The
  *     first call on each device looks the array's device address up
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current.
+ *   - Every call polls its convergence flags into host memory and
+ *     synchronises cuda_stream, so it must never be made while a stream is
+ *     being captured into a CUDA graph.
  *   - Every call shares the one array: calls that overlap on the GPU (two
  *     streams, two host threads) race and give wrong results.  The array
  *     keeps the previous call's contents; the call clears what must start at
@@ -267,7 +283,6 @@ ns_status ns_poisson_solve_noalloc(int nx, int ny, int nz, double lx, double ly,
                                    const int *bc, double rtol, int maxit, const double *b,
                                    double *p, void *cuda_stream, int *iters);
 
-/* Message of the last failure on the calling host thread ("" if none). */
 /* Advances several independent grids at once: for each i < n exactly what
  * ns_step_fine(grids[i], states[i], dts[i], nsteps[i]) computes.  Each grid
  * runs on a stream of its own (ordered after, and joined back into, the
@@ -316,6 +331,7 @@ ns_status ns_graph_launch(ns_graph *graph, void *cuda_stream);
 ns_status ns_graph_check(ns_graph *graph, void *cuda_stream);
 ns_status ns_graph_destroy(ns_graph *graph);
 
+/* Message of the last failure on the calling host thread ("" if none). */
 const char *ns_last_error(void);
 
 #ifdef __cplusplus

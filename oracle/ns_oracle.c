@@ -165,6 +165,14 @@ static double vget(const og_grid *g, int c, const double *a, int i, int j, int k
     return 2.0 * wall_speed(g, c, d, side) - mirror;
 }
 
+/* vget for the tests that pin the ghost rules by hand values: the value of
+ * velocity component c (0 u, 1 v, 2 w) of field a at (i,j,k), up to two
+ * positions outside the stored range along one axis. */
+double og_vget(const og_grid *g, int c, const double *a, int i, int j, int k)
+{
+    return vget(g, c, a, i, j, k);
+}
+
 static double pget(const og_grid *g, const double *p, int i, int j, int k)
 {
     int idx[3] = {i, j, k};

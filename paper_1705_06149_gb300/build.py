@@ -15,11 +15,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libns.so")
+PEAKS_LIB = os.path.join(HERE, "libns_peaks.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
 def _sources():
-    out = [os.path.join(INCLUDE, "ns.h")]
+    out = [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h")]
     for f in sorted(os.listdir(CSRC)):
         if f.endswith((".cu", ".cuh", ".h")):
             out.append(os.path.join(CSRC, f))
@@ -34,24 +35,51 @@ def nvcc() -> str:
 
 
 def needs_build() -> bool:
-    if not os.path.exists(LIB):
+    return _stale(LIB) or _stale(PEAKS_LIB)
+
+
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/ns_api.cu into libns.so for sm_103a; returns the path."""
-    if not force and not needs_build():
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, os.path.join(CSRC, "ns_api.cu"), os.path.join(CSRC, "ns_noalloc.cu"),
-           "-o", tmp]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    """Compile csrc/ into libns.so (the stepper's C ABI) and libns_peaks.so
+    (the FMA throughput probe of the benchmark) for sm_103a, the translation
+    units in parallel; returns the path of libns.so."""
+    jobs = []
+    parts = [(LIB, ["ns_api.cu", "ns_noalloc.cu"]), (PEAKS_LIB, ["ns_peaks.cu"])]
+    for lib, srcs in parts:
+        if not force and not _stale(lib):
+            continue
+        tmp = lib + f".tmp{os.getpid()}"
+        objs = []
+        for src in srcs:
+            obj = os.path.join(HERE, f".{os.path.splitext(src)[0]}.{os.getpid()}.o")
+            cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            jobs.append(subprocess.Popen(cmd))
+            objs.append(obj)
+        parts_done = (lib, tmp, objs)
+        jobs.append(parts_done)
+    procs = [j for j in jobs if isinstance(j, subprocess.Popen)]
+    rcs = [p.wait() for p in procs]
+    links = [j for j in jobs if isinstance(j, tuple)]
+    try:
+        if any(rcs):
+            raise subprocess.CalledProcessError(max(rcs), "nvcc")
+        for lib, tmp, objs in links:
+            subprocess.run([nvcc(), ARCH, "-shared", *objs, "-o", tmp], check=True)
+            os.replace(tmp, lib)
+    finally:
+        for _, _, objs in links:
+            for o in objs:
+                if os.path.exists(o):
+                    os.remove(o)
     return LIB
 
 

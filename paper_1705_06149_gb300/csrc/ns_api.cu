@@ -46,12 +46,34 @@ ns_status fail(ns_status st, const std::string& msg) {
 
 constexpr int kMaxOuterDefault = 40;
 
+// Makes `dev` the calling thread's current device for the guard's lifetime
+// (host threads start on device 0; a grid's launches, copies and lazy
+// allocations must all go to the device its memory lives on).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 }  // namespace
 
 struct ns_grid {
     ns_grid_desc d{};
     Geo geo{};
     cudaStream_t stream = nullptr;
+    int device = 0;       // the CUDA device the grid's memory and streams live on
+    long long gen = 0;    // bumped when a setting that captured graphs hold changes
     int cap = 0;
     bool fp32 = false;
     int maxit = 0;
@@ -530,11 +552,16 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
         NS_LAUNCH(g, MODE == SRC_P ? NS_K_KRYLOV_A : NS_K_KRYLOV_B, 0,
                   (k_mg_src<T, MODE, false><<<dim3(L0.ctas, batch), blk, 0, g->stream>>>(
                       L0, mb, g->ctl, nullptr, dst)));
+    // NS_K_MG_COARSE and NS_K_MG_BLOCK count words moved (algorithmic model):
+    // smoothing b -> y: 2 per cell; restriction b, y -> coarse b: 2 + 1/8;
+    // prolongation y, coarse e -> y: 2 + 1/8; the one-CTA levels: the right
+    // side in, the iterate out (2 per cell of the first one-CTA level)
     for (int l = 0; l < lc; ++l) {
         const T* bsrc = l == 0 ? src : mb.B[l];
         const T* bsrc_odd = l == 0 ? src_odd : nullptr;
         const T* ysrc = l == 0 ? dst : mb.Yl[l];
-        NS_LAUNCH(g, l == 0 ? NS_K_MG_RESTRICT0 : NS_K_MG_COARSE, 0,
+        const long long rwords = l == 0 ? 0 : (P.lev[l].cells * 17 / 8) * batch;
+        NS_LAUNCH(g, l == 0 ? NS_K_MG_RESTRICT0 : NS_K_MG_COARSE, rwords,
                   k_mg_restrict<T><<<dim3(P.lev[l].rctas, batch), blk, 0, g->stream>>>(
                       P.lev[l], P.lev[l + 1], g->ctl, bsrc, bsrc_odd, ysrc, mb.B[l + 1]));
         if (l + 1 < lc) {
@@ -542,12 +569,12 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
             if (Ls.fcode == nullptr && Ls.n[0] % 2 == 0) {
                 // x pairs per thread (a level that is restricted has an even nx)
                 const int pbx = ceil_div(Ls.n[0], 64);
-                NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+                NS_LAUNCH(g, NS_K_MG_COARSE, 2 * Ls.cells * batch,
                           (k_mg_src_pair<T, SRC_ARR>
                            <<<dim3(pbx * Ls.by * Ls.bz, batch), blk, 0, g->stream>>>(
                                Ls, mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1], pbx)));
             } else {
-                NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+                NS_LAUNCH(g, NS_K_MG_COARSE, 2 * Ls.cells * batch,
                           (k_mg_src<T, SRC_ARR, true>
                            <<<dim3(Ls.ctas, batch), blk, 0, g->stream>>>(
                                Ls, mb, g->ctl, mb.B[l + 1], mb.Yl[l + 1])));
@@ -557,22 +584,23 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
     T* bin = lc == 0 ? src : mb.B[lc];
     T* bin_odd = lc == 0 ? src_odd : nullptr;
     T* bout = lc == 0 ? dst : mb.Yl[lc];
-    NS_LAUNCH(g, NS_K_MG_COARSE, 0,
+    NS_LAUNCH(g, NS_K_MG_BLOCK, 2 * P.lev[lc].cells * batch,
               k_mg_block<T><<<batch, MG_BLOCK_THREADS, g->mg_smem, g->stream>>>(
                   P, g->ctl, bin, bin_odd, bout));
     for (int l = lc - 1; l >= 0; --l) {
         T* y = l == 0 ? dst : mb.Yl[l];
         const Lev& L = P.lev[l];
+        const long long pwords = l == 0 ? 0 : (L.cells * 17 / 8) * batch;
         if (L.fcode == nullptr) {
             // x pairs per thread (no solid cells; nx is even on every level
             // prolonged to)
             const int pbx = ceil_div(L.n[0], 64);
-            NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
+            NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, pwords,
                       k_mg_prolong_pair<T><<<dim3(pbx * L.by * L.bz, batch), blk, 0,
                                              g->stream>>>(L, P.lev[l + 1], g->ctl, y,
                                                           mb.Yl[l + 1], pbx));
         } else {
-            NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, 0,
+            NS_LAUNCH(g, l == 0 ? NS_K_MG_PROLONG0 : NS_K_MG_COARSE, pwords,
                       k_mg_prolong<T><<<dim3(L.ctas, batch), blk, 0, g->stream>>>(
                           L, P.lev[l + 1], g->ctl, y, mb.Yl[l + 1]));
         }
@@ -1018,6 +1046,7 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
 
 ns_status step_any(ns_grid* g, const ns_state& io, double dt, int nsteps, const char* what) {
     if (!g) return fail(NS_ERR_ARG, std::string(what) + ": null grid");
+    const DeviceGuard dg(g->device);
     NS_TRY(check_state(g, io, what));
     if (!(dt > 0.0) || !std::isfinite(dt))
         return fail(NS_ERR_ARG, std::string(what) + ": dt must be positive and finite");
@@ -1366,6 +1395,8 @@ ns_status parareal_iteration_chunked(ns_grid* g, ns_state slices, int N, int S, 
         cv.notify_all();
     };
     std::thread chain_thread([&]() {
+        // a new host thread starts on device 0
+        const DeviceGuard dg(g->device);
         auto run = [&]() -> ns_status {
             NS_CUDA(cudaStreamWaitEvent(h->stream, ev_start, 0));
             NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
@@ -1729,6 +1760,11 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         }
     }
     g->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return fail(NS_ERR_CUDA, "ns_create_grid: cudaGetDevice failed");
+    }
     g->cap = d.batch;
     g->fp32 = d.precision == NS_FP32_REFINE;
     g->maxit = d.poisson_maxit > 0 ? d.poisson_maxit : 20 * std::max(d.nx, std::max(d.ny, d.nz));
@@ -1853,6 +1889,7 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
 
 ns_status ns_destroy_grid(ns_grid* grid) {
     if (!grid) return NS_OK;
+    const DeviceGuard dg(grid->device);
     cudaStreamSynchronize(grid->stream);
     if (grid->chain_exec) cudaGraphExecDestroy(grid->chain_exec);
     if (grid->chain_graph) cudaGraphDestroy(grid->chain_graph);
@@ -1888,6 +1925,7 @@ ns_status ns_step_coarse(ns_grid* grid, ns_state io, double dt_coarse, int nstep
 ns_status ns_project(ns_grid* grid, ns_state io) {
     g_last_error.clear();
     if (!grid) return fail(NS_ERR_ARG, "ns_project: null grid");
+    const DeviceGuard dg(grid->device);
     NS_TRY(check_state(grid, io, "ns_project"));
     ns_status st = grid->fp32 ? project_impl<float>(grid, io) : project_impl<double>(grid, io);
     if (st == NS_OK) NS_TRY(sync_stream(grid));
@@ -1897,6 +1935,7 @@ ns_status ns_project(ns_grid* grid, ns_state io) {
 ns_status ns_predict(ns_grid* grid, ns_state in, double dt, void* fu, void* fv, void* fw) {
     g_last_error.clear();
     if (!grid) return fail(NS_ERR_ARG, "ns_predict: null grid");
+    const DeviceGuard dg(grid->device);
     NS_TRY(check_state(grid, in, "ns_predict"));
     if (!fu || !fv || !fw) return fail(NS_ERR_ARG, "ns_predict: null output pointer");
     if (!std::isfinite(dt)) return fail(NS_ERR_ARG, "ns_predict: dt not finite");
@@ -1922,6 +1961,7 @@ ns_status ns_predict(ns_grid* grid, ns_state in, double dt, void* fu, void* fv, 
 ns_status ns_poisson_solve(ns_grid* grid, const double* b, double* p, int batch, int* iters) {
     g_last_error.clear();
     if (!grid) return fail(NS_ERR_ARG, "ns_poisson_solve: null grid");
+    const DeviceGuard dg(grid->device);
     if (!b || !p) return fail(NS_ERR_ARG, "ns_poisson_solve: null pointer");
     if (batch < 1 || batch > grid->cap)
         return fail(NS_ERR_ARG, "ns_poisson_solve: batch outside [1, capacity]");
@@ -1969,6 +2009,7 @@ ns_status ns_parareal_iterate(ns_grid* grid, ns_state u0, ns_state slices, int n
     g_last_error.clear();
     if (k_done) *k_done = 0;
     if (!grid) return fail(NS_ERR_ARG, "ns_parareal_iterate: null grid");
+    const DeviceGuard dg(grid->device);
     if (n_slices < 1 || n_slices > grid->cap)
         return fail(NS_ERR_ARG, "ns_parareal_iterate: n_slices outside [1, capacity]");
     if (u0.batch != 1) return fail(NS_ERR_ARG, "ns_parareal_iterate: u0 must hold one state");
@@ -1995,6 +2036,7 @@ ns_status ns_adjoint(ns_grid* grid, ns_state u0, double dt, int nsteps, int ckpt
                      ns_state grad_u0, double* dJ_dulid) {
     g_last_error.clear();
     if (!grid) return fail(NS_ERR_ARG, "ns_adjoint: null grid");
+    const DeviceGuard dg(grid->device);
     NS_TRY(check_state(grid, u0, "ns_adjoint(u0)"));
     if (grid->fp32) return fail(NS_ERR_ARG, "ns_adjoint: needs an NS_FP64 grid");
     if (grid->geo.solid) return fail(NS_ERR_ARG, "ns_adjoint: grids with solid cells are not "
@@ -2013,12 +2055,35 @@ ns_status ns_set_lid_speed(ns_grid* grid, double u_lid) {
     if (!std::isfinite(u_lid)) return fail(NS_ERR_ARG, "ns_set_lid_speed: u_lid not finite");
     grid->d.u_lid = u_lid;
     grid->geo.u_lid = u_lid;
+    // the coarse propagator's companion grid and every graph captured from
+    // this grid hold the description by value: update the companion, drop
+    // the chain graphs (recaptured on next use), and invalidate the stored
+    // coarse values G(y^k_n) of the old lid (a resume then needs a fresh
+    // start) and the graphs of ns_graph_create (their launches then fail)
+    const DeviceGuard dg(grid->device);
+    if (grid->chain) {
+        cudaStreamSynchronize(grid->chain->stream);
+        grid->chain->d.u_lid = u_lid;
+        grid->chain->geo.u_lid = u_lid;
+        grid->chain->gen += 1;
+    }
+    if (grid->chain_exec) cudaGraphExecDestroy(grid->chain_exec);
+    if (grid->chain_graph) cudaGraphDestroy(grid->chain_graph);
+    grid->chain_exec = nullptr;
+    grid->chain_graph = nullptr;
+    for (cudaGraphExec_t e : grid->chunk_exec) cudaGraphExecDestroy(e);
+    for (cudaGraph_t c : grid->chunk_graph) cudaGraphDestroy(c);
+    grid->chunk_exec.clear();
+    grid->chunk_graph.clear();
+    grid->pr_valid = false;
+    grid->gen += 1;
     return NS_OK;
 }
 
 ns_status ns_profile_enable(ns_grid* grid, int on, int min_batch) {
     g_last_error.clear();
     if (!grid) return fail(NS_ERR_ARG, "ns_profile_enable: null grid");
+    const DeviceGuard dg(grid->device);
     auto& P = grid->prof;
     if (on && P.cap == 0) {
         const int pairs = 8192;
@@ -2039,6 +2104,7 @@ ns_status ns_profile_enable(ns_grid* grid, int on, int min_batch) {
 ns_status ns_profile_read(ns_grid* grid, ns_kernel_time* out, int n) {
     g_last_error.clear();
     if (!grid || !out) return fail(NS_ERR_ARG, "ns_profile_read: null argument");
+    const DeviceGuard dg(grid->device);
     NS_TRY(sync_stream(grid));
     for (int q = 0; q < std::min<int>(n, NS_K_KINDS); ++q) out[q] = grid->prof.acc[q];
     return NS_OK;
@@ -2071,6 +2137,7 @@ ns_status ns_step_fine_many(ns_grid* const* grids, const ns_state* states, const
     std::vector<cudaEvent_t> ev(2 * n, nullptr);
     ns_status st = NS_OK;
     for (int i = 0; i < n && st == NS_OK; ++i) {
+        const DeviceGuard dg(grids[i]->device);
         if (cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ev[2 * i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&ev[2 * i + 1], cudaEventDisableTiming) != cudaSuccess ||
@@ -2088,11 +2155,13 @@ ns_status ns_step_fine_many(ns_grid* const* grids, const ns_state* states, const
         }
         for (int i = 0; i < n; ++i)
             threads.emplace_back([&, i]() {
+                // a new host thread starts on device 0: step_any selects the grid's
                 res[i] = step_any(grids[i], states[i], dts[i], nsteps[i], "ns_step_fine_many");
                 if (res[i] != NS_OK) msg[i] = g_last_error;
             });
         for (auto& t : threads) t.join();
         for (int i = 0; i < n; ++i) {
+            const DeviceGuard dg(grids[i]->device);
             grids[i]->stream = saved[i];
             if (cudaEventRecord(ev[2 * i + 1], own[i]) != cudaSuccess ||
                 cudaStreamWaitEvent(saved[i], ev[2 * i + 1], 0) != cudaSuccess)
@@ -2120,6 +2189,7 @@ struct ns_graph {
     std::vector<cudaGraph_t> graphs;
     std::vector<cudaGraphExec_t> execs;
     std::vector<ns_grid*> grids;
+    std::vector<long long> gens;        // each grid's settings generation at capture
     std::vector<int> batch, nsteps;
     std::vector<cudaStream_t> streams;  // 2 per branch: top level, loop bodies
     std::vector<cudaEvent_t> events;    // per branch: done; last: fork
@@ -2197,6 +2267,7 @@ ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const d
         gr->graphs.push_back(graph);
         gr->execs.push_back(exec);
         gr->grids.push_back(g);
+        gr->gens.push_back(g->gen);
         gr->batch.push_back(states[i].batch);
         gr->nsteps.push_back(nsteps[i]);
         LoopCount lc{};
@@ -2214,6 +2285,11 @@ ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const d
 
 ns_status ns_graph_launch(ns_graph* gr, void* cuda_stream) {
     if (!gr || gr->execs.empty()) return fail(NS_ERR_ARG, "ns_graph_launch: null graph");
+    for (size_t i = 0; i < gr->grids.size(); ++i)
+        if (gr->grids[i]->gen != gr->gens[i])
+            return fail(NS_ERR_ARG, "ns_graph_launch: the lid speed of the grid of branch " +
+                                        std::to_string(i) +
+                                        " changed after the capture; create the graph again");
     const cudaStream_t cs = (cudaStream_t)cuda_stream;
     const size_t n = gr->execs.size();
     NS_CUDA(cudaEventRecord(gr->events[n], cs));

@@ -37,6 +37,18 @@ def test_library_builds_loads_and_exports_every_declared_symbol():
         assert set(declared_entry_points()) <= exported
 
 
+def test_peaks_library_exports_its_declared_probe():
+    from paper_1705_06149_gb300 import build as nb
+    nb.build()
+    src = open(os.path.join(ROOT, "include", "ns_peaks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(nsp_[a-z_]+)\s*\(", src)))
+    assert names == ["nsp_fma_probe"]
+    lib = ctypes.CDLL(nb.PEAKS_LIB)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
 def test_last_error_is_empty_string_initially():
     from paper_1705_06149_gb300 import _native
     lib = _native.load(build_if_missing=True)

@@ -97,6 +97,37 @@ def test_graph_matches_the_oracle(prec):
     graph.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_graph_matches_the_oracle_above_the_one_cta_levels(prec):
+    """A 32^3 cavity and a 40 x 32 x 24 one (periodic z), two states each, so
+    that the finest level (32768 / 30720 cells, far above the 4096-cell one-CTA
+    levels) runs in the graph's grid-level kernels: restriction, smoothing,
+    prolongation, the BiCGStab phases and the refinement, in the conditional
+    while loops."""
+    for dims, bc in (((32, 32, 32), ("wall",) * 3), ((40, 32, 24), ("wall", "wall", "periodic"))):
+        inits = [inputs.random_state(*dims, seed=40 + s, sigma=0.2, bc=bc) for s in range(2)]
+        og = oracle.Grid(*dims, re=400.0, bc=bc, rtol=1e-13)
+        wants = []
+        for init in inits:
+            want = oracle.copy_state(init)
+            og.step(want, 1e-3, 4)
+            wants.append(want)
+        g = Grid(*dims, re=400.0, bc=bc, precision=prec, batch=2, poisson_rtol=1e-13)
+        st = g.state_from([np.stack([i[c] for i in inits]) for c in range(4)])
+        graph = StepGraph([(g, st, 1e-3, 4)])
+        graph.launch()
+        graph.check()
+        got = st.numpy()
+        for s, want in enumerate(wants):
+            vg = np.concatenate([np.ravel(got[c][s]) for c in range(3)])
+            vw = np.concatenate([np.ravel(want[c]) for c in range(3)])
+            ev = np.linalg.norm(vg - vw) / np.linalg.norm(vw)
+            ep = np.linalg.norm(got[3][s] - want[3]) / np.linalg.norm(want[3])
+            assert ev <= TOL[prec] and ep <= TOL[prec], (dims, s, ev, ep)
+        graph.close()
+        g.close()
+
+
 def test_graph_reports_a_solve_that_hits_its_iteration_limit():
     dims = (16, 16, 16)
     g = Grid(*dims, re=100.0, batch=1, poisson_rtol=1e-30, poisson_maxit=3)

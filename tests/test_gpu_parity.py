@@ -197,6 +197,41 @@ def test_cavity16_parareal(cavity16_oracle, prec, pc):
                 assert torch.equal(ser.fields()[c][0], slices.fields()[c][n + 1]), (n, c)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_lid_speed_change_reaches_the_coarse_propagator(prec):
+    """ns_set_lid_speed after a Parareal call: the next call's fine AND coarse
+    propagators use the new lid (K < N, so G enters the result), the coarse
+    values stored for a resume are dropped, and a graph captured before the
+    change refuses to launch."""
+    from paper_1705_06149_gb300 import StepGraph
+    og = oracle.Grid(16, 16, 16, re=100.0, u_lid=0.5)
+    F = opr.fine_propagator(og, 1e-3, 20)
+    G = opr.coarse_propagator(og, 1e-2, 2)
+    y_ref, d_ref = opr.parareal(og.zeros(), 4, F, G, kmax=2)
+    g = Grid(16, 16, 16, re=100.0, u_lid=1.0, precision=prec, batch=4)
+    u0 = g.zeros(1)
+    slices = g.zeros(5)
+    g.parareal(u0, slices, 4, 20, 2, 1e-3, kmax=1)  # companion grid and chain graph at lid 1
+    other = g.zeros(1)
+    graph = StepGraph([(g, other, 1e-3, 1)])
+    g.set_lid_speed(0.5)
+    with pytest.raises(NSError) as e:
+        g.parareal(u0, slices, 4, 20, 2, 1e-3, kmax=1, resume=True)
+    assert e.value.status == N.NS_ERR_ARG
+    with pytest.raises(NSError) as e:
+        graph.launch()
+    assert e.value.status == N.NS_ERR_ARG
+    graph.close()
+    k, defects = g.parareal(u0, slices, 4, 20, 2, 1e-3, kmax=2)
+    assert k == 2
+    got = slices.numpy()
+    for n in range(5):
+        assert_state_close([a[n] for a in got], y_ref[n], TOL[prec], f"slice {n}")
+    dabs = 0.0 if prec == "fp64" else 5e-7
+    for a, b in zip(defects, d_ref):
+        assert abs(a - b) <= 1e-3 * b + dabs
+
+
 def test_parareal_resume_and_tolerance():
     g = Grid(12, 12, 12, re=100.0, batch=3)
     u0 = g.zeros(1)
