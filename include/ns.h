@@ -120,7 +120,17 @@ typedef struct {
 /* Create a grid object: validates the description, chooses the CUDA tiling
  * and allocates the workspace for `batch` states.  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream).  On success *out owns the
- * workspace until ns_destroy_grid. */
+ * workspace until ns_destroy_grid.
+ * Persistent solves: with NS_PERSISTENT=1 in the environment when the grid is
+ * created (multigrid preconditioner, cooperative launch available), every
+ * pressure solve of one state outside graph capture and outside
+ * ns_step_fine_many runs as ONE cooperative kernel (one CTA per SM, grid-wide
+ * barriers between the solver's phases); results agree with the default
+ * launched kernels to rounding level.  Its solves are checked on the host at
+ * the end of the call that issued them.  Each barrier wait is bounded by
+ * NS_PERSIST_SPIN_NS nanoseconds (default 2e9); a wait that gives up ends the
+ * launch and the call returns NS_ERR_TIMEOUT.  Two persistent solves must not
+ * run concurrently on one GPU. */
 ns_status ns_create_grid(const ns_grid_desc *desc, void *cuda_stream, ns_grid **out);
 ns_status ns_destroy_grid(ns_grid *grid);
 ns_status ns_set_stream(ns_grid *grid, void *cuda_stream);
@@ -185,12 +195,24 @@ ns_status ns_parareal_iterate(ns_grid *grid, ns_state u0, ns_state slices, int n
  * with R = Re^-1 lap_h u - div_h(u u) (SMART faces, the branch the forward
  * took).  The forward states are recomputed from (u, p) checkpoints taken
  * every ckpt_every steps; the pressure solves are taken as exact.
- * NS_FP64 grids only (NS_ERR_ARG otherwise).  u0: device state, batch B.
- * J, dJ_dulid: host arrays of B doubles.  grad_u0: device u, v, w buffers of
- * batch B (p unused).  Workspace (checkpoints, one segment of states, the
- * adjoint fields) is allocated for the call and freed before it returns. */
+ * NS_FP64 grids run everything in FP64; NS_FP32_REFINE grids run the forward
+ * steps, the adjoint projections (the same FP32 inner solve with FP64-accurate
+ * refinement) and the adjoint stencils in FP32, with J and dJ/du_lid summed in
+ * FP64.  (dR/du)^T mu is gathered per stored value and every sum has a fixed
+ * order, so repeated calls return identical bits.  Grids with solid cells are
+ * rejected (NS_ERR_ARG).  u0: device state, batch B.  J, dJ_dulid: host
+ * arrays of B doubles.  grad_u0: device u, v, w buffers of batch B in the
+ * grid's velocity type (p unused).  Workspace (checkpoints, one segment of
+ * states, the adjoint fields) is allocated for the call and freed before it
+ * returns. */
 ns_status ns_adjoint(ns_grid *grid, ns_state u0, double dt, int nsteps, int ckpt_every,
                      double *J, ns_state grad_u0, double *dJ_dulid);
+
+/* The objective of ns_adjoint without the gradient: J[b] = 1/2 sum over the
+ * active faces of state b of (component^2) h_x h_y h_z, for each state of
+ * `state` (device, grid's precision; p unused), summed in a fixed order.  J:
+ * host array of state.batch doubles.  Synchronises the grid's stream. */
+ns_status ns_kinetic_energy(ns_grid *grid, ns_state state, double *J);
 
 /* Sets the lid speed u_lid of the grid (for derivative checks in u_lid).
  * It reaches every later call, including the coarse propagator of
@@ -225,7 +247,9 @@ typedef enum {
                               (smoothing, restriction, prolongation)              */
     NS_K_ADJOINT = 15,     /* adjoint: (dR/du)^T mu, terminal and update kernels */
     NS_K_MG_BLOCK = 16,    /* multigrid: the one-CTA levels (one CTA per state)   */
-    NS_K_KINDS = 17
+    NS_K_PERSIST = 17,     /* a whole pressure solve in one persistent cooperative
+                              launch (small batches, multigrid preconditioner)    */
+    NS_K_KINDS = 18
 } ns_kernel_kind;
 
 typedef struct {

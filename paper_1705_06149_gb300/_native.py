@@ -21,12 +21,13 @@ EXPORTS = ("ns_create_grid", "ns_destroy_grid", "ns_set_stream", "ns_step_fine",
            "ns_step_coarse", "ns_project", "ns_predict", "ns_poisson_solve",
            "ns_parareal_iterate", "ns_adjoint", "ns_get_stats", "ns_reset_stats",
            "ns_profile_enable", "ns_profile_read", "ns_poisson_solve_noalloc",
-           "ns_set_lid_speed", "ns_step_fine_many", "ns_graph_create", "ns_graph_launch", "ns_graph_check",
+           "ns_set_lid_speed", "ns_kinetic_energy", "ns_step_fine_many", "ns_graph_create", "ns_graph_launch", "ns_graph_check",
            "ns_graph_destroy", "ns_last_error")
 
 KERNEL_KINDS = ("predict", "divergence", "solve_init", "krylov_A", "krylov_B", "krylov_C",
                 "inner_init", "refine", "correct", "parareal", "mg_lap_v", "mg_lap_t",
-                "mg_restrict0", "mg_prolong0", "mg_coarse", "adjoint", "mg_block")
+                "mg_restrict0", "mg_prolong0", "mg_coarse", "adjoint", "mg_block",
+                "persist")
 
 
 class NSError(RuntimeError):
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = False):
                            vp],
             "ns_get_stats": [vp, ctypes.POINTER(Stats)],
             "ns_set_lid_speed": [vp, ctypes.c_double],
+            "ns_kinetic_energy": [vp, StateC, dp],
             "ns_reset_stats": [vp],
             "ns_profile_enable": [vp, ctypes.c_int, ctypes.c_int],
             "ns_profile_read": [vp, ctypes.POINTER(KernelTime), ctypes.c_int],

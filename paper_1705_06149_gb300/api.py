@@ -239,8 +239,17 @@ class Grid:
         torch.cuda.current_stream(self.device).synchronize()
         return k, d, h2d, d2h
 
+    def kinetic_energy(self, st: State) -> List[float]:
+        """J = 1/2 sum over active faces of component^2 * hx*hy*hz per state."""
+        self._check(st, "kinetic_energy")
+        self._sync_stream()
+        J = (ctypes.c_double * st.batch)()
+        N.check(self.lib.ns_kinetic_energy(self._h, st._c(), J), "ns_kinetic_energy")
+        return [J[i] for i in range(st.batch)]
+
     def adjoint(self, u0: State, dt: float, nsteps: int, ckpt_every: int = 25):
-        """Discrete adjoint of nsteps fine steps (FP64 grids).  Returns
+        """Discrete adjoint of nsteps fine steps (FP64, or FP32 storage with
+        FP64-accurate refinement on fp32_refine grids).  Returns
         (J per state, gradient State (u, v, w; p zero), dJ/du_lid per state)
         for J = 1/2 sum over active faces of component^2 * hx*hy*hz."""
         self._check(u0, "adjoint(u0)")

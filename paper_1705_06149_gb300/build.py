@@ -50,7 +50,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     (the FMA throughput probe of the benchmark) for sm_103a, the translation
     units in parallel; returns the path of libns.so."""
     jobs = []
-    parts = [(LIB, ["ns_api.cu", "ns_noalloc.cu"]), (PEAKS_LIB, ["ns_peaks.cu"])]
+    parts = [(LIB, ["ns_api.cu", "ns_noalloc.cu", "ns_persist.cu"]),
+             (PEAKS_LIB, ["ns_peaks.cu"])]
     for lib, srcs in parts:
         if not force and not _stale(lib):
             continue

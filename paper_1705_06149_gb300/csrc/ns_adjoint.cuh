@@ -5,88 +5,53 @@
 // symmetric since D = -G^T), R = Re^-1 lap_h u - div_h(u u) with SMART faces.
 // Its adjoint maps lambda = dJ/du+ to
 //   mu = P lambda,   dJ/du = mu + dt (dR/du)^T mu,   dJ/du_lid += dt (dR/du_lid)^T mu.
-// (dR/du)^T mu is formed by differentiating every stencil term of R with
-// respect to the stored values (and the lid speed) it reads, and adding the
-// products into the output with FP64 atomics.  SMART takes the branch the
-// forward kernel took (the same division-free comparisons); a flux with zero
-// transporting velocity takes the derivative of its left-upwind form.
+// (dR/du)^T mu is gathered: every stored value sums the derivatives of the
+// stencil terms that read it (directly, or through the ghost rule of a wall
+// reading it as a mirror), each interface flux weighted by the difference of
+// mu on its two faces.  Every output is written by one thread in a fixed
+// order, so the gradient does not depend on scheduling.  SMART takes the
+// branch the forward kernel took (the same division-free comparisons); a
+// flux with zero transporting velocity takes the derivative of its
+// left-upwind form.  T = double (FP64 grids) or float (FP32 storage; the lid
+// derivative and J are summed in FP64).
 #pragma once
 
 #include "ns_kernels.cuh"
 
 namespace nsk {
 
-// value of component c at (i,j,k) = sign * a[idx] + lid * u_lid
-struct VSrc {
-    long long idx;
-    double sign;
-    double lid;
-};
-
-__device__ __forceinline__ VSrc vel_src(const Geo& g, int c, int i, int j, int k) {
-    int q[3] = {i, j, k};
-    double sign = 1.0, lid = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int e = g.ext[c][d];
-        int x = q[d];
-        if (x < 0 || x >= e) {
-            const int n = g.n[d];
-            if (g.bc[d] == BC_PERIODIC) {
-                x = x < 0 ? x + e : x - e;
-            } else if (d == c) {
-                x = x < 0 ? -x : 2 * n - x;
-                sign = -sign;
-            } else {
-                const bool hi = x >= e;
-                x = hi ? 2 * n - 1 - x : -x - 1;
-                if (g.bc[d] == BC_WALL) {
-                    sign = -sign;
-                    if (c == 0 && d == 1 && hi) lid = 2.0;
-                }
-            }
-            q[d] = x;
-        }
-    }
-    VSrc r;
-    r.idx = vindex(g, c, q[0], q[1], q[2]);
-    r.sign = sign;
-    r.lid = lid;
-    return r;
-}
-
 // partial derivatives of smart_face(U, C, D), branch by branch
-__device__ __forceinline__ void smart_partials(double U, double C, double D, double& dU,
-                                               double& dC, double& dD) {
-    dU = dC = dD = 0.0;
-    const double dd = D - U;
-    const double cc = C - U;
-    if (dd == 0.0) {
-        dC = 1.0;
+template <typename T>
+__device__ __forceinline__ void smart_partials(T U, T C, T D, T& dU, T& dC, T& dD) {
+    dU = dC = dD = T(0);
+    const T dd = D - U;
+    const T cc = C - U;
+    if (dd == T(0)) {
+        dC = T(1);
         return;
     }
-    const double a = dd > 0.0 ? cc : -cc;
-    const double b = fabs(dd);
-    if (a < 0.0 || a > b) {
-        dC = 1.0;
-    } else if (6.0 * a <= b) {
-        dU = -2.0;
-        dC = 3.0;
-    } else if (6.0 * a <= 5.0 * b) {
-        dU = -0.125;
-        dC = 0.75;
-        dD = 0.375;
+    const T a = dd > T(0) ? cc : -cc;
+    const T b = fabs(dd);
+    if (a < T(0) || a > b) {
+        dC = T(1);
+    } else if (T(6) * a <= b) {
+        dU = T(-2);
+        dC = T(3);
+    } else if (T(6) * a <= T(5) * b) {
+        dU = T(-0.125);
+        dC = T(0.75);
+        dD = T(0.375);
     } else {
-        dD = 1.0;
+        dD = T(1);
     }
 }
 
 // flux uf * phi between b (lower) and f (higher): d/d uf and d/d (bb, b, f, ff)
-__device__ __forceinline__ void flux_partials(double uf, double bb, double b, double f,
-                                              double ff, double& duf, double (&d4)[4]) {
-    double dU, dC, dD;
-    d4[0] = d4[1] = d4[2] = d4[3] = 0.0;
-    if (uf < 0.0) {
+template <typename T>
+__device__ __forceinline__ void flux_partials(T uf, T bb, T b, T f, T ff, T& duf, T (&d4)[4]) {
+    T dU, dC, dD;
+    d4[0] = d4[1] = d4[2] = d4[3] = T(0);
+    if (uf < T(0)) {
         duf = smart_face(ff, f, b);
         smart_partials(ff, f, b, dU, dC, dD);
         d4[3] = uf * dU;
@@ -101,101 +66,222 @@ __device__ __forceinline__ void flux_partials(double uf, double bb, double b, do
     }
 }
 
-__device__ __forceinline__ void adj_scatter(double* const* out, int c, const VSrc& s, double w,
-                                            double& dlid) {
-    if (w != 0.0) atomicAdd(out[c] + s.idx, s.sign * w);
-    dlid += s.lid * w;
+// mu of component c at f (f[d] may lie outside the stored range along d):
+// wrapped along a periodic axis, zero outside the stored range and on
+// inactive (wall-normal boundary) faces.
+template <typename T>
+__device__ __forceinline__ T adj_mu_at(const Geo& g, int c, const T* __restrict__ mu, int d,
+                                       const int f[3]) {
+    int q[3] = {f[0], f[1], f[2]};
+    const int e = g.ext[c][d];
+    if (q[d] < 0 || q[d] >= e) {
+        if (g.bc[d] != BC_PERIODIC) return T(0);
+        q[d] = q[d] < 0 ? q[d] + e : q[d] - e;
+    }
+    const bool active = g.bc[c] == BC_PERIODIC || (q[c] > 0 && q[c] < g.n[c]);
+    return active ? mu[vindex(g, c, q[0], q[1], q[2])] : T(0);
 }
 
-// out += (dR/du)^T mu for every state of the batch; dlid[s] += (dR/du_lid)^T mu.
+// Is p an interface of component c along d that a forward flux is evaluated
+// at (between positions p and p+1)?  Periodic axes wrap p.  Normal
+// component: between the active faces 1..n-1 and their neighbours (0..n-1);
+// tangential: -1..n-1 (the edges on the walls included).
+__device__ __forceinline__ bool adj_iface(const Geo& g, int c, int d, int& p) {
+    if (g.bc[d] == BC_PERIODIC) {
+        const int e = g.ext[c][d];
+        p = p < 0 ? p + e : (p >= e ? p - e : p);
+        return true;
+    }
+    return d == c ? (p >= 0 && p <= g.n[d] - 1) : (p >= -1 && p <= g.n[d] - 1);
+}
+
+// Derivatives of the forward flux of component c through the interface
+// between f and f + e_d (f[d] = p): with respect to its transporting
+// velocity (duf) and to the four values at f - e_d .. f + 2 e_d (d4).
+template <typename T>
+__device__ __forceinline__ void adj_iface_flux(const Geo& g, int c, int d,
+                                               const T* const (&vel3)[3], const int f[3],
+                                               T& duf, T (&d4)[4]) {
+    T a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int r[3] = {f[0], f[1], f[2]};
+        r[d] += q - 1;
+        a[q] = vel(g, c, vel3[c], r[0], r[1], r[2]);
+    }
+    T uf;
+    if (d == c) {
+        uf = T(0.5) * (a[1] + a[2]);
+    } else {
+        int q0[3] = {f[0], f[1], f[2]};
+        int q1[3] = {f[0], f[1], f[2]};
+        q0[c] -= 1;
+        q0[d] += 1;
+        q1[d] += 1;
+        uf = T(0.5) * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
+                       vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
+    }
+    flux_partials(uf, a[0], a[1], a[2], a[3], duf, d4);
+}
+
+// (dR/du)^T mu at the stored value t of component c, and its share of
+// (dR/du_lid)^T mu (returned in dl).
+template <typename T>
+__device__ __forceinline__ T adj_gather(const Geo& g, int c, const int t[3],
+                                        const T* const (&vel3)[3], const T* const (&mu3)[3],
+                                        double& dl) {
+    T acc = T(0);
+    const T inv_re = g_inv_re<T>(g);
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        const T ih = g_ih<T>(g, d), ih2 = g_ih2<T>(g, d);
+        const int n = g.n[d], x = t[d];
+        // the positions whose value is t's: t itself and the ghosts that
+        // mirror it (sign, and the lid's coefficient in the ghost value)
+        int r[3];
+        T sg[3];
+        T lid[3];
+        int nim = 0;
+        r[nim] = x;
+        sg[nim] = T(1);
+        lid[nim++] = T(0);
+        if (g.bc[d] != BC_PERIODIC) {
+            if (d == c) {
+                if (x >= 1 && x <= 2) {
+                    r[nim] = -x;
+                    sg[nim] = T(-1);
+                    lid[nim++] = T(0);
+                }
+                if (x >= n - 2 && x <= n - 1 && x >= 0) {
+                    r[nim] = 2 * n - x;
+                    sg[nim] = T(-1);
+                    lid[nim++] = T(0);
+                }
+            } else {
+                const T s = g.bc[d] == BC_SLIP ? T(1) : T(-1);
+                if (x <= 1) {
+                    r[nim] = -x - 1;
+                    sg[nim] = s;
+                    lid[nim++] = T(0);
+                }
+                if (x >= n - 2) {
+                    r[nim] = 2 * n - 1 - x;
+                    sg[nim] = s;
+                    lid[nim++] = (g.bc[d] == BC_WALL && c == 0 && d == 1) ? T(2) : T(0);
+                }
+            }
+        }
+#pragma unroll 1
+        for (int m = 0; m < nim; ++m) {
+            int f[3] = {t[0], t[1], t[2]};
+            // diffusion Re^-1 (a3 - 2 a2 + a1) / h^2 of the faces r+1, r, r-1
+            T sd = T(0);
+#pragma unroll
+            for (int o = -1; o <= 1; ++o) {
+                f[d] = r[m] + o;
+                sd += (o == 0 ? T(-2) : T(1)) * adj_mu_at(g, c, mu3[c], d, f);
+            }
+            T tot = inv_re * ih2 * sd;
+            // convection -(F(p) - F(p-1)) / h: the interfaces p = r - k that
+            // read r in role k (k = -1: far upwind below, 0, 1, 2)
+#pragma unroll 1
+            for (int k = -1; k <= 2; ++k) {
+                int p = r[m] - k;
+                if (!adj_iface(g, c, d, p)) continue;
+                f[d] = p + 1;
+                const T hi = adj_mu_at(g, c, mu3[c], d, f);
+                f[d] = p;
+                const T lo = adj_mu_at(g, c, mu3[c], d, f);
+                const T nu = (hi - lo) * ih;
+                if (nu == T(0)) continue;
+                T duf, d4[4];
+                adj_iface_flux(g, c, d, vel3, f, duf, d4);
+                T w = d4[k + 1];
+                if (d == c && (k == 0 || k == 1)) w += T(0.5) * duf;
+                tot += nu * w;
+            }
+            acc += sg[m] * tot;
+            dl += double(lid[m]) * double(tot);
+        }
+    }
+    // t as the transporting velocity of the other components' fluxes along
+    // its own axis: the interfaces of faces t - e_c and t - e_c + e_c2
+#pragma unroll 1
+    for (int c2 = 0; c2 < 3; ++c2) {
+        if (c2 == c) continue;
+        const int d = c;
+        const T ih = g_ih<T>(g, d);
+#pragma unroll 1
+        for (int cand = 0; cand < 2; ++cand) {
+            int f[3] = {t[0], t[1], t[2]};
+            int p = f[d] - 1;
+            if (!adj_iface(g, c2, d, p)) continue;
+            f[d] = p;
+            if (cand) {
+                f[c2] += 1;
+                if (f[c2] >= g.ext[c2][c2]) {
+                    if (g.bc[c2] != BC_PERIODIC) continue;
+                    f[c2] -= g.ext[c2][c2];
+                }
+            }
+            int fh[3] = {f[0], f[1], f[2]};
+            fh[d] += 1;
+            const T nu = (adj_mu_at(g, c2, mu3[c2], d, fh) - adj_mu_at(g, c2, mu3[c2], d, f)) * ih;
+            if (nu == T(0)) continue;
+            T duf, d4[4];
+            adj_iface_flux(g, c2, d, vel3, f, duf, d4);
+            acc += T(0.5) * nu * duf;
+        }
+    }
+    return acc;
+}
+
+// out = (dR/du)^T mu for every state of the batch (blockIdx.y), every stored
+// value written once; per-CTA partial sums of (dR/du_lid)^T mu in
+// part_lid[state][cta] (summed in a fixed order by k_adj_sum).
+template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
-    k_adj_rhs(Geo g, const double* __restrict__ u, const double* __restrict__ v,
-              const double* __restrict__ w, const double* __restrict__ mu_u,
-              const double* __restrict__ mu_v, const double* __restrict__ mu_w, double* ou,
-              double* ov, double* ow, double* __restrict__ dlid) {
+    k_adj_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+              const T* __restrict__ mu_u, const T* __restrict__ mu_v, const T* __restrict__ mu_w,
+              T* __restrict__ ou, T* __restrict__ ov, T* __restrict__ ow,
+              double* __restrict__ part_lid) {
     const long long s = blockIdx.y;
-    const double* vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
-    const double* mu3[3] = {mu_u + s * g.cnt[0], mu_v + s * g.cnt[1], mu_w + s * g.cnt[2]};
-    double* out[3] = {ou + s * g.cnt[0], ov + s * g.cnt[1], ow + s * g.cnt[2]};
+    const T* const vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
+    const T* const mu3[3] = {mu_u + s * g.cnt[0], mu_v + s * g.cnt[1], mu_w + s * g.cnt[2]};
+    T* const out[3] = {ou + s * g.cnt[0], ov + s * g.cnt[1], ow + s * g.cnt[2]};
     int i, j, k0;
     tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
     const int k1 = min(k0 + g.tz, g.n[2] + 1);
     double dl = 0.0;
     for (int k = k0; k < k1; ++k) {
+#pragma unroll 1
         for (int c = 0; c < 3; ++c) {
             if (!(i < g.ext[c][0] && j < g.ext[c][1] && k < g.ext[c][2])) continue;
-            const int f[3] = {i, j, k};
-            const bool active = g.bc[c] == BC_PERIODIC || (f[c] > 0 && f[c] < g.n[c]);
-            if (!active) continue;
-            const double m = mu3[c][vindex(g, c, i, j, k)];
-            if (m == 0.0) continue;
-            for (int d = 0; d < 3; ++d) {
-                VSrc sa[5];
-                double a[5];
-                for (int q = 0; q < 5; ++q) {
-                    int p3[3] = {f[0], f[1], f[2]};
-                    p3[d] += q - 2;
-                    sa[q] = vel_src(g, c, p3[0], p3[1], p3[2]);
-                    a[q] = vel(g, c, vel3[c], p3[0], p3[1], p3[2]);
-                }
-                // diffusion Re^-1 (a3 - 2 a2 + a1) / h^2
-                const double wd = g.inv_re * g.ih2[d] * m;
-                adj_scatter(out, c, sa[3], wd, dl);
-                adj_scatter(out, c, sa[2], -2.0 * wd, dl);
-                adj_scatter(out, c, sa[1], wd, dl);
-                // convection -(Fp - Fm) / h
-                double up, um;
-                VSrc tp[2], tm[2];
-                int tc;
-                if (d == c) {
-                    tc = c;
-                    tp[0] = sa[2];
-                    tp[1] = sa[3];
-                    tm[0] = sa[1];
-                    tm[1] = sa[2];
-                    up = 0.5 * (a[2] + a[3]);
-                    um = 0.5 * (a[1] + a[2]);
-                } else {
-                    tc = d;
-                    int q0[3] = {f[0], f[1], f[2]};
-                    int q1[3] = {f[0], f[1], f[2]};
-                    q0[c] = f[c] - 1;
-                    q0[d] = f[d] + 1;
-                    q1[d] = f[d] + 1;
-                    tp[0] = vel_src(g, d, q0[0], q0[1], q0[2]);
-                    tp[1] = vel_src(g, d, q1[0], q1[1], q1[2]);
-                    up = 0.5 * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
-                                vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
-                    q0[d] = f[d];
-                    q1[d] = f[d];
-                    tm[0] = vel_src(g, d, q0[0], q0[1], q0[2]);
-                    tm[1] = vel_src(g, d, q1[0], q1[1], q1[2]);
-                    um = 0.5 * (vel(g, d, vel3[d], q0[0], q0[1], q0[2]) +
-                                vel(g, d, vel3[d], q1[0], q1[1], q1[2]));
-                }
-                double dup, dum, dp[4], dm[4];
-                flux_partials(up, a[1], a[2], a[3], a[4], dup, dp);
-                flux_partials(um, a[0], a[1], a[2], a[3], dum, dm);
-                const double wc = -m * g.ih[d];
-                for (int q = 0; q < 4; ++q) {
-                    adj_scatter(out, c, sa[q + 1], wc * dp[q], dl);
-                    adj_scatter(out, c, sa[q], -wc * dm[q], dl);
-                }
-                for (int q = 0; q < 2; ++q) {
-                    adj_scatter(out, tc, tp[q], 0.5 * wc * dup, dl);
-                    adj_scatter(out, tc, tm[q], -0.5 * wc * dum, dl);
-                }
-            }
+            const int t[3] = {i, j, k};
+            out[c][vindex(g, c, i, j, k)] = adj_gather(g, c, t, vel3, mu3, dl);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
-    if ((threadIdx.x & 31) == 0 && dl != 0.0) atomicAdd(dlid + s, dl);
+    double v1[1] = {dl};
+    write_partials<1>(v1, part_lid + s * g.fctas + blockIdx.x);
+}
+
+// out[s] (+)= sum of part[s][0..n-1] in order, one thread per state.
+__global__ void __launch_bounds__(32)
+    k_adj_sum(const double* __restrict__ part, int n, int batch, double* __restrict__ out,
+              int add) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= batch) return;
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q) acc += part[(long long)s * n + q];
+    out[s] = add ? out[s] + acc : acc;
 }
 
 // lambda = mu + dt * acc on active faces, 0 elsewhere; acc is zeroed for reuse.
+template <typename T>
 __global__ void __launch_bounds__(256)
-    k_adj_finish(Geo g, int c, long long n_total, const double* __restrict__ mu,
-                 double* __restrict__ acc, double* __restrict__ lam, double dt) {
+    k_adj_finish(Geo g, int c, long long n_total, const T* __restrict__ mu,
+                 T* __restrict__ acc, T* __restrict__ lam, double dt) {
+    const T tdt = T(dt);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n_total;
          q += (long long)gridDim.x * blockDim.x) {
         const long long local = q % g.cnt[c];
@@ -204,34 +290,38 @@ __global__ void __launch_bounds__(256)
         const int k = int(local / ((long long)g.ext[c][0] * g.ext[c][1]));
         const int f[3] = {i, j, k};
         const bool active = g.bc[c] == BC_PERIODIC || (f[c] > 0 && f[c] < g.n[c]);
-        lam[q] = active ? mu[q] + dt * acc[q] : 0.0;
-        acc[q] = 0.0;
+        lam[q] = active ? mu[q] + tdt * acc[q] : T(0);
+        acc[q] = T(0);
     }
 }
 
-// lambda = u * vol on active faces (0 elsewhere) and J[s] += 1/2 sum u^2 vol
-// (blockIdx.y = state; one atomic per warp).
-__global__ void __launch_bounds__(256)
-    k_adj_terminal(Geo g, int c, const double* __restrict__ u, double* __restrict__ lam,
-                   double* __restrict__ J, double vol) {
+// lambda = u * vol on active faces (0 elsewhere; skipped when lam is null)
+// and the per-CTA partial sums of J = 1/2 sum u^2 vol in part[state][cta]
+// (blockIdx.y = state; the CTAs of the three components at offsets
+// c * gridDim.x).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+    k_adj_terminal(Geo g, int c, const T* __restrict__ u, T* __restrict__ lam,
+                   double* __restrict__ part, double vol) {
     const long long s = blockIdx.y;
     const long long per = g.cnt[c];
-    const double* us = u + s * per;
-    double* ls = lam + s * per;
+    const T* us = u + s * per;
+    T* ls = lam ? lam + s * per : nullptr;
+    const T tvol = T(vol);
     double acc = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < per;
-         q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = blockIdx.x * (long long)NTHREADS + tid_flat(); q < per;
+         q += (long long)gridDim.x * NTHREADS) {
         const int i = int(q % g.ext[c][0]);
         const int j = int((q / g.ext[c][0]) % g.ext[c][1]);
         const int k = int(q / ((long long)g.ext[c][0] * g.ext[c][1]));
         const int f[3] = {i, j, k};
         const bool active = g.bc[c] == BC_PERIODIC || (f[c] > 0 && f[c] < g.n[c]);
-        const double x = active ? us[q] : 0.0;
-        ls[q] = x * vol;
-        acc += 0.5 * x * x * vol;
+        const T x = active ? us[q] : T(0);
+        if (ls) ls[q] = x * tvol;
+        acc += 0.5 * double(x) * double(x) * vol;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(J + s, acc);
+    double v1[1] = {acc};
+    write_partials<1>(v1, part + s * 3LL * gridDim.x + (long long)c * gridDim.x + blockIdx.x);
 }
 
 }  // namespace nsk

@@ -19,6 +19,7 @@
 #include "ns.h"
 #include "ns_adjoint.cuh"
 #include "ns_mg.cuh"
+#include "ns_persist.h"
 
 using namespace nsk;
 
@@ -151,6 +152,20 @@ struct ns_grid {
     double chain_key_dt = 0.0;
     LoopCount chain_seen_lc{};
     SliceCtl chain_seen_ctl{};
+    // persistent pressure solves (batch <= persist_max_batch, multigrid, not
+    // while capturing): one cooperative launch per solve, checked on the host
+    // only at the end of the call that issued them (or of the coarse chain)
+    bool persist = false;
+    int persist_grid = 0;            // CTAs of a persistent launch (one per SM)
+    int persist_max_batch = 1;
+    unsigned* pbar = nullptr;        // grid barrier words
+    int* perr = nullptr;             // a barrier wait gave up
+    long long spin_ns = 2000000000LL;
+    int persist_pending = 0;         // solves issued since the last check
+    int persist_batch = 0;
+    bool defer = false;              // the caller checks the pending solves itself
+    SliceCtl* psnap_ctl = nullptr;   // control blocks before the pending solves
+    LoopCount* psnap_lc = nullptr;
     // the chain of each chunk of the chunked schedule as a graph of its own
     std::vector<cudaGraph_t> chunk_graph;
     std::vector<cudaGraphExec_t> chunk_exec;
@@ -801,6 +816,123 @@ ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
 }
 
 
+// ---------------------------------------------------------------------------
+// persistent solves: the whole solve in one cooperative launch (ns_persist.cu)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+PSolve<T> make_psolve(const ns_grid* g, int batch, const double* p_in) {
+    PSolve<T> a{};
+    a.plan = g->plan;
+    a.mb = mgbuf<T>(g);
+    if (g->fp32) a.ff = ffbuf(g);
+    a.ctl = g->ctl;
+    a.part_div = g->part_div;
+    a.part_mg = g->part_mg;
+    a.b = g->b;
+    a.p_in = p_in;
+    a.p_prev = g->p_prev;
+    a.loopc = g->loopc;
+    a.bar = g->pbar;
+    a.err = g->perr;
+    a.spin_ns = g->spin_ns;
+    a.otol2 = g->d.refine_rtol * g->d.refine_rtol;
+    a.itol2 = g->inner_rtol * g->inner_rtol;
+    a.tol2 = g->d.poisson_rtol * g->d.poisson_rtol;
+    a.maxit = g->maxit;
+    a.max_outer = g->max_outer;
+    a.n_fluid = g->geo.n_fluid;
+    a.batch = batch;
+    // the graph loops' caps: one body per inner iteration (+2), times the
+    // outer corrections (+2) for FP32+refine
+    a.cap = g->fp32 ? (unsigned)((g->maxit + 2) * (g->max_outer + 2)) : (unsigned)(g->maxit + 2);
+    return a;
+}
+
+// Reads back what the pending persistent solves did: adds their solves,
+// iterations and refinement steps to ns_stats and reports a solve that
+// failed (sticky bits, then cleared) or a barrier wait that gave up.
+ns_status persist_check(ns_grid* g) {
+    if (g->persist_pending == 0) return NS_OK;
+    const int B = g->persist_batch;
+    g->persist_pending = 0;
+    NS_TRY(sync_stream(g));
+    std::vector<SliceCtl> now(B), before(B);
+    int err = 0;
+    NS_CUDA(cudaMemcpy(now.data(), g->ctl, sizeof(SliceCtl) * B, cudaMemcpyDeviceToHost));
+    NS_CUDA(cudaMemcpy(before.data(), g->psnap_ctl, sizeof(SliceCtl) * B, cudaMemcpyDeviceToHost));
+    NS_CUDA(cudaMemcpy(&err, g->perr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        // the launch ended early: reset the barrier, the flag and the
+        // per-state arrival counters for the next one
+        NS_CUDA(cudaMemset(g->perr, 0, sizeof(int)));
+        NS_CUDA(cudaMemset(g->pbar, 0, PERSIST_BAR_WORDS * sizeof(unsigned)));
+        NS_CUDA(cudaMemset(g->counter, 0, sizeof(unsigned) * g->cap));
+        return fail(NS_ERR_TIMEOUT, "persistent pressure solve: a grid-wide barrier wait gave up "
+                                    "after " + std::to_string(g->spin_ns) + " ns");
+    }
+    ns_status result = NS_OK;
+    int mx = 0;
+    double mr = 0.0;
+    for (int s = 0; s < B; ++s) {
+        const SliceCtl& c = now[s];
+        g->stats.solves += c.total_solves - before[s].total_solves;
+        g->stats.krylov_iters += c.total_iters - before[s].total_iters;
+        g->stats.refine_steps += c.total_outer - before[s].total_outer;
+        mx = std::max(mx, c.it_cur);
+        const double rel = g->fp32 ? (c.o_bb > 0 ? std::sqrt(c.o_rr / c.o_bb) : std::sqrt(c.o_rr))
+                                   : (c.bb > 0 ? std::sqrt(c.rr / c.bb) : std::sqrt(c.rr));
+        mr = std::max(mr, rel);
+        if (c.fail && result == NS_OK)
+            result = fail(c.fail & 2 ? NS_ERR_NONFINITE : NS_ERR_NOT_CONVERGED,
+                          std::string("pressure solve of state ") + std::to_string(s) +
+                              (c.fail & 2 ? " met a non-finite residual"
+                                          : " did not reach its tolerance"));
+        if (c.fail) {
+            const int zero = 0;
+            NS_CUDA(cudaMemcpy(&g->ctl[s].fail, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        }
+    }
+    g->stats.last_max_iters = mx;
+    g->stats.last_rel_residual = mr;
+    return result;
+}
+
+ns_status solve_pressure_persist(ns_grid* g, int batch, const double* p_in) {
+    if (g->persist_pending && batch != g->persist_batch) NS_TRY(persist_check(g));
+    if (g->persist_pending == 0) {
+        // the totals before the solves, for persist_check
+        NS_CUDA(cudaMemcpyAsync(g->psnap_ctl, g->ctl, sizeof(SliceCtl) * batch,
+                                cudaMemcpyDeviceToDevice, g->stream));
+        g->persist_batch = batch;
+    }
+    g->persist_pending += 1;
+    const long long units = g->plan.lev[0].cells * batch;
+    cudaError_t e = cudaSuccess;
+    if (g->fp32) {
+        const PSolve<float> a = make_psolve<float>(g, batch, p_in);
+        NS_LAUNCH(g, NS_K_PERSIST, units,
+                  e = persist_solve_launch(a, g->persist_grid, g->mg_smem, g->stream));
+    } else {
+        const PSolve<double> a = make_psolve<double>(g, batch, p_in);
+        NS_LAUNCH(g, NS_K_PERSIST, units,
+                  e = persist_solve_launch(a, g->persist_grid, g->mg_smem, g->stream));
+    }
+    if (e != cudaSuccess) {
+        g->persist_pending -= 1;
+        return fail(NS_ERR_CUDA, std::string("persistent pressure solve launch: ") +
+                                     cudaGetErrorString(e));
+    }
+    return NS_OK;
+}
+
+// Checks the persistent solves a top-level call issued (unless its caller
+// checks them later).
+ns_status persist_settle(ns_grid* g) {
+    if (g->defer || g->capturing) return NS_OK;
+    return persist_check(g);
+}
+
 ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
     const Lev& L0 = g->plan.lev[0];
     const dim3 grid(L0.ctas, batch), blk = block_dim();
@@ -846,6 +978,7 @@ ns_status solve_pressure_mg_graph(ns_grid* g, int batch, const double* p_in) {
 
 ns_status solve_pressure_mg(ns_grid* g, int batch, const double* p_in) {
     if (g->capturing) return solve_pressure_mg_graph(g, batch, p_in);
+    if (g->persist && batch <= g->persist_max_batch) return solve_pressure_persist(g, batch, p_in);
     const Lev& L0 = g->plan.lev[0];
     const dim3 grid(L0.ctas, batch), blk = block_dim();
     int max_iters = 0;
@@ -1041,7 +1174,7 @@ ns_status step_impl(ns_grid* g, const ns_state& io, double dt, int nsteps) {
         NS_CUDA(cudaGetLastError());
         if (!g->capturing) g->stats.steps += B;
     }
-    return NS_OK;
+    return persist_settle(g);
 }
 
 ns_status step_any(ns_grid* g, const ns_state& io, double dt, int nsteps, const char* what) {
@@ -1083,7 +1216,7 @@ ns_status project_impl(ns_grid* g, const ns_state& io) {
                   k_correct<T, false><<<gface, block_dim(), 0, g->stream>>>(
                       G, g->ctl, u, v, w, u, v, w, x0, x1, nullptr, 1.0));
     NS_CUDA(cudaGetLastError());
-    return NS_OK;
+    return persist_settle(g);
 }
 
 template <typename T>
@@ -1499,6 +1632,12 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
         // iteration 0: the serial coarse sweep y_{n+1} = G(y_n)
         NS_TRY(ensure_chain(g));
         NS_TRY(on_chain(g, [&](ns_grid* h) -> ns_status {
+            // persistent solves: checked once, after the whole sweep
+            h->defer = true;
+            struct Undefer {
+                ns_grid* h;
+                ~Undefer() { h->defer = false; }
+            } undefer{h};
             NS_TRY(copy_states<T>(h, ys, u0s, 0, 0, 1));
             for (int n = 0; n < N; ++n) {
                 NS_TRY(copy_states<T>(h, ys, ys, n + 1, n, 1));
@@ -1509,7 +1648,8 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
                 NS_TRY(step_impl<T>(h, one, dtc, M));
                 NS_TRY(copy_states<T>(h, g->pr_gold, ys, n, n + 1, 1));
             }
-            return NS_OK;
+            h->defer = false;
+            return persist_check(h);
         }));
     }
     g->pr_valid = false;
@@ -1541,6 +1681,17 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
             NS_TRY(on_chain(g, [&](ns_grid* h) -> ns_status {
                 if (!h->mg) {
                     NS_TRY(chain(h));
+                } else if (h->persist) {
+                    // every coarse solve is one persistent launch: the chain
+                    // is issued directly and its solves checked at its end
+                    h->defer = true;
+                    const ns_status sc = chain(h);
+                    h->defer = false;
+                    if (sc != NS_OK) {
+                        h->persist_pending = 0;
+                        return sc;
+                    }
+                    NS_TRY(persist_check(h));
                 } else {
                     // the whole chain is one graph launch: its solver loops
                     // run on the device, with no host round trip per solve
@@ -1577,7 +1728,11 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
 // Reverse mode through nsteps fine steps with checkpoints of (u, p) every
 // ckpt_every steps: forward once storing checkpoints, then per segment (last
 // first) recompute its states from the checkpoint and run the adjoint steps
-// back through it.  All buffers are allocated for the call and freed after.
+// back through it.  T is the grid's velocity type: the FP32+refine grid runs
+// the forward steps, the adjoint projections (its float-float refined solve)
+// and the adjoint stencils in FP32, with J and dJ/du_lid summed in FP64.  All
+// buffers are allocated for the call and freed after.
+template <typename T>
 ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, double* J,
                        const ns_state& grad, double* dlid_out) {
     const Geo& G = g->geo;
@@ -1587,102 +1742,105 @@ ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, 
     const size_t vel_elems = nv[0] + nv[1] + nv[2];
     const int nck = N > 0 ? (N + C - 1) / C : 0;
     const int seg_len = std::min(C, std::max(N, 1));
+    const int tblocks = (int)std::min<long long>((std::max(G.cnt[0], std::max(G.cnt[1], G.cnt[2])) +
+                                                  NTHREADS - 1) / NTHREADS, 512);
     std::vector<void*> mine;
-    auto alloc = [&](size_t bytes) -> double* {
+    auto alloc = [&](size_t bytes) -> void* {
         void* p = nullptr;
         if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
         mine.push_back(p);
-        return (double*)p;
+        return p;
     };
     auto release = [&]() {
         cudaStreamSynchronize(g->stream);
         for (void* p : mine) cudaFree(p);
         mine.clear();
     };
-    double* cur = alloc(sizeof(double) * (vel_elems + np));
-    double* ck = alloc(sizeof(double) * (vel_elems + np) * std::max(nck, 1));
-    double* seg = alloc(sizeof(double) * vel_elems * seg_len);
-    double* lam = alloc(sizeof(double) * vel_elems);
-    double* mu = alloc(sizeof(double) * vel_elems);
-    double* acc = alloc(sizeof(double) * vel_elems);
-    double* pmu = alloc(sizeof(double) * np);
-    double* dJ = alloc(sizeof(double) * 2 * B);
-    if (mine.size() != 8) {
+    T* cur = (T*)alloc(sizeof(T) * vel_elems);
+    double* cur_p = (double*)alloc(sizeof(double) * np);
+    T* ck = (T*)alloc(sizeof(T) * vel_elems * std::max(nck, 1));
+    double* ck_p = (double*)alloc(sizeof(double) * np * std::max(nck, 1));
+    T* seg = (T*)alloc(sizeof(T) * vel_elems * seg_len);
+    T* lam = (T*)alloc(sizeof(T) * vel_elems);
+    T* mu = (T*)alloc(sizeof(T) * vel_elems);
+    T* acc = (T*)alloc(sizeof(T) * vel_elems);
+    double* pmu = (double*)alloc(sizeof(double) * np);
+    double* dJ = (double*)alloc(sizeof(double) * 2 * B);
+    double* part_J = (double*)alloc(sizeof(double) * 3 * tblocks * B);
+    double* part_lid = (double*)alloc(sizeof(double) * G.fctas * B);
+    if (mine.size() != 12) {
         release();
         return fail(NS_ERR_OOM, "ns_adjoint: workspace allocation failed");
     }
-    auto state_at = [&](double* base, int batch) {
-        ns_state st{base, base + nv[0], base + nv[0] + nv[1], base + vel_elems, batch};
-        return st;
-    };
-    auto vel_at = [&](double* base) {
-        ns_state st{base, base + nv[0], base + nv[0] + nv[1], pmu, B};
+    auto vel_state = [&](T* base, double* p) {
+        ns_state st{base, base + nv[0], base + nv[0] + nv[1], p, B};
         return st;
     };
     const void* src0[4] = {u0.u, u0.v, u0.w, u0.p};
-    ns_state cs = state_at(cur, B);
+    ns_state cs = vel_state(cur, cur_p);
     void* dst0[4] = {cs.u, cs.v, cs.w, cs.p};
-    ns_status st = copy_states<double>(g, dst0, src0, 0, 0, B);
-    NS_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * vel_elems, g->stream));
+    ns_status st = copy_states<T>(g, dst0, src0, 0, 0, B);
+    NS_CUDA(cudaMemsetAsync(acc, 0, sizeof(T) * vel_elems, g->stream));
     NS_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double) * 2 * B, g->stream));
-    const size_t state_bytes = sizeof(double) * (vel_elems + np);
+    auto copy = [&](void* dst, const void* src, size_t bytes, const char* what) {
+        if (st == NS_OK && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice,
+                                           g->stream) != cudaSuccess)
+            st = fail(NS_ERR_CUDA, std::string("ns_adjoint: ") + what + " copy failed");
+    };
     // forward with checkpoints
     for (int n = 0; n < N && st == NS_OK; ++n) {
-        if (n % C == 0)
-            if (cudaMemcpyAsync((char*)ck + (size_t)(n / C) * state_bytes, cur, state_bytes,
-                                cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
-                st = fail(NS_ERR_CUDA, "ns_adjoint: checkpoint copy failed");
-        if (st == NS_OK) st = step_impl<double>(g, cs, dt, 1);
+        if (n % C == 0) {
+            copy(ck + (size_t)(n / C) * vel_elems, cur, sizeof(T) * vel_elems, "checkpoint");
+            copy(ck_p + (size_t)(n / C) * np, cur_p, sizeof(double) * np, "checkpoint");
+        }
+        if (st == NS_OK) st = step_impl<T>(g, cs, dt, 1);
     }
-    // terminal adjoint and J
+    // terminal adjoint and J (per-CTA partials, summed in a fixed order)
     const double vol = G.h[0] * G.h[1] * G.h[2];
     if (st == NS_OK) {
         for (int c = 0; c < 3; ++c) {
             const size_t off = c == 0 ? 0 : (c == 1 ? nv[0] : nv[0] + nv[1]);
-            const int blocks = (int)std::min<long long>((G.cnt[c] + 255) / 256, 1024);
             NS_LAUNCH(g, NS_K_ADJOINT, 0,
-                      k_adj_terminal<<<dim3(blocks, B), 256, 0, g->stream>>>(
-                          G, c, cur + off, lam + off, dJ, vol));
+                      k_adj_terminal<T><<<dim3(tblocks, B), block_dim(), 0, g->stream>>>(
+                          G, c, cur + off, lam + off, part_J, vol));
         }
+        NS_LAUNCH(g, NS_K_ADJOINT, 0,
+                  k_adj_sum<<<(B + 31) / 32, 32, 0, g->stream>>>(part_J, 3 * tblocks, B, dJ, 0));
         if (cudaGetLastError() != cudaSuccess) st = fail(NS_ERR_CUDA, "ns_adjoint: launch failed");
     }
     // reverse, segment by segment
     for (int sg = nck - 1; sg >= 0 && st == NS_OK; --sg) {
         const int n0 = sg * C, n1 = std::min(N, n0 + C);
-        if (cudaMemcpyAsync(cur, (char*)ck + (size_t)sg * state_bytes, state_bytes,
-                            cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
-            st = fail(NS_ERR_CUDA, "ns_adjoint: checkpoint copy failed");
+        copy(cur, ck + (size_t)sg * vel_elems, sizeof(T) * vel_elems, "checkpoint");
+        copy(cur_p, ck_p + (size_t)sg * np, sizeof(double) * np, "checkpoint");
         for (int n = n0; n < n1 && st == NS_OK; ++n) {
-            if (cudaMemcpyAsync(seg + (size_t)(n - n0) * vel_elems, cur,
-                                sizeof(double) * vel_elems, cudaMemcpyDeviceToDevice,
-                                g->stream) != cudaSuccess)
-                st = fail(NS_ERR_CUDA, "ns_adjoint: segment copy failed");
-            if (st == NS_OK && n + 1 < n1) st = step_impl<double>(g, cs, dt, 1);
+            copy(seg + (size_t)(n - n0) * vel_elems, cur, sizeof(T) * vel_elems, "segment");
+            if (st == NS_OK && n + 1 < n1) st = step_impl<T>(g, cs, dt, 1);
         }
         for (int n = n1 - 1; n >= n0 && st == NS_OK; --n) {
             // mu = P lambda
-            if (cudaMemcpyAsync(mu, lam, sizeof(double) * vel_elems, cudaMemcpyDeviceToDevice,
-                                g->stream) != cudaSuccess) {
-                st = fail(NS_ERR_CUDA, "ns_adjoint: copy failed");
-                break;
-            }
-            st = project_impl<double>(g, vel_at(mu));
+            copy(mu, lam, sizeof(T) * vel_elems, "adjoint");
+            if (st != NS_OK) break;
+            st = project_impl<T>(g, vel_state(mu, pmu));
             if (st != NS_OK) break;
             // acc = (dR/du)^T mu at u^n, dJ/du_lid += dt (dR/du_lid)^T mu
-            double* un = seg + (size_t)(n - n0) * vel_elems;
+            T* un = seg + (size_t)(n - n0) * vel_elems;
             NS_LAUNCH(g, NS_K_ADJOINT, 0,
-                      k_adj_rhs<<<dim3(G.fctas, B), block_dim(), 0, g->stream>>>(
+                      k_adj_rhs<T><<<dim3(G.fctas, B), block_dim(), 0, g->stream>>>(
                           G, un, un + nv[0], un + nv[0] + nv[1], mu, mu + nv[0],
-                          mu + nv[0] + nv[1], acc, acc + nv[0], acc + nv[0] + nv[1], dJ + B));
+                          mu + nv[0] + nv[1], acc, acc + nv[0], acc + nv[0] + nv[1], part_lid));
+            NS_LAUNCH(g, NS_K_ADJOINT, 0,
+                      k_adj_sum<<<(B + 31) / 32, 32, 0, g->stream>>>(part_lid, G.fctas, B,
+                                                                    dJ + B, 1));
             // lambda = mu + dt acc (active faces); acc <- 0
             for (int c = 0; c < 3; ++c) {
                 const size_t off = c == 0 ? 0 : (c == 1 ? nv[0] : nv[0] + nv[1]);
                 const int blocks = (int)std::min<long long>(((long long)nv[c] + 255) / 256, 4096);
                 NS_LAUNCH(g, NS_K_ADJOINT, 0,
-                          k_adj_finish<<<blocks, 256, 0, g->stream>>>(
+                          k_adj_finish<T><<<blocks, 256, 0, g->stream>>>(
                               G, c, (long long)nv[c], mu + off, acc + off, lam + off, dt));
             }
             if (cudaGetLastError() != cudaSuccess)
@@ -1693,9 +1851,7 @@ ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, 
         void* gd[3] = {grad.u, grad.v, grad.w};
         for (int c = 0; c < 3 && st == NS_OK; ++c) {
             const size_t off = c == 0 ? 0 : (c == 1 ? nv[0] : nv[0] + nv[1]);
-            if (cudaMemcpyAsync(gd[c], lam + off, sizeof(double) * nv[c],
-                                cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
-                st = fail(NS_ERR_CUDA, "ns_adjoint: gradient copy failed");
+            copy(gd[c], lam + off, sizeof(T) * nv[c], "gradient");
         }
         std::vector<double> h(2 * B);
         if (st == NS_OK &&
@@ -1831,6 +1987,39 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         if (g->fp32)
             for (int q = 0; q < 8; ++q) A((void**)&g->ffb[q], ncell * sizeof(float) * B);
         A((void**)&g->part_mg, nparts * 6 * sizeof(double));
+    }
+    if (g->mg && st == NS_OK) {
+        // persistent solves for small batches, on request (NS_PERSISTENT=1 in
+        // the environment): one cooperative launch of one CTA per SM per
+        // solve; NS_PERSIST_SPIN_NS bounds each barrier wait.  Measured on the
+        // 64^3 coarse chain they are slower than the graph of launched
+        // kernels (each phase costs a grid barrier on top of the same
+        // memory-latency chain), so they are off by default.
+        const char* env = std::getenv("NS_PERSISTENT");
+        const bool want = env && std::atoi(env) != 0;
+        int coop = 0, sms = 0;
+        if (want &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device) == cudaSuccess &&
+            coop &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) == cudaSuccess &&
+            persist_prepare() == cudaSuccess &&
+            persist_blocks_per_sm(g->fp32, g->mg_smem) >= 1) {
+            g->persist = true;
+            g->persist_grid = sms;
+        }
+        cudaGetLastError();
+        const char* spin = std::getenv("NS_PERSIST_SPIN_NS");
+        if (spin) g->spin_ns = std::max(1LL, std::atoll(spin));
+        if (g->persist) {
+            A((void**)&g->pbar, PERSIST_BAR_WORDS * sizeof(unsigned));
+            A((void**)&g->perr, sizeof(int));
+            A((void**)&g->psnap_ctl, sizeof(SliceCtl) * B);
+            if (st == NS_OK && (cudaMemsetAsync(g->pbar, 0, PERSIST_BAR_WORDS * sizeof(unsigned),
+                                                g->stream) !=
+                                    cudaSuccess ||
+                                cudaMemsetAsync(g->perr, 0, sizeof(int), g->stream) != cudaSuccess))
+                st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
+        }
     }
     A((void**)&g->d_defect, sizeof(unsigned long long));
     if (st == NS_OK) {
@@ -1997,6 +2186,7 @@ ns_status ns_poisson_solve(ns_grid* grid, const double* b, double* p, int batch,
                       (double*)grid->fs[2], (double*)grid->fs[0], (double*)grid->fs[1],
                       (double*)grid->fs[2], x0, x1, p, 0.0));
     NS_CUDA(cudaGetLastError());
+    NS_TRY(persist_settle(grid));
     NS_TRY(sync_stream(grid));
     if (iters) *iters = grid->stats.last_max_iters;
     return NS_OK;
@@ -2038,7 +2228,6 @@ ns_status ns_adjoint(ns_grid* grid, ns_state u0, double dt, int nsteps, int ckpt
     if (!grid) return fail(NS_ERR_ARG, "ns_adjoint: null grid");
     const DeviceGuard dg(grid->device);
     NS_TRY(check_state(grid, u0, "ns_adjoint(u0)"));
-    if (grid->fp32) return fail(NS_ERR_ARG, "ns_adjoint: needs an NS_FP64 grid");
     if (grid->geo.solid) return fail(NS_ERR_ARG, "ns_adjoint: grids with solid cells are not "
                                                  "supported");
     if (!grad_u0.u || !grad_u0.v || !grad_u0.w || grad_u0.batch != u0.batch)
@@ -2046,7 +2235,52 @@ ns_status ns_adjoint(ns_grid* grid, ns_state u0, double dt, int nsteps, int ckpt
     if (!J || !dJ_dulid) return fail(NS_ERR_ARG, "ns_adjoint: null J or dJ_dulid");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || ckpt_every < 1)
         return fail(NS_ERR_ARG, "ns_adjoint: need dt > 0, nsteps >= 0, ckpt_every >= 1");
-    return adjoint_impl(grid, u0, dt, nsteps, ckpt_every, J, grad_u0, dJ_dulid);
+    return grid->fp32 ? adjoint_impl<float>(grid, u0, dt, nsteps, ckpt_every, J, grad_u0, dJ_dulid)
+                      : adjoint_impl<double>(grid, u0, dt, nsteps, ckpt_every, J, grad_u0,
+                                             dJ_dulid);
+}
+
+ns_status ns_kinetic_energy(ns_grid* grid, ns_state state, double* J) {
+    g_last_error.clear();
+    if (!grid) return fail(NS_ERR_ARG, "ns_kinetic_energy: null grid");
+    const DeviceGuard dg(grid->device);
+    if (!state.u || !state.v || !state.w || state.batch < 1)
+        return fail(NS_ERR_ARG, "ns_kinetic_energy: null velocity or batch < 1");
+    if (!J) return fail(NS_ERR_ARG, "ns_kinetic_energy: null J");
+    const Geo& G = grid->geo;
+    const int B = state.batch;
+    const int tblocks = (int)std::min<long long>(
+        (std::max(G.cnt[0], std::max(G.cnt[1], G.cnt[2])) + NTHREADS - 1) / NTHREADS, 512);
+    double* part = nullptr;
+    double* dJ = nullptr;
+    if (cudaMalloc(&part, sizeof(double) * 3 * tblocks * B) != cudaSuccess ||
+        cudaMalloc(&dJ, sizeof(double) * B) != cudaSuccess) {
+        cudaGetLastError();
+        if (part) cudaFree(part);
+        return fail(NS_ERR_OOM, "ns_kinetic_energy: workspace allocation failed");
+    }
+    const double vol = G.h[0] * G.h[1] * G.h[2];
+    const void* vel[3] = {state.u, state.v, state.w};
+    for (int c = 0; c < 3; ++c) {
+        if (grid->fp32)
+            k_adj_terminal<float><<<dim3(tblocks, B), block_dim(), 0, grid->stream>>>(
+                G, c, (const float*)vel[c], nullptr, part, vol);
+        else
+            k_adj_terminal<double><<<dim3(tblocks, B), block_dim(), 0, grid->stream>>>(
+                G, c, (const double*)vel[c], nullptr, part, vol);
+        grid->stats.launches += 1;
+    }
+    k_adj_sum<<<(B + 31) / 32, 32, 0, grid->stream>>>(part, 3 * tblocks, B, dJ, 0);
+    grid->stats.launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(J, dJ, sizeof(double) * B, cudaMemcpyDeviceToHost, grid->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(grid->stream);
+    cudaFree(part);
+    cudaFree(dJ);
+    if (e != cudaSuccess)
+        return fail(NS_ERR_CUDA, std::string("ns_kinetic_energy: ") + cudaGetErrorString(e));
+    return NS_OK;
 }
 
 ns_status ns_set_lid_speed(ns_grid* grid, double u_lid) {
@@ -2149,9 +2383,17 @@ ns_status ns_step_fine_many(ns_grid* const* grids, const ns_state* states, const
     std::vector<std::string> msg(n);
     if (st == NS_OK) {
         std::vector<std::thread> threads;
+        // the grids' kernels overlap here: no persistent (cooperative) solves,
+        // whose CTAs must all be resident at once
+        std::vector<char> persist_saved(n);
         for (int i = 0; i < n; ++i) {
             saved[i] = grids[i]->stream;
             grids[i]->stream = own[i];
+            persist_saved[i] = grids[i]->persist;
+            const DeviceGuard dg(grids[i]->device);
+            const ns_status sp = persist_check(grids[i]);
+            if (sp != NS_OK && st == NS_OK) st = sp;
+            grids[i]->persist = false;
         }
         for (int i = 0; i < n; ++i)
             threads.emplace_back([&, i]() {
@@ -2162,6 +2404,7 @@ ns_status ns_step_fine_many(ns_grid* const* grids, const ns_state* states, const
         for (auto& t : threads) t.join();
         for (int i = 0; i < n; ++i) {
             const DeviceGuard dg(grids[i]->device);
+            grids[i]->persist = persist_saved[i] != 0;
             grids[i]->stream = saved[i];
             if (cudaEventRecord(ev[2 * i + 1], own[i]) != cudaSuccess ||
                 cudaStreamWaitEvent(saved[i], ev[2 * i + 1], 0) != cudaSuccess)
@@ -2248,10 +2491,16 @@ ns_status ns_graph_create(ns_grid* const* grids, const ns_state* states, const d
             return bail(fail(NS_ERR_CUDA, "ns_graph_create: event creation failed"));
         gr->events.push_back(e);
     }
-    // the branches must see the states as the caller's streams left them
-    for (int i = 0; i < n; ++i)
+    // the branches must see the states as the caller's streams left them; a
+    // grid in a graph no longer takes persistent solves (the graph's
+    // accounting reads the same control-block totals)
+    for (int i = 0; i < n; ++i) {
+        const ns_status sp = persist_check(grids[i]);
+        if (sp != NS_OK) return bail(sp);
+        grids[i]->persist = false;
         if (cudaStreamSynchronize(grids[i]->stream) != cudaSuccess)
             return bail(fail(NS_ERR_CUDA, "ns_graph_create: stream synchronisation failed"));
+    }
     for (int i = 0; i < n; ++i) {
         ns_grid* g = grids[i];
         cudaGraph_t graph;

@@ -21,6 +21,26 @@ constexpr int TX = 32;
 constexpr int TY = 4;
 constexpr int NTHREADS = TX * TY;
 constexpr int NWARPS = NTHREADS / 32;
+// Groups of NTHREADS threads (threadIdx.z) that one CTA runs as separate
+// cell-kernel CTAs: 1 for the launched kernels; the persistent solver's
+// translation unit defines NS_PERSISTENT_GROUPS (1024-thread CTAs).
+#ifndef NS_PERSISTENT_GROUPS
+#define NS_PERSISTENT_GROUPS 1
+#endif
+constexpr int NSUB = NS_PERSISTENT_GROUPS;
+
+// The calling thread's group (0 in the launched kernels).
+__device__ __forceinline__ int sub_id() { return NSUB > 1 ? (int)threadIdx.z : 0; }
+
+// Barrier over the NTHREADS threads of a (sub-)CTA: __syncthreads in the
+// launched kernels, one named barrier per group in the persistent solver.
+__device__ __forceinline__ void sub_sync() {
+#if defined(__CUDA_ARCH__) && NS_PERSISTENT_GROUPS > 1
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.z), "r"(NTHREADS) : "memory");
+#else
+    __syncthreads();
+#endif
+}
 
 struct Geo {
     int n[3];            // cells per axis
@@ -230,7 +250,8 @@ __device__ __forceinline__ bool face_in_solid_dev(const Geo& g, int c, const int
 // Sum of NV per-thread values over the CTA; the result is valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
-    __shared__ double sm[NV][NWARPS];
+    __shared__ double sm_all[NSUB][NV][NWARPS];
+    double(&sm)[NV][NWARPS] = sm_all[sub_id()];
     const int t = tid_flat();
     const int lane = t & 31, warp = t >> 5;
 #pragma unroll
@@ -238,12 +259,12 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     }
-    __syncthreads();
+    sub_sync();
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) sm[q][warp] = v[q];
     }
-    __syncthreads();
+    sub_sync();
     if (warp == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -261,7 +282,8 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 template <int NV>
 __device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ctas,
                                                 double (&out)[NV]) {
-    __shared__ double bc[NV];
+    __shared__ double bc_all[NSUB][NV];
+    double(&bc)[NV] = bc_all[sub_id()];
     // each thread sums the CTAs t, t + NTHREADS, ... in that order, loading a
     // batch of them before adding so that the batch's reads overlap
     constexpr int UB = NV <= 3 ? 4 : 2;
@@ -289,10 +311,10 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
 #pragma unroll
         for (int q = 0; q < NV; ++q) bc[q] = v[q];
     }
-    __syncthreads();
+    sub_sync();
 #pragma unroll
     for (int q = 0; q < NV; ++q) out[q] = bc[q];
-    __syncthreads();
+    sub_sync();
 }
 
 template <int NV>

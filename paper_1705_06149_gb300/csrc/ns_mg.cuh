@@ -328,17 +328,19 @@ __device__ __forceinline__ void lev_origin(const Lev& L, int cta, int& i, int& j
 // Arrival at the per-state counter after this CTA's partials are written.
 // Returns true in the last CTA of the state, which may then read all partials.
 __device__ __forceinline__ bool arrive_last(unsigned int* counter, int ctas) {
-    __shared__ int last;
+    __shared__ int last_all[NSUB];
+    int& last = last_all[sub_id()];
     __threadfence();
-    __syncthreads();
+    sub_sync();
     if (tid_flat() == 0) {
         const unsigned int prev = atomicAdd(counter, 1u);
         last = prev + 1 == (unsigned int)ctas;
         if (last) *counter = 0u;  // every other CTA has arrived: reset for the next phase
     }
-    __syncthreads();
-    if (last) __threadfence();
-    return last != 0;
+    sub_sync();
+    const bool is_last = last != 0;
+    if (is_last) __threadfence();
+    return is_last;
 }
 
 // Fixed-order sum of [ctas][NV] partials, read through L2, in the last CTA.
@@ -378,7 +380,8 @@ __device__ __forceinline__ void sum_partials_l2(const double* part, int ctas, do
 // kernels this keeps the FP64 pipe out of the per-thread work.
 template <typename A, int NV>
 __device__ __forceinline__ void block_sum_mixed(A (&v)[NV], double (&out)[NV]) {
-    __shared__ double sm[NV][NWARPS];
+    __shared__ double sm_all[NSUB][NV][NWARPS];
+    double(&sm)[NV][NWARPS] = sm_all[sub_id()];
     const int t = tid_flat();
     const int lane = t & 31, warp = t >> 5;
 #pragma unroll
@@ -386,12 +389,12 @@ __device__ __forceinline__ void block_sum_mixed(A (&v)[NV], double (&out)[NV]) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     }
-    __syncthreads();
+    sub_sync();
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) sm[q][warp] = double(v[q]);
     }
-    __syncthreads();
+    sub_sync();
     if (t == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -1084,11 +1087,13 @@ __device__ __forceinline__ T blk_lap(const Lev& L, int pk, int q, const T* a) {
 // A Jacobi sweep stages its results in registers and writes them back after a
 // barrier; the residual b - L y replaces b (a V(2,0) cycle does not need b
 // again) and the restriction is the mean of its 8 children.
+// The body, for state s, all threads of the CTA taking part (the persistent
+// solver calls it with the plan held in its kernel parameters).
 template <typename T>
-__global__ void __launch_bounds__(MG_BLOCK_THREADS)
-    k_mg_block(MgPlan plan, SliceCtl* __restrict__ ctl, const T* __restrict__ in_even,
-               const T* __restrict__ in_odd, T* __restrict__ out) {
-    const long long s = blockIdx.x;
+__device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __restrict__ ctl,
+                                                const T* __restrict__ in_even,
+                                                const T* __restrict__ in_odd,
+                                                T* __restrict__ out, long long s) {
     if (ctl[s].status != ST_ITER) return;
     // the input is in_even, or with in_odd given the parity's one of the pair
     const T* __restrict__ in = in_odd != nullptr && iter_parity(ctl + s) ? in_odd : in_even;
@@ -1106,7 +1111,10 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
             o += 2 * n;
         }
     }
-    const unsigned t = threadIdx.x, nt = blockDim.x;
+    // flat thread index: the CTA is 1024 x 1 x 1 here, 32 x 4 x 8 in the
+    // persistent solver
+    const unsigned t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const unsigned nt = blockDim.x * blockDim.y * blockDim.z;
     const T w = T(MG_OMEGA);
     // the thread's cells of level m: packed coordinates and Jacobi weights
     int pk[MG_BLOCK_PER_THREAD];
@@ -1252,6 +1260,15 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
         T* __restrict__ dst = out + s * L.cells;
         for (unsigned q = t; q < (unsigned)L.cells; q += nt) dst[q] = yq[lc][q];
     }
+}
+
+// One CTA per state (blockIdx.x); the plan stays in the kernel parameters.
+template <typename T>
+__global__ void __launch_bounds__(MG_BLOCK_THREADS)
+    k_mg_block(const __grid_constant__ MgPlan plan, SliceCtl* __restrict__ ctl,
+               const T* __restrict__ in_even, const T* __restrict__ in_odd,
+               T* __restrict__ out) {
+    mg_block_levels<T>(plan, ctl, in_even, in_odd, out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

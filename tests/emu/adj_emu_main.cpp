@@ -1,10 +1,12 @@
 // Driver of the host emulation of the adjoint right side (test support):
-// k_adj_rhs, out += (dR/du)^T mu and dlid += (dR/du_lid)^T mu for one state,
-// FP64, every CTA as host threads (its atomics as real atomic additions).
+// k_adj_rhs, out = (dR/du)^T mu and the per-CTA partials of (dR/du_lid)^T mu
+// for one state, then k_adj_sum over the partials; every CTA as host threads.
+// prec "d" runs the FP64 kernel, "f" the FP32 one on the inputs rounded to
+// FP32.
 //
-// usage: adj_emu nx ny nz bcx bcy bcz re u_lid in.bin out.bin
+// usage: adj_emu prec nx ny nz bcx bcy bcz re u_lid in.bin out.bin
 //   in.bin: u, v, w, then mu_u, mu_v, mu_w (FP64); out.bin: the three adjoint
-//   right sides, then dlid.
+//   right sides, then dlid (FP64).
 
 #include <functional>
 
@@ -29,8 +31,32 @@ static void launch(int gx, const std::function<void()>& body) {
     }
 }
 
+template <typename T>
+static int run(const Geo& G, const std::vector<double>& in, std::vector<double>& out,
+               double& dlid) {
+    const long long nv = G.cnt[0] + G.cnt[1] + G.cnt[2];
+    std::vector<T> u(in.begin(), in.begin() + nv), mu(in.begin() + nv, in.end());
+    std::vector<T> o(nv, T(-7));
+    std::vector<double> part(G.fctas, -7.0);
+    launch(G.fctas, [&] {
+        k_adj_rhs<T>(G, u.data(), u.data() + G.cnt[0], u.data() + G.cnt[0] + G.cnt[1], mu.data(),
+                     mu.data() + G.cnt[0], mu.data() + G.cnt[0] + G.cnt[1], o.data(),
+                     o.data() + G.cnt[0], o.data() + G.cnt[0] + G.cnt[1], part.data());
+    });
+    blockDim.x = 32;
+    blockDim.y = 1;
+    threadIdx.x = 0;
+    threadIdx.y = 0;
+    blockIdx.x = 0;
+    k_adj_sum(part.data(), G.fctas, 1, &dlid, 0);
+    out.assign(o.begin(), o.end());
+    return 0;
+}
+
 int main(int argc, char** argv) {
-    if (argc != 11) return 1;
+    if (argc != 12) return 1;
+    const char prec = argv[1][0];
+    argv += 1;
     Geo G{};
     for (int a = 0; a < 3; ++a) {
         G.n[a] = atoi(argv[1 + a]);
@@ -38,8 +64,11 @@ int main(int argc, char** argv) {
         G.h[a] = 1.0 / G.n[a];
         G.ih[a] = 1.0 / G.h[a];
         G.ih2[a] = 1.0 / (G.h[a] * G.h[a]);
+        G.fih[a] = (float)G.ih[a];
+        G.fih2[a] = (float)G.ih2[a];
     }
     G.inv_re = 1.0 / atof(argv[7]);
+    G.finv_re = (float)G.inv_re;
     G.u_lid = atof(argv[8]);
     for (int c = 0; c < 3; ++c)
         for (int a = 0; a < 3; ++a)
@@ -56,15 +85,10 @@ int main(int argc, char** argv) {
     FILE* f = fopen(argv[9], "rb");
     if (!f || fread(in.data(), 8, in.size(), f) != in.size()) return 3;
     fclose(f);
-    const double* u = in.data();
-    const double* mu = in.data() + nv;
-    std::vector<double> out(nv, 0.0);
+    std::vector<double> out;
     double dlid = 0.0;
-    launch(G.fctas, [&] {
-        k_adj_rhs(G, u, u + G.cnt[0], u + G.cnt[0] + G.cnt[1], mu, mu + G.cnt[0],
-                  mu + G.cnt[0] + G.cnt[1], out.data(), out.data() + G.cnt[0],
-                  out.data() + G.cnt[0] + G.cnt[1], &dlid);
-    });
+    const int rc = prec == 'f' ? run<float>(G, in, out, dlid) : run<double>(G, in, out, dlid);
+    if (rc) return rc;
     f = fopen(argv[10], "wb");
     if (!f) return 5;
     fwrite(out.data(), 8, out.size(), f);

@@ -1,8 +1,9 @@
 // Driver of the host emulation of the adjoint's terminal condition and
-// finishing update (test support): k_adj_terminal and k_adj_finish for each
-// velocity component of `batch` states, FP64, grids of 256-thread CTAs
+// finishing update (test support): k_adj_terminal (128-thread CTAs, per-CTA
+// partial sums of J), k_adj_finish (256-thread CTAs) for each velocity
+// component of `batch` states and k_adj_sum over the partials, FP64, grids
 // smaller than the arrays (the grid-stride loops take several passes), every
-// CTA as host threads, the atomics as real atomic additions.
+// CTA as host threads.
 //
 // usage: adjterm_emu nx ny nz bcx bcy bcz batch vol dt in.bin out.bin
 //   in.bin: for c = 0, 1, 2: u_c, mu_c, acc_c [batch][faces of c] (FP64).
@@ -11,21 +12,23 @@
 
 #include <functional>
 
-static void launch(int gx, int gy, const std::function<void()>& body) {
-    constexpr int NT = 256;
-    blockDim.x = NT;
+// nt threads per CTA: 32 x (nt / 32) (the 128-thread kernels read
+// threadIdx.y), or 256 x 1 when flat
+static void launch(int gx, int gy, int nt, bool flat, const std::function<void()>& body) {
+    blockDim.x = flat ? (unsigned)nt : 32u;
+    blockDim.y = flat ? 1u : (unsigned)(nt / 32);
     gridDim.x = (unsigned)gx;
     gridDim.y = (unsigned)gy;
     for (int by = 0; by < gy; ++by)
         for (int bx = 0; bx < gx; ++bx) {
-            std::barrier<> bar(NT);
+            std::barrier<> bar(nt);
             emu_cta_barrier = &bar;
-            for (int w = 0; w < NT / 32; ++w) emu_warp_barrier[w] = new std::barrier<>(32);
+            for (int w = 0; w < nt / 32; ++w) emu_warp_barrier[w] = new std::barrier<>(32);
             std::vector<std::thread> th;
-            for (int t = 0; t < NT; ++t)
+            for (int t = 0; t < nt; ++t)
                 th.emplace_back([&, t, bx, by]() {
-                    threadIdx.x = (unsigned)t;
-                    threadIdx.y = 0;
+                    threadIdx.x = flat ? (unsigned)t : (unsigned)(t % 32);
+                    threadIdx.y = flat ? 0u : (unsigned)(t / 32);
                     blockIdx.x = (unsigned)bx;
                     blockIdx.y = (unsigned)by;
                     body();
@@ -33,7 +36,7 @@ static void launch(int gx, int gy, const std::function<void()>& body) {
                     bar.arrive_and_drop();
                 });
             for (auto& x : th) x.join();
-            for (int w = 0; w < NT / 32; ++w) delete emu_warp_barrier[w];
+            for (int w = 0; w < nt / 32; ++w) delete emu_warp_barrier[w];
         }
 }
 
@@ -65,20 +68,25 @@ int main(int argc, char** argv) {
     FILE* out = fopen(argv[11], "wb");
     if (!out) return 5;
     std::vector<double> J((size_t)batch, 0.0);
+    // the same CTA count for every component, about a third of the largest
+    // component's faces per pass of the grid-stride loops
+    long long most = std::max(G.cnt[0], std::max(G.cnt[1], G.cnt[2]));
+    const int gx = (int)std::max<long long>(1, most / (3 * NTHREADS));
+    std::vector<double> part((size_t)batch * 3 * gx, -7.0);
     for (int c = 0; c < 3; ++c) {
         const size_t n = (size_t)batch * G.cnt[c];
         std::vector<double> lam(n, -7.0), lam2(n, -7.0);
-        // about a third of the faces per pass of the grid-stride loops
-        const int gx = (int)std::max<long long>(1, G.cnt[c] / (3 * 256));
-        launch(gx, batch, [&] { k_adj_terminal(G, c, u[c].data(), lam.data(), J.data(), vol); });
+        launch(gx, batch, NTHREADS, false,
+               [&] { k_adj_terminal<double>(G, c, u[c].data(), lam.data(), part.data(), vol); });
         const int gf = (int)std::max<long long>(1, (long long)n / (3 * 256));
-        launch(gf, 1, [&] {
-            k_adj_finish(G, c, (long long)n, mu[c].data(), acc[c].data(), lam2.data(), dt);
+        launch(gf, 1, 256, true, [&] {
+            k_adj_finish<double>(G, c, (long long)n, mu[c].data(), acc[c].data(), lam2.data(), dt);
         });
         fwrite(lam.data(), 8, n, out);
         fwrite(lam2.data(), 8, n, out);
         fwrite(acc[c].data(), 8, n, out);
     }
+    launch(1, 1, 32, true, [&] { k_adj_sum(part.data(), 3 * gx, batch, J.data(), 0); });
     fwrite(J.data(), 8, J.size(), out);
     fclose(out);
     return 0;

@@ -27,12 +27,15 @@ using std::min;
 #define __launch_bounds__(x)
 #define __restrict__
 #define __align__(x)
+#define __grid_constant__
+#define NS_PERSISTENT_GROUPS 1
 
 struct EmuDim3 {
     unsigned x = 0, y = 0, z = 0;
 };
 thread_local EmuDim3 threadIdx, blockIdx;
-EmuDim3 blockDim, gridDim;
+// unset extents are 1, as in a launch (a 1-D CTA has blockDim.y = blockDim.z = 1)
+EmuDim3 blockDim{0, 1, 1}, gridDim{0, 1, 1};
 
 std::barrier<>* emu_cta_barrier;
 std::barrier<>* emu_warp_barrier[32];

@@ -1,6 +1,7 @@
 """The adjoint's terminal condition and finishing update run on the host:
 k_adj_terminal (lambda = u vol on active faces, 0 on wall-normal boundary
-faces, and J = 1/2 sum of u^2 vol per state) and k_adj_finish (lambda = mu +
+faces, and per-CTA partial sums of J = 1/2 sum of u^2 vol per state, summed in
+a fixed order by k_adj_sum) and k_adj_finish (lambda = mu +
 dt acc on active faces, 0 elsewhere, acc cleared for reuse), taken verbatim
 from csrc/ns_adjoint.cuh and compiled as C++ with every CTA as host threads
 (tests/emu/) under AddressSanitizer and UBSan, on grids smaller than the
@@ -28,7 +29,7 @@ def _source() -> str:
     adj = open(os.path.join(CSRC, "ns_adjoint.cuh")).read()
     a = dev.index("enum { BC_WALL")
     b = dev.index("}  // namespace nsk")
-    s = adj.index("// lambda = mu + dt * acc on active faces")
+    s = adj.index("// out[s] (+)= sum of part[s][0..n-1] in order")
     start = adj.index("    k_adj_terminal(")
     e = adj.index("\n}\n", start) + 3
     return dev[a:b] + "\n\n" + adj[s:e]

@@ -38,6 +38,9 @@ def _source() -> str:
         _extract(dev, r"^constexpr int TY ="),
         _extract(dev, r"^constexpr int NTHREADS ="),
         _extract(dev, r"^constexpr int NWARPS ="),
+        _extract(dev, r"^constexpr int NSUB ="),
+        _extract(dev, r"^__device__ __forceinline__ int sub_id\("),
+        _extract(dev, r"^__device__ __forceinline__ void sub_sync\("),
         _extract(dev, r"^__device__ __forceinline__ int tid_flat\("),
         _extract(dev, r"^__device__ __forceinline__ void block_sum\("),
         _extract(ker, r"^enum \{ ST_ITER"),
