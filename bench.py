@@ -703,26 +703,19 @@ def run_mixed(args):
     cavities with (nx, ny, nz) drawn from {32, 48, 64, 96} and Re ~ U[100,
     2000] (seed 0), all from rest, dt = 5e-4.  `steps` timed calls (after
     `warmup`) of ns_step_fine_many, 20 fine steps of every grid per call, the
-    grids on streams and host threads of their own; against the same work
-    issued grid by grid, as one CUDA graph with a branch per grid, and the
-    256^3 grid's 20 steps alone on the stream path and as a graph."""
+    grids on streams and host threads of their own, once with the tiles the
+    autotuner times for each grid (predictor tile and tile_z, cached) and once
+    with the default tiles; with the tuned tiles also the same work issued grid
+    by grid, as one CUDA graph with a branch per grid, and the 256^3 grid's 20
+    steps alone on the stream path and as a graph."""
     import torch
     from paper_1705_06149_gb300 import Grid, StepGraph, inputs, step_fine_many
+    from paper_1705_06149_gb300.autotune import autotune
     dt, per_call = 5e-4, 20
     dims, res = inputs.mixed_batch_sizes(24, seed=0)
     specs = [((256, 256, 256), 1000.0, 16)] + [(d, r, 1) for d, r in zip(dims, res)]
-    from paper_1705_06149_gb300.autotune import seed_order
-    grids, states, tiles = [], [], []
-    for d, re, b in specs:
-        tz = seed_order(*d, b)[0][0]  # the autotuner's seeded tile height
-        g = Grid(*d, re=re, precision=args.precision, batch=b, inner_rtol=args.inner_rtol,
-                 tile_z=tz)
-        grids.append(g)
-        states.append(g.zeros(b))
-        tiles.append(tz)
     cells = [b * d[0] * d[1] * d[2] for d, _, b in specs]
     cell_steps = per_call * sum(cells)
-    branches = [(g, s, dt, per_call) for g, s in zip(grids, states)]
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
@@ -735,51 +728,77 @@ def run_mixed(args):
         torch.cuda.synchronize()
         return ev[0].elapsed_time(ev[1]) / reps
 
-    for _ in range(args.warmup):
-        step_fine_many(branches)
-    for g in grids:
-        g.reset_stats()
-    ms_many = timed(lambda: step_fine_many(branches), args.steps)
-    st = [g.stats() for g in grids]
+    def build(tuned):
+        grids, states, tiles = [], [], []
+        t0 = time.perf_counter()
+        for d, re, b in specs:
+            kw = {}
+            if tuned:
+                r = autotune(*d, batch=b, precision=args.precision, top=2, steps=1,
+                             grid_kwargs={"re": re, "inner_rtol": args.inner_rtol})
+                kw = {"tile_z": r["tile_z"], "predict_tile": r["predict_tile"]}
+                tiles.append({"tile_z": r["tile_z"], "predict_tile": list(r["predict_tile"]),
+                              "cached": r["cached"]})
+            g = Grid(*d, re=re, precision=args.precision, batch=b, inner_rtol=args.inner_rtol,
+                     **kw)
+            grids.append(g)
+            states.append(g.zeros(b))
+        return grids, states, tiles, time.perf_counter() - t0
 
-    def sequential():
-        for g, s in zip(grids, states):
-            g.step_fine(s, dt, per_call)
-    ms_seq = timed(sequential, 1)
-    # the same 20 steps of every grid as one CUDA graph (a branch per grid)
-    graph = StepGraph(branches)
-    graph.launch()
-    graph.check()
-    ms_graph = timed(graph.launch, args.steps)
-    graph.check()
-    graph.close()
-    # the 256^3 grid alone: stream path against one CUDA graph of its 20 steps
-    ms_big_stream = timed(lambda: grids[0].step_fine(states[0], dt, per_call), 1)
-    graph = StepGraph([branches[0]])
-    graph.launch()
-    graph.check()
-    ms_big_graph = timed(graph.launch, 1)
-    graph.check()
-    graph.close()
-    iters = sum(x["krylov_iters"] for x in st) / max(1, sum(x["solves"] for x in st))
-    print(json.dumps({"mode": "mixed", "precision": args.precision,
-                      "workload": "256^3 cavity x 16 states (Re 1000) + 24 cavities, sizes "
-                      "from {32,48,64,96}^3, Re ~ U[100,2000] (seed 0), from rest, dt 5e-4, "
-                      "20 fine steps of every grid per call",
-                      "metric": "fine cell-steps/s over the whole mixed batch",
-                      "value": cell_steps / (ms_many / 1e3), "unit": UNIT,
-                      "ms_per_call": ms_many, "ms_grid_by_grid": ms_seq,
-                      "grid_by_grid_value": cell_steps / (ms_seq / 1e3),
-                      "ms_per_graph_launch": ms_graph,
-                      "graph_value": cell_steps / (ms_graph / 1e3),
-                      "big_grid": {"cells": cells[0], "ms_stream": ms_big_stream,
-                                   "ms_graph": ms_big_graph,
-                                   "graph_value": per_call * cells[0] / (ms_big_graph / 1e3)},
-                      "grids": len(grids), "krylov_iters_per_solve": iters,
-                      "shapes": [list(d) for d, _, _ in specs], "tile_z": tiles}),
-          flush=True)
-    for g in grids:
-        g.close()
+    out = {"mode": "mixed", "precision": args.precision,
+           "workload": "256^3 cavity x 16 states (Re 1000) + 24 cavities, sizes from "
+                       "{32,48,64,96}^3, Re ~ U[100,2000] (seed 0), from rest, dt 5e-4, "
+                       "20 fine steps of every grid per call",
+           "metric": "fine cell-steps/s over the whole mixed batch", "unit": UNIT,
+           "grids": len(specs), "shapes": [list(d) for d, _, _ in specs]}
+    for tuned in (True, False):
+        grids, states, tiles, t_build = build(tuned)
+        branches = [(g, s, dt, per_call) for g, s in zip(grids, states)]
+        for _ in range(args.warmup):
+            step_fine_many(branches)
+        for g in grids:
+            g.reset_stats()
+        ms_many = timed(lambda: step_fine_many(branches), args.steps)
+        st = [g.stats() for g in grids]
+        iters = sum(x["krylov_iters"] for x in st) / max(1, sum(x["solves"] for x in st))
+        tag = "tuned" if tuned else "default_tiles"
+        out[tag] = {"value": cell_steps / (ms_many / 1e3), "ms_per_call": ms_many,
+                    "krylov_iters_per_solve": iters, "setup_s": t_build}
+        if tuned:
+            out["value"] = out[tag]["value"]
+            out["tiles"] = tiles
+
+            def sequential():
+                for g, s in zip(grids, states):
+                    g.step_fine(s, dt, per_call)
+            ms_seq = timed(sequential, 1)
+            graph = StepGraph(branches)
+            graph.launch()
+            graph.check()
+            ms_graph = timed(graph.launch, args.steps)
+            graph.check()
+            graph.close()
+            ms_big_stream = timed(lambda: grids[0].step_fine(states[0], dt, per_call), 1)
+            graph = StepGraph([branches[0]])
+            graph.launch()
+            graph.check()
+            ms_big_graph = timed(graph.launch, 1)
+            graph.check()
+            graph.close()
+            out[tag].update({"ms_grid_by_grid": ms_seq,
+                             "grid_by_grid_value": cell_steps / (ms_seq / 1e3),
+                             "ms_per_graph_launch": ms_graph,
+                             "graph_value": cell_steps / (ms_graph / 1e3),
+                             "big_grid": {"cells": cells[0], "ms_stream": ms_big_stream,
+                                          "ms_graph": ms_big_graph,
+                                          "graph_value": per_call * cells[0] /
+                                          (ms_big_graph / 1e3)}})
+        for g in grids:
+            g.close()
+        del grids, states, branches
+        torch.cuda.empty_cache()
+    out["tuned_over_default"] = out["tuned"]["value"] / out["default_tiles"]["value"]
+    print(json.dumps(out), flush=True)
     return 0
 
 

@@ -93,6 +93,12 @@ typedef struct {
                                 runs on a second stream while the next chunk's fine
                                 sweep runs.  <= 0: one sweep over all slices, then
                                 the chain.  Results are bit-identical either way.  */
+    int predict_tile_y;      /* tile of the predictor (grids without solid cells): */
+    int predict_tile_z;      /* 32 x predict_tile_y x predict_tile_z cells, one
+                                thread per (x, y) column marching z; (y, z) one of
+                                (4,4) (4,8) (8,2) (8,4) (8,8) (16,4), else
+                                NS_ERR_ARG; (0, 0): (8, 4).  Results do not depend
+                                on it (each face is computed the same way).       */
 } ns_grid_desc;
 
 typedef enum { NS_PC_NONE = 0, NS_PC_MULTIGRID = 1 } ns_preconditioner;

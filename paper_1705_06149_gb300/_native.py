@@ -46,7 +46,8 @@ class GridDesc(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
                 ("batch", ctypes.c_int),
                 ("preconditioner", ctypes.c_int), ("tile_z", ctypes.c_int),
-                ("parareal_chunk", ctypes.c_int)]
+                ("parareal_chunk", ctypes.c_int),
+                ("predict_tile_y", ctypes.c_int), ("predict_tile_z", ctypes.c_int)]
 
 
 class StateC(ctypes.Structure):

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "ns.h"
@@ -167,6 +168,16 @@ struct ns_grid {
     SliceCtl* psnap_ctl = nullptr;   // control blocks before the pending solves
     LoopCount* psnap_lc = nullptr;
     // the chain of each chunk of the chunked schedule as a graph of its own
+    // the batched fine sweep of an iteration (S steps of the N slices in
+    // pr_f) as one CUDA graph with device-resident solver loops (rebuilt when
+    // N, S, dt or the settings change)
+    cudaStream_t sweep_cap[2] = {nullptr, nullptr};
+    cudaGraph_t sweep_graph = nullptr;
+    cudaGraphExec_t sweep_exec = nullptr;
+    int sweep_key_n = 0, sweep_key_s = 0;
+    double sweep_key_dt = 0.0;
+    LoopCount sweep_seen_lc{};
+    std::vector<SliceCtl> sweep_seen_ctl;
     std::vector<cudaGraph_t> chunk_graph;
     std::vector<cudaGraphExec_t> chunk_exec;
     int chunk_key = 0;
@@ -243,6 +254,9 @@ void setup_geo(ns_grid* g) {
     G.fbz = ceil_div(G.n[2] + 1, G.tz);
     G.fctas = G.fbx * G.fby * G.fbz;
     G.n_fluid = G.n[0] * G.n[1] * G.n[2];
+    const bool deflt = d.predict_tile_y == 0 && d.predict_tile_z == 0;
+    G.pty = deflt ? PT_Y : d.predict_tile_y;
+    G.ptz = deflt ? PT_Z : d.predict_tile_z;
 }
 
 // Face codes of the finest level with solid cells (FC_FLUID and one bit per
@@ -282,9 +296,12 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
     MgPlan& P = g->plan;
     P = MgPlan{};
     const int tz0 = G.tz;
-    auto fill = [tz0](Lev& L) {
+    // the finest level marches tz0 cells per thread (its reductions' order
+    // depends on it); the coarser levels, which reduce nothing, march 2, so
+    // their small latency-bound launches spread over more CTAs
+    auto fill = [](Lev& L, int tz) {
         L.cells = (long long)L.n[0] * L.n[1] * L.n[2];
-        L.tz = std::min(std::max(tz0, 2), L.n[2]);
+        L.tz = std::min(std::max(tz, 2), L.n[2]);
         L.bx = ceil_div(L.n[0], TX);
         L.by = ceil_div(L.n[1], TY);
         L.bz = ceil_div(L.n[2], L.tz);
@@ -301,7 +318,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
         L0.fih2[a] = (float)G.ih2[a];
         L0.lih2[a] = (float)(G.ih2[a] - (double)L0.fih2[a]);
     }
-    fill(L0);
+    fill(L0, tz0);
     P.lev[0] = L0;
     P.nlev = 1;
     while (P.nlev < MG_MAX_LEVELS) {
@@ -317,7 +334,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
             C.fih2[a] = (float)C.ih2[a];
             C.lih2[a] = (float)(C.ih2[a] - (double)C.fih2[a]);
         }
-        fill(C);
+        fill(C, 2);
         P.lev[P.nlev++] = C;
     }
     P.lc = P.nlev - 1;
@@ -1115,11 +1132,57 @@ void launch_predict(ns_grid* g, int batch, const T* u, const T* v, const T* w, T
             G, u, v, w, fu, fv, fw, dt);
         return;
     }
-    const int tbx = ceil_div(G.n[0], PT_X), tby = ceil_div(G.n[1], PT_Y),
-              tbz = ceil_div(G.n[2], PT_Z);
-    const size_t smem = 3 * (size_t)PS_N * sizeof(T);
-    k_predict_tile<T, INCR><<<dim3(tbx * tby * tbz, batch), PT_THREADS, smem, g->stream>>>(
-        G, u, v, w, fu, fv, fw, dt, tbx, tby);
+    auto go = [&](auto py_c, auto pz_c) {
+        constexpr int PY = decltype(py_c)::value, PZ = decltype(pz_c)::value;
+        const int tbx = ceil_div(G.n[0], PT_X), tby = ceil_div(G.n[1], PY),
+                  tbz = ceil_div(G.n[2], PZ);
+        const size_t smem = 3 * (size_t)ptile_elems<PY, PZ>() * sizeof(T);
+        k_predict_tile<T, INCR, PY, PZ><<<dim3(tbx * tby * tbz, batch), PT_X * PY, smem,
+                                          g->stream>>>(G, u, v, w, fu, fv, fw, dt, tbx, tby);
+    };
+    using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
+    using I16 = std::integral_constant<int, 16>;
+    const int key = G.pty * 100 + G.ptz;
+    switch (key) {
+        case 404: go(I4{}, I4{}); break;
+        case 408: go(I4{}, I8{}); break;
+        case 802: go(I8{}, I2{}); break;
+        case 808: go(I8{}, I8{}); break;
+        case 1604: go(I16{}, I4{}); break;
+        default: go(I8{}, I4{}); break;
+    }
+}
+
+// Shared memory limit of the predictor instantiation the grid uses (a value
+// fixed per instantiation, so grids never lower each other's).
+template <typename T, bool INCR>
+cudaError_t predict_smem_attr(int pty, int ptz) {
+    auto set = [](auto py_c, auto pz_c) {
+        constexpr int PY = decltype(py_c)::value, PZ = decltype(pz_c)::value;
+        const int bytes = 3 * ptile_elems<PY, PZ>() * (int)sizeof(T);
+        if (bytes <= 48 * 1024) return cudaSuccess;
+        return cudaFuncSetAttribute(k_predict_tile<T, INCR, PY, PZ>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
+    using I16 = std::integral_constant<int, 16>;
+    switch (pty * 100 + ptz) {
+        case 404: return set(I4{}, I4{});
+        case 408: return set(I4{}, I8{});
+        case 802: return set(I8{}, I2{});
+        case 808: return set(I8{}, I8{});
+        case 1604: return set(I16{}, I4{});
+        default: return set(I8{}, I4{});
+    }
+}
+
+bool predict_tile_ok(int y, int z) {
+    const int key = y * 100 + z;
+    return key == 404 || key == 408 || key == 802 || key == 804 || key == 808 || key == 1604;
 }
 
 // FP64 states take F* = u + dt RHS as in Section 2.  FP32 states take the
@@ -1605,6 +1668,42 @@ ns_status parareal_iteration_chunked(ns_grid* g, ns_state slices, int N, int S, 
     return NS_OK;
 }
 
+void drop_sweep_graph(ns_grid* g) {
+    if (g->sweep_exec) cudaGraphExecDestroy(g->sweep_exec);
+    if (g->sweep_graph) cudaGraphDestroy(g->sweep_graph);
+    g->sweep_exec = nullptr;
+    g->sweep_graph = nullptr;
+}
+
+// The fine sweep F(y^k_n) of all N slices (S steps of dt, in place in pr_f)
+// as one graph launch: captured on first use, then replayed; its solver
+// loops are conditional while nodes, so no solve waits for the host.  The
+// work is accounted (and failed solves reported) after the iteration's
+// synchronisation by sweep_account.
+template <typename T>
+ns_status sweep_launch(ns_grid* g, int N, int S, double dt) {
+    if (!(g->sweep_exec && g->sweep_key_n == N && g->sweep_key_s == S && g->sweep_key_dt == dt)) {
+        drop_sweep_graph(g);
+        for (cudaStream_t& cs : g->sweep_cap)
+            if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        NS_TRY(sync_stream(g));
+        ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
+        NS_TRY(capture_exec(g, g->sweep_cap[0], g->sweep_cap[1],
+                            [&]() -> ns_status { return step_impl<T>(g, fb, dt, S); },
+                            &g->sweep_graph, &g->sweep_exec));
+        g->sweep_key_n = N;
+        g->sweep_key_s = S;
+        g->sweep_key_dt = dt;
+        g->sweep_seen_ctl.assign(N, SliceCtl{});
+        NS_CUDA(cudaMemcpy(&g->sweep_seen_lc, g->loopc, sizeof(LoopCount),
+                           cudaMemcpyDeviceToHost));
+        NS_CUDA(cudaMemcpy(g->sweep_seen_ctl.data(), g->ctl, sizeof(SliceCtl) * N,
+                           cudaMemcpyDeviceToHost));
+    }
+    NS_CUDA(cudaGraphLaunch(g->sweep_exec, g->stream));
+    return NS_OK;
+}
+
 template <typename T>
 ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, int M,
                         double dt, int kmax, double tol, int resume, int* k_done,
@@ -1664,10 +1763,17 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
             else
                 NS_TRY(parareal_iteration_chunked<T>(g, slices, N, S, M, dt, chunk, &dk));
         } else {
-            // F(y^k_n) for all n in one batched sweep
+            // F(y^k_n) for all n in one batched sweep: one graph launch with
+            // the multigrid solver (per-launch timing, when on, needs the
+            // stream path's launches)
             NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
-            ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
-            NS_TRY(step_impl<T>(g, fb, dt, S));
+            const bool graphed = g->mg && !(g->prof.on && N >= g->prof.min_batch);
+            if (graphed) {
+                NS_TRY(sweep_launch<T>(g, N, S, dt));
+            } else {
+                ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
+                NS_TRY(step_impl<T>(g, fb, dt, S));
+            }
             // serial coarse sweep with the update of Eq. 6, on the companion
             auto chain = [&](ns_grid* h) -> ns_status {
                 NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
@@ -1707,6 +1813,9 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
                 return NS_OK;
             }));
             NS_TRY(sync_stream(g));
+            if (graphed)
+                NS_TRY(account_graph(g, N, S, 0, g->sweep_seen_lc, g->sweep_seen_ctl.data(),
+                                     "ns_parareal_iterate (fine sweep)"));
             std::memcpy(&dk, g->chain->h_defect, sizeof(double));
         }
         if (defects) defects[k] = dk;
@@ -1900,6 +2009,11 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
     if (d.precision == NS_FP32_REFINE && !(d.refine_rtol > 0))
         return fail(NS_ERR_ARG, "ns_create_grid: refine_rtol must be positive");
     if (d.batch < 1) return fail(NS_ERR_ARG, "ns_create_grid: batch must be >= 1");
+    if (!(d.predict_tile_y == 0 && d.predict_tile_z == 0) &&
+        !predict_tile_ok(d.predict_tile_y, d.predict_tile_z))
+        return fail(NS_ERR_ARG, "ns_create_grid: unsupported predictor tile (" +
+                                    std::to_string(d.predict_tile_y) + ", " +
+                                    std::to_string(d.predict_tile_z) + ")");
 
     ns_grid* g = new (std::nothrow) ns_grid();
     if (!g) return fail(NS_ERR_OOM, "ns_create_grid: host allocation failed");
@@ -2044,14 +2158,12 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
             cudaMemsetAsync(g->loopc, 0, sizeof(LoopCount), g->stream) != cudaSuccess)
             st = fail(NS_ERR_CUDA, "ns_create_grid: memset failed");
         if (st == NS_OK) {
-            const int ps = 3 * PS_N * (int)sizeof(double);
-            if (cudaFuncSetAttribute(k_predict_tile<double, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ps) !=
-                    cudaSuccess ||
-                cudaFuncSetAttribute(k_predict_tile<double, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ps) !=
-                    cudaSuccess)
-                st = fail(NS_ERR_CUDA, "ns_create_grid: predictor shared memory attribute");
+            const int py = g->geo.pty, pz = g->geo.ptz;
+            const bool ok = g->fp32 ? (predict_smem_attr<float, false>(py, pz) == cudaSuccess &&
+                                       predict_smem_attr<float, true>(py, pz) == cudaSuccess)
+                                    : (predict_smem_attr<double, false>(py, pz) == cudaSuccess &&
+                                       predict_smem_attr<double, true>(py, pz) == cudaSuccess);
+            if (!ok) st = fail(NS_ERR_CUDA, "ns_create_grid: predictor shared memory attribute");
         }
         if (st == NS_OK && g->mg) {
             if (cudaMemsetAsync(g->counter, 0, sizeof(unsigned int) * B, g->stream) !=
@@ -2085,6 +2197,9 @@ ns_status ns_destroy_grid(ns_grid* grid) {
     for (cudaGraphExec_t e : grid->chunk_exec) cudaGraphExecDestroy(e);
     for (cudaGraph_t c : grid->chunk_graph) cudaGraphDestroy(c);
     for (cudaStream_t cs : grid->chain_cap)
+        if (cs) cudaStreamDestroy(cs);
+    drop_sweep_graph(grid);
+    for (cudaStream_t cs : grid->sweep_cap)
         if (cs) cudaStreamDestroy(cs);
     if (grid->chain) ns_destroy_grid(grid->chain);
     if (grid->chain_stream) cudaStreamDestroy(grid->chain_stream);
@@ -2309,6 +2424,7 @@ ns_status ns_set_lid_speed(ns_grid* grid, double u_lid) {
     for (cudaGraph_t c : grid->chunk_graph) cudaGraphDestroy(c);
     grid->chunk_exec.clear();
     grid->chunk_graph.clear();
+    drop_sweep_graph(grid);
     grid->pr_valid = false;
     grid->gen += 1;
     return NS_OK;

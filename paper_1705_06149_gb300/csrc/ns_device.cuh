@@ -55,6 +55,7 @@ struct Geo {
     int n_fluid;         // fluid cells per state
     const uint8_t* solid;  // device cell mask (1 = solid), nullptr without obstacles
     float fih[3], fih2[3], finv_re;  // FP32 copies (no FP64 conversions in FP32 kernels)
+    int pty, ptz;        // predictor tile: 32 x pty x ptz cells
 };
 
 // h^-1, h^-2 and 1/Re in the kernel's precision

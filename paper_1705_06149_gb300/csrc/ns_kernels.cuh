@@ -63,17 +63,29 @@ struct KBuf {       // Krylov vectors of all states, [batch][cells]
 // evaluates every face of the tile from shared memory with constant strides.
 // Faces owned by the tile: the low face of each of its cells along each
 // component's axis, plus the high wall face of the last cell of the domain.
+// The tile is PT_X x PY x PZ cells (PT_X x PY threads); the default is
+// 32 x 8 x 4, and the tile autotuner chooses among the instantiated shapes.
 constexpr int PT_X = 32, PT_Y = 8, PT_Z = 4;
-constexpr int PT_THREADS = 256;
+constexpr int PT_THREADS = PT_X * PT_Y;
 constexpr int PH = 2;  // halo
 constexpr int PS_X = PT_X + 2 * PH, PS_Y = PT_Y + 2 * PH, PS_Z = PT_Z + 2 * PH;
 constexpr int PS_N = PS_X * PS_Y * PS_Z;
 
-template <typename T, bool INCR>
-__global__ void __launch_bounds__(PT_THREADS)
+// Staged elements of one component for a PT_X x PY x PZ tile.
+template <int PY, int PZ>
+constexpr int ptile_elems() {
+    return (PT_X + 2 * PH) * (PY + 2 * PH) * (PZ + 2 * PH);
+}
+
+template <typename T, bool INCR, int PY = PT_Y, int PZ = PT_Z>
+__global__ void __launch_bounds__(PT_X * PY)
     k_predict_tile(Geo g, const T* __restrict__ u, const T* __restrict__ v,
                    const T* __restrict__ w, T* __restrict__ fu, T* __restrict__ fv,
                    T* __restrict__ fw, double dt, int tbx, int tby) {
+    constexpr int PT_Y = PY, PT_Z = PZ;
+    constexpr int PT_THREADS = PT_X * PY;
+    constexpr int PS_Y = PY + 2 * PH, PS_Z = PZ + 2 * PH;
+    constexpr int PS_N = PS_X * PS_Y * PS_Z;
     extern __shared__ __align__(16) unsigned char psm_raw[];
     T* sm = reinterpret_cast<T*>(psm_raw);  // [3][PS_Z][PS_Y][PS_X]
     const long long s = blockIdx.y;

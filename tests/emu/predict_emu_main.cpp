@@ -3,12 +3,14 @@
 // solid cells) or k_predict_masked (with a cell mask) in FP64 for one state,
 // every CTA as host threads, and writes F* (or its increment).
 //
-// usage: predict_emu nx ny nz bcx bcy bcz re u_lid dt incr in.bin solid.bin|- out.bin
-//   in.bin: u, v, w (FP64, canonical layout) one after another.
+// usage: predict_emu nx ny nz bcx bcy bcz re u_lid dt incr in.bin solid.bin|- out.bin [py pz]
+//   in.bin: u, v, w (FP64, canonical layout) one after another; py pz: the
+//   tile of k_predict_tile (default 8 4).
 
 #include <functional>
+#include <type_traits>
 
-static void launch(int gx, int threads, const std::function<void()>& body) {
+static void launch(int gx, int threads, const std::function<void()>& body, bool flat = false) {
     for (int bx = 0; bx < gx; ++bx) {
         std::barrier<> bar(threads);
         emu_cta_barrier = &bar;
@@ -17,8 +19,8 @@ static void launch(int gx, int threads, const std::function<void()>& body) {
         std::vector<std::thread> th;
         for (int t = 0; t < threads; ++t)
             th.emplace_back([&, t, bx]() {
-                threadIdx.x = (unsigned)(threads == NTHREADS ? t % TX : t);
-                threadIdx.y = (unsigned)(threads == NTHREADS ? t / TX : 0);
+                threadIdx.x = (unsigned)(!flat && threads == NTHREADS ? t % TX : t);
+                threadIdx.y = (unsigned)(!flat && threads == NTHREADS ? t / TX : 0);
                 blockIdx.x = (unsigned)bx;
                 blockIdx.y = 0;
                 body();
@@ -31,7 +33,7 @@ static void launch(int gx, int threads, const std::function<void()>& body) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 14) return 1;
+    if (argc != 14 && argc != 16) return 1;
     Geo G{};
     for (int a = 0; a < 3; ++a) {
         G.n[a] = atoi(argv[1 + a]);
@@ -84,14 +86,30 @@ int main(int argc, char** argv) {
     double* fv = fu + G.cnt[0];
     double* fw = fv + G.cnt[1];
     if (G.solid == nullptr) {
-        const int tbx = (G.n[0] + PT_X - 1) / PT_X, tby = (G.n[1] + PT_Y - 1) / PT_Y,
-                  tbz = (G.n[2] + PT_Z - 1) / PT_Z;
-        std::vector<unsigned char> smem(3 * PS_N * sizeof(double));
-        emu_smem = smem.data();
-        if (incr)
-            launch(tbx * tby * tbz, PT_THREADS, [&] { k_predict_tile<double, true>(G, u, v, w, fu, fv, fw, dt, tbx, tby); });
-        else
-            launch(tbx * tby * tbz, PT_THREADS, [&] { k_predict_tile<double, false>(G, u, v, w, fu, fv, fw, dt, tbx, tby); });
+        const int py = argc > 15 ? atoi(argv[14]) : PT_Y, pz = argc > 15 ? atoi(argv[15]) : PT_Z;
+        auto run = [&](auto py_c, auto pz_c) {
+            constexpr int PY = decltype(py_c)::value, PZ = decltype(pz_c)::value;
+            const int tbx = (G.n[0] + PT_X - 1) / PT_X, tby = (G.n[1] + PY - 1) / PY,
+                      tbz = (G.n[2] + PZ - 1) / PZ;
+            std::vector<unsigned char> smem(3 * ptile_elems<PY, PZ>() * sizeof(double));
+            emu_smem = smem.data();
+            if (incr)
+                launch(tbx * tby * tbz, PT_X * PY, [&] { k_predict_tile<double, true, PY, PZ>(G, u, v, w, fu, fv, fw, dt, tbx, tby); }, true);
+            else
+                launch(tbx * tby * tbz, PT_X * PY, [&] { k_predict_tile<double, false, PY, PZ>(G, u, v, w, fu, fv, fw, dt, tbx, tby); }, true);
+        };
+        using I2 = std::integral_constant<int, 2>;
+        using I4 = std::integral_constant<int, 4>;
+        using I8 = std::integral_constant<int, 8>;
+        using I16 = std::integral_constant<int, 16>;
+        switch (py * 100 + pz) {
+            case 404: run(I4{}, I4{}); break;
+            case 408: run(I4{}, I8{}); break;
+            case 802: run(I8{}, I2{}); break;
+            case 808: run(I8{}, I8{}); break;
+            case 1604: run(I16{}, I4{}); break;
+            default: run(I8{}, I4{}); break;
+        }
     } else {
         if (incr)
             launch(G.fctas, NTHREADS, [&] { k_predict_masked<double, true>(G, u, v, w, fu, fv, fw, dt); });

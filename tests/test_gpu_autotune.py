@@ -31,3 +31,53 @@ def test_tile_z_changes_results_only_at_rounding_level(prec, tol):
     for c in range(4):
         a, b = np.ravel(out[0][c][0]), np.ravel(out[1][c][0])
         assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), c
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_predictor_tiles_give_identical_results(prec):
+    """Every face is evaluated from the same operands whatever the tile:
+    every predictor tile the autotuner may choose gives the same bits."""
+    from paper_1705_06149_gb300.autotune import PREDICT_TILES
+    dims = (40, 24, 20)  # ragged against every tile
+    init = inputs.random_state(*dims, seed=5, sigma=0.3)
+    ref = None
+    for tile in PREDICT_TILES:
+        g = Grid(*dims, re=300.0, precision=prec, batch=2, predict_tile=tile)
+        st = g.state_from([np.stack([a, a]) for a in init])
+        f = g.predict(st, 1e-3)
+        g.step_fine(st, 1e-3, 2)
+        torch.cuda.synchronize()
+        got = [t.clone() for t in f] + [t.clone() for t in st.fields()]
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(got, ref):
+                assert torch.equal(a, b), tile
+        g.close()
+
+
+def test_predictor_tile_outside_the_instantiated_set_is_rejected():
+    from paper_1705_06149_gb300 import NSError
+    from paper_1705_06149_gb300 import _native as N
+    with pytest.raises(NSError) as e:
+        Grid(16, 16, 16, predict_tile=(2, 2))
+    assert e.value.status == N.NS_ERR_ARG
+
+
+def test_autotune_3d_times_seeded_tiles_and_caches(tmp_path, monkeypatch):
+    from paper_1705_06149_gb300 import autotune as at
+    monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    r = at.autotune(48, 32, 32, batch=2, precision="fp32_refine", top=2, steps=1,
+                    grid_kwargs={"re": 500.0})
+    assert not r["cached"]
+    seeded_tiles = [tuple(t) for t, _ in r["seed"]["predict"][:2]]
+    seeded_z = [t for t, _ in r["seed"]["tile_z"][:2]]
+    assert tuple(r["predict_tile"]) in seeded_tiles
+    assert r["tile_z"] in seeded_z
+    assert len(r["ms"]["predict"]) == 2 and len(r["ms"]["step"]) == 2
+    assert r["seed"]["sms"] == torch.cuda.get_device_properties(0).multi_processor_count
+    again = at.autotune(48, 32, 32, batch=2, precision="fp32_refine", top=2, steps=1,
+                        grid_kwargs={"re": 500.0})
+    assert again["cached"]
+    assert tuple(again["predict_tile"]) == tuple(r["predict_tile"])
+    assert again["tile_z"] == r["tile_z"]

@@ -68,9 +68,25 @@ CASES = [
 ]
 
 
+TILES = [(8, 4), (4, 4), (4, 8), (8, 2), (8, 8), (16, 4)]
+
+
 @pytest.mark.parametrize("incr", [False, True])
 @pytest.mark.parametrize("dims,bc,masked", CASES)
 def test_predictor_matches_oracle(predict_emulator, dims, bc, masked, incr):
+    _run_predictor(predict_emulator, dims, bc, masked, incr, None)
+
+
+@pytest.mark.parametrize("tile", TILES[1:])
+@pytest.mark.parametrize("dims,bc", [((40, 10, 9), ("wall",) * 3),
+                                     ((16, 12, 6), ("periodic", "wall", "slip"))])
+def test_predictor_tiles_match_oracle(predict_emulator, dims, bc, tile):
+    """Every instantiated tile shape of k_predict_tile (the autotuner's
+    choices) against the oracle, on ragged tiles and periodic / slip axes."""
+    _run_predictor(predict_emulator, dims, bc, False, True, tile)
+
+
+def _run_predictor(predict_emulator, dims, bc, masked, incr, tile):
     exe, d = predict_emulator
     solid = None
     if masked:
@@ -79,13 +95,15 @@ def test_predictor_matches_oracle(predict_emulator, dims, bc, masked, incr):
     re, u_lid, dt = 50.0, 1.0, 2e-3
     og = oracle.Grid(*dims, re=re, u_lid=u_lid, bc=bc, solid=solid)
     want = og.predict(*rs[:3], dt)
-    tag = f"{os.getpid()}_{'_'.join(map(str, dims))}_{int(masked)}_{int(incr)}"
+    tag = f"{os.getpid()}_{'_'.join(map(str, dims))}_{int(masked)}_{int(incr)}_{tile}"
     fin, fsol, fout = d / f"in_{tag}.bin", d / f"solid_{tag}.bin", d / f"out_{tag}.bin"
     np.concatenate([np.ravel(a) for a in rs[:3]]).astype(np.float64).tofile(fin)
     if masked:
         np.ascontiguousarray(solid, dtype=np.uint8).tofile(fsol)
     args = [exe, *map(str, dims), *(str(BC[b]) for b in bc), repr(re), repr(u_lid), repr(dt),
             "1" if incr else "0", str(fin), str(fsol) if masked else "-", str(fout)]
+    if tile is not None:
+        args += [str(tile[0]), str(tile[1])]
     r = subprocess.run(args, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, (r.returncode, r.stderr[-3000:])
     out = np.fromfile(fout, dtype=np.float64)
