@@ -628,14 +628,18 @@ def run_coarse_only(args):
 
 
 def run_adjoint(args):
-    """Gradient of J = 1/2 |u(T)|^2 (kinetic energy, FP64) with respect to the
+    """Gradient of J = 1/2 |u(T)|^2 (kinetic energy) with respect to the
     initial velocity and the lid speed: 64^3 cavity, Re 400, from rest, 500
-    steps of 1e-3, checkpoints every 25 steps; `steps` timed gradients after
-    `warmup` untimed ones of 25 steps."""
+    steps of 1e-3, checkpoints every 25 steps, in the precision given
+    (fp32_refine: FP32 adjoint stencils and projections with FP64-accurate
+    refinement); `steps` timed gradients after `warmup` untimed ones of 25
+    steps, then one gradient with per-launch timing for the kernel table."""
     import torch
     from paper_1705_06149_gb300 import Grid
     n, nsteps, dt, ckpt = 64, 500, 1e-3, 25
-    g = Grid(n, n, n, re=400.0, precision="fp64", batch=1)
+    prec = args.precision
+    esz = 4 if prec == "fp32_refine" else 8
+    g = Grid(n, n, n, re=400.0, precision=prec, batch=1, inner_rtol=args.inner_rtol)
     u0 = g.zeros(1)
     for _ in range(args.warmup):
         g.adjoint(u0, dt, 25, ckpt)
@@ -646,13 +650,42 @@ def run_adjoint(args):
         J, grad, dl = g.adjoint(u0, dt, nsteps, ckpt)
     torch.cuda.synchronize()
     t = (time.perf_counter() - t0) / args.steps
+    stats = g.stats()
+    # one more gradient with CUDA events around every launch
+    g.profile(True, min_batch=1)
+    g.adjoint(u0, dt, nsteps, ckpt)
+    prof = g.profile_read()
+    g.profile(False)
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    cells = n ** 3
+    # the adjoint kernels per adjoint step and cell, in values: (dR/du)^T mu
+    # reads u and mu and writes the result (3 + 3 + 3), the finishing update
+    # reads mu and acc and writes lambda and acc (4 per component), the copy
+    # mu <- lambda reads and writes 3 each; the terminal condition (once) is
+    # not counted
+    words_adj = 9 + 12 + 6
+    adj = prof["adjoint"]
+    adj_bytes = nsteps * cells * words_adj * esz
+    kernels = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in prof.items()
+               if v["launches"]}
     gn = float(sum((f[0].double() ** 2).sum() for f in grad.fields()[:3]) ** 0.5)
-    print(json.dumps({"mode": "adjoint", "workload": "64^3 cavity, Re 400, u_lid 1, from rest, "
-                      "500 steps of 1e-3, checkpoints every 25 steps, FP64",
+    print(json.dumps({"mode": "adjoint", "precision": prec,
+                      "workload": "64^3 cavity, Re 400, u_lid 1, from rest, 500 steps of 1e-3, "
+                                  "checkpoints every 25 steps",
                       "metric": "gradient cell-steps/s (forward + checkpoint recompute + "
-                      "adjoint sweep)", "value": nsteps * n ** 3 / t, "unit": UNIT,
+                      "adjoint sweep)", "value": nsteps * cells / t, "unit": UNIT,
                       "s_per_gradient": t, "J": J[0], "grad_l2": gn, "dJ_dulid": dl[0],
-                      "stats": g.stats()}), flush=True)
+                      "adjoint_kernels": {
+                          "ms": adj["ms"], "algorithmic_bytes": adj_bytes,
+                          "achieved_gbs": adj_bytes / (adj["ms"] / 1e3) / 1e9
+                          if adj["ms"] > 0 else None,
+                          "frac": adj_bytes / (adj["ms"] / 1e3) / 1e9 / peak
+                          if adj["ms"] > 0 else None,
+                          "peak": peak, "peak_source": f"{peak_kind} hbm_gbs",
+                          "words_per_cell_step": words_adj},
+                      "kernels_profiled_gradient": kernels,
+                      "stats": stats}), flush=True)
     g.close()
     return 0
 

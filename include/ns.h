@@ -97,8 +97,10 @@ typedef struct {
     int predict_tile_z;      /* 32 x predict_tile_y x predict_tile_z cells, one
                                 thread per (x, y) column marching z; (y, z) one of
                                 (4,4) (4,8) (8,2) (8,4) (8,8) (16,4), else
-                                NS_ERR_ARG; (0, 0): (8, 4).  Results do not depend
-                                on it (each face is computed the same way).       */
+                                NS_ERR_ARG; (0, 0): (8, 4).  Every face takes the
+                                same operands whatever the tile; results move only
+                                at rounding level (the compiler may fuse products
+                                into multiply-adds differently per shape).        */
 } ns_grid_desc;
 
 typedef enum { NS_PC_NONE = 0, NS_PC_MULTIGRID = 1 } ns_preconditioner;

@@ -20,9 +20,10 @@ best seeded candidates through the C ABI and keeps the fastest.  Timed choices
 are cached per (grid, boundary conditions, precision, batch, device) in a JSON
 file (NS_AUTOTUNE_CACHE, else ~/.cache/paper_1705_06149_gb300/autotune.json).
 
-The predictor tile does not change any result (every face is evaluated from
-the same operands); `tile_z` changes the order of the solver's per-state
-reductions, so results move at rounding level with it.
+Neither choice changes the method's arithmetic: every face of the predictor
+is evaluated from the same operands whatever its tile, and `tile_z` fixes the
+order of the solver's per-state reductions, so results move at rounding
+level only.
 """
 from __future__ import annotations
 
@@ -172,8 +173,8 @@ def autotune(nx: int, ny: int, nz: int, batch: int = 1, precision: str = "fp32_r
              top: int = 3, steps: int = 2, dt: float = 5e-4, grid_kwargs: Optional[dict] = None,
              seed: int = 0, use_cache: bool = True) -> Dict:
     """Chooses the predictor tile and tile_z for a grid by timing the best
-    seeded candidates: `top` predictor tiles (their predictor launches alone,
-    the tile changes no result) and `top` tile_z values (`steps` fine steps
+    seeded candidates: `top` predictor tiles (their predictor launches alone)
+    and `top` tile_z values (`steps` fine steps
     after a warm one).  Returns {"predict_tile": (py, pz), "tile_z": tz,
     "seed": {...}, "ms": {...}, "cached": bool}; timed results are cached."""
     import torch

@@ -296,9 +296,9 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
     MgPlan& P = g->plan;
     P = MgPlan{};
     const int tz0 = G.tz;
-    // the finest level marches tz0 cells per thread (its reductions' order
-    // depends on it); the coarser levels, which reduce nothing, march 2, so
-    // their small latency-bound launches spread over more CTAs
+    // every level marches tz0 cells per thread (the finest level's reduction
+    // order depends on it; on the coarser levels, which reduce nothing, 2
+    // cells per thread was measured slower in the batched sweep)
     auto fill = [](Lev& L, int tz) {
         L.cells = (long long)L.n[0] * L.n[1] * L.n[2];
         L.tz = std::min(std::max(tz, 2), L.n[2]);
@@ -334,7 +334,7 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
             C.fih2[a] = (float)C.ih2[a];
             C.lih2[a] = (float)(C.ih2[a] - (double)C.fih2[a]);
         }
-        fill(C, 2);
+        fill(C, tz0);
         P.lev[P.nlev++] = C;
     }
     P.lc = P.nlev - 1;

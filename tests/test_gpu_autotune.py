@@ -34,9 +34,11 @@ def test_tile_z_changes_results_only_at_rounding_level(prec, tol):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
-def test_predictor_tiles_give_identical_results(prec):
-    """Every face is evaluated from the same operands whatever the tile:
-    every predictor tile the autotuner may choose gives the same bits."""
+def test_predictor_tiles_agree_to_rounding(prec):
+    """Every face is evaluated from the same operands whatever the tile, so
+    every predictor tile the autotuner may choose gives the same predictor
+    and steps up to rounding (the compiler may fuse products into
+    multiply-adds differently per instantiated shape)."""
     from paper_1705_06149_gb300.autotune import PREDICT_TILES
     dims = (40, 24, 20)  # ragged against every tile
     init = inputs.random_state(*dims, seed=5, sigma=0.3)
@@ -51,8 +53,10 @@ def test_predictor_tiles_give_identical_results(prec):
         if ref is None:
             ref = got
         else:
+            tol = 1e-13 if prec == "fp64" else 1e-6
             for a, b in zip(got, ref):
-                assert torch.equal(a, b), tile
+                a, b = a.double(), b.double()
+                assert float((a - b).norm()) <= tol * float(b.norm()), tile
         g.close()
 
 
