@@ -237,8 +237,13 @@ __device__ __forceinline__ T adj_gather(const Geo& g, int c, const int t[3],
 }
 
 // out = (dR/du)^T mu for every state of the batch (blockIdx.y), every stored
-// value written once; per-CTA partial sums of (dR/du_lid)^T mu in
-// part_lid[state][cta] (summed in a fixed order by k_adj_sum).
+// value written once, component blockIdx.z; each thread gathers ADJ_TZ
+// positions along z of a 32 x 4 column tile (the gather is latency-bound, so
+// the launch spreads over many CTAs).  Per-CTA partial sums of
+// (dR/du_lid)^T mu go to part_lid[state][component][cta] (summed in a fixed
+// order by k_adj_sum).
+constexpr int ADJ_TZ = 2;
+
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_adj_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
@@ -246,23 +251,25 @@ __global__ void __launch_bounds__(NTHREADS)
               T* __restrict__ ou, T* __restrict__ ov, T* __restrict__ ow,
               double* __restrict__ part_lid) {
     const long long s = blockIdx.y;
+    const int c = blockIdx.z;
     const T* const vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
     const T* const mu3[3] = {mu_u + s * g.cnt[0], mu_v + s * g.cnt[1], mu_w + s * g.cnt[2]};
-    T* const out[3] = {ou + s * g.cnt[0], ov + s * g.cnt[1], ow + s * g.cnt[2]};
-    int i, j, k0;
-    tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
-    const int k1 = min(k0 + g.tz, g.n[2] + 1);
+    T* const out = (c == 0 ? ou : (c == 1 ? ov : ow)) + s * g.cnt[c];
+    const int cta = blockIdx.x;
+    const int i = (cta % g.fbx) * TX + (int)threadIdx.x;
+    const int r = cta / g.fbx;
+    const int j = (r % g.fby) * TY + (int)threadIdx.y;
+    const int k0 = (r / g.fby) * ADJ_TZ;
+    const int k1 = min(k0 + ADJ_TZ, g.ext[c][2]);
     double dl = 0.0;
-    for (int k = k0; k < k1; ++k) {
-#pragma unroll 1
-        for (int c = 0; c < 3; ++c) {
-            if (!(i < g.ext[c][0] && j < g.ext[c][1] && k < g.ext[c][2])) continue;
+    if (i < g.ext[c][0] && j < g.ext[c][1]) {
+        for (int k = k0; k < k1; ++k) {
             const int t[3] = {i, j, k};
-            out[c][vindex(g, c, i, j, k)] = adj_gather(g, c, t, vel3, mu3, dl);
+            out[vindex(g, c, i, j, k)] = adj_gather(g, c, t, vel3, mu3, dl);
         }
     }
     double v1[1] = {dl};
-    write_partials<1>(v1, part_lid + s * g.fctas + blockIdx.x);
+    write_partials<1>(v1, part_lid + (s * 3 + c) * (long long)gridDim.x + blockIdx.x);
 }
 
 // out[s] (+)= sum of part[s][0..n-1] in order, one thread per state.

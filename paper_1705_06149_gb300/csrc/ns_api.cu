@@ -1252,7 +1252,10 @@ ns_status step_any(ns_grid* g, const ns_state& io, double dt, int nsteps, const 
 }
 
 template <typename T>
-ns_status project_impl(ns_grid* g, const ns_state& io) {
+// u <- u - G phi with L phi = D u.  phi (device, [batch][cells], may be null):
+// the warm start of the solve and, on return, the gauged phi; null: the solve
+// starts from zero.
+ns_status project_impl(ns_grid* g, const ns_state& io, double* phi = nullptr) {
     const Geo& G = g->geo;
     const int B = io.batch;
     const dim3 gcell(G.ctas, B), gface(G.fctas, B);
@@ -1263,21 +1266,23 @@ ns_status project_impl(ns_grid* g, const ns_state& io) {
     NS_LAUNCH(g, NS_K_DIVERGENCE, G.cnt[3] * B,
               k_divergence<T><<<gcell, block_dim(), 0, g->stream>>>(
                   G, u, v, w, nullptr, nullptr, nullptr, g->b, g->part_div, 1.0));
-    NS_CUDA(cudaMemsetAsync(g->p64[1], 0, sizeof(double) * G.cnt[3] * B, g->stream));
+    if (!phi) {
+        // zero warm start: p64[1] is free scratch at this point in both precisions
+        NS_CUDA(cudaMemsetAsync(g->p64[1], 0, sizeof(double) * G.cnt[3] * B, g->stream));
+    }
     NS_CUDA(cudaGetLastError());
-    // zero warm start: p64[1] is free scratch at this point in both precisions
-    NS_TRY(solve_pressure(g, B, g->p64[1]));
+    NS_TRY(solve_pressure(g, B, phi ? phi : g->p64[1]));
     const double* x0 = g->fp32 ? g->p64[0] : (const double*)g->kv[0];
     const double* x1 = g->fp32 ? g->p64[1] : (const double*)g->kv[0];
     if (g->fp32 && g->mg)
         NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
                   k_correct_ff<false><<<gface, block_dim(), 0, g->stream>>>(
                       G, g->ctl, (const float*)u, (const float*)v, (const float*)w, (float*)u,
-                      (float*)v, (float*)w, ffbuf(g), nullptr, dt_ih(G, 1.0), 0));
+                      (float*)v, (float*)w, ffbuf(g), phi, dt_ih(G, 1.0), 0));
     else
         NS_LAUNCH(g, NS_K_CORRECT, G.cnt[3] * B,
                   k_correct<T, false><<<gface, block_dim(), 0, g->stream>>>(
-                      G, g->ctl, u, v, w, u, v, w, x0, x1, nullptr, 1.0));
+                      G, g->ctl, u, v, w, u, v, w, x0, x1, phi, 1.0));
     NS_CUDA(cudaGetLastError());
     return persist_settle(g);
 }
@@ -1876,10 +1881,13 @@ ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, 
     T* lam = (T*)alloc(sizeof(T) * vel_elems);
     T* mu = (T*)alloc(sizeof(T) * vel_elems);
     T* acc = (T*)alloc(sizeof(T) * vel_elems);
-    double* pmu = (double*)alloc(sizeof(double) * np);
+    double* pmu = (double*)alloc(sizeof(double) * np);  // phi of the adjoint projections
     double* dJ = (double*)alloc(sizeof(double) * 2 * B);
     double* part_J = (double*)alloc(sizeof(double) * 3 * tblocks * B);
-    double* part_lid = (double*)alloc(sizeof(double) * G.fctas * B);
+    // (dR/du)^T mu: 32 x 4 column tiles over the face extents, ADJ_TZ
+    // positions along z per thread, one grid z-slice per component
+    const int adj_ctas = G.fbx * G.fby * ceil_div(G.n[2] + 1, ADJ_TZ);
+    double* part_lid = (double*)alloc(sizeof(double) * 3 * adj_ctas * B);
     if (mine.size() != 12) {
         release();
         return fail(NS_ERR_OOM, "ns_adjoint: workspace allocation failed");
@@ -1894,6 +1902,7 @@ ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, 
     ns_status st = copy_states<T>(g, dst0, src0, 0, 0, B);
     NS_CUDA(cudaMemsetAsync(acc, 0, sizeof(T) * vel_elems, g->stream));
     NS_CUDA(cudaMemsetAsync(dJ, 0, sizeof(double) * 2 * B, g->stream));
+    NS_CUDA(cudaMemsetAsync(pmu, 0, sizeof(double) * np, g->stream));
     auto copy = [&](void* dst, const void* src, size_t bytes, const char* what) {
         if (st == NS_OK && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice,
                                            g->stream) != cudaSuccess)
@@ -1933,16 +1942,17 @@ ns_status adjoint_impl(ns_grid* g, const ns_state& u0, double dt, int N, int C, 
             // mu = P lambda
             copy(mu, lam, sizeof(T) * vel_elems, "adjoint");
             if (st != NS_OK) break;
-            st = project_impl<T>(g, vel_state(mu, pmu));
+            // each adjoint projection starts from the previous one's phi
+            st = project_impl<T>(g, vel_state(mu, pmu), pmu);
             if (st != NS_OK) break;
             // acc = (dR/du)^T mu at u^n, dJ/du_lid += dt (dR/du_lid)^T mu
             T* un = seg + (size_t)(n - n0) * vel_elems;
             NS_LAUNCH(g, NS_K_ADJOINT, 0,
-                      k_adj_rhs<T><<<dim3(G.fctas, B), block_dim(), 0, g->stream>>>(
+                      k_adj_rhs<T><<<dim3(adj_ctas, B, 3), block_dim(), 0, g->stream>>>(
                           G, un, un + nv[0], un + nv[0] + nv[1], mu, mu + nv[0],
                           mu + nv[0] + nv[1], acc, acc + nv[0], acc + nv[0] + nv[1], part_lid));
             NS_LAUNCH(g, NS_K_ADJOINT, 0,
-                      k_adj_sum<<<(B + 31) / 32, 32, 0, g->stream>>>(part_lid, G.fctas, B,
+                      k_adj_sum<<<(B + 31) / 32, 32, 0, g->stream>>>(part_lid, 3 * adj_ctas, B,
                                                                     dJ + B, 1));
             // lambda = mu + dt acc (active faces); acc <- 0
             for (int c = 0; c < 3; ++c) {

@@ -1,6 +1,7 @@
 // Driver of the host emulation of the adjoint right side (test support):
 // k_adj_rhs, out = (dR/du)^T mu and the per-CTA partials of (dR/du_lid)^T mu
-// for one state, then k_adj_sum over the partials; every CTA as host threads.
+// for one state (the three components as grid z-slices), then k_adj_sum over
+// the partials; every CTA as host threads.
 // prec "d" runs the FP64 kernel, "f" the FP32 one on the inputs rounded to
 // FP32.
 //
@@ -37,18 +38,24 @@ static int run(const Geo& G, const std::vector<double>& in, std::vector<double>&
     const long long nv = G.cnt[0] + G.cnt[1] + G.cnt[2];
     std::vector<T> u(in.begin(), in.begin() + nv), mu(in.begin() + nv, in.end());
     std::vector<T> o(nv, T(-7));
-    std::vector<double> part(G.fctas, -7.0);
-    launch(G.fctas, [&] {
-        k_adj_rhs<T>(G, u.data(), u.data() + G.cnt[0], u.data() + G.cnt[0] + G.cnt[1], mu.data(),
-                     mu.data() + G.cnt[0], mu.data() + G.cnt[0] + G.cnt[1], o.data(),
-                     o.data() + G.cnt[0], o.data() + G.cnt[0] + G.cnt[1], part.data());
-    });
+    const int ctas = G.fbx * G.fby * ((G.n[2] + 1 + ADJ_TZ - 1) / ADJ_TZ);
+    std::vector<double> part(3 * ctas, -7.0);
+    gridDim.x = (unsigned)ctas;
+    for (int c = 0; c < 3; ++c)
+        launch(ctas, [&] {
+            blockIdx.z = (unsigned)c;
+            k_adj_rhs<T>(G, u.data(), u.data() + G.cnt[0], u.data() + G.cnt[0] + G.cnt[1],
+                         mu.data(), mu.data() + G.cnt[0], mu.data() + G.cnt[0] + G.cnt[1],
+                         o.data(), o.data() + G.cnt[0], o.data() + G.cnt[0] + G.cnt[1],
+                         part.data());
+        });
     blockDim.x = 32;
     blockDim.y = 1;
     threadIdx.x = 0;
     threadIdx.y = 0;
     blockIdx.x = 0;
-    k_adj_sum(part.data(), G.fctas, 1, &dlid, 0);
+    blockIdx.z = 0;
+    k_adj_sum(part.data(), 3 * ctas, 1, &dlid, 0);
     out.assign(o.begin(), o.end());
     return 0;
 }

@@ -32,6 +32,7 @@ def _source() -> str:
     b = dev.index("}  // namespace nsk")
     s = adj.index("// partial derivatives of smart_face")
     start = adj.index("    k_adj_sum(")
+    assert adj.index("    k_adj_rhs(") < start
     e = adj.index("\n}\n", start) + 3
     return dev[a:b] + "\n\n" + adj[s:e]
 
