@@ -134,6 +134,10 @@ struct ns_grid {
     // while nodes whose bodies are captured on body_stream[0] / [1]
     bool capturing = false;
     cudaStream_t body_stream[2] = {nullptr, nullptr};
+    std::vector<cudaGraph_t> cap_bodies;  // loop bodies of the capture in progress
+    // the coarse chain's graph with programmatic dependencies between its
+    // consecutive kernels (NS_CHAIN_PDL=0 in the environment at creation: off)
+    bool chain_pdl = true;
     LoopCount* loopc = nullptr;
     long long cap_launches = 0;  // kernels captured so far
     // Parareal's coarse propagator: a batch-1 companion grid (this grid's
@@ -779,6 +783,7 @@ ns_status add_while(ns_grid* g, cudaStream_t bst, cudaGraphConditionalHandle h, 
     prm.conditional.size = 1;
     cudaGraphNode_t node;
     NS_CUDA(cudaGraphAddNode(&node, gr, deps, nullptr, nd, &prm));
+    g->cap_bodies.push_back(prm.conditional.phGraph_out[0]);
     NS_CUDA(cudaStreamBeginCaptureToGraph(bst, prm.conditional.phGraph_out[0], nullptr, nullptr,
                                           0, cudaStreamCaptureModeRelaxed));
     g->stream = bst;
@@ -795,13 +800,50 @@ ns_status add_while(ns_grid* g, cudaStream_t bst, cudaGraphConditionalHandle h, 
     return NS_OK;
 }
 
+// Turns every plain dependency between two kernel nodes of `graph` into a
+// programmatic one (the successor's CTAs may launch once every CTA of the
+// predecessor passed its pdl_wait, and wait there for its completion).
+cudaError_t make_programmatic(cudaGraph_t graph) {
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetEdges(graph, nullptr, nullptr, nullptr, &n);
+    if (e != cudaSuccess || n == 0) return e;
+    std::vector<cudaGraphNode_t> from(n), to(n);
+    std::vector<cudaGraphEdgeData> ed(n);
+    e = cudaGraphGetEdges(graph, from.data(), to.data(), ed.data(), &n);
+    if (e != cudaSuccess) return e;
+    for (size_t q = 0; q < n; ++q) {
+        cudaGraphNodeType tf, tt;
+        if ((e = cudaGraphNodeGetType(from[q], &tf)) != cudaSuccess) return e;
+        if ((e = cudaGraphNodeGetType(to[q], &tt)) != cudaSuccess) return e;
+        if (tf != cudaGraphNodeTypeKernel || tt != cudaGraphNodeTypeKernel ||
+            ed[q].type != cudaGraphDependencyTypeDefault || ed[q].from_port != 0)
+            continue;
+        if ((e = cudaGraphRemoveDependencies(graph, &from[q], &to[q], &ed[q], 1)) != cudaSuccess)
+            return e;
+        cudaGraphEdgeData pe{};
+        pe.from_port = cudaGraphKernelNodePortProgrammatic;
+        pe.type = cudaGraphDependencyTypeProgrammatic;
+        if ((e = cudaGraphAddDependencies(graph, &from[q], &to[q], &pe, 1)) != cudaSuccess) {
+            // put the plain dependency back: the graph stays correct
+            cudaGraphAddDependencies(graph, &from[q], &to[q], &ed[q], 1);
+            return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 // Captures the launches fn() issues on g->stream into an executable graph:
-// the capture runs on `top`, the solver loops' bodies on `body`.
+// the capture runs on `top`, the solver loops' bodies on `body`.  With
+// `programmatic`, consecutive kernels (in the graph and in its loop bodies)
+// get programmatic dependencies; where the runtime refuses them the plain
+// dependencies stay.
 template <typename F>
 ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
-                       cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
+                       cudaGraph_t* graph_out, cudaGraphExec_t* exec_out,
+                       bool programmatic = false) {
     *graph_out = nullptr;
     *exec_out = nullptr;
+    g->cap_bodies.clear();
     NS_CUDA(cudaStreamBeginCapture(top, cudaStreamCaptureModeRelaxed));
     const cudaStream_t saved = g->stream;
     const bool prof_active = g->prof.active;
@@ -822,7 +864,20 @@ ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
     if (e != cudaSuccess)
         return fail(NS_ERR_CUDA, std::string("graph capture: cudaStreamEndCapture: ") +
                                      cudaGetErrorString(e));
-    const cudaError_t ei = cudaGraphInstantiate(exec_out, graph, 0);
+    if (programmatic) {
+        bool ok = make_programmatic(graph) == cudaSuccess;
+        for (cudaGraph_t b : g->cap_bodies) ok = ok && make_programmatic(b) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    g->cap_bodies.clear();
+    cudaError_t ei = cudaGraphInstantiate(exec_out, graph, 0);
+    if (ei != cudaSuccess && programmatic) {
+        // the runtime refused the programmatic edges: capture again without
+        cudaGetLastError();
+        cudaGraphDestroy(graph);
+        g->chain_pdl = false;
+        return capture_exec(g, top, body, std::forward<F>(fn), graph_out, exec_out, false);
+    }
     if (ei != cudaSuccess) {
         cudaGraphDestroy(graph);
         return fail(NS_ERR_CUDA, std::string("graph capture: cudaGraphInstantiate: ") +
@@ -1439,7 +1494,7 @@ ns_status ensure_chain_graph(ns_grid* g, const void* ys, int N, int M, double dt
     ns_grid* h = g->chain;
     NS_CUDA(cudaStreamSynchronize(h->stream));
     NS_TRY(capture_exec(h, g->chain_cap[0], g->chain_cap[1], build, &g->chain_graph,
-                        &g->chain_exec));
+                        &g->chain_exec, g->chain_pdl));
     g->chain_key_ys = ys;
     g->chain_key_f = g->pr_f[0];
     g->chain_key_n = N;
@@ -2132,6 +2187,8 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
             g->persist_grid = sms;
         }
         cudaGetLastError();
+        const char* pdl = std::getenv("NS_CHAIN_PDL");
+        g->chain_pdl = !(pdl && std::atoi(pdl) == 0);
         const char* spin = std::getenv("NS_PERSIST_SPIN_NS");
         if (spin) g->spin_ns = std::max(1LL, std::atoll(spin));
         if (g->persist) {

@@ -32,6 +32,22 @@ constexpr int NSUB = NS_PERSISTENT_GROUPS;
 // The calling thread's group (0 in the launched kernels).
 __device__ __forceinline__ int sub_id() { return NSUB > 1 ? (int)threadIdx.z : 0; }
 
+#ifndef NS_HOST_EMULATION
+// First statement of every kernel of the solve and step sequence.  With a
+// programmatic dependency on the previous kernel (the coarse chain's graph
+// edges), this kernel's CTAs may become resident before that kernel ends:
+// they wait here for its completion and memory, then allow the next kernel
+// to start launching (it fires once every CTA of this grid has passed this
+// point, so a waiting successor never holds the slots this grid's later CTAs
+// need).  Without such a dependency both instructions return at once.
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+#endif
+
 // Barrier over the NTHREADS threads of a (sub-)CTA: __syncthreads in the
 // launched kernels, one named barrier per group in the persistent solver.
 __device__ __forceinline__ void sub_sync() {

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(PT_X * PY)
     k_predict_tile(Geo g, const T* __restrict__ u, const T* __restrict__ v,
                    const T* __restrict__ w, T* __restrict__ fu, T* __restrict__ fv,
                    T* __restrict__ fw, double dt, int tbx, int tby) {
+    pdl_wait();
     constexpr int PT_Y = PY, PT_Z = PZ;
     constexpr int PT_THREADS = PT_X * PY;
     constexpr int PS_Y = PY + 2 * PH, PS_Z = PZ + 2 * PH;
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(NTHREADS)
     k_predict_masked(Geo g, const T* __restrict__ u, const T* __restrict__ v,
                      const T* __restrict__ w, T* __restrict__ fu, T* __restrict__ fv,
                      T* __restrict__ fw, double dt) {
+    pdl_wait();
     const long long s = blockIdx.y;
     const T* vel3[3] = {u + s * g.cnt[0], v + s * g.cnt[1], w + s * g.cnt[2]};
     T* out[3] = {fu + s * g.cnt[0], fv + s * g.cnt[1], fw + s * g.cnt[2]};
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(NTHREADS)
                  const T* __restrict__ fw, const T* __restrict__ u, const T* __restrict__ v,
                  const T* __restrict__ w, double* __restrict__ b, double* __restrict__ part,
                  double inv_dt) {
+    pdl_wait();
     const long long s = blockIdx.y;
     fu += s * g.cnt[0];
     fv += s * g.cnt[1];
@@ -803,6 +806,7 @@ __global__ void __launch_bounds__(NTHREADS)
     k_correct(Geo g, const SliceCtl* __restrict__ ctl, const T* fu, const T* fv, const T* fw,
               T* u, T* v, T* w, const double* __restrict__ x0, const double* __restrict__ x1,
               double* __restrict__ p_out, double dt, double* __restrict__ p_keep = nullptr) {
+    pdl_wait();
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     const double* x = (c->p_final ? x1 : x0) + s * g.cnt[3];
@@ -857,6 +861,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_parareal_update(long long n, const T* __restrict__ fy, const T* __restrict__ gnew,
                       T* __restrict__ gold, T* __restrict__ y, unsigned long long* defect) {
+    pdl_wait();
     double dmax = 0.0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {

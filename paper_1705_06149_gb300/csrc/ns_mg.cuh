@@ -471,6 +471,7 @@ template <typename T, int MODE, bool PRE>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_src(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, const T* __restrict__ barr,
              T* __restrict__ ydst) {
+    pdl_wait();
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -590,6 +591,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_src_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, const T* __restrict__ barr,
                   T* __restrict__ ydst, int pbx) {
+    pdl_wait();
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -752,6 +754,7 @@ __global__ void __launch_bounds__(NTHREADS)
     k_mg_restrict(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, const T* __restrict__ bsrc,
                   const T* __restrict__ bsrc_odd, const T* __restrict__ ysrc,
                   T* __restrict__ bdst) {
+    pdl_wait();
     const long long s = blockIdx.y;
     if (ctl[s].status != ST_ITER) return;
     const T* __restrict__ b =
@@ -888,6 +891,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_prolong(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
                  const T* __restrict__ ecoarse) {
+    pdl_wait();
     const long long s = blockIdx.y;
     if (ctl[s].status != ST_ITER) return;
     T* __restrict__ y = ydst + s * L.cells;
@@ -959,6 +963,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_prolong_pair(Lev L, Lev Lc, SliceCtl* __restrict__ ctl, T* __restrict__ ydst,
                       const T* __restrict__ ecoarse, int pbx) {
+    pdl_wait();
     const long long s = blockIdx.y;
     if (ctl[s].status != ST_ITER) return;
     T* __restrict__ y = ydst + s * L.cells;
@@ -1268,6 +1273,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
     k_mg_block(const __grid_constant__ MgPlan plan, SliceCtl* __restrict__ ctl,
                const T* __restrict__ in_even, const T* __restrict__ in_odd,
                T* __restrict__ out) {
+    pdl_wait();
     mg_block_levels<T>(plan, ctl, in_even, in_odd, out, blockIdx.x);
 }
 
@@ -1279,6 +1285,7 @@ __global__ void __launch_bounds__(MG_BLOCK_THREADS)
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_lapdot_v(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -1326,6 +1333,7 @@ __global__ void __launch_bounds__(NTHREADS)
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_lapdot_t(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -1380,6 +1388,7 @@ template <typename T, int WHICH>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_lapdot_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
                      int pbx, int ctas) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -1502,6 +1511,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_update(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
                 double tol2, int maxit, int zero_start) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -1571,6 +1581,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
     k_mg_update_pair(Lev L, MgBuf<T> mb, SliceCtl* __restrict__ ctl, double* __restrict__ part,
                      double tol2, int maxit, int zero_start, int pbx, int ctas) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->status != ST_ITER) return;
@@ -1653,6 +1664,7 @@ __global__ void __launch_bounds__(NTHREADS)
                    const double* __restrict__ part_b, int nfluid, T* __restrict__ bvec,
                    const T* __restrict__ x0, double* __restrict__ part, double tol2,
                    int maxit) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     double sb[1];
@@ -1779,6 +1791,7 @@ __global__ void __launch_bounds__(NTHREADS)
                         const double* __restrict__ bvec, const double* __restrict__ p_in,
                         FFBuf f, double* __restrict__ part, double otol2, double itol2,
                         int maxit) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     double sb[1];
@@ -1873,6 +1886,7 @@ __global__ void __launch_bounds__(NTHREADS)
     k_mg_refine_update_ff(Lev L, MgBuf<float> mb, SliceCtl* __restrict__ ctl, FFBuf f,
                           int nfluid, double* __restrict__ part, double otol2, double itol2,
                           int maxit, int max_outer, int skip_iterating) {
+    pdl_wait();
     const long long s = blockIdx.y;
     SliceCtl* c = ctl + s;
     if (c->o_status != OS_REFINE) return;
@@ -1991,6 +2005,7 @@ __global__ void __launch_bounds__(NTHREADS)
     k_correct_ff(Geo g, const SliceCtl* __restrict__ ctl, const float* fu, const float* fv,
                  const float* fw, float* u, float* v, float* w, FFBuf f,
                  double* __restrict__ p_out, float3 dt_ih, int keep) {
+    pdl_wait();
     const long long s = blockIdx.y;
     const SliceCtl* c = ctl + s;
     const long long off = s * g.cnt[3];
@@ -2071,6 +2086,7 @@ enum {
 __global__ void __launch_bounds__(32)
     k_loop_cond(SliceCtl* __restrict__ ctl, int batch, LoopCount* __restrict__ lc,
                 cudaGraphConditionalHandle h, int mode, unsigned cap) {
+    pdl_wait();
     const int lane = threadIdx.x;
     bool iter = false, refine = false;
     for (int s = lane; s < batch; s += 32) {

@@ -29,6 +29,9 @@ using std::min;
 #define __align__(x)
 #define __grid_constant__
 #define NS_PERSISTENT_GROUPS 1
+// the kernels' dependent-launch wait: nothing to wait for on the host
+#define NS_HOST_EMULATION 1
+inline void pdl_wait() {}
 
 struct EmuDim3 {
     unsigned x = 0, y = 0, z = 0;
