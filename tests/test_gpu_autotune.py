@@ -53,7 +53,9 @@ def test_predictor_tiles_agree_to_rounding(prec):
         if ref is None:
             ref = got
         else:
-            tol = 1e-13 if prec == "fp64" else 1e-6
+            # the predictor alone agrees to a few ulps; two steps carry those
+            # through the pressure solves (conditioning ~1e3)
+            tol = 1e-11 if prec == "fp64" else 1e-5
             for a, b in zip(got, ref):
                 a, b = a.double(), b.double()
                 assert float((a - b).norm()) <= tol * float(b.norm()), tile
