@@ -83,7 +83,13 @@ typedef struct {
                                 The levels with at most 4096 cells (FP32_REFINE;
                                 512 in FP64) run in one CTA per state; the
                                 environment variable NS_MG_BLOCK_CELLS, read at
-                                ns_create_grid, overrides that size (>= 8).     */
+                                ns_create_grid, overrides that size (>= 8).
+                                Where the coarse levels split into z slabs of an
+                                even number of planes, everything below the
+                                finest level runs instead as one launch of a
+                                thread-block cluster per state (2 to 8 CTAs; the
+                                same V-cycle, results move at rounding level);
+                                NS_MG_CLUSTER=0 at ns_create_grid turns that off. */
     int tile_z;              /* cells each thread marches along z in the stencil and
                                 solver kernels: an even number >= 2 (clamped to nz);
                                 0: 8.  Results depend on it at rounding level (it
@@ -257,7 +263,9 @@ typedef enum {
     NS_K_MG_BLOCK = 16,    /* multigrid: the one-CTA levels (one CTA per state)   */
     NS_K_PERSIST = 17,     /* a whole pressure solve in one persistent cooperative
                               launch (small batches, multigrid preconditioner)    */
-    NS_K_KINDS = 18
+    NS_K_MG_CLUSTER = 18,  /* multigrid: the coarse levels on a thread-block cluster
+                              per state (everything below the finest level)       */
+    NS_K_KINDS = 19
 } ns_kernel_kind;
 
 typedef struct {
@@ -265,11 +273,12 @@ typedef struct {
     long long launches;    /* timed launches                                         */
     long long cell_units;  /* cells processed by them: for the Krylov phases the sum
                               over states of (iterations x cells), elsewhere
-                              (states x cells) per launch; for NS_K_MG_COARSE and
-                              NS_K_MG_BLOCK the values (words) the launches read
-                              and write by the algorithmic model: 2 per cell for
-                              smoothing and for the one-CTA levels' input and
-                              output, 2 + 1/8 for restriction and prolongation */
+                              (states x cells) per launch; for NS_K_MG_COARSE,
+                              NS_K_MG_BLOCK and NS_K_MG_CLUSTER the values (words)
+                              the launches read and write by the algorithmic
+                              model: 2 per cell for smoothing and for the one-CTA
+                              and cluster levels' input and output, 2 + 1/8 for
+                              restriction and prolongation */
 } ns_kernel_time;
 
 /* Turns per-launch timing on (on != 0) or off.  While on, every launch made by

@@ -27,7 +27,7 @@ EXPORTS = ("ns_create_grid", "ns_destroy_grid", "ns_set_stream", "ns_step_fine",
 KERNEL_KINDS = ("predict", "divergence", "solve_init", "krylov_A", "krylov_B", "krylov_C",
                 "inner_init", "refine", "correct", "parareal", "mg_lap_v", "mg_lap_t",
                 "mg_restrict0", "mg_prolong0", "mg_coarse", "adjoint", "mg_block",
-                "persist")
+                "persist", "mg_cluster")
 
 
 class NSError(RuntimeError):

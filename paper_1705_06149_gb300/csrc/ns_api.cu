@@ -20,6 +20,7 @@
 #include "ns.h"
 #include "ns_adjoint.cuh"
 #include "ns_mg.cuh"
+#include "ns_mg_cluster.cuh"
 #include "ns_persist.h"
 
 using namespace nsk;
@@ -90,6 +91,10 @@ struct ns_grid {
     bool mg = false;
     MgPlan plan{};
     size_t mg_smem = 0;
+    // the coarse levels on a thread-block cluster per state
+    bool cl = false;
+    ClPlan cplan{};
+    size_t cl_smem = 0;
     void* mg_vec[3] = {};                       // Y, Z, S at level 0
     void* mg_B[MG_MAX_LEVELS] = {};             // restricted right sides, levels 1..lc
     void* mg_Y[MG_MAX_LEVELS] = {};             // level iterates, levels 1..lc
@@ -362,6 +367,51 @@ bool setup_mg(ns_grid* g, int block_cells, size_t elem, bool masked) {
     return P.block_ok != 0;
 }
 
+// Shared memory a cluster launch may take (one fixed limit for the kernel, so
+// grids created later never lower it).
+constexpr size_t MG_CL_MAX_SMEM = 200 * 1024;
+
+// The cluster form of the V-cycle below the finest level (ns_mg_cluster.cuh):
+// the largest cluster (8, 4 or 2 CTAs) whose clusters for `cap` states fit the
+// device's SMs at one CTA each (else 2 CTAs) and that has a plan (cl_plan).
+bool setup_cluster(ns_grid* g, size_t elem, int cap, int sms) {
+    for (int C = MG_CL_MAX_CTAS; C >= 2; C /= 2) {
+        if (C > 2 && (long long)cap * C > sms) continue;
+        if (cl_plan(g->plan, C, elem, MG_CL_MAX_SMEM, g->cplan, g->cl_smem)) return true;
+    }
+    return false;
+}
+
+// Launch configuration of the cluster kernel for `batch` states.
+void cluster_config(const ns_grid* g, int batch, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3(g->cplan.C, batch);
+    cfg.blockDim = dim3(MG_CL_THREADS);
+    cfg.dynamicSmemBytes = g->cl_smem;
+    cfg.stream = g->stream;
+    at[0] = cudaLaunchAttribute{};
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = g->cplan.C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+
+// Whether the device runs the grid's cluster launch (its shared memory limit
+// set, at least one cluster resident).
+template <typename T>
+bool cluster_ready(ns_grid* g) {
+    if (cudaFuncSetAttribute(k_mg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)MG_CL_MAX_SMEM) != cudaSuccess)
+        return false;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    cluster_config(g, 1, cfg, at);
+    int n = 0;
+    return cudaOccupancyMaxActiveClusters(&n, k_mg_cluster<T>, &cfg) == cudaSuccess && n >= 1;
+}
+
 ns_status check_state(const ns_grid* g, const ns_state& s, const char* what) {
     if (!s.u || !s.v || !s.w || !s.p)
         return fail(NS_ERR_ARG, std::string(what) + ": null state pointer");
@@ -570,7 +620,9 @@ void launch_refine_init_ff(ns_grid* g, int batch, const double* p_in, double oto
 template <typename T, int MODE>
 void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
     const MgPlan& P = g->plan;
-    const int lc = P.lc;
+    // the first level below the grid-level ones: the cluster kernel's top
+    // level, else the first one-CTA level
+    const int lc = g->cl ? g->cplan.J : P.lc;
     const dim3 blk = block_dim();
     const Lev& L0 = P.lev[0];
     if (lc > 0 && L0.fcode == nullptr && L0.n[0] % 2 == 0) {
@@ -617,12 +669,22 @@ void mg_apply(ns_grid* g, int batch, MgBuf<T>& mb, T* src, T* src_odd, T* dst) {
             }
         }
     }
-    T* bin = lc == 0 ? src : mb.B[lc];
-    T* bin_odd = lc == 0 ? src_odd : nullptr;
-    T* bout = lc == 0 ? dst : mb.Yl[lc];
-    NS_LAUNCH(g, NS_K_MG_BLOCK, 2 * P.lev[lc].cells * batch,
-              k_mg_block<T><<<batch, MG_BLOCK_THREADS, g->mg_smem, g->stream>>>(
-                  P, g->ctl, bin, bin_odd, bout));
+    if (g->cl) {
+        // everything below the finest level: one cluster per state
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute at[1];
+        cluster_config(g, batch, cfg, at);
+        const T* bin = mb.B[lc];
+        NS_LAUNCH(g, NS_K_MG_CLUSTER, 2 * P.lev[lc].cells * batch,
+                  cudaLaunchKernelEx(&cfg, k_mg_cluster<T>, P, g->cplan, g->ctl, bin, mb.Yl[lc]));
+    } else {
+        T* bin = lc == 0 ? src : mb.B[lc];
+        T* bin_odd = lc == 0 ? src_odd : nullptr;
+        T* bout = lc == 0 ? dst : mb.Yl[lc];
+        NS_LAUNCH(g, NS_K_MG_BLOCK, 2 * P.lev[lc].cells * batch,
+                  k_mg_block<T><<<batch, MG_BLOCK_THREADS, g->mg_smem, g->stream>>>(
+                      P, g->ctl, bin, bin_odd, bout));
+    }
     for (int l = lc - 1; l >= 0; --l) {
         T* y = l == 0 ? dst : mb.Yl[l];
         const Lev& L = P.lev[l];
@@ -2166,6 +2228,17 @@ ns_status ns_create_grid(const ns_grid_desc* desc, void* cuda_stream, ns_grid** 
         if (g->fp32)
             for (int q = 0; q < 8; ++q) A((void**)&g->ffb[q], ncell * sizeof(float) * B);
         A((void**)&g->part_mg, nparts * 6 * sizeof(double));
+    }
+    if (g->mg && st == NS_OK) {
+        // the coarse levels on a thread-block cluster per state, where they
+        // split into slabs (NS_MG_CLUSTER=0 turns it off)
+        const char* ce = std::getenv("NS_MG_CLUSTER");
+        int sms = 0;
+        if (!(ce && std::atoi(ce) == 0) &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device) == cudaSuccess &&
+            setup_cluster(g, ev, (int)B, sms))
+            g->cl = g->fp32 ? cluster_ready<float>(g) : cluster_ready<double>(g);
+        cudaGetLastError();
     }
     if (g->mg && st == NS_OK) {
         // persistent solves for small batches, on request (NS_PERSISTENT=1 in

@@ -1084,43 +1084,24 @@ __device__ __forceinline__ T blk_lap(const Lev& L, int pk, int q, const T* a) {
     return s;
 }
 
-// V(2,0) cycle on levels plan.lc .. nlev-1 for the right side `in` (global,
-// level lc); writes the result to `out` (global, level lc).  Shared memory per
-// level m: the right side b_m and the iterate y_m.  Thread t holds the cells
-// t + c * blockDim.x (c < MG_BLOCK_PER_THREAD) of a level; their coordinates
-// and Jacobi weights are computed once per level visit and kept in registers.
-// A Jacobi sweep stages its results in registers and writes them back after a
-// barrier; the residual b - L y replaces b (a V(2,0) cycle does not need b
-// again) and the restriction is the mean of its 8 children.
-// The body, for state s, all threads of the CTA taking part (the persistent
-// solver calls it with the plan held in its kernel parameters).
+// V(2,0) cycle on the one-CTA levels lc .. nlev-1 held in shared memory: per
+// level m the right side bq[m] and the iterate yq[m].  On entry bq[lc] holds
+// the right side (visible to every thread); on exit yq[lc] holds the result
+// (after a barrier).  Thread t of nt holds the cells t + c * nt
+// (c < MG_BLOCK_PER_THREAD) of a level; their coordinates and Jacobi weights
+// are computed once per level visit and kept in registers.  A Jacobi sweep
+// stages its results in registers and writes them back after a barrier; the
+// residual b - L y replaces b (a V(2,0) cycle does not need b again) and the
+// restriction is the mean of its 8 children.
 template <typename T>
-__device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __restrict__ ctl,
-                                                const T* __restrict__ in_even,
-                                                const T* __restrict__ in_odd,
-                                                T* __restrict__ out, long long s) {
-    if (ctl[s].status != ST_ITER) return;
-    // the input is in_even, or with in_odd given the parity's one of the pair
-    const T* __restrict__ in = in_odd != nullptr && iter_parity(ctl + s) ? in_odd : in_even;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* __restrict__ sm = reinterpret_cast<T*>(smem_raw);
-    const int lc = plan.lc, nl = plan.nlev;
-    T* bq[MG_MAX_LEVELS];
-    T* yq[MG_MAX_LEVELS];
-    {
-        long long o = 0;
-        for (int m = lc; m < nl; ++m) {
-            const long long n = plan.lev[m].cells;
-            bq[m] = sm + o;
-            yq[m] = sm + o + n;
-            o += 2 * n;
-        }
-    }
-    // flat thread index: the CTA is 1024 x 1 x 1 here, 32 x 4 x 8 in the
-    // persistent solver
-    const unsigned t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const unsigned nt = blockDim.x * blockDim.y * blockDim.z;
+__device__ __forceinline__ void mg_block_core(const MgPlan& plan, int lc, T* const* bq,
+                                              T* const* yq, unsigned t, unsigned nt) {
+    const int nl = plan.nlev;
     const T w = T(MG_OMEGA);
+    // the first thread of this thread's warp: slot c of the warp holds cells
+    // only if wt + c nt < cells, a warp-uniform test, so warps beyond a small
+    // level's cells skip a slot's work instead of issuing it predicated off
+    const unsigned wt = t & ~31u;
     // the thread's cells of level m: packed coordinates and Jacobi weights
     int pk[MG_BLOCK_PER_THREAD];
     T wd[MG_BLOCK_PER_THREAD];
@@ -1132,7 +1113,7 @@ __device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __
             const unsigned q = t + c * nt;
             pk[c] = 0;
             wd[c] = T(0);
-            if (q < (unsigned)L.cells) {
+            if (wt + c * nt < (unsigned)L.cells && q < (unsigned)L.cells) {
                 int i, j, k;
                 lev_ijk(L, rc, q, i, j, k);
                 pk[c] = blk_pack(i, j, k);
@@ -1147,23 +1128,17 @@ __device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __
 #pragma unroll
         for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
             const unsigned q = t + c * nt;
-            if (q < cells)
+            if (wt + c * nt < cells && q < cells)
                 nv[c] = yq[m][q] + wd[c] * (bq[m][q] - blk_lap<T>(plan.lev[m], pk[c], (int)q, yq[m]));
         }
         __syncthreads();
 #pragma unroll
         for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
             const unsigned q = t + c * nt;
-            if (q < cells) yq[m][q] = nv[c];
+            if (wt + c * nt < cells && q < cells) yq[m][q] = nv[c];
         }
         __syncthreads();
     };
-    {
-        const Lev& L = plan.lev[lc];
-        const T* __restrict__ src = in + s * L.cells;
-        for (unsigned q = t; q < (unsigned)L.cells; q += nt) bq[lc][q] = src[q];
-    }
-    __syncthreads();
     // down: two Jacobi sweeps from zero, the residual, its restriction
     for (int m = lc; m < nl - 1; ++m) {
         const Lev& L = plan.lev[m];
@@ -1173,14 +1148,15 @@ __device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __
 #pragma unroll
         for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
             const unsigned q = t + c * nt;
-            if (q < cells) yq[m][q] = wd[c] * bq[m][q];
+            if (wt + c * nt < cells && q < cells) yq[m][q] = wd[c] * bq[m][q];
         }
         __syncthreads();
         sweep(m);
 #pragma unroll
         for (int c = 0; c < MG_BLOCK_PER_THREAD; ++c) {
             const unsigned q = t + c * nt;
-            if (q < cells) bq[m][q] = bq[m][q] - blk_lap<T>(L, pk[c], (int)q, yq[m]);
+            if (wt + c * nt < cells && q < cells)
+                bq[m][q] = bq[m][q] - blk_lap<T>(L, pk[c], (int)q, yq[m]);
         }
         __syncthreads();
         const LevRcp rcc = lev_rcp(Lc);
@@ -1260,6 +1236,46 @@ __device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __
         }
         __syncthreads();
     }
+}
+
+// V(2,0) cycle on levels plan.lc .. nlev-1 for the right side `in` (global,
+// level lc); writes the result to `out` (global, level lc), with the levels in
+// shared memory (mg_block_core).
+// The body, for state s, all threads of the CTA taking part (the persistent
+// solver calls it with the plan held in its kernel parameters).
+template <typename T>
+__device__ __forceinline__ void mg_block_levels(const MgPlan& plan, SliceCtl* __restrict__ ctl,
+                                                const T* __restrict__ in_even,
+                                                const T* __restrict__ in_odd,
+                                                T* __restrict__ out, long long s) {
+    if (ctl[s].status != ST_ITER) return;
+    // the input is in_even, or with in_odd given the parity's one of the pair
+    const T* __restrict__ in = in_odd != nullptr && iter_parity(ctl + s) ? in_odd : in_even;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* __restrict__ sm = reinterpret_cast<T*>(smem_raw);
+    const int lc = plan.lc, nl = plan.nlev;
+    T* bq[MG_MAX_LEVELS];
+    T* yq[MG_MAX_LEVELS];
+    {
+        long long o = 0;
+        for (int m = lc; m < nl; ++m) {
+            const long long n = plan.lev[m].cells;
+            bq[m] = sm + o;
+            yq[m] = sm + o + n;
+            o += 2 * n;
+        }
+    }
+    // flat thread index: the CTA is 1024 x 1 x 1 here, 32 x 4 x 8 in the
+    // persistent solver
+    const unsigned t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const unsigned nt = blockDim.x * blockDim.y * blockDim.z;
+    {
+        const Lev& L = plan.lev[lc];
+        const T* __restrict__ src = in + s * L.cells;
+        for (unsigned q = t; q < (unsigned)L.cells; q += nt) bq[lc][q] = src[q];
+    }
+    __syncthreads();
+    mg_block_core<T>(plan, lc, bq, yq, t, nt);
     {
         const Lev& L = plan.lev[lc];
         T* __restrict__ dst = out + s * L.cells;

@@ -85,6 +85,7 @@ def _kernel_source() -> str:
         _extract(mg, r"^__device__ __forceinline__ int blk_pack\("),
         _extract(mg, r"^__device__ __forceinline__ T blk_wd\("),
         _extract(mg, r"^__device__ __forceinline__ T blk_lap\("),
+        _extract(mg, r"^__device__ __forceinline__ void mg_block_core\("),
         _extract(mg, r"^__device__ __forceinline__ void mg_block_levels\("),
         _extract(mg, r"^    k_mg_block\("),
     ]
