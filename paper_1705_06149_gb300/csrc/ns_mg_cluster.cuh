@@ -566,13 +566,26 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
             yq[m] = sm + cp.oy[m];
         }
         mg_block_core<T>(plan, R, bq, yq, (unsigned)t, (unsigned)nt);
-        for (int m = R - 1; m >= J && cp.own[m] == 1; --m) {
+        int m = R - 1;
+        for (; m >= J && cp.own[m] == 1; --m) {
             const ClLev v = cl_lev(plan.lev[m], 1, 0);
             const bool from_core = m + 1 == R;
             const T* e = from_core ? sm + cp.oy[R] : sm + cp.oy2[m + 1];
             cl_prolong<T>(v, plan.lev[m + 1], e, from_core ? 0 : 1, 0, sm + cp.oy2[m], nullptr,
                           nullptr, m == J ? out : nullptr, t, nt);
             __syncthreads();
+        }
+        // the split level above reads the correction of the level below it
+        // whole: a copy into every CTA, so that those reads stay local
+        {
+            const bool from_core = m + 1 == R;
+            T* src = from_core ? sm + cp.oy[R] : sm + cp.oy2[m + 1];
+            const Lev& Lb = plan.lev[m + 1];
+            const long long n = from_core ? Lb.cells : (long long)(Lb.n[2] + 2) * Lb.n[0] * Lb.n[1];
+            for (long long q = t; q < n; q += nt) {
+                const T x = src[q];
+                for (int rk = 1; rk < C; ++rk) *cl_map(src + q, (unsigned)rk) = x;
+            }
         }
     }
     cl_sync();
@@ -583,10 +596,10 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
         const bool from_core = m + 1 == R;
         const bool from0 = from_core || cp.own[m + 1] == 1;
         // the coarse correction: rank 0's core level (slot z) or whole slab
-        // level (slot z + 1), or this CTA's coarse slab with its halo planes
-        // (slot z - Kc0 + 1, wrapped across a periodic seam)
-        const T* e = from_core ? cl_map(sm + cp.oy[R], 0u)
-                               : (from0 ? cl_map(sm + cp.oy2[m + 1], 0u) : sm + cp.oy2[m + 1]);
+        // level (slot z + 1), copied into this CTA, or this CTA's coarse slab
+        // with its halo planes (slot z - Kc0 + 1, wrapped across a periodic
+        // seam)
+        const T* e = from_core ? sm + cp.oy[R] : sm + cp.oy2[m + 1];
         const int zoff = from_core ? 0 : (from0 ? 1 : 1 - v.k0 / 2);
         const int nzw = from0 ? 0 : plan.lev[m + 1].n[2];
         T *lo = nullptr, *hi = nullptr;
@@ -594,9 +607,8 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
         cl_prolong<T>(v, plan.lev[m + 1], e, zoff, nzw, sm + cp.oy2[m], lo, hi,
                       m == J ? out : nullptr, t, nt);
         // the next level up reads the halo planes just written; after level
-        // J no CTA reads another's shared memory, except rank 0's when the
-        // level below J is rank 0's
-        if (m > J || from0) cl_sync();
+        // J no CTA touches another's shared memory
+        if (m > J) cl_sync();
     }
 }
 
