@@ -355,28 +355,51 @@ __global__ void __launch_bounds__(NTHREADS)
         const int k1 = min(k0 + g.tz, g.n[2]);
         const int ip = (g.bc[0] == BC_PERIODIC && i + 1 == g.n[0]) ? 0 : i + 1;
         const int jp = (g.bc[1] == BC_PERIODIC && j + 1 == g.n[1]) ? 0 : j + 1;
-        for (int k = k0; k < k1; ++k) {
-            const int kp = (g.bc[2] == BC_PERIODIC && k + 1 == g.n[2]) ? 0 : k + 1;
-            // D of the stored F* (or increment) in the storage precision; in
-            // FP32 this is the increment, whose differences carry no
-            // cancellation against u
-            T dt_ = (fu[vindex(g, 0, ip, j, k)] - fu[vindex(g, 0, i, j, k)]) * g_ih<T>(g, 0);
-            dt_ += (fv[vindex(g, 1, i, jp, k)] - fv[vindex(g, 1, i, j, k)]) * g_ih<T>(g, 1);
-            dt_ += (fw[vindex(g, 2, i, j, kp)] - fw[vindex(g, 2, i, j, k)]) * g_ih<T>(g, 2);
-            double dv = double(dt_);
-            if (with_u) {
-                // the stored u itself: differences taken exactly in FP64
-                double du = (double(u[vindex(g, 0, ip, j, k)]) - double(u[vindex(g, 0, i, j, k)])) *
-                            g.ih[0];
-                du += (double(v[vindex(g, 1, i, jp, k)]) - double(v[vindex(g, 1, i, j, k)])) *
-                      g.ih[1];
-                du += (double(w[vindex(g, 2, i, j, kp)]) - double(w[vindex(g, 2, i, j, k)])) *
-                      g.ih[2];
-                dv += du;
+        // a batch of DIV_ZB cells' face values is loaded before any of them
+        // is differenced, so the loads of the batch are in flight together
+        constexpr int DIV_ZB = 4;
+        for (int kb = k0; kb < k1; kb += DIV_ZB) {
+            T fa[DIV_ZB][6];
+#pragma unroll
+            for (int z = 0; z < DIV_ZB; ++z) {
+                const int k = kb + z;
+                if (k < k1) {
+                    const int kp = (g.bc[2] == BC_PERIODIC && k + 1 == g.n[2]) ? 0 : k + 1;
+                    fa[z][0] = fu[vindex(g, 0, ip, j, k)];
+                    fa[z][1] = fu[vindex(g, 0, i, j, k)];
+                    fa[z][2] = fv[vindex(g, 1, i, jp, k)];
+                    fa[z][3] = fv[vindex(g, 1, i, j, k)];
+                    fa[z][4] = fw[vindex(g, 2, i, j, kp)];
+                    fa[z][5] = fw[vindex(g, 2, i, j, k)];
+                }
             }
-            const double bv = cell_solid(g, i, j, k) ? 0.0 : dv * inv_dt;
-            b[cindex(g, i, j, k)] = bv;
-            acc[0] += bv;
+#pragma unroll
+            for (int z = 0; z < DIV_ZB; ++z) {
+                const int k = kb + z;
+                if (k >= k1) break;
+                const int kp = (g.bc[2] == BC_PERIODIC && k + 1 == g.n[2]) ? 0 : k + 1;
+                // D of the stored F* (or increment) in the storage precision; in
+                // FP32 this is the increment, whose differences carry no
+                // cancellation against u
+                T dt_ = (fa[z][0] - fa[z][1]) * g_ih<T>(g, 0);
+                dt_ += (fa[z][2] - fa[z][3]) * g_ih<T>(g, 1);
+                dt_ += (fa[z][4] - fa[z][5]) * g_ih<T>(g, 2);
+                double dv = double(dt_);
+                if (with_u) {
+                    // the stored u itself: differences taken exactly in FP64
+                    double du =
+                        (double(u[vindex(g, 0, ip, j, k)]) - double(u[vindex(g, 0, i, j, k)])) *
+                        g.ih[0];
+                    du += (double(v[vindex(g, 1, i, jp, k)]) - double(v[vindex(g, 1, i, j, k)])) *
+                          g.ih[1];
+                    du += (double(w[vindex(g, 2, i, j, kp)]) - double(w[vindex(g, 2, i, j, k)])) *
+                          g.ih[2];
+                    dv += du;
+                }
+                const double bv = cell_solid(g, i, j, k) ? 0.0 : dv * inv_dt;
+                b[cindex(g, i, j, k)] = bv;
+                acc[0] += bv;
+            }
         }
     }
     write_partials<1>(acc, part + (s * g.ctas + blockIdx.x));

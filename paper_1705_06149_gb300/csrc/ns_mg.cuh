@@ -405,6 +405,30 @@ __device__ __forceinline__ void block_sum_mixed(A (&v)[NV], double (&out)[NV]) {
     }
 }
 
+// Sum over the CTA of per-warp FP64 values held by each warp's lane 0 (the
+// other lanes' values are ignored), valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_warps(const double (&v)[NV], double (&out)[NV]) {
+    __shared__ double sw_all[NSUB][NV][NWARPS];
+    double(&sm)[NV][NWARPS] = sw_all[sub_id()];
+    const int t = tid_flat();
+    const int lane = t & 31, warp = t >> 5;
+    sub_sync();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sm[q][warp] = v[q];
+    }
+    sub_sync();
+    if (t == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = 0.0;
+            for (int w = 0; w < NWARPS; ++w) x += sm[q][w];
+            out[q] = x;
+        }
+    }
+}
+
 // Writes this CTA's partials and returns whether it is the last CTA of the
 // state; the last one then holds the state's totals in thread 0.
 template <typename A, int NV>
@@ -1774,10 +1798,22 @@ __device__ __forceinline__ bool partials_arrive_ff(float (&v)[NF], const FF (&x)
                                                    int ctas, double (&total)[NF + NX]) {
     constexpr int NV = NF + NX;
     double bf[NF], bx[NX], dx[NX];
+    // the float-float sums: a warp tree in float-float arithmetic (the FP32
+    // pipe), each warp's sum converted to FP64 once, then summed over warps
+    // in FP64 (lane 0's value; the other lanes add zeros)
+    const int lane = tid_flat() & 31;
 #pragma unroll
-    for (int q = 0; q < NX; ++q) dx[q] = ff_to_double(x[q]);
+    for (int q = 0; q < NX; ++q) {
+        FF a = x[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const FF b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+            a = ff_add(a, b);
+        }
+        dx[q] = lane == 0 ? ff_to_double(a) : 0.0;
+    }
     block_sum_mixed<float, NF>(v, bf);
-    block_sum_mixed<double, NX>(dx, bx);
+    block_sum_warps<NX>(dx, bx);
     if (tid_flat() == 0) {
 #pragma unroll
         for (int q = 0; q < NF; ++q) part_state[(long long)blockIdx.x * NV + q] = bf[q];
@@ -1822,7 +1858,52 @@ __global__ void __launch_bounds__(NTHREADS)
     lev_origin(L, blockIdx.x, i, j, k0);
     SqAcc arr, abb;
     FF sp{0.0f, 0.0f}, sr{0.0f, 0.0f};
-    if (i < L.n[0] && j < L.n[1]) {
+    if (!FROM64 && i < L.n[0] && j < L.n[1]) {
+        // the warm start w in float-float: a batch of MG_ZB cells' loads (b,
+        // the 7-point values of both parts of w) before their arithmetic
+        const int k1 = min(k0 + L.tz, L.n[2]);
+        const NbrXY xy = make_nbr_xy(L, i, j);
+        const float* __restrict__ wh = f.w_hi + off;
+        const float* __restrict__ wl = f.w_lo + off;
+        for (int kb = k0; kb < k1; kb += MG_ZB) {
+            Vals7<float> hv[MG_ZB], lv[MG_ZB];
+            double bb[MG_ZB];
+            int ids[MG_ZB];
+            bool fl[MG_ZB];
+#pragma unroll
+            for (int u = 0; u < MG_ZB; ++u) {
+                if (kb + u < k1) {
+                    const Nbr nb = nbr_at(L, xy, kb + u);
+                    ids[u] = nb.c;
+                    fl[u] = lev_fluid(L, nb.c);
+                    bb[u] = b[nb.c];
+                    hv[u] = load7<float>(nb, wh);
+                    lv[u] = load7<float>(nb, wl);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < MG_ZB; ++u) {
+                if (kb + u < k1) {
+                    const int id = ids[u];
+                    const double bv = fl[u] ? bb[u] - mean : 0.0;
+                    const FF p0{hv[u].c, lv[u].c};
+                    const FF lp = ff_add_f(lap_ff_vals(L, hv[u]), lap_vals<float>(L, lv[u]));
+                    const FF res = ff_add(ff_from_double(bv), ff_neg(lp));
+                    f.p_hi[off + id] = p0.hi;
+                    f.p_lo[off + id] = p0.lo;
+                    f.r_hi[off + id] = res.hi;
+                    f.r_lo[off + id] = res.lo;
+                    r[id] = res.hi;
+                    rh[id] = res.hi;
+                    arr.add(res.hi);
+                    abb.add(float(bv));
+                    sp = ff_add(sp, p0);
+                    sr = ff_add(sr, res);
+                }
+            }
+        }
+    }
+    if (FROM64 && i < L.n[0] && j < L.n[1]) {
         const int k1 = min(k0 + L.tz, L.n[2]);
         const NbrXY xy = make_nbr_xy(L, i, j);
         for (int k = k0; k < k1; ++k) {
@@ -2034,38 +2115,81 @@ __global__ void __launch_bounds__(NTHREADS)
     int i, j, k0;
     tile_origin(g, blockIdx.x, g.fbx, g.fby, i, j, k0);
     const int k1 = min(k0 + g.tz, g.n[2] + 1);
-    for (int k = k0; k < k1; ++k) {
-        const int q3[3] = {i, j, k};
+    // a batch of CF_ZB planes' loads (F*, u, the pressure pairs on both sides
+    // of every active face, the cell's q) before their arithmetic, so the
+    // loads of the batch are in flight together; the arithmetic is the
+    // plane-by-plane march's
+    constexpr int CF_ZB = 4;
+    for (int kb = k0; kb < k1; kb += CF_ZB) {
+        float fa[CF_ZB][3], oa[CF_ZB][3], hb[CF_ZB][3], lb[CF_ZB][3];
+        float ha[CF_ZB], la[CF_ZB], qh[CF_ZB], ql[CF_ZB];
+        bool act[CF_ZB][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (i < g.ext[d][0] && j < g.ext[d][1] && k < g.ext[d][2]) {
-                const long long id = vindex(g, d, i, j, k);
-                if (!face_active_dev(g, d, q3)) {
-                    o3[d][id] = 0.0f;
-                } else {
+        for (int z = 0; z < CF_ZB; ++z) {
+            const int k = kb + z;
+            if (k >= k1) break;
+            const int q3[3] = {i, j, k};
+            bool any = false;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                act[z][d] = false;
+                if (i < g.ext[d][0] && j < g.ext[d][1] && k < g.ext[d][2] &&
+                    face_active_dev(g, d, q3)) {
+                    act[z][d] = true;
+                    any = true;
+                    const long long id = vindex(g, d, i, j, k);
                     int lo[3] = {i, j, k};
                     lo[d] = q3[d] == 0 ? g.n[d] - 1 : q3[d] - 1;
-                    const int a = cindex(g, i, j, k), b = cindex(g, lo[0], lo[1], lo[2]);
-                    const float dgp = ((ph[a] - ph[b]) + (pl[a] - pl[b])) * dtih[d];
-                    if (INCR)
-                        o3[d][id] = o3[d][id] + (f3[d][id] - dgp);
-                    else
-                        o3[d][id] = f3[d][id] - dgp;
+                    const int bq = cindex(g, lo[0], lo[1], lo[2]);
+                    fa[z][d] = f3[d][id];
+                    if (INCR) oa[z][d] = o3[d][id];
+                    hb[z][d] = ph[bq];
+                    lb[z][d] = pl[bq];
+                }
+            }
+            // an active face has its cell (i, j, k) in the grid
+            if (any || (i < g.n[0] && j < g.n[1] && k < g.n[2])) {
+                const int id = cindex(g, i, j, k);
+                ha[z] = ph[id];
+                la[z] = pl[id];
+                if (keep && i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+                    qh[z] = f.q_hi[off + id];
+                    ql[z] = f.q_lo[off + id];
                 }
             }
         }
-        if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
-            const int id = cindex(g, i, j, k);
-            const bool sol = cell_solid(g, i, j, k);
-            const FF pg = sol ? FF{0.0f, 0.0f} : ff_add(FF{ph[id], pl[id]}, ff_neg(mean));
-            if (p_out) p_out[off + id] = ff_to_double(pg);
-            if (keep) {
-                const FF q{f.q_hi[off + id], f.q_lo[off + id]};
-                const FF wn = ff_add(FF{2.0f * pg.hi, 2.0f * pg.lo}, ff_neg(q));
-                f.w_hi[off + id] = wn.hi;
-                f.w_lo[off + id] = wn.lo;
-                f.q_hi[off + id] = pg.hi;
-                f.q_lo[off + id] = pg.lo;
+#pragma unroll
+        for (int z = 0; z < CF_ZB; ++z) {
+            const int k = kb + z;
+            if (k >= k1) break;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (i < g.ext[d][0] && j < g.ext[d][1] && k < g.ext[d][2]) {
+                    const long long id = vindex(g, d, i, j, k);
+                    if (!act[z][d]) {
+                        o3[d][id] = 0.0f;
+                    } else {
+                        const float dgp = ((ha[z] - hb[z][d]) + (la[z] - lb[z][d])) * dtih[d];
+                        if (INCR)
+                            o3[d][id] = oa[z][d] + (fa[z][d] - dgp);
+                        else
+                            o3[d][id] = fa[z][d] - dgp;
+                    }
+                }
+            }
+            if (i < g.n[0] && j < g.n[1] && k < g.n[2]) {
+                const int id = cindex(g, i, j, k);
+                const bool sol = cell_solid(g, i, j, k);
+                const FF pg = sol ? FF{0.0f, 0.0f} : ff_add(FF{ha[z], la[z]}, ff_neg(mean));
+                if (p_out) p_out[off + id] = ff_to_double(pg);
+                if (keep) {
+                    const FF q{qh[z], ql[z]};
+                    const FF wn = ff_add(FF{2.0f * pg.hi, 2.0f * pg.lo}, ff_neg(q));
+                    f.w_hi[off + id] = wn.hi;
+                    f.w_lo[off + id] = wn.lo;
+                    f.q_hi[off + id] = pg.hi;
+                    f.q_lo[off + id] = pg.lo;
+                }
             }
         }
     }

@@ -38,6 +38,7 @@ int main(int argc, char** argv) {
         G.h[a] = 1.0 / G.n[a];
         G.ih[a] = 1.0 / G.h[a];
         G.ih2[a] = 1.0 / (G.h[a] * G.h[a]);
+        G.fih[a] = (float)G.ih[a];
     }
     const double dt = atof(argv[7]);
     for (int c = 0; c < 3; ++c)
@@ -81,7 +82,18 @@ int main(int argc, char** argv) {
     double sb = 0.0, bsum = 0.0;
     for (double x : part) sb += x;
     for (double x : b) bsum += x;
-    printf("partials %.17g %.17g\n", sb, bsum);
+    printf("partials %.17g %.17g", sb, bsum);
+    // the FP32 storage: F* rounded to FP32, b as the float-float product
+    std::vector<float> f32(in.begin(), in.begin() + nv);
+    std::vector<double> b32(G.cnt[3], -12345.0), part32((size_t)G.ctas, 0.0);
+    launch(G.ctas, [&] {
+        k_divergence<float>(G, f32.data(), f32.data() + G.cnt[0], f32.data() + G.cnt[0] + G.cnt[1],
+                            nullptr, nullptr, nullptr, b32.data(), part32.data(), 1.0 / dt);
+    });
+    double sb32 = 0.0, bsum32 = 0.0;
+    for (double x : part32) sb32 += x;
+    for (double x : b32) bsum32 += x;
+    printf(" %.17g %.17g\n", sb32, bsum32);
     SliceCtl ctl{};
     ctl.p_final = 0;
     for (long long q = 0; q < G.cnt[3]; ++q)
@@ -96,7 +108,8 @@ int main(int argc, char** argv) {
     f = fopen(argv[10], "wb");
     if (!f || fwrite(b.data(), sizeof(double), b.size(), f) != b.size() ||
         fwrite(vel.data(), sizeof(double), vel.size(), f) != vel.size() ||
-        fwrite(pout.data(), sizeof(double), pout.size(), f) != pout.size())
+        fwrite(pout.data(), sizeof(double), pout.size(), f) != pout.size() ||
+        fwrite(b32.data(), sizeof(double), b32.size(), f) != b32.size())
         return 5;
     fclose(f);
     return 0;

@@ -84,7 +84,7 @@ def test_divergence_and_correction_match_oracle(proj_emulator, dims, bc, masked)
             str(fsol) if masked else "-", str(fout)]
     r = subprocess.run(args, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, (r.returncode, r.stderr[-3000:])
-    _, sb, bsum = r.stdout.split()
+    _, sb, bsum, sb32, bsum32 = r.stdout.split()
     out = np.fromfile(fout, dtype=np.float64)
     nb = p.size
     b = out[:nb].reshape(p.shape)
@@ -99,7 +99,28 @@ def test_divergence_and_correction_match_oracle(proj_emulator, dims, bc, masked)
         o += fstar[c].size
         want = fstar[c] - dt * grad[c]
         assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want)), c
-    pout = out[o:].reshape(p.shape)
+    pout = out[o:o + nb].reshape(p.shape)
+    o += nb
+    # FP32 storage: the FP32 divergence of F* rounded to FP32 (the kernel's
+    # operations in its order), times 1/dt as a float-float product (~2^-48)
+    b32 = out[o:o + nb].reshape(p.shape)
+    f32 = [a.astype(np.float32) for a in fstar]
+    ih = [np.float32(n) for n in dims]
+
+    def fdiff(a, c):
+        ax = 2 - c
+        if bc[c] == "periodic":
+            return (np.roll(a, -1, axis=ax) - a).astype(np.float32)
+        return np.diff(a, axis=ax).astype(np.float32)
+
+    d32 = (fdiff(f32[0], 0) * ih[0]).astype(np.float32)
+    d32 = (d32 + (fdiff(f32[1], 1) * ih[1]).astype(np.float32)).astype(np.float32)
+    d32 = (d32 + (fdiff(f32[2], 2) * ih[2]).astype(np.float32)).astype(np.float32)
+    want_b32 = d32.astype(np.float64) * (1.0 / dt)
+    if masked:
+        want_b32[solid != 0] = 0.0
+    assert np.max(np.abs(b32 - want_b32)) <= 1e-13 * np.max(np.abs(want_b32))
+    assert abs(float(sb32) - float(bsum32)) <= 1e-13 * np.sum(np.abs(b32))
     fluid = np.ones(p.shape, bool) if solid is None else solid == 0
     want_p = np.where(fluid, p - p[fluid].mean(), 0.0)
     assert np.max(np.abs(pout - want_p)) <= 1e-13 * np.max(np.abs(want_p))
