@@ -377,7 +377,7 @@ constexpr size_t MG_CL_MAX_SMEM = 200 * 1024;
 bool setup_cluster(ns_grid* g, size_t elem, int cap, int sms) {
     for (int C = MG_CL_MAX_CTAS; C >= 2; C /= 2) {
         if (C > 2 && (long long)cap * C > sms) continue;
-        if (cl_plan(g->plan, C, elem, MG_CL_MAX_SMEM, g->cplan, g->cl_smem)) return true;
+        if (cl_plan(g->plan, C, MG_CL_THREADS, elem, MG_CL_MAX_SMEM, g->cplan, g->cl_smem)) return true;
     }
     return false;
 }

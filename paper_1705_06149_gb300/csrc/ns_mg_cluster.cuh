@@ -33,6 +33,20 @@ constexpr int MG_CL_THREADS = 512;
 constexpr int MG_CL_MAX_CTAS = 8;       // the portable cluster size
 constexpr long long MG_CL_SMALL = 512;  // slab levels at or below this size: rank 0 alone
 
+// A slab level's constants, computed on the host so that a phase starts
+// without an integer division: extents, plane size, x quads per row, planes
+// per owner; the work items of the sweep / prolongation (x quads of the
+// planes' rows) and of the restriction (x quads of row pairs) with the
+// threads per item group (nt / items, 0 with more items than threads); the
+// FP32 reciprocals of the item counts and of the quads per row, by which a
+// thread index or an item divides exactly (its + 1/2 stays below 2^22).
+struct ClLevC {
+    int nx, ny, nz, P, nq, pz;
+    int nit, git, nrt, grt;
+    float rit, rrt, rnq;
+    int px, py, pzp;
+};
+
 struct ClPlan {
     int J;  // first level (its right side comes from global memory, its result goes there)
     int R;  // first level of the one-CTA core in rank 0 (J < R)
@@ -44,6 +58,7 @@ struct ClPlan {
     // (planes per owner + 2 each); a core level's B and Y (one per cell)
     long long otab;
     long long ob[MG_MAX_LEVELS], oy[MG_MAX_LEVELS], oy2[MG_MAX_LEVELS];
+    ClLevC lc[MG_MAX_LEVELS];  // the slab levels' constants
 };
 
 // Byte offsets of the plan copies in shared memory.
@@ -65,7 +80,7 @@ inline size_t cl_align(size_t elems, size_t elem) {
 // and whose arrays fit max_bytes of shared memory.  The core levels must fit
 // the one-CTA core (MG_BLOCK_PER_THREAD cells per thread).  Returns false
 // where there is no such plan; else fills Q and the bytes it takes.
-inline bool cl_plan(const MgPlan& P, int C, size_t elem, size_t max_bytes, ClPlan& Q,
+inline bool cl_plan(const MgPlan& P, int C, int nt, size_t elem, size_t max_bytes, ClPlan& Q,
                     size_t& bytes) {
     const int nl = P.nlev;
     int R = nl - 1;
@@ -91,6 +106,23 @@ inline bool cl_plan(const MgPlan& P, int C, size_t elem, size_t max_bytes, ClPla
             const Lev& L = P.lev[m];
             split = split && splits(m);
             q.own[m] = split ? C : 1;
+            ClLevC& c = q.lc[m];
+            c.nx = L.n[0];
+            c.ny = L.n[1];
+            c.nz = L.n[2];
+            c.P = c.nx * c.ny;
+            c.nq = c.nx / 4;
+            c.pz = c.nz / q.own[m];
+            c.nit = c.nq * c.ny;
+            c.git = c.nit <= nt ? nt / c.nit : 0;
+            c.nrt = c.nq * (c.ny / 2);
+            c.grt = c.nrt <= nt ? nt / c.nrt : 0;
+            c.rit = 1.0f / (float)c.nit;
+            c.rrt = 1.0f / (float)c.nrt;
+            c.rnq = 1.0f / (float)c.nq;
+            c.px = L.bc[0] == BC_PERIODIC;
+            c.py = L.bc[1] == BC_PERIODIC;
+            c.pzp = L.bc[2] == BC_PERIODIC;
             const size_t slab =
                 cl_align((size_t)(L.n[2] / q.own[m] + 2) * L.n[0] * L.n[1], elem);
             q.ob[m] = (long long)o;
@@ -212,28 +244,42 @@ __device__ __forceinline__ T cl_wd_entry(const Lev& L, int c, T w) {
     return -neg_over<T>(w, d);
 }
 
-// A slab level as this CTA sees it: extents, x quads per row, planes per
-// owner and this CTA's first plane, periodic axes, whether it holds planes.
+// A slab level as CTA r sees it: the plan's constants, the first plane r
+// holds, whether it holds planes.
 struct ClLev {
     int nx, ny, nz, P, nq, pz, k0;
+    int nit, git, nrt, grt;
+    float rit, rrt, rnq;
     bool px, py, pzp, held;
 };
 
-__device__ __forceinline__ ClLev cl_lev(const Lev& L, int owners, int r) {
+__device__ __forceinline__ ClLev cl_lev(const ClLevC& c, int owners, int r) {
     ClLev v;
-    v.nx = L.n[0];
-    v.ny = L.n[1];
-    v.nz = L.n[2];
-    v.P = v.nx * v.ny;
-    v.nq = v.nx / 4;
-    v.pz = v.nz / owners;
-    v.k0 = owners > 1 ? r * v.pz : 0;
-    v.px = L.bc[0] == BC_PERIODIC;
-    v.py = L.bc[1] == BC_PERIODIC;
-    v.pzp = L.bc[2] == BC_PERIODIC;
+    v.nx = c.nx;
+    v.ny = c.ny;
+    v.nz = c.nz;
+    v.P = c.P;
+    v.nq = c.nq;
+    v.pz = c.pz;
+    v.k0 = owners > 1 ? r * c.pz : 0;
+    v.nit = c.nit;
+    v.git = c.git;
+    v.nrt = c.nrt;
+    v.grt = c.grt;
+    v.rit = c.rit;
+    v.rrt = c.rrt;
+    v.rnq = c.rnq;
+    v.px = c.px != 0;
+    v.py = c.py != 0;
+    v.pzp = c.pzp != 0;
     v.held = owners > 1 || r == 0;
     return v;
 }
+
+// Exact floor(x / d) for 0 <= x, x + 1/2 < 2^22, with rd = fl32(1 / d): the
+// product's relative error is below 2^-23 and x / d lies at least 1/(2d)
+// from the next integer.
+__device__ __forceinline__ int cl_div(int x, float rd) { return (int)((float(x) + 0.5f) * rd); }
 
 // Where the first and the last plane of an owner's slab go besides the slab
 // itself: the halo plane of the owner below / above (across a periodic seam
@@ -244,8 +290,8 @@ __device__ __forceinline__ ClLev cl_lev(const Lev& L, int owners, int r) {
 template <typename T>
 __device__ __forceinline__ void cl_halo_dst(T* local, const ClLev& vo, int owners, int owner,
                                             T*& lo, T*& hi) {
-    const int rl = owners > 1 ? (owner + owners - 1) % owners : owner;
-    const int ru = owners > 1 ? (owner + 1) % owners : owner;
+    const int rl = owners > 1 ? (owner > 0 ? owner - 1 : owners - 1) : owner;
+    const int ru = owners > 1 ? (owner + 1 < owners ? owner + 1 : 0) : owner;
     const int top = (vo.pz + 1) * vo.P;
     lo = (vo.k0 > 0 || vo.pzp) ? cl_map(local + top, (unsigned)rl) : cl_map(local, (unsigned)owner);
     hi = (vo.k0 + vo.pz < vo.nz || vo.pzp) ? cl_map(local, (unsigned)ru)
@@ -303,15 +349,15 @@ __device__ __forceinline__ Q4<T> cl_wd4(const T* wd, const ClLev& v, int a, int 
 
 // Work items of a level (x quads or x pairs of rows) spread over the CTA's
 // threads: with n <= nt items, G = nt / n threads share an item, taking the
-// planes g, g + G, ...; else thread t takes the items t, t + nt, ... and
-// every plane.
+// planes g, g + G, ...; else (G = 0) thread t takes the items t, t + nt, ...
+// and every plane.
 struct ClItems {
     int i0, is, p0, ps, n;
 };
 
-__device__ __forceinline__ ClItems cl_items(int n, int t, int nt) {
-    if (n <= nt) {
-        const int G = nt / n, g = t / n;
+__device__ __forceinline__ ClItems cl_items(int n, int G, float rn, int t, int nt) {
+    if (G > 0) {
+        const int g = cl_div(t, rn);
         return g < G ? ClItems{t - g * n, n, g, G, n} : ClItems{n, n, 0, 1, n};
     }
     return ClItems{t, nt, 0, 1, n};
@@ -322,9 +368,9 @@ __device__ __forceinline__ ClItems cl_items(int n, int t, int nt) {
 template <typename T>
 __device__ __forceinline__ void cl_sweep(const ClLev& v, const T* wd, const T* B, const T* Y,
                                          T* Y2, T* lo, T* hi, T w0, T w1, T w2, int t, int nt) {
-    const ClItems it = cl_items(v.nq * v.ny, t, nt);
+    const ClItems it = cl_items(v.nit, v.git, v.rit, t, nt);
     for (int item = it.i0; item < it.n; item += it.is) {
-        const int j = item / v.nq, a = item - j * v.nq;
+        const int j = cl_div(item, v.rnq), a = item - j * v.nq;
         const int xy = j * v.nx + 4 * a;
         int lx, hx, ly, hy;
         cl_qx(v, a, lx, hx);
@@ -354,11 +400,11 @@ template <typename T>
 __device__ __forceinline__ void cl_restrict(const ClLev& v, const ClLev& vc, const T* wdc,
                                             const T* B, const T* Y2, T* Bc, T* Yc, T* lo, T* hi,
                                             bool to_slab, T w0, T w1, T w2, int t, int nt) {
-    const int ncx = v.nx / 2, npair = v.nq, pzc = v.pz / 2, Kc0 = v.k0 / 2;
-    const int ncy = v.ny / 2, Pc = ncx * ncy;
-    const ClItems it = cl_items(npair * ncy, t, nt);
+    const int ncx = v.nx >> 1, pzc = v.pz >> 1, Kc0 = v.k0 >> 1;
+    const int ncy = v.ny >> 1, Pc = ncx * ncy;
+    const ClItems it = cl_items(v.nrt, v.grt, v.rrt, t, nt);
     for (int item = it.i0; item < it.n; item += it.is) {
-        const int Jc = item / npair, a = item - Jc * npair;
+        const int Jc = cl_div(item, v.rnq), a = item - Jc * v.nq;
         int lx, hx;
         cl_qx(v, a, lx, hx);
         int ly[2], hy[2];
@@ -407,9 +453,9 @@ __device__ __forceinline__ void cl_prolong(const ClLev& v, const Lev& Lc, const 
                                            int nzw, T* Y2, T* lo, T* hi, T* out, int t, int nt) {
     const int ncx = Lc.n[0], ncy = Lc.n[1], nzc = Lc.n[2], Pc = ncx * ncy;
     const bool xper = Lc.bc[0] == BC_PERIODIC;
-    const ClItems it = cl_items(v.nq * v.ny, t, nt);
+    const ClItems it = cl_items(v.nit, v.git, v.rit, t, nt);
     for (int item = it.i0; item < it.n; item += it.is) {
-        const int j = item / v.nq, a = item - j * v.nq;
+        const int j = cl_div(item, v.rnq), a = item - j * v.nq;
         const int xy = j * v.nx + 4 * a;
         // coarse x cells 2a-1 .. 2a+2 as offsets from 2a: clamped across a
         // wall, wrapped across a seam (fine cell 4a+c takes c0 = 2a + c/2 with
@@ -485,13 +531,13 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
         // level J (split): b and y1 = w b / d on the slab and its halo planes
         // from global memory; across a wall the halo plane repeats the
         // boundary plane's y1
-        const ClLev v = cl_lev(plan.lev[J], C, r);
+        const ClLev v = cl_lev(cp.lc[J], C, r);
         const T* wd = wdt + 27 * J;
         T* B = sm + cp.ob[J];
         T* Y = sm + cp.oy[J];
-        const ClItems it = cl_items(v.nq * v.ny, t, nt);
+        const ClItems it = cl_items(v.nit, v.git, v.rit, t, nt);
         for (int item = it.i0; item < it.n; item += it.is) {
-            const int j = item / v.nq, a = item - j * v.nq;
+            const int j = cl_div(item, v.rnq), a = item - j * v.nq;
             const int xy = j * v.nx + 4 * a;
 #pragma unroll 2
             for (int lp = it.p0; lp < v.pz + 2; lp += it.ps) {
@@ -522,7 +568,7 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
     for (int m = J; m < R; ++m) {
         const int owners = cp.own[m];
         const bool split = owners > 1;
-        const ClLev v = cl_lev(plan.lev[m], owners, r);
+        const ClLev v = cl_lev(cp.lc[m], owners, r);
         const Lev& L = plan.lev[m];
         const T w0 = lw<T>(L, 0), w1 = lw<T>(L, 1), w2 = lw<T>(L, 2);
         if (v.held) {
@@ -541,7 +587,7 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
             // the owner of this CTA's coarse planes: this CTA when the coarse
             // level splits too, else rank 0
             const unsigned dst = oc > 1 ? (unsigned)r : 0u;
-            const ClLev vc = cl_lev(plan.lev[m + 1], oc, (int)dst);
+            const ClLev vc = cl_lev(cp.lc[to_slab ? m + 1 : m], oc, (int)dst);
             T* Bc = cl_map(sm + cp.ob[m + 1], dst);
             T* Yc = nullptr;
             T *lo = nullptr, *hi = nullptr;
@@ -568,7 +614,7 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
         mg_block_core<T>(plan, R, bq, yq, (unsigned)t, (unsigned)nt);
         int m = R - 1;
         for (; m >= J && cp.own[m] == 1; --m) {
-            const ClLev v = cl_lev(plan.lev[m], 1, 0);
+            const ClLev v = cl_lev(cp.lc[m], 1, 0);
             const bool from_core = m + 1 == R;
             const T* e = from_core ? sm + cp.oy[R] : sm + cp.oy2[m + 1];
             cl_prolong<T>(v, plan.lev[m + 1], e, from_core ? 0 : 1, 0, sm + cp.oy2[m], nullptr,
@@ -592,7 +638,7 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
     // up through the split levels
     for (int m = R - 1; m >= J; --m) {
         if (cp.own[m] == 1) continue;
-        const ClLev v = cl_lev(plan.lev[m], C, r);
+        const ClLev v = cl_lev(cp.lc[m], C, r);
         const bool from_core = m + 1 == R;
         const bool from0 = from_core || cp.own[m + 1] == 1;
         // the coarse correction: rank 0's core level (slot z) or whole slab

@@ -49,7 +49,7 @@ static int run(const int n0[3], const int bcs[3], int C, int nt, const char* fin
         }
     ClPlan Q{};
     size_t bytes = 0;
-    if (!cl_plan(P, C, sizeof(T), 200 * 1024, Q, bytes)) {
+    if (!cl_plan(P, C, nt, sizeof(T), 200 * 1024, Q, bytes)) {
         fprintf(stderr, "no cluster plan\n");
         return 5;
     }
