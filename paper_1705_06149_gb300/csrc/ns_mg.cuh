@@ -1108,6 +1108,57 @@ __device__ __forceinline__ T blk_lap(const Lev& L, int pk, int q, const T* a) {
     return s;
 }
 
+// Jacobi sweeps on the coarsest level: enough for its size (a 2^3 level
+// needs few).
+__device__ __forceinline__ int mg_coarsest_sweeps(const Lev& L) {
+    const int nmax = max(L.n[0], max(L.n[1], L.n[2]));
+    return min(MG_COARSEST_SWEEPS, 4 * ((nmax + 1) / 2) * 2);
+}
+
+// The coarsest level when it has at most 32 cells: y = mg_coarsest_sweeps
+// damped-Jacobi sweeps from zero on L y = b by the 32 lanes of one warp (all
+// of them call it), lane t holding cell t; the neighbours' iterates come by
+// register shuffles, so the sweeps need no barrier (the same face terms as
+// blk_lap, in its order).
+template <typename T>
+__device__ __forceinline__ void mg_coarsest_warp(const Lev& L, const T* b, T* y, unsigned lane,
+                                                 T w) {
+    const bool own = lane < (unsigned)L.cells;
+    int c3[3] = {0, 0, 0};
+    if (own) lev_ijk(L, lev_rcp(L), lane, c3[0], c3[1], c3[2]);
+    const T wd = own ? blk_wd<T>(L, blk_pack(c3[0], c3[1], c3[2]), w) : T(0);
+    const int st[3] = {1, L.n[0], L.n[0] * L.n[1]};
+    int lo[3], hi[3];  // the neighbours' lanes
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int n = L.n[d];
+        const bool per = L.bc[d] == BC_PERIODIC;
+        lo[d] = (int)lane;
+        hi[d] = (int)lane;
+        if (own) {
+            lo[d] += c3[d] > 0 ? -st[d] : (per ? (n - 1) * st[d] : 0);
+            hi[d] += c3[d] + 1 < n ? st[d] : (per ? -(n - 1) * st[d] : 0);
+        }
+    }
+    const T bv = own ? b[lane] : T(0);
+    T v = T(0);
+    const int sweeps = mg_coarsest_sweeps(L);
+    for (int q = 0; q < sweeps; ++q) {
+        const T vc = v;
+        T sl = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const T vh = __shfl_sync(0xffffffffu, vc, hi[d]);
+            const T vl = __shfl_sync(0xffffffffu, vc, lo[d]);
+            const T wgt = lw<T>(L, d);
+            sl += (vh - vc) * wgt;
+            sl -= (vc - vl) * wgt;
+        }
+        v = vc + wd * (bv - sl);
+    }
+    if (own) y[lane] = v;
+}
+
 // V(2,0) cycle on the one-CTA levels lc .. nlev-1 held in shared memory: per
 // level m the right side bq[m] and the iterate yq[m].  On entry bq[lc] holds
 // the right side (visible to every thread); on exit yq[lc] holds the result
@@ -1200,52 +1251,14 @@ __device__ __forceinline__ void mg_block_core(const MgPlan& plan, int lc, T* con
     {
         const int m = nl - 1;
         const Lev& L = plan.lev[m];
-        cells_of(m);
-        // enough sweeps for the coarsest level's size; a 2^3 level needs few
-        const int nmax = max(L.n[0], max(L.n[1], L.n[2]));
-        const int sweeps = min(MG_COARSEST_SWEEPS, 4 * ((nmax + 1) / 2) * 2);
         if (L.cells <= 32) {
-            // at most 32 cells: warp 0 alone, lane t holding cell t; the
-            // neighbours' iterates come by register shuffles, so the sweeps
-            // need no barrier (the same face terms as blk_lap, in its order)
-            if (t < 32u) {
-                const bool own = t < (unsigned)L.cells;
-                const int c3[3] = {pk[0] & 1023, (pk[0] >> 10) & 1023, pk[0] >> 20};
-                const int st[3] = {1, L.n[0], L.n[0] * L.n[1]};
-                int lo[3], hi[3];  // the neighbours' lanes
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int n = L.n[d];
-                    const bool per = L.bc[d] == BC_PERIODIC;
-                    lo[d] = (int)t;
-                    hi[d] = (int)t;
-                    if (own) {
-                        lo[d] += c3[d] > 0 ? -st[d] : (per ? (n - 1) * st[d] : 0);
-                        hi[d] += c3[d] + 1 < n ? st[d] : (per ? -(n - 1) * st[d] : 0);
-                    }
-                }
-                const T bv = own ? bq[m][t] : T(0);
-                T y = T(0);
-                for (int q = 0; q < sweeps; ++q) {
-                    const T vc = y;
-                    T sl = T(0);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const T vh = __shfl_sync(0xffffffffu, vc, hi[d]);
-                        const T vl = __shfl_sync(0xffffffffu, vc, lo[d]);
-                        const T wgt = lw<T>(L, d);
-                        sl += (vh - vc) * wgt;
-                        sl -= (vc - vl) * wgt;
-                    }
-                    y = vc + wd[0] * (bv - sl);
-                }
-                if (own) yq[m][t] = y;
-            }
+            if (t < 32u) mg_coarsest_warp<T>(L, bq[m], yq[m], t, w);
             __syncthreads();
         } else {
+            cells_of(m);
             for (unsigned q = t; q < (unsigned)L.cells; q += nt) yq[m][q] = T(0);
             __syncthreads();
-            for (int q = 0; q < sweeps; ++q) sweep(m);
+            for (int q = 0; q < mg_coarsest_sweeps(L); ++q) sweep(m);
         }
     }
     // up: add the prolonged coarse correction

@@ -564,24 +564,35 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
     __syncthreads();
     cl_wait();
     // down through the slab levels: the split ones by the whole cluster
-    // (cluster barriers), then rank 0's (CTA barriers)
+    // (cluster barriers), then rank 0's (CTA barriers; a rank-0 level of at
+    // most 64 cells by warp 0 alone, with warp barriers)
+    auto level_sync = [&](bool split, bool tiny) {
+        if (split)
+            cl_sync();
+        else if (r == 0 && !tiny)
+            __syncthreads();
+        else if (r == 0 && t < 32)
+            __syncwarp();
+    };
     for (int m = J; m < R; ++m) {
         const int owners = cp.own[m];
         const bool split = owners > 1;
         const ClLev v = cl_lev(cp.lc[m], owners, r);
+        // a level of at most 64 cells has at most 16 (quad, plane) items: the
+        // CTA-wide grouping gives each its own thread of warp 0
+        const bool tiny = !split && v.P * v.nz <= 64;
+        const int ntl = tiny ? 32 : nt;
+        const bool work = v.held && t < ntl;
         const Lev& L = plan.lev[m];
         const T w0 = lw<T>(L, 0), w1 = lw<T>(L, 1), w2 = lw<T>(L, 2);
-        if (v.held) {
+        if (work) {
             T *lo, *hi;
             cl_halo_dst(sm + cp.oy2[m], v, owners, r, lo, hi);
             cl_sweep<T>(v, wdt + 27 * m, sm + cp.ob[m], sm + cp.oy[m], sm + cp.oy2[m], lo, hi,
-                        w0, w1, w2, t, nt);
+                        w0, w1, w2, t, ntl);
         }
-        if (split)
-            cl_sync();
-        else if (r == 0)
-            __syncthreads();
-        if (v.held) {
+        level_sync(split, tiny);
+        if (work) {
             const bool to_slab = m + 1 < R;
             const int oc = to_slab ? cp.own[m + 1] : 1;
             // the owner of this CTA's coarse planes: this CTA when the coarse
@@ -596,31 +607,49 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
                 cl_halo_dst(sm + cp.oy[m + 1], vc, oc, (int)dst, lo, hi);
             }
             cl_restrict<T>(v, vc, wdt + 27 * (m + 1), sm + cp.ob[m], sm + cp.oy2[m], Bc, Yc, lo,
-                           hi, to_slab, w0, w1, w2, t, nt);
+                           hi, to_slab, w0, w1, w2, t, ntl);
         }
-        if (split)
-            cl_sync();
-        else if (r == 0)
-            __syncthreads();
+        level_sync(split, tiny);
     }
     if (r == 0) {
-        // the core levels, then up through rank 0's slab levels
-        T* bq[MG_MAX_LEVELS];
-        T* yq[MG_MAX_LEVELS];
-        for (int m = R; m < plan.nlev; ++m) {
-            bq[m] = sm + cp.ob[m];
-            yq[m] = sm + cp.oy[m];
+        // the core levels (the coarsest alone, when it has at most 32 cells:
+        // warp 0 with register shuffles), then up through rank 0's slab
+        // levels, each after the barrier its predecessor's writers need
+        if (R == plan.nlev - 1 && plan.lev[R].cells <= 32) {
+            if (t < 32) {
+                __syncwarp();
+                mg_coarsest_warp<T>(plan.lev[R], sm + cp.ob[R], sm + cp.oy[R], (unsigned)t,
+                                    T(MG_OMEGA));
+            }
+        } else {
+            __syncthreads();
+            T* bq[MG_MAX_LEVELS];
+            T* yq[MG_MAX_LEVELS];
+            for (int m = R; m < plan.nlev; ++m) {
+                bq[m] = sm + cp.ob[m];
+                yq[m] = sm + cp.oy[m];
+            }
+            mg_block_core<T>(plan, R, bq, yq, (unsigned)t, (unsigned)nt);
         }
-        mg_block_core<T>(plan, R, bq, yq, (unsigned)t, (unsigned)nt);
         int m = R - 1;
         for (; m >= J && cp.own[m] == 1; --m) {
             const ClLev v = cl_lev(cp.lc[m], 1, 0);
+            const bool tiny = v.P * v.nz <= 64;
             const bool from_core = m + 1 == R;
             const T* e = from_core ? sm + cp.oy[R] : sm + cp.oy2[m + 1];
-            cl_prolong<T>(v, plan.lev[m + 1], e, from_core ? 0 : 1, 0, sm + cp.oy2[m], nullptr,
-                          nullptr, m == J ? out : nullptr, t, nt);
-            __syncthreads();
+            if (tiny) {
+                if (t < 32) {
+                    __syncwarp();
+                    cl_prolong<T>(v, plan.lev[m + 1], e, from_core ? 0 : 1, 0, sm + cp.oy2[m],
+                                  nullptr, nullptr, m == J ? out : nullptr, t, 32);
+                }
+            } else {
+                __syncthreads();
+                cl_prolong<T>(v, plan.lev[m + 1], e, from_core ? 0 : 1, 0, sm + cp.oy2[m], nullptr,
+                              nullptr, m == J ? out : nullptr, t, nt);
+            }
         }
+        __syncthreads();
         // the split level above reads the correction of the level below it
         // whole: a copy into every CTA, so that those reads stay local
         {
@@ -661,15 +690,13 @@ __device__ __forceinline__ void mg_cluster_levels(const MgPlan& plan, const ClPl
 // One cluster of cp.C CTAs per state (blockIdx.y).  Each CTA copies both
 // plans into the start of its shared memory (the level loops read them from
 // there, not from the kernel parameters) and fills the Jacobi weight tables
-// of the slab levels.
+// of the slab levels, then waits for the preceding kernel.
 template <typename T>
 __global__ void __launch_bounds__(MG_CL_THREADS)
     k_mg_cluster(const __grid_constant__ MgPlan plan, const __grid_constant__ ClPlan cp,
                  SliceCtl* __restrict__ ctl, const T* __restrict__ in, T* __restrict__ out) {
-    pdl_wait();
-    const long long s = blockIdx.y;
-    // the whole cluster returns together: the flag is the state's
-    if (ctl[s].status != ST_ITER) return;
+    // the prologue reads the kernel parameters only, so under a programmatic
+    // dependency it runs before the wait for the preceding kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int t = (int)threadIdx.x, nt = (int)blockDim.x;
     {
@@ -687,6 +714,10 @@ __global__ void __launch_bounds__(MG_CL_THREADS)
         wdt[27 * m + c] = cl_wd_entry<T>(plan.lev[m], c, w);
     }
     __syncthreads();
+    pdl_wait();
+    const long long s = blockIdx.y;
+    // the whole cluster returns together: the flag is the state's
+    if (ctl[s].status != ST_ITER) return;
     const MgPlan& sp = *reinterpret_cast<const MgPlan*>(smem_raw);
     const ClPlan& sc = *reinterpret_cast<const ClPlan*>(smem_raw + CL_OFF_CP);
     const long long cells = sp.lev[sc.J].cells;

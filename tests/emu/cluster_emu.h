@@ -54,6 +54,8 @@ std::vector<unsigned char*> emu_cl_smem;
 std::barrier<>* emu_warp_barrier[32];
 
 inline void __syncthreads() { emu_cta_barrier->arrive_and_wait(); }
+// a barrier over the caller's warp (only rank 0's warps use the warp barriers)
+inline void __syncwarp() { emu_warp_barrier[threadIdx.x / 32]->arrive_and_wait(); }
 
 inline unsigned cl_rank() { return (unsigned)emu_rank; }
 inline void cl_sync() { emu_cl_barrier->arrive_and_wait(); }

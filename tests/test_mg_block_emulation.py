@@ -85,6 +85,8 @@ def _kernel_source() -> str:
         _extract(mg, r"^__device__ __forceinline__ int blk_pack\("),
         _extract(mg, r"^__device__ __forceinline__ T blk_wd\("),
         _extract(mg, r"^__device__ __forceinline__ T blk_lap\("),
+        _extract(mg, r"^__device__ __forceinline__ int mg_coarsest_sweeps\("),
+        _extract(mg, r"^__device__ __forceinline__ void mg_coarsest_warp\("),
         _extract(mg, r"^__device__ __forceinline__ void mg_block_core\("),
         _extract(mg, r"^__device__ __forceinline__ void mg_block_levels\("),
         _extract(mg, r"^    k_mg_block\("),
