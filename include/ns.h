@@ -95,10 +95,20 @@ typedef struct {
                                 0: 8.  Results depend on it at rounding level (it
                                 fixes the order of the per-state reductions).       */
     int parareal_chunk;      /* ns_parareal_iterate: slices per chunk of the fine
-                                sweep (> 0); the coarse chain of a chunk's slices
-                                runs on a second stream while the next chunk's fine
-                                sweep runs.  <= 0: one sweep over all slices, then
-                                the chain.  Results are bit-identical either way.  */
+                                sweep (> 0).  With the multigrid solver the chunks'
+                                sweeps and coarse chains are graph launches
+                                pipelined across the iterations of one call: the
+                                sweep of chunk c in iteration k+1 starts once the
+                                chain of iteration k has passed chunk c, and the
+                                chain (on a high-priority stream) runs under the
+                                sweeps; with plain BiCGStab the chain of chunk c
+                                overlaps the sweep of chunk c+1 of the same
+                                iteration.  0: automatic -- two chunks, pipelined,
+                                when a call runs >= 2 iterations of >= 4 slices with
+                                the multigrid solver (and no per-launch timing, no
+                                persistent coarse solves), else one sweep.  < 0:
+                                always one sweep over all slices, then the chain.
+                                Results are bit-identical in every case.           */
     int predict_tile_y;      /* tile of the predictor (grids without solid cells): */
     int predict_tile_z;      /* 32 x predict_tile_y x predict_tile_z cells, one
                                 thread per (x, y) column marching z; (y, z) one of

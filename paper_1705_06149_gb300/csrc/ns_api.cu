@@ -190,6 +190,16 @@ struct ns_grid {
     std::vector<cudaGraph_t> chunk_graph;
     std::vector<cudaGraphExec_t> chunk_exec;
     int chunk_key = 0;
+    // the fine sweep of each chunk of the pipelined schedule (S steps of the
+    // chunk's slices in pr_f) as a graph of its own
+    std::vector<cudaGraph_t> swc_graph;
+    std::vector<cudaGraphExec_t> swc_exec;
+    int swc_key_chunk = 0, swc_key_n = 0, swc_key_s = 0;
+    double swc_key_dt = 0.0;
+    const void* swc_key_f = nullptr;
+    // pinned host slots for the defects of the iterations of one call
+    double* h_defects = nullptr;
+    int h_defects_cap = 0;
     std::vector<void*> allocs;
 };
 
@@ -217,8 +227,11 @@ void free_all(ns_grid* g) {
     g->allocs.clear();
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
     if (g->h_defect) cudaFreeHost(g->h_defect);
+    if (g->h_defects) cudaFreeHost(g->h_defects);
     g->h_ctl = nullptr;
     g->h_defect = nullptr;
+    g->h_defects = nullptr;
+    g->h_defects_cap = 0;
 }
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
@@ -1448,21 +1461,24 @@ long long mg_iteration_launches(const ns_grid* g) {
     return 2 * apply + 3;
 }
 
-// After graph launches of `steps` fine steps per state of a batch-B grid have
-// completed: adds the work the device counters show since `seen_*` to the
+// After graph launches that took `state_steps` state-steps in `step_groups`
+// batched fine steps have completed on the first B states of the grid's
+// workspace: adds the work the device counters show since `seen_*` to the
 // grid's ns_stats (plus extra_launches kernels outside the steps) and reports
 // (then clears) a failed solve.
-ns_status account_graph(ns_grid* g, int B, long long steps, long long extra_launches,
-                        LoopCount& seen_lc, SliceCtl* seen_ctl, const std::string& what) {
+ns_status account_graph(ns_grid* g, int B, long long state_steps, long long step_groups,
+                        long long extra_launches, LoopCount& seen_lc, SliceCtl* seen_ctl,
+                        const std::string& what) {
     LoopCount lc{};
     std::vector<SliceCtl> ctl(B);
     NS_CUDA(cudaMemcpy(&lc, g->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
     NS_CUDA(cudaMemcpy(ctl.data(), g->ctl, sizeof(SliceCtl) * B, cudaMemcpyDeviceToHost));
     const long long bodies = (long long)(lc.inner_total - seen_lc.inner_total);
-    g->stats.steps += steps * B;
+    g->stats.steps += state_steps;
     // per step: predict, divergence, solve start, loop condition, correction;
     // per loop body: one iteration, (FP32) the outer correction, the condition
-    g->stats.launches += steps * 5 + bodies * (mg_iteration_launches(g) + (g->fp32 ? 2 : 1)) +
+    g->stats.launches += step_groups * 5 +
+                         bodies * (mg_iteration_launches(g) + (g->fp32 ? 2 : 1)) +
                          extra_launches;
     ns_status result = NS_OK;
     for (int s = 0; s < B; ++s) {
@@ -1564,102 +1580,6 @@ ns_status ensure_chain_graph(ns_grid* g, const void* ys, int N, int M, double dt
     g->chain_key_dt = dtc;
     NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
     NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
-    return NS_OK;
-}
-
-// One chunked iteration with every chunk's chain a graph launch: the copies
-// of all slices first, then per chunk its sweep (this thread, polling the
-// solves) and its chain (a graph on the companion's stream, after the
-// chunk's sweep), so the chain of chunk c runs while chunk c+1 is swept.  The
-// chain of chunk c writes y_{n+1} of the next chunk's first slice, which the
-// up-front copy has already taken.
-template <typename T>
-ns_status parareal_iteration_chunked_graphs(ns_grid* g, ns_state slices, int N, int S, int M,
-                                            double dt, int chunk, double* defect) {
-    const Geo& G = g->geo;
-    const int C = (N + chunk - 1) / chunk;
-    ns_grid* h = g->chain;
-    void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
-    const double dtc = dt * S / M;
-    ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
-    const bool same = (int)g->chunk_exec.size() == C && g->chunk_key == chunk &&
-                      g->chain_key_ys == ys[0] && g->chain_key_f == g->pr_f[0] &&
-                      g->chain_key_n == N && g->chain_key_m == M && g->chain_key_dt == dtc;
-    if (!same) {
-        for (cudaGraphExec_t e : g->chunk_exec) cudaGraphExecDestroy(e);
-        for (cudaGraph_t c : g->chunk_graph) cudaGraphDestroy(c);
-        g->chunk_exec.clear();
-        g->chunk_graph.clear();
-        // the whole-chain graph shares the key fields: drop it too
-        if (g->chain_exec) cudaGraphExecDestroy(g->chain_exec);
-        if (g->chain_graph) cudaGraphDestroy(g->chain_graph);
-        g->chain_exec = nullptr;
-        g->chain_graph = nullptr;
-        for (cudaStream_t& cs : g->chain_cap)
-            if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        NS_CUDA(cudaStreamSynchronize(h->stream));
-        for (int c = 0; c < C; ++c) {
-            cudaGraph_t gr;
-            cudaGraphExec_t ex;
-            const int n1 = std::min(N, (c + 1) * chunk);
-            NS_TRY(capture_exec(
-                h, g->chain_cap[0], g->chain_cap[1],
-                [&]() -> ns_status {
-                    for (int n = c * chunk; n < n1; ++n) {
-                        NS_TRY(copy_states<T>(h, g->pr_g, ys, 0, n, 1));
-                        NS_TRY(step_impl<T>(h, gs, dtc, M));
-                        NS_TRY(parareal_update<T>(h, g->pr_f, g->pr_g, g->pr_gold, ys, n, n,
-                                                  n + 1));
-                    }
-                    return NS_OK;
-                },
-                &gr, &ex));
-            g->chunk_graph.push_back(gr);
-            g->chunk_exec.push_back(ex);
-        }
-        g->chunk_key = chunk;
-        g->chain_key_ys = ys[0];
-        g->chain_key_f = g->pr_f[0];
-        g->chain_key_n = N;
-        g->chain_key_m = M;
-        g->chain_key_dt = dtc;
-        NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount),
-                           cudaMemcpyDeviceToHost));
-        NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
-    }
-    while ((int)g->pipe_ev.size() < C + 2) {
-        cudaEvent_t e;
-        NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        g->pipe_ev.push_back(e);
-    }
-    cudaEvent_t ev_start = g->pipe_ev[0], ev_end = g->pipe_ev[1];
-    cudaEvent_t* ev_swept = g->pipe_ev.data() + 2;
-    NS_TRY(copy_states<T>(g, g->pr_f, ys, 0, 0, N));
-    NS_CUDA(cudaEventRecord(ev_start, g->stream));
-    NS_CUDA(cudaStreamWaitEvent(h->stream, ev_start, 0));
-    NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
-    for (int c = 0; c < C; ++c) {
-        const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
-        ns_state fb{(char*)g->pr_f[0] + (size_t)n0 * G.cnt[0] * sizeof(T),
-                    (char*)g->pr_f[1] + (size_t)n0 * G.cnt[1] * sizeof(T),
-                    (char*)g->pr_f[2] + (size_t)n0 * G.cnt[2] * sizeof(T),
-                    (char*)g->pr_f[3] + (size_t)n0 * G.cnt[3] * sizeof(double), m};
-        NS_TRY(step_impl<T>(g, fb, dt, S));
-        NS_CUDA(cudaEventRecord(ev_swept[c], g->stream));
-        NS_CUDA(cudaStreamWaitEvent(h->stream, ev_swept[c], 0));
-        NS_CUDA(cudaGraphLaunch(g->chunk_exec[c], h->stream));
-    }
-    NS_CUDA(cudaMemcpyAsync(h->h_defect, h->d_defect, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, h->stream));
-    NS_CUDA(cudaEventRecord(ev_end, h->stream));
-    NS_CUDA(cudaStreamWaitEvent(g->stream, ev_end, 0));
-    NS_TRY(sync_stream(g));
-    const ns_stats chain0 = h->stats;
-    const ns_status st = account_graph(h, 1, (long long)N * M, 4LL * N, g->chain_seen_lc,
-                                       &g->chain_seen_ctl, "ns_parareal_iterate");
-    merge_chain_stats(g, chain0);
-    NS_TRY(st);
-    std::memcpy(defect, h->h_defect, sizeof(double));
     return NS_OK;
 }
 
@@ -1790,11 +1710,18 @@ ns_status parareal_iteration_chunked(ns_grid* g, ns_state slices, int N, int S, 
     return NS_OK;
 }
 
+// Drops the graphs of the whole sweep and of the chunks' sweeps (they share
+// the capture streams and the accounting baseline).
 void drop_sweep_graph(ns_grid* g) {
     if (g->sweep_exec) cudaGraphExecDestroy(g->sweep_exec);
     if (g->sweep_graph) cudaGraphDestroy(g->sweep_graph);
     g->sweep_exec = nullptr;
     g->sweep_graph = nullptr;
+    for (cudaGraphExec_t e : g->swc_exec) cudaGraphExecDestroy(e);
+    for (cudaGraph_t c : g->swc_graph) cudaGraphDestroy(c);
+    g->swc_exec.clear();
+    g->swc_graph.clear();
+    g->swc_key_chunk = 0;
 }
 
 // The fine sweep F(y^k_n) of all N slices (S steps of dt, in place in pr_f)
@@ -1823,6 +1750,231 @@ ns_status sweep_launch(ns_grid* g, int N, int S, double dt) {
                            cudaMemcpyDeviceToHost));
     }
     NS_CUDA(cudaGraphLaunch(g->sweep_exec, g->stream));
+    return NS_OK;
+}
+
+// The chain of each chunk of `chunk` slices (copy of y_n, M coarse steps, the
+// update of Eq. 6 for every slice of the chunk) as a graph of its own on the
+// companion, captured on first use.
+template <typename T>
+ns_status ensure_chunk_chains(ns_grid* g, ns_state slices, int N, int M, double dtc,
+                              int chunk) {
+    const int C = (N + chunk - 1) / chunk;
+    ns_grid* h = g->chain;
+    void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
+    ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
+    if ((int)g->chunk_exec.size() == C && g->chunk_key == chunk && g->chain_key_ys == ys[0] &&
+        g->chain_key_f == g->pr_f[0] && g->chain_key_n == N && g->chain_key_m == M &&
+        g->chain_key_dt == dtc)
+        return NS_OK;
+    for (cudaGraphExec_t e : g->chunk_exec) cudaGraphExecDestroy(e);
+    for (cudaGraph_t c : g->chunk_graph) cudaGraphDestroy(c);
+    g->chunk_exec.clear();
+    g->chunk_graph.clear();
+    // the whole-chain graph shares the key fields: drop it too
+    if (g->chain_exec) cudaGraphExecDestroy(g->chain_exec);
+    if (g->chain_graph) cudaGraphDestroy(g->chain_graph);
+    g->chain_exec = nullptr;
+    g->chain_graph = nullptr;
+    g->chunk_key = 0;
+    for (cudaStream_t& cs : g->chain_cap)
+        if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    NS_CUDA(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < C; ++c) {
+        cudaGraph_t gr;
+        cudaGraphExec_t ex;
+        const int n1 = std::min(N, (c + 1) * chunk);
+        NS_TRY(capture_exec(
+            h, g->chain_cap[0], g->chain_cap[1],
+            [&]() -> ns_status {
+                for (int n = c * chunk; n < n1; ++n) {
+                    NS_TRY(copy_states<T>(h, g->pr_g, ys, 0, n, 1));
+                    NS_TRY(step_impl<T>(h, gs, dtc, M));
+                    NS_TRY(parareal_update<T>(h, g->pr_f, g->pr_g, g->pr_gold, ys, n, n, n + 1));
+                }
+                return NS_OK;
+            },
+            &gr, &ex, g->chain_pdl));
+        g->chunk_graph.push_back(gr);
+        g->chunk_exec.push_back(ex);
+    }
+    g->chunk_key = chunk;
+    g->chain_key_ys = ys[0];
+    g->chain_key_f = g->pr_f[0];
+    g->chain_key_n = N;
+    g->chain_key_m = M;
+    g->chain_key_dt = dtc;
+    NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
+    NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
+    return NS_OK;
+}
+
+// The fine sweep of each chunk (S steps of dt of the chunk's slices, in
+// place in pr_f) as a graph of its own, captured on first use.  Every chunk
+// uses the first states of this grid's workspace, so the chunks' sweeps run
+// one after another on this grid's stream.
+template <typename T>
+ns_status ensure_chunk_sweeps(ns_grid* g, int N, int S, double dt, int chunk) {
+    const Geo& G = g->geo;
+    const int C = (N + chunk - 1) / chunk;
+    if ((int)g->swc_exec.size() == C && g->swc_key_chunk == chunk && g->swc_key_n == N &&
+        g->swc_key_s == S && g->swc_key_dt == dt && g->swc_key_f == g->pr_f[0])
+        return NS_OK;
+    drop_sweep_graph(g);
+    for (cudaStream_t& cs : g->sweep_cap)
+        if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    NS_TRY(sync_stream(g));
+    for (int c = 0; c < C; ++c) {
+        const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
+        ns_state fb{(char*)g->pr_f[0] + (size_t)n0 * G.cnt[0] * sizeof(T),
+                    (char*)g->pr_f[1] + (size_t)n0 * G.cnt[1] * sizeof(T),
+                    (char*)g->pr_f[2] + (size_t)n0 * G.cnt[2] * sizeof(T),
+                    (char*)g->pr_f[3] + (size_t)n0 * G.cnt[3] * sizeof(double), m};
+        cudaGraph_t gr;
+        cudaGraphExec_t ex;
+        NS_TRY(capture_exec(g, g->sweep_cap[0], g->sweep_cap[1],
+                            [&]() -> ns_status { return step_impl<T>(g, fb, dt, S); }, &gr,
+                            &ex));
+        g->swc_graph.push_back(gr);
+        g->swc_exec.push_back(ex);
+    }
+    g->swc_key_chunk = chunk;
+    g->swc_key_n = N;
+    g->swc_key_s = S;
+    g->swc_key_dt = dt;
+    g->swc_key_f = g->pr_f[0];
+    g->sweep_seen_ctl.assign(g->cap, SliceCtl{});
+    NS_CUDA(cudaMemcpy(&g->sweep_seen_lc, g->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
+    NS_CUDA(cudaMemcpy(g->sweep_seen_ctl.data(), g->ctl, sizeof(SliceCtl) * g->cap,
+                       cudaMemcpyDeviceToHost));
+    return NS_OK;
+}
+
+// Up to kmax Parareal iterations with the fine sweep in chunks of `chunk`
+// slices, pipelined across iterations.  SW(k, c), the sweep of chunk c in
+// iteration k, needs y^{k-1}_n of the chunk's slices, which the chain of
+// chunk c in iteration k-1, CH(k-1, c), writes (and that chain must have
+// consumed the F values SW(k, c) overwrites); CH(k, c) needs SW(k, c) and
+// CH(k, c-1).  So the sweep of chunk 0 of the next iteration starts as soon
+// as the chain has passed chunk 0, while the chain works through the later
+// chunks: the sweeps run one after another on this grid's stream, the chains
+// on the companion's high-priority stream, and the serial chain hides under
+// the sweeps.  Every state is computed by the same kernels in the same order
+// as in the unpipelined iteration (a slice's reductions do not depend on the
+// batch), so results are bit-identical.  The sweep of chunk 0 of iteration
+// k+1 is issued before the defect of iteration k is known (it writes only
+// pr_f, never the slices); with tol > 0 the host waits for each iteration's
+// defect before it issues the next iteration's chains.
+template <typename T>
+ns_status parareal_pipelined(ns_grid* g, ns_state slices, int N, int S, int M, double dt,
+                             int chunk, int kmax, double tol, int* k_out, double* defects) {
+    const int C = (N + chunk - 1) / chunk;
+    ns_grid* h = g->chain;
+    void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
+    const double dtc = dt * S / M;
+    NS_TRY(ensure_chunk_chains<T>(g, slices, N, M, dtc, chunk));
+    NS_TRY(ensure_chunk_sweeps<T>(g, N, S, dt, chunk));
+    while ((int)g->pipe_ev.size() < 2 + 3 * C + 2) {
+        cudaEvent_t e;
+        NS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g->pipe_ev.push_back(e);
+    }
+    if (g->h_defects_cap < kmax) {
+        if (g->h_defects) cudaFreeHost(g->h_defects);
+        g->h_defects = nullptr;
+        g->h_defects_cap = 0;
+        NS_CUDA(cudaMallocHost((void**)&g->h_defects, sizeof(double) * kmax));
+        g->h_defects_cap = kmax;
+    }
+    cudaEvent_t* ev_copied = g->pipe_ev.data() + 2;
+    cudaEvent_t* ev_swept = ev_copied + C;
+    cudaEvent_t* ev_chained = ev_swept + C;
+    cudaEvent_t ev_start = ev_chained[C], ev_defect = ev_chained[C + 1];
+    const ns_stats chain0 = h->stats;
+    long long swept_states = 0, sweeps = 0;
+    int k = 0;
+
+    auto sweep = [&](int kk, int c) -> ns_status {
+        const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
+        // y^{kk-1} of the chunk is written and its F values consumed
+        if (kk > 0) NS_CUDA(cudaStreamWaitEvent(g->stream, ev_chained[c], 0));
+        NS_TRY(copy_states<T>(g, g->pr_f, ys, n0, n0, m));
+        NS_CUDA(cudaEventRecord(ev_copied[c], g->stream));
+        NS_CUDA(cudaGraphLaunch(g->swc_exec[c], g->stream));
+        NS_CUDA(cudaEventRecord(ev_swept[c], g->stream));
+        swept_states += m;
+        sweeps += 1;
+        return NS_OK;
+    };
+    auto chain = [&](int kk, int c) -> ns_status {
+        NS_CUDA(cudaStreamWaitEvent(h->stream, ev_swept[c], 0));
+        // the chain of chunk c writes y of the next chunk's first slice: after
+        // that chunk has copied its inputs
+        if (c + 1 < C) NS_CUDA(cudaStreamWaitEvent(h->stream, ev_copied[c + 1], 0));
+        if (c == 0)
+            NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
+        NS_CUDA(cudaGraphLaunch(g->chunk_exec[c], h->stream));
+        NS_CUDA(cudaEventRecord(ev_chained[c], h->stream));
+        if (c == C - 1) {
+            NS_CUDA(cudaMemcpyAsync(g->h_defects + kk, h->d_defect, sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream));
+            NS_CUDA(cudaEventRecord(ev_defect, h->stream));
+        }
+        return NS_OK;
+    };
+    // issue order: SW(k, c) before CH(k, c - 1) (which waits for its copy),
+    // CH(k, c) before SW(k + 1, c) (which waits for it); an event wait takes
+    // the event's latest record at the time it is issued
+    auto issue = [&]() -> ns_status {
+        NS_CUDA(cudaEventRecord(ev_start, g->stream));
+        NS_CUDA(cudaStreamWaitEvent(h->stream, ev_start, 0));
+        NS_TRY(sweep(0, 0));
+        for (; k < kmax; ++k) {
+            if (tol > 0.0 && k > 0) {
+                // the defect of iteration k - 1 decides whether iteration k runs
+                NS_CUDA(cudaEventSynchronize(ev_defect));
+                const double dk = g->h_defects[k - 1];
+                if (!std::isfinite(dk) || dk <= tol) break;
+            }
+            for (int c = 1; c < C; ++c) {
+                NS_TRY(sweep(k, c));
+                NS_TRY(chain(k, c - 1));
+            }
+            NS_TRY(chain(k, C - 1));
+            if (k + 1 < kmax) NS_TRY(sweep(k + 1, 0));
+        }
+        return NS_OK;
+    };
+    const ns_status st_issue = issue();
+    const std::string err_issue = g_last_error;
+    // the slices are written by the chain: later work on this stream waits for it
+    const cudaError_t e1 = cudaEventRecord(ev_start, h->stream);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(g->stream, ev_start, 0) : e1;
+    const cudaError_t e3 = cudaStreamSynchronize(g->stream);
+    const cudaError_t e4 = cudaStreamSynchronize(h->stream);
+    if (st_issue != NS_OK) return fail(st_issue, err_issue);
+    for (cudaError_t e : {e2, e3, e4})
+        if (e != cudaSuccess)
+            return fail(NS_ERR_CUDA, std::string("pipelined Parareal: ") + cudaGetErrorString(e));
+    // the work of every launch, and a failed solve, from the device counters
+    const ns_status st_f = account_graph(g, std::min(N, chunk), swept_states * S, sweeps * S, 0,
+                                        g->sweep_seen_lc, g->sweep_seen_ctl.data(),
+                                        "ns_parareal_iterate (fine sweep)");
+    const std::string err_f = g_last_error;
+    const ns_status st_c = account_graph(h, 1, (long long)k * N * M, (long long)k * N * M,
+                                        4LL * N * k, g->chain_seen_lc, &g->chain_seen_ctl,
+                                        "ns_parareal_iterate");
+    merge_chain_stats(g, chain0);
+    if (st_f != NS_OK) return fail(st_f, err_f);
+    NS_TRY(st_c);
+    for (int i = 0; i < k; ++i) {
+        if (defects) defects[i] = g->h_defects[i];
+        if (!std::isfinite(g->h_defects[i])) {
+            *k_out = i + 1;
+            return fail(NS_ERR_NONFINITE, "non-finite Parareal defect");
+        }
+    }
+    *k_out = k;
     return NS_OK;
 }
 
@@ -1874,16 +2026,34 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
         }));
     }
     g->pr_valid = false;
-    const int chunk = g->d.parareal_chunk > 0 ? g->d.parareal_chunk : 0;
+    const bool prof_sweep = g->prof.on && N >= g->prof.min_batch;
+    int chunk = g->d.parareal_chunk > 0 ? g->d.parareal_chunk : 0;
+    if (g->d.parareal_chunk == 0 && kmax >= 2 && N >= 4 && g->mg && !prof_sweep) {
+        // automatic: two chunks pipelined across the call's iterations, where
+        // both grids' graphs apply
+        NS_TRY(ensure_chain(g));
+        if (g->chain->mg && !g->chain->persist) chunk = (N + 1) / 2;
+    }
+    if (chunk > 0 && chunk < N && kmax > 0) {
+        NS_TRY(ensure_chain(g));
+        // chunks' sweeps and chains as graphs, pipelined across iterations
+        // (per-launch timing, when on, needs the stream path's launches)
+        if (g->mg && g->chain->mg && !prof_sweep) {
+            int kd = 0;
+            const ns_status st =
+                parareal_pipelined<T>(g, slices, N, S, M, dt, chunk, kmax, tol, &kd, defects);
+            if (k_done) *k_done = kd;
+            NS_TRY(st);
+            g->pr_valid = true;
+            g->pr_slices_u = slices.u;
+            return sync_stream(g);
+        }
+    }
     int k = 0;
     for (; k < kmax; ++k) {
         double dk;
         if (chunk > 0 && chunk < N) {
-            NS_TRY(ensure_chain(g));
-            if (g->chain->mg)
-                NS_TRY(parareal_iteration_chunked_graphs<T>(g, slices, N, S, M, dt, chunk, &dk));
-            else
-                NS_TRY(parareal_iteration_chunked<T>(g, slices, N, S, M, dt, chunk, &dk));
+            NS_TRY(parareal_iteration_chunked<T>(g, slices, N, S, M, dt, chunk, &dk));
         } else {
             // F(y^k_n) for all n in one batched sweep: one graph launch with
             // the multigrid solver (per-launch timing, when on, needs the
@@ -1927,7 +2097,8 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
                     NS_CUDA(cudaGraphLaunch(g->chain_exec, h->stream));
                     NS_CUDA(cudaStreamSynchronize(h->stream));
                     // N x M coarse steps, plus the 4 update kernels per slice
-                    NS_TRY(account_graph(h, 1, (long long)N * M, 4LL * N, g->chain_seen_lc,
+                    NS_TRY(account_graph(h, 1, (long long)N * M, (long long)N * M, 4LL * N,
+                                         g->chain_seen_lc,
                                          &g->chain_seen_ctl, "ns_parareal_iterate"));
                 }
                 NS_CUDA(cudaMemcpyAsync(h->h_defect, h->d_defect, sizeof(unsigned long long),
@@ -1936,7 +2107,8 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
             }));
             NS_TRY(sync_stream(g));
             if (graphed)
-                NS_TRY(account_graph(g, N, S, 0, g->sweep_seen_lc, g->sweep_seen_ctl.data(),
+                NS_TRY(account_graph(g, N, (long long)N * S, S, 0, g->sweep_seen_lc,
+                                     g->sweep_seen_ctl.data(),
                                      "ns_parareal_iterate (fine sweep)"));
             std::memcpy(&dk, g->chain->h_defect, sizeof(double));
         }
@@ -2816,7 +2988,8 @@ ns_status ns_graph_check(ns_graph* gr, void* cuda_stream) {
     std::string msg;
     for (size_t i = 0; i < gr->grids.size(); ++i) {
         const ns_status st = account_graph(
-            gr->grids[i], gr->batch[i], gr->launched * gr->nsteps[i], 0, gr->seen_loops[i],
+            gr->grids[i], gr->batch[i], gr->launched * gr->nsteps[i] * gr->batch[i],
+            gr->launched * gr->nsteps[i], 0, gr->seen_loops[i],
             gr->seen_ctl[i].data(), "ns_graph_check: branch " + std::to_string(i));
         if (st != NS_OK && result == NS_OK) {
             result = st;

@@ -334,23 +334,65 @@ def test_iteration_limit_is_reported(prec, pc):
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
 def test_chunked_parareal_is_bit_identical(prec, pc):
     """The fine sweep in chunks, each chunk's coarse chain overlapped with the
-    next chunk's sweep on a second stream (graph launches with the multigrid
-    solver, a second host thread with plain BiCGStab), computes exactly the
-    unchunked iteration: same slices bit for bit, same defects."""
+    sweeps of later chunks (with the multigrid solver: graph launches
+    pipelined across the iterations of one call; with plain BiCGStab: a
+    second host thread per iteration) computes exactly the unchunked
+    iterations: same slices bit for bit, same defects, same work.  Chunks of
+    4 and 8 divide the 16 slices, 5 leaves a last chunk of one slice, 0 is the
+    library's automatic choice (two chunks for calls of two or more
+    iterations); -1 sweeps all slices at once."""
     runs = {}
-    for chunk in (0, 4, 8):
+    for chunk in (-1, 0, 4, 5, 8):
         g = Grid(16, 16, 16, re=400.0, precision=prec, batch=16, parareal_chunk=chunk,
                  preconditioner=pc)
         u0 = g.state_from(inputs.random_state(16, 16, 16, seed=11, sigma=0.2))
         g.project(u0)
         slices = g.zeros(17)
         k1, d1 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=1)
-        k2, d2 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=1, resume=True)
-        runs[chunk] = (slices, d1 + d2, g.stats())
-    ref, dref, sref = runs[0]
-    for chunk in (4, 8):
+        # two iterations in one call, then one more
+        k2, d2 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=2, resume=True)
+        k3, d3 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=1, resume=True)
+        assert (k1, k2, k3) == (1, 2, 1)
+        runs[chunk] = (slices, d1 + d2 + d3, g.stats())
+    ref, dref, sref = runs[-1]
+    for chunk in (0, 4, 5, 8):
         got, d, s = runs[chunk]
         assert d == dref, (chunk, d, dref)
         for c in range(4):
             assert torch.equal(got.fields()[c], ref.fields()[c]), (chunk, c)
         assert s["steps"] == sref["steps"] and s["solves"] == sref["solves"]
+        assert s["krylov_iters"] == sref["krylov_iters"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_pipelined_parareal_stops_at_the_tolerance(prec):
+    """With a defect tolerance the pipelined iterations stop after the same
+    iteration as the unchunked ones, with the same slices and defects (the
+    sweep of the first chunk of the iteration after the last one may have
+    run: it writes only the library's F buffers)."""
+    runs = {}
+    tol = None
+    for chunk in (-1, 0, 5):
+        g = Grid(16, 16, 16, re=400.0, precision=prec, batch=16, parareal_chunk=chunk)
+        u0 = g.state_from(inputs.random_state(16, 16, 16, seed=12, sigma=0.2))
+        g.project(u0)
+        slices = g.zeros(17)
+        if tol is None:
+            # a tolerance that the defect first meets at iteration i >= 1
+            probe = g.zeros(17)
+            _, dp = g.parareal(u0, probe, 16, 10, 2, 1e-3, kmax=5)
+            i = max(j for j in range(1, 5) if dp[j] < min(dp[:j]))
+            tol = (dp[i] + min(dp[:i])) / 2
+            k_want = i + 1
+        k, d = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=8, tol=tol)
+        assert k == k_want and d[-1] <= tol and min(d[:-1]) > tol, (chunk, k, d)
+        runs[chunk] = (slices, d)
+        # a resume continues from the stored coarse values
+        k2, d2 = g.parareal(u0, slices, 16, 10, 2, 1e-3, kmax=1, resume=True)
+        runs[chunk] = (slices, d + d2)
+    ref, dref = runs[-1]
+    for chunk in (0, 5):
+        got, d = runs[chunk]
+        assert d == dref, (chunk, d, dref)
+        for c in range(4):
+            assert torch.equal(got.fields()[c], ref.fields()[c]), (chunk, c)
