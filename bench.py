@@ -101,6 +101,11 @@ def parse():
                     help="slices per fine-sweep chunk, pipelined with the coarse chain "
                          "(0: the library's automatic choice, two chunks; -1: one sweep "
                          "over all slices, then the chain)")
+    ap.add_argument("--tile-z", type=int, default=0,
+                    help="cells each thread of the fine sweep marches along z (0 with "
+                         "--coarse-tile-z 0: chosen by autotune_parareal)")
+    ap.add_argument("--coarse-tile-z", type=int, default=0,
+                    help="the coarse propagator's march (0: see --tile-z)")
     ap.add_argument("--inner-rtol", type=float, default=3e-4,
                     help="FP32+refine: relative residual of each inner FP32 solve")
     ap.add_argument("--mode", choices=["bench", "kernels", "coarse", "adjoint", "obstacles",
@@ -399,9 +404,22 @@ def run_ours(args, world, rank, local, pg):
     peaks, peak_kind = measured_peaks()
 
     init = initial_field_gpu(prec)
+    tiles = {"tile_z": args.tile_z, "coarse_tile_z": args.coarse_tile_z, "chosen_by": "flags"}
+    if (args.tile_z == 0 and args.coarse_tile_z == 0 and args.preconditioner == "multigrid"
+            and args.parareal_chunk == 0):
+        # the sweep's and the coarse propagator's marches, timed under the
+        # pipelined schedule (before the timed region)
+        from paper_1705_06149_gb300.autotune import autotune_parareal
+        r = autotune_parareal(N_CELLS, N_CELLS, N_CELLS, N_SLICES, FINE_STEPS, COARSE_STEPS,
+                              DT_FINE, precision=prec, init=init,
+                              grid_kwargs=dict(re=RE, u_lid=1.0, inner_rtol=args.inner_rtol))
+        tiles = {"tile_z": r["tile_z"], "coarse_tile_z": r["coarse_tile_z"],
+                 "chosen_by": "autotune_parareal" + (" (cached)" if r["cached"] else ""),
+                 "ms_per_iteration": r["ms_per_iteration"]}
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, u_lid=1.0, precision=prec, batch=N_SLICES,
              preconditioner=args.preconditioner, inner_rtol=args.inner_rtol,
-             parareal_chunk=args.parareal_chunk)
+             parareal_chunk=args.parareal_chunk, tile_z=tiles["tile_z"],
+             coarse_tile_z=tiles["coarse_tile_z"])
     u0 = g.state_from(init)
     g.project(u0)
     slices = g.zeros(N_SLICES + 1)
@@ -550,6 +568,7 @@ def run_ours(args, world, rank, local, pg):
                    "fine_steps_per_slice": FINE_STEPS, "coarse_steps_per_slice": COARSE_STEPS,
                    "grid": [N_CELLS] * 3, "parallelism": f"replicas x{world}",
                    "schedule": schedule_text(args.parareal_chunk),
+                   "tiles": tiles,
                    "timed": "one ns_parareal_iterate call of `steps` consecutive Parareal "
                             "iterations (resume) after the coarse sweep and a warm-up call of "
                             "`warmup` iterations; the per-iteration cost does not depend on "
@@ -581,12 +600,14 @@ def run_ours(args, world, rank, local, pg):
 
 def run_kernels_only(args):
     """A short run of the batched fine sweep alone, for profilers: the 64^3
-    start state copied to all 32 slices, `steps` fine steps."""
+    start state copied to all 32 slices, `steps` fine steps (march --tile-z;
+    0: the library's default)."""
     import torch
     from paper_1705_06149_gb300 import Grid
     init = initial_field_gpu(args.precision)
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=N_SLICES,
-             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol)
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol,
+             tile_z=args.tile_z)
     st = g.state_from(init)
     g.project(st)
     batch = g.state_from([t.expand((N_SLICES,) + tuple(t.shape[1:])).cpu().numpy()
@@ -611,12 +632,14 @@ def run_kernels_only(args):
 def run_coarse_only(args):
     """The serial coarse chain alone (the G sweep of one Parareal iteration,
     without the update kernels), for profilers: `steps` repetitions, on a
-    batch-1 grid tiled like Parareal's coarse grid (2 cells per thread in z)."""
+    batch-1 grid tiled like Parareal's coarse grid (--coarse-tile-z cells per
+    thread in z; 0: 8, the library's default for it)."""
     import torch
     from paper_1705_06149_gb300 import Grid
     init = initial_field_gpu(args.precision)
     g = Grid(N_CELLS, N_CELLS, N_CELLS, re=RE, precision=args.precision, batch=1,
-             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol, tile_z=2)
+             preconditioner=args.preconditioner, inner_rtol=args.inner_rtol,
+             tile_z=args.coarse_tile_z or 8)
     st = g.state_from(init)
     g.project(st)
     dtc = DT_FINE * FINE_STEPS / COARSE_STEPS

@@ -117,6 +117,12 @@ typedef struct {
                                 same operands whatever the tile; results move only
                                 at rounding level (the compiler may fuse products
                                 into multiply-adds differently per shape).        */
+    int coarse_tile_z;       /* tile_z of the batch-1 companion grid on which
+                                ns_parareal_iterate evaluates the coarse
+                                propagator (every G of a grid, so G_new and G_old
+                                of equal inputs stay bit-identical); 0: 8.  Deep
+                                marches (few CTAs) suit the pipelined schedule,
+                                whose chain shares the GPU with the sweeps.       */
 } ns_grid_desc;
 
 typedef enum { NS_PC_NONE = 0, NS_PC_MULTIGRID = 1 } ns_preconditioner;

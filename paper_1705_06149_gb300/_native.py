@@ -47,7 +47,8 @@ class GridDesc(ctypes.Structure):
                 ("batch", ctypes.c_int),
                 ("preconditioner", ctypes.c_int), ("tile_z", ctypes.c_int),
                 ("parareal_chunk", ctypes.c_int),
-                ("predict_tile_y", ctypes.c_int), ("predict_tile_z", ctypes.c_int)]
+                ("predict_tile_y", ctypes.c_int), ("predict_tile_z", ctypes.c_int),
+                ("coarse_tile_z", ctypes.c_int)]
 
 
 class StateC(ctypes.Structure):

@@ -70,7 +70,7 @@ class Grid:
                  refine_rtol: float = 1e-10, inner_rtol: float = 3e-4, batch: int = 1,
                  preconditioner: str = "multigrid", solid: Optional[np.ndarray] = None,
                  tile_z: int = 0, parareal_chunk: int = 0, refine_maxit: int = 0,
-                 predict_tile: Tuple[int, int] = (0, 0),
+                 predict_tile: Tuple[int, int] = (0, 0), coarse_tile_z: int = 0,
                  device: Optional[torch.device] = None):
         self.lib = N.load()
         self.device = torch.device(device) if device is not None else torch.device(
@@ -103,6 +103,7 @@ class Grid:
         desc.tile_z = tile_z
         desc.parareal_chunk = parareal_chunk
         desc.predict_tile_y, desc.predict_tile_z = int(predict_tile[0]), int(predict_tile[1])
+        desc.coarse_tile_z = int(coarse_tile_z)
         self.preconditioner = preconditioner
         self._desc = desc
         with torch.cuda.device(self.device):

@@ -266,3 +266,69 @@ def autotune_tile_z(nx: int, ny: int, nz: int, batch: int = 1, top: int = 3, ste
         g.close()
     best = min(times, key=times.get)
     return {"tile_z": best, "seed": order, "ms_per_step": times}
+
+
+COARSE_TILE_Z = (4, 8)
+
+
+def autotune_parareal(nx: int, ny: int, nz: int, slices: int, fine_steps: int,
+                      coarse_steps: int, dt: float, precision: str = "fp32_refine",
+                      coarse_candidates: Iterable[int] = COARSE_TILE_Z, top: int = 2,
+                      iterations: int = 3, init=None, grid_kwargs: Optional[dict] = None,
+                      seed: int = 0, use_cache: bool = True) -> Dict:
+    """Chooses the fine sweep's tile_z and the coarse propagator's
+    coarse_tile_z for ns_parareal_iterate by timing Parareal iterations.
+
+    A call of two or more iterations sweeps the slices in two chunks pipelined
+    with the coarse chain, so the sweep's candidates are the `top` seeded
+    tile_z values for a batch of half the slices; the chain shares the GPU
+    with the sweeps, and which march suits it then is measured rather than
+    modelled (the seed model assumes a launch has the SMs to itself), over
+    `coarse_candidates`.  Each pair is timed over `iterations` iterations of
+    one call after the coarse sweep and a warm call of two iterations, from
+    `init` (u, v, w, p of one state; default a seeded random state).  Returns
+    {"tile_z", "coarse_tile_z", "ms_per_iteration": {"tz/ctz": ms}, "seed",
+    "cached"}; timed results are cached."""
+    import torch
+
+    from . import inputs
+    from .api import Grid
+    kw = dict(grid_kwargs or {})
+    bc = tuple(kw.get("bc", ("wall", "wall", "wall")))
+    dev = torch.cuda.get_device_name(torch.cuda.current_device())
+    key = (cache_key(nx, ny, nz, slices, precision, bc, dev) +
+           f"|parareal|S{fine_steps}|M{coarse_steps}|dt{dt:g}")
+    if use_cache and kw.get("solid") is None:
+        hit = _load_cache().get(key)
+        if hit:
+            return {"tile_z": hit["tile_z"], "coarse_tile_z": hit["coarse_tile_z"],
+                    "ms_per_iteration": hit.get("ms_per_iteration"), "seed": hit.get("seed"),
+                    "cached": True}
+    order = seed_order(nx, ny, nz, (slices + 1) // 2)
+    if init is None:
+        init = inputs.random_state(nx, ny, nz, seed=seed, sigma=0.1, bc=bc,
+                                   solid=kw.get("solid"))
+    times: Dict[str, float] = {}
+    for tz, _ in order[:max(1, top)]:
+        for ctz in coarse_candidates:
+            g = Grid(nx, ny, nz, batch=slices, precision=precision, tile_z=tz,
+                     coarse_tile_z=ctz, **kw)
+            u0 = g.state_from(init)
+            g.project(u0)
+            ys = g.zeros(slices + 1)
+            g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=0)
+            g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=2, resume=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=iterations,
+                       resume=True)
+            torch.cuda.synchronize()
+            times[f"{tz}/{ctz}"] = 1e3 * (time.perf_counter() - t0) / iterations
+            g.close()
+    best = min(times, key=times.get)
+    tz, ctz = (int(x) for x in best.split("/"))
+    out = {"tile_z": tz, "coarse_tile_z": ctz, "ms_per_iteration": times,
+           "seed": [[t, c] for t, c in order], "cached": False}
+    if use_cache and kw.get("solid") is None:
+        _store_cache(key, {k: v for k, v in out.items() if k != "cached"})
+    return out

@@ -1504,16 +1504,16 @@ ns_status account_graph(ns_grid* g, int B, long long state_steps, long long step
 }
 
 // The coarse propagator's grid: a batch-1 companion with this grid's
-// description, tiled for one state (2 cells per thread along z: four times
-// the CTAs of the batched sweep's tiling), on its own high-priority stream.
-// Every coarse evaluation of Parareal runs on it, so G_new and G_old of equal
-// inputs are bit-identical.
+// description and its own march (coarse_tile_z, 8 cells per thread along z
+// by default: few CTAs, which find room beside a concurrent sweep), on its
+// own high-priority stream.  Every coarse evaluation of Parareal runs on it,
+// so G_new and G_old of equal inputs are bit-identical.
 ns_status ensure_chain(ns_grid* g) {
     if (g->chain) return NS_OK;
     ns_grid_desc d = g->d;
     d.batch = 1;
     d.parareal_chunk = 0;
-    d.tile_z = 2;
+    d.tile_z = g->d.coarse_tile_z > 0 ? g->d.coarse_tile_z : 8;
     d.solid_mask = g->mask_host.empty() ? nullptr : g->mask_host.data();
     int lo = 0, hi = 0;
     NS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));

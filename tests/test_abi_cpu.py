@@ -88,3 +88,32 @@ def test_input_generators_are_seeded_and_shaped():
     boxes, mask = inputs.obstacle_boxes((32, 32, 32), seed=0, count=4)
     assert boxes.shape == (4, 2, 3) and mask.any()
     assert np.all(boxes[:, 1, 1] <= 0.8 + 1e-12)
+
+
+def test_binding_structs_have_the_header_layout(tmp_path):
+    """The ctypes mirrors of ns_grid_desc, ns_state and ns_stats have the
+    size and field offsets the C compiler gives the header's structs."""
+    import shutil
+    from paper_1705_06149_gb300 import _native as N
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"ns_grid_desc": N.GridDesc, "ns_state": N.StateC, "ns_stats": N.Stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ns.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for cname, py in mirrors.items():
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert int(got[f"{cname} {f[0]}"]) == getattr(py, f[0]).offset, (cname, f[0])

@@ -87,3 +87,46 @@ def test_autotune_3d_times_seeded_tiles_and_caches(tmp_path, monkeypatch):
     assert again["cached"]
     assert tuple(again["predict_tile"]) == tuple(r["predict_tile"])
     assert again["tile_z"] == r["tile_z"]
+
+
+def test_parareal_autotuner_times_seeded_pairs_and_caches(tmp_path, monkeypatch):
+    from paper_1705_06149_gb300 import autotune as at
+    monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    args = (16, 16, 16, 8, 10, 2, 1e-3)
+    kw = dict(precision="fp32_refine", coarse_candidates=(2, 8), iterations=2,
+              grid_kwargs={"re": 400.0})
+    r = at.autotune_parareal(*args, **kw)
+    assert not r["cached"]
+    seeded = [t for t, _ in r["seed"][:2]]
+    assert set(r["ms_per_iteration"]) == {f"{t}/{c}" for t in seeded for c in (2, 8)}
+    assert r["tile_z"] in seeded and r["coarse_tile_z"] in (2, 8)
+    assert all(t > 0 for t in r["ms_per_iteration"].values())
+    again = at.autotune_parareal(*args, **kw)
+    assert again["cached"]
+    assert (again["tile_z"], again["coarse_tile_z"]) == (r["tile_z"], r["coarse_tile_z"])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32_refine", 1e-5)])
+def test_coarse_tile_z_changes_parareal_only_at_rounding_level(prec, tol):
+    """The coarse propagator's march fixes the order of its reductions only:
+    Parareal iterates with coarse_tile_z 2 and 8 agree to rounding after two
+    iterations, and after K = N = 4 every slice is the serial fine solution
+    on both, bit for bit (the same fine kernels on the same inputs)."""
+    init = inputs.random_state(16, 16, 16, seed=5, sigma=0.2)
+    half, full = [], []
+    for ctz in (2, 8):
+        g = Grid(16, 16, 16, re=300.0, precision=prec, batch=4, coarse_tile_z=ctz)
+        u0 = g.state_from(init)
+        g.project(u0)
+        ys = g.zeros(5)
+        k, _ = g.parareal(u0, ys, 4, 10, 2, 1e-3, kmax=2)
+        assert k == 2
+        half.append(ys.clone())
+        k, _ = g.parareal(u0, ys, 4, 10, 2, 1e-3, kmax=2, resume=True)
+        assert k == 2
+        full.append(ys)
+        g.close()
+    for c in range(4):
+        a, b = half[0].fields()[c].double(), half[1].fields()[c].double()
+        assert float((a - b).norm()) <= tol * float(b.norm()), c
+        assert torch.equal(full[0].fields()[c], full[1].fields()[c]), c
