@@ -331,15 +331,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, tile_z: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    was taken on the current kernel source and the same march (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
-    if rec.get("source_sha256") != kernel_source_hash():
+    if rec.get("source_sha256") != kernel_source_hash() or rec.get("tile_z") != tile_z:
         return None
     k = rec.get("kernels", {}).get(kernel)
     if not k:
@@ -492,7 +492,7 @@ def run_ours(args, world, rank, local, pg):
     kern = max(single, key=lambda k: single[k]["ms_per_step"])
     kp = prof[kern]
     achieved = per_kernel[kern]["achieved_gbs"]
-    traffic = traffic_for(kern)
+    traffic = traffic_for(kern, tiles["tile_z"] or 8)
     per_launch_units = kp["cell_units"] / max(kp["launches"], 1)
     sweep_ms = sum(v["ms"] for v in prof.values()) / args.steps
     modelled_ms = sum(v["ms_per_step"] for v in per_kernel.values())

@@ -42,6 +42,8 @@ struct SliceCtl {
     float o_fsc;       // FP32+refine: the scale the next correction gives its right side
     float mean_hi, mean_lo;  // FP32+refine: the fluid mean of the iterate, float-float
     float rmean_hi, rmean_lo;  // FP32+refine: the fluid mean of the outer residual
+    double tol2_in;    // FP32+refine: squared relative tolerance of the inner solve in
+                       // progress, when looser than the launch's (else 0)
 };
 
 template <typename T>

@@ -1527,8 +1527,22 @@ __global__ void __launch_bounds__(NTHREADS)
     }
 }
 
+// FP32+refine: the squared relative tolerance of the next inner solve.  The
+// outer residual must fall from o_rr to otol2 o_bb; an inner solve that
+// reduces its residual by f leaves about f^2 o_rr, so the inner solve needs
+// no more than a reduction whose square is otol2 o_bb / o_rr; it aims a
+// factor 2 (4 in squares) below that, for the rounding of the FP32
+// correction.  The tolerance is the looser of that and itol2, so the last
+// outer step of a solve stops as soon as the target is in reach instead of
+// always reducing by itol, and no inner solve is asked for more than itol.
+__device__ __forceinline__ double inner_tol2(double otol2, double o_bb, double o_rr,
+                                             double itol2) {
+    return fmax(itol2, 0.25 * otol2 * o_bb / o_rr);
+}
+
 // Decision after an iteration (or after a start), in the last CTA:
-// convergence on (r, r) <= tol2 bb, the iteration limit, or the next beta.
+// convergence on (r, r) <= tol2 bb (tol2_in bb when the state's inner solve
+// set a looser one), the iteration limit, or the next beta.
 __device__ __forceinline__ void bicg_decide(SliceCtl* c, double rho_new, double rr, double sx,
                                             double tol2, int maxit) {
     const int it = c->it_cur;
@@ -1538,7 +1552,7 @@ __device__ __forceinline__ void bicg_decide(SliceCtl* c, double rho_new, double 
         c->status = ST_NONFINITE;
         return;
     }
-    if (rr <= tol2 * c->bb) {
+    if (rr <= fmax(tol2, c->tol2_in) * c->bb) {
         c->status = ST_CONV;
         return;
     }
@@ -1984,6 +1998,7 @@ __global__ void __launch_bounds__(NTHREADS)
             c->bb = tot[0];
             c->omega = 1.0;
             c->alpha = 1.0;
+            c->tol2_in = inner_tol2(otol2, tot[1], tot[0], itol2);
             bicg_decide(c, tot[0], tot[0], 0.0, itol2, maxit);
         }
     }
@@ -2100,6 +2115,7 @@ __global__ void __launch_bounds__(NTHREADS)
             c->bb = rr;
             c->omega = 1.0;
             c->alpha = 1.0;
+            c->tol2_in = inner_tol2(otol2, c->o_bb, tot[0], itol2);
             bicg_decide(c, rr, rr, 0.0, itol2, maxit);
         }
     }
