@@ -143,6 +143,8 @@ struct ns_grid {
     // the coarse chain's graph with programmatic dependencies between its
     // consecutive kernels (NS_CHAIN_PDL=0 in the environment at creation: off)
     bool chain_pdl = true;
+    // the fine sweep's graphs: programmatic edges into the cluster V-cycle
+    bool sweep_pdl = true;
     LoopCount* loopc = nullptr;
     long long cap_launches = 0;  // kernels captured so far
     // Parareal's coarse propagator: a batch-1 companion grid (this grid's
@@ -877,8 +879,10 @@ ns_status add_while(ns_grid* g, cudaStream_t bst, cudaGraphConditionalHandle h, 
 
 // Turns every plain dependency between two kernel nodes of `graph` into a
 // programmatic one (the successor's CTAs may launch once every CTA of the
-// predecessor passed its pdl_wait, and wait there for its completion).
-cudaError_t make_programmatic(cudaGraph_t graph) {
+// predecessor passed its pdl_wait, and wait there for its completion); with
+// only_into, just those into a kernel node of that function (or only_into2).
+cudaError_t make_programmatic(cudaGraph_t graph, const void* only_into = nullptr,
+                              const void* only_into2 = nullptr) {
     size_t n = 0;
     cudaError_t e = cudaGraphGetEdges(graph, nullptr, nullptr, nullptr, &n);
     if (e != cudaSuccess || n == 0) return e;
@@ -893,6 +897,11 @@ cudaError_t make_programmatic(cudaGraph_t graph) {
         if (tf != cudaGraphNodeTypeKernel || tt != cudaGraphNodeTypeKernel ||
             ed[q].type != cudaGraphDependencyTypeDefault || ed[q].from_port != 0)
             continue;
+        if (only_into) {
+            cudaKernelNodeParams kp{};
+            if ((e = cudaGraphKernelNodeGetParams(to[q], &kp)) != cudaSuccess) return e;
+            if (kp.func != only_into && kp.func != only_into2) continue;
+        }
         if ((e = cudaGraphRemoveDependencies(graph, &from[q], &to[q], &ed[q], 1)) != cudaSuccess)
             return e;
         cudaGraphEdgeData pe{};
@@ -910,12 +919,14 @@ cudaError_t make_programmatic(cudaGraph_t graph) {
 // Captures the launches fn() issues on g->stream into an executable graph:
 // the capture runs on `top`, the solver loops' bodies on `body`.  With
 // `programmatic`, consecutive kernels (in the graph and in its loop bodies)
-// get programmatic dependencies; where the runtime refuses them the plain
-// dependencies stay.
+// get programmatic dependencies -- with `into_cluster_only` just the edges
+// into the cluster V-cycle, whose CTAs then stage their plan while the
+// restriction before them finishes; where the runtime refuses them the
+// plain dependencies stay.
 template <typename F>
 ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
                        cudaGraph_t* graph_out, cudaGraphExec_t* exec_out,
-                       bool programmatic = false) {
+                       bool programmatic = false, bool into_cluster_only = false) {
     *graph_out = nullptr;
     *exec_out = nullptr;
     g->cap_bodies.clear();
@@ -940,8 +951,10 @@ ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
         return fail(NS_ERR_CUDA, std::string("graph capture: cudaStreamEndCapture: ") +
                                      cudaGetErrorString(e));
     if (programmatic) {
-        bool ok = make_programmatic(graph) == cudaSuccess;
-        for (cudaGraph_t b : g->cap_bodies) ok = ok && make_programmatic(b) == cudaSuccess;
+        const void* k32 = into_cluster_only ? (const void*)k_mg_cluster<float> : nullptr;
+        const void* k64 = into_cluster_only ? (const void*)k_mg_cluster<double> : nullptr;
+        bool ok = make_programmatic(graph, k32, k64) == cudaSuccess;
+        for (cudaGraph_t b : g->cap_bodies) ok = ok && make_programmatic(b, k32, k64) == cudaSuccess;
         if (!ok) cudaGetLastError();
     }
     g->cap_bodies.clear();
@@ -950,7 +963,10 @@ ns_status capture_exec(ns_grid* g, cudaStream_t top, cudaStream_t body, F&& fn,
         // the runtime refused the programmatic edges: capture again without
         cudaGetLastError();
         cudaGraphDestroy(graph);
-        g->chain_pdl = false;
+        if (into_cluster_only)
+            g->sweep_pdl = false;
+        else
+            g->chain_pdl = false;
         return capture_exec(g, top, body, std::forward<F>(fn), graph_out, exec_out, false);
     }
     if (ei != cudaSuccess) {
@@ -1739,7 +1755,7 @@ ns_status sweep_launch(ns_grid* g, int N, int S, double dt) {
         ns_state fb{g->pr_f[0], g->pr_f[1], g->pr_f[2], g->pr_f[3], N};
         NS_TRY(capture_exec(g, g->sweep_cap[0], g->sweep_cap[1],
                             [&]() -> ns_status { return step_impl<T>(g, fb, dt, S); },
-                            &g->sweep_graph, &g->sweep_exec));
+                            &g->sweep_graph, &g->sweep_exec, g->sweep_pdl, true));
         g->sweep_key_n = N;
         g->sweep_key_s = S;
         g->sweep_key_dt = dt;
@@ -1834,7 +1850,7 @@ ns_status ensure_chunk_sweeps(ns_grid* g, int N, int S, double dt, int chunk) {
         cudaGraphExec_t ex;
         NS_TRY(capture_exec(g, g->sweep_cap[0], g->sweep_cap[1],
                             [&]() -> ns_status { return step_impl<T>(g, fb, dt, S); }, &gr,
-                            &ex));
+                            &ex, g->sweep_pdl, true));
         g->swc_graph.push_back(gr);
         g->swc_exec.push_back(ex);
     }
