@@ -10,7 +10,10 @@
 //   p_lo, r_hi, r_lo, q_hi, q_lo [C each], F*u [Fu], F*v [Fv], F*w [Fw], then
 //   FP64: rmean, mean.
 //   out.bin, FP32 unless noted: init p_hi p_lo r_hi r_lo r32 rhat; update p_hi
-//   p_lo r_hi r_lo r32 rhat; correct u v w, p_out (FP64), w_hi w_lo q_hi q_lo.
+//   p_lo r_hi r_lo r32 rhat; correct u v w, p_out (FP64), w_hi w_lo q_hi q_lo;
+//   then FP64, for the start and for the correction: o_bb, o_rr, bb, tol2_in,
+//   status, o_status of the control block (the start with otol2 1e-4, the
+//   correction with 1e-30; itol2 1e-8 both).
 
 #include <functional>
 
@@ -95,6 +98,11 @@ int main(int argc, char** argv) {
     fclose(f);
     if (!ok) return 4;
     FILE* out = fopen(argv[12], "wb");
+    std::vector<double> decisions;
+    auto keep = [&](const SliceCtl& c) {
+        for (double v : {c.o_bb, c.o_rr, c.bb, c.tol2_in, (double)c.status, (double)c.o_status})
+            decisions.push_back(v);
+    };
     // start of a refined solve from the warm start w
     {
         std::vector<float> Ph(C), Pl(C), Rh(C), Rl(C), r32(C), rhat(C), x(C, 0.0f), Wh = wh, Wl = wl;
@@ -110,9 +118,10 @@ int main(int argc, char** argv) {
         FFBuf fb{Ph.data(), Pl.data(), Rh.data(), Rl.data(), Wh.data(), Wl.data(), nullptr, nullptr};
         launch(L.ctas, [&] {
             k_mg_refine_init_ff<false>(L, mb, &ctl, part_b.data(), (int)C, b.data(), nullptr, fb,
-                                       part.data(), 1e-30, 1e-8, 100);
+                                       part.data(), 1e-4, 1e-8, 100);
         });
         for (auto* v : {&Ph, &Pl, &Rh, &Rl, &r32, &rhat}) put(out, *v);
+        keep(ctl);
     }
     // one outer correction p += e / s, r -= L e / s (minus the residual's mean)
     {
@@ -138,6 +147,7 @@ int main(int argc, char** argv) {
             k_mg_refine_update_ff(L, mb, &ctl, fb, (int)C, part.data(), 1e-30, 1e-8, 100, 40, 0);
         });
         for (auto* v : {&Ph, &Pl, &Rh, &Rl, &r32, &rhat}) put(out, *v);
+        keep(ctl);
     }
     // velocity correction with the float-float pressure, gauged output, warm start
     {
@@ -159,6 +169,7 @@ int main(int argc, char** argv) {
         put(out, pout);
         for (auto* v : {&Wh, &Wl, &Qh, &Ql}) put(out, *v);
     }
+    put(out, decisions);
     fclose(out);
     return 0;
 }

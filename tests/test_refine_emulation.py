@@ -8,6 +8,8 @@ UBSan, against the same operations in FP64:
   start:      p = w, r = (b - mean b) - L w, r32 = r_hat = hi(r);
   correction: p += e / s, r -= L e / s and the residual's fluid mean,
               r32 = r_hat = hi(r) * s';
+  decisions:  each inner solve's tolerance, the looser of itol and what the
+              outer target still needs (a factor 2 below it);
   velocity:   u = F* - dt G p on active faces (0 on wall faces), p_out =
               p - mean, q = p - mean, w = 2 (p - mean) - q_old,
 
@@ -171,6 +173,17 @@ def test_float_float_refinement_matches_fp64(refine_emulator, dims, bc):
     assert np.max(np.abs((Qh + Ql) - (p - mean))) <= tol * np.max(np.abs(p - mean))
     want_w = 2.0 * (p - mean) - f64(qh, ql)
     assert np.max(np.abs((Wh + Wl) - want_w)) <= tol * np.max(np.abs(want_w))
+    # the decisions: each inner solve starts (status 0 = iterate, outer status
+    # 0 = refine) with the looser of itol2 and a quarter of the squared
+    # reduction the outer target still needs -- at the start (target 1e-4 in
+    # squares) that need is the looser one, after the correction (1e-30) itol2
+    dec = take(np.float64, (2, 6))
+    for (o_bb, o_rr, bb, tol2_in, st, ost), otol2 in zip(dec, (1e-4, 1e-30)):
+        assert st == 0 and ost == 0
+        assert tol2_in == max(1e-8, 0.25 * otol2 * o_bb / o_rr)
+    assert dec[0][3] > 1e-8 and dec[1][3] == 1e-8
+    assert dec[0][2] == dec[0][1]  # the start's inner solve: bb = the outer residual
+    assert off == len(raw)
 
 
 def bc_codes(bc):
