@@ -22,6 +22,7 @@
 #include "ns_mg.cuh"
 #include "ns_mg_cluster.cuh"
 #include "ns_persist.h"
+#include "ns_pipeline.h"
 
 using namespace nsk;
 
@@ -1902,66 +1903,71 @@ ns_status parareal_pipelined(ns_grid* g, ns_state slices, int N, int S, int M, d
         NS_CUDA(cudaMallocHost((void**)&g->h_defects, sizeof(double) * kmax));
         g->h_defects_cap = kmax;
     }
-    cudaEvent_t* ev_copied = g->pipe_ev.data() + 2;
-    cudaEvent_t* ev_swept = ev_copied + C;
-    cudaEvent_t* ev_chained = ev_swept + C;
-    cudaEvent_t ev_start = ev_chained[C], ev_defect = ev_chained[C + 1];
+    cudaEvent_t* ev = g->pipe_ev.data() + 2;  // [kind][chunk]: copied, swept, chained
+    cudaEvent_t ev_start = ev[3 * C];  // ev[3 C + 1]: the last defect copied
     const ns_stats chain0 = h->stats;
     long long swept_states = 0, sweeps = 0;
+    ns_status st_issue = NS_OK;
+    // the primitives of pipeline_issue on this grid's and the companion's streams
+    struct Ops {
+        ns_grid *g, *h;
+        cudaEvent_t* ev;
+        int C, N, chunk;
+        double tol;
+        void* const* ys;
+        long long *swept_states, *sweeps;
+        ns_status* st;
+        cudaStream_t stream(int s) const { return s == PS_SWEEP ? g->stream : h->stream; }
+        bool ok(cudaError_t e, const char* what) {
+            if (e == cudaSuccess) return true;
+            *st = fail(NS_ERR_CUDA, std::string("pipelined Parareal: ") + what + ": " +
+                                        cudaGetErrorString(e));
+            return false;
+        }
+        bool wait(int s, int kind, int c) {
+            return ok(cudaStreamWaitEvent(stream(s), ev[kind * C + c], 0), "event wait");
+        }
+        bool record(int s, int kind, int c) {
+            return ok(cudaEventRecord(ev[kind * C + c], stream(s)), "event record");
+        }
+        bool copy_in(int c) {
+            const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
+            *st = copy_states<T>(g, g->pr_f, ys, n0, n0, m);
+            return *st == NS_OK;
+        }
+        bool sweep(int c) {
+            const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
+            *swept_states += m;
+            *sweeps += 1;
+            return ok(cudaGraphLaunch(g->swc_exec[c], g->stream), "sweep graph launch");
+        }
+        bool defect_reset() {
+            return ok(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream),
+                      "defect reset");
+        }
+        bool chain(int c) {
+            return ok(cudaGraphLaunch(g->chunk_exec[c], h->stream), "chain graph launch");
+        }
+        bool defect_out(int k) {
+            return ok(cudaMemcpyAsync(g->h_defects + k, h->d_defect, sizeof(double),
+                                      cudaMemcpyDeviceToHost, h->stream),
+                      "defect copy") &&
+                   ok(cudaEventRecord(ev[3 * C + 1], h->stream), "event record");
+        }
+        int converged(int k) {
+            if (!ok(cudaEventSynchronize(ev[3 * C + 1]), "defect wait")) return -1;
+            const double dk = g->h_defects[k];
+            return !std::isfinite(dk) || dk <= tol ? 1 : 0;
+        }
+    } ops{g, h, ev, C, N, chunk, tol, ys, &swept_states, &sweeps, &st_issue};
     int k = 0;
-
-    auto sweep = [&](int kk, int c) -> ns_status {
-        const int n0 = c * chunk, m = std::min(N, n0 + chunk) - n0;
-        // y^{kk-1} of the chunk is written and its F values consumed
-        if (kk > 0) NS_CUDA(cudaStreamWaitEvent(g->stream, ev_chained[c], 0));
-        NS_TRY(copy_states<T>(g, g->pr_f, ys, n0, n0, m));
-        NS_CUDA(cudaEventRecord(ev_copied[c], g->stream));
-        NS_CUDA(cudaGraphLaunch(g->swc_exec[c], g->stream));
-        NS_CUDA(cudaEventRecord(ev_swept[c], g->stream));
-        swept_states += m;
-        sweeps += 1;
-        return NS_OK;
-    };
-    auto chain = [&](int kk, int c) -> ns_status {
-        NS_CUDA(cudaStreamWaitEvent(h->stream, ev_swept[c], 0));
-        // the chain of chunk c writes y of the next chunk's first slice: after
-        // that chunk has copied its inputs
-        if (c + 1 < C) NS_CUDA(cudaStreamWaitEvent(h->stream, ev_copied[c + 1], 0));
-        if (c == 0)
-            NS_CUDA(cudaMemsetAsync(h->d_defect, 0, sizeof(unsigned long long), h->stream));
-        NS_CUDA(cudaGraphLaunch(g->chunk_exec[c], h->stream));
-        NS_CUDA(cudaEventRecord(ev_chained[c], h->stream));
-        if (c == C - 1) {
-            NS_CUDA(cudaMemcpyAsync(g->h_defects + kk, h->d_defect, sizeof(double),
-                                    cudaMemcpyDeviceToHost, h->stream));
-            NS_CUDA(cudaEventRecord(ev_defect, h->stream));
-        }
-        return NS_OK;
-    };
-    // issue order: SW(k, c) before CH(k, c - 1) (which waits for its copy),
-    // CH(k, c) before SW(k + 1, c) (which waits for it); an event wait takes
-    // the event's latest record at the time it is issued
-    auto issue = [&]() -> ns_status {
-        NS_CUDA(cudaEventRecord(ev_start, g->stream));
-        NS_CUDA(cudaStreamWaitEvent(h->stream, ev_start, 0));
-        NS_TRY(sweep(0, 0));
-        for (; k < kmax; ++k) {
-            if (tol > 0.0 && k > 0) {
-                // the defect of iteration k - 1 decides whether iteration k runs
-                NS_CUDA(cudaEventSynchronize(ev_defect));
-                const double dk = g->h_defects[k - 1];
-                if (!std::isfinite(dk) || dk <= tol) break;
-            }
-            for (int c = 1; c < C; ++c) {
-                NS_TRY(sweep(k, c));
-                NS_TRY(chain(k, c - 1));
-            }
-            NS_TRY(chain(k, C - 1));
-            if (k + 1 < kmax) NS_TRY(sweep(k + 1, 0));
-        }
-        return NS_OK;
-    };
-    const ns_status st_issue = issue();
+    if (cudaEventRecord(ev_start, g->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(h->stream, ev_start, 0) != cudaSuccess)
+        st_issue = fail(NS_ERR_CUDA, "pipelined Parareal: event record failed");
+    else {
+        k = pipeline_issue(C, kmax, tol > 0.0, ops);
+        if (k < 0) k = 0;
+    }
     const std::string err_issue = g_last_error;
     // the slices are written by the chain: later work on this stream waits for it
     const cudaError_t e1 = cudaEventRecord(ev_start, h->stream);
