@@ -656,10 +656,33 @@ def run_coarse_only(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
+    stats = g.stats()
+    # the same 160 coarse steps as one CUDA graph with device-resident solver
+    # loops (as Parareal issues its chain, there with programmatic edges and
+    # the update kernels in between), timed with events
+    from paper_1705_06149_gb300 import StepGraph
+    s = st.clone()
+    sg = StepGraph([(g, s, dtc, N_SLICES * COARSE_STEPS)])
+    sg.launch()
+    sg.check()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms_graph = []
+    for _ in range(max(1, args.steps)):
+        e0.record()
+        sg.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_graph.append(e0.elapsed_time(e1))
+    sg.check()
+    sg.close()
     print(json.dumps({"mode": "coarse", "precision": args.precision,
                       "ms_per_chain": 1e3 * t / args.steps,
                       "ms_per_coarse_step": 1e3 * t / (args.steps * N_SLICES * COARSE_STEPS),
-                      "stats": g.stats()}), flush=True)
+                      "ms_per_coarse_step_graph": min(ms_graph) / (N_SLICES * COARSE_STEPS),
+                      "note": "ms_per_coarse_step: ns_step_coarse per slice (host-polled "
+                              "solves); _graph: the 160 steps as one graph launch",
+                      "stats": stats}), flush=True)
     g.close()
     return 0
 
