@@ -365,6 +365,28 @@ def test_chunked_parareal_is_bit_identical(prec, pc):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_chunked_parareal_with_cluster_v_cycles_is_bit_identical(prec):
+    """On a 32^3 grid the V-cycle's coarse levels run as thread-block
+    clusters (4 CTAs per state), launched for 24 slices at once by the
+    unchunked sweep and for chunks of 12 by the pipelined schedule; the
+    pipelined iterations give the unchunked ones bit for bit."""
+    runs = {}
+    for chunk in (-1, 0):
+        g = Grid(32, 32, 32, re=400.0, precision=prec, batch=24, parareal_chunk=chunk)
+        u0 = g.state_from(inputs.random_state(32, 32, 32, seed=13, sigma=0.2))
+        g.project(u0)
+        slices = g.zeros(25)
+        k, d = g.parareal(u0, slices, 24, 4, 1, 1e-3, kmax=2)
+        assert k == 2
+        runs[chunk] = (slices, d, g.stats())
+    (ref, dref, sref), (got, d, s) = runs[-1], runs[0]
+    assert d == dref, (d, dref)
+    for c in range(4):
+        assert torch.equal(got.fields()[c], ref.fields()[c]), c
+    assert s["krylov_iters"] == sref["krylov_iters"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
 def test_pipelined_parareal_stops_at_the_tolerance(prec):
     """With a defect tolerance the pipelined iterations stop after the same
     iteration as the unchunked ones, with the same slices and defects (the
