@@ -192,7 +192,13 @@ struct ns_grid {
     std::vector<SliceCtl> sweep_seen_ctl;
     std::vector<cudaGraph_t> chunk_graph;
     std::vector<cudaGraphExec_t> chunk_exec;
+    // what the chunks' chain graphs were captured for (their own key: the
+    // whole-chain graph may since have been captured for other slices)
     int chunk_key = 0;
+    const void* chunk_key_ys = nullptr;
+    const void* chunk_key_f = nullptr;
+    int chunk_key_n = 0, chunk_key_m = 0;
+    double chunk_key_dt = 0.0;
     // the fine sweep of each chunk of the pipelined schedule (S steps of the
     // chunk's slices in pr_f) as a graph of its own
     std::vector<cudaGraph_t> swc_graph;
@@ -1780,19 +1786,14 @@ ns_status ensure_chunk_chains(ns_grid* g, ns_state slices, int N, int M, double 
     ns_grid* h = g->chain;
     void* ys[4] = {slices.u, slices.v, slices.w, slices.p};
     ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
-    if ((int)g->chunk_exec.size() == C && g->chunk_key == chunk && g->chain_key_ys == ys[0] &&
-        g->chain_key_f == g->pr_f[0] && g->chain_key_n == N && g->chain_key_m == M &&
-        g->chain_key_dt == dtc)
+    if ((int)g->chunk_exec.size() == C && g->chunk_key == chunk && g->chunk_key_ys == ys[0] &&
+        g->chunk_key_f == g->pr_f[0] && g->chunk_key_n == N && g->chunk_key_m == M &&
+        g->chunk_key_dt == dtc)
         return NS_OK;
     for (cudaGraphExec_t e : g->chunk_exec) cudaGraphExecDestroy(e);
     for (cudaGraph_t c : g->chunk_graph) cudaGraphDestroy(c);
     g->chunk_exec.clear();
     g->chunk_graph.clear();
-    // the whole-chain graph shares the key fields: drop it too
-    if (g->chain_exec) cudaGraphExecDestroy(g->chain_exec);
-    if (g->chain_graph) cudaGraphDestroy(g->chain_graph);
-    g->chain_exec = nullptr;
-    g->chain_graph = nullptr;
     g->chunk_key = 0;
     for (cudaStream_t& cs : g->chain_cap)
         if (!cs) NS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1816,11 +1817,11 @@ ns_status ensure_chunk_chains(ns_grid* g, ns_state slices, int N, int M, double 
         g->chunk_exec.push_back(ex);
     }
     g->chunk_key = chunk;
-    g->chain_key_ys = ys[0];
-    g->chain_key_f = g->pr_f[0];
-    g->chain_key_n = N;
-    g->chain_key_m = M;
-    g->chain_key_dt = dtc;
+    g->chunk_key_ys = ys[0];
+    g->chunk_key_f = g->pr_f[0];
+    g->chunk_key_n = N;
+    g->chunk_key_m = M;
+    g->chunk_key_dt = dtc;
     NS_CUDA(cudaMemcpy(&g->chain_seen_lc, h->loopc, sizeof(LoopCount), cudaMemcpyDeviceToHost));
     NS_CUDA(cudaMemcpy(&g->chain_seen_ctl, h->ctl, sizeof(SliceCtl), cudaMemcpyDeviceToHost));
     return NS_OK;

@@ -314,6 +314,36 @@ def test_nonfinite_input_is_reported():
     assert e.value.status == N.NS_ERR_NONFINITE
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_nonfinite_slice_in_pipelined_parareal_is_reported(prec):
+    """A non-finite value in one slice's state stops a pipelined Parareal call
+    with NS_ERR_NONFINITE (the solver loops on the device end on the
+    non-finite residual; the failure is read from the control blocks after
+    the call); the grid then runs a clean call as before.  Calls on other
+    slice buffers, unchunked (one iteration) and pipelined, never write the
+    first call's slices (the cached graphs are keyed by the buffers)."""
+    g = Grid(16, 16, 16, re=400.0, precision=prec, batch=4)
+    u0 = g.state_from(inputs.random_state(16, 16, 16, seed=14, sigma=0.2))
+    g.project(u0)
+    ref = g.zeros(5)
+    k, d_ref = g.parareal(u0, ref, 4, 5, 1, 1e-3, kmax=2)
+    assert k == 2
+    ref_copy = ref.clone()
+    bad = g.zeros(5)
+    g.parareal(u0, bad, 4, 5, 1, 1e-3, kmax=1)
+    bad.u[2, 5, 5, 5] = float("nan")
+    with pytest.raises(NSError) as e:
+        g.parareal(u0, bad, 4, 5, 1, 1e-3, kmax=3, resume=True)
+    assert e.value.status == N.NS_ERR_NONFINITE
+    for c in range(4):
+        assert torch.equal(ref.fields()[c], ref_copy.fields()[c]), c
+    again = g.zeros(5)
+    k, d = g.parareal(u0, again, 4, 5, 1, 1e-3, kmax=2)
+    assert k == 2 and d == d_ref
+    for c in range(4):
+        assert torch.equal(again.fields()[c], ref.fields()[c]), c
+
+
 @pytest.mark.parametrize("pc", PCS)
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
 def test_iteration_limit_is_reported(prec, pc):
