@@ -1869,20 +1869,16 @@ ns_status ensure_chunk_sweeps(ns_grid* g, int N, int S, double dt, int chunk) {
 }
 
 // Up to kmax Parareal iterations with the fine sweep in chunks of `chunk`
-// slices, pipelined across iterations.  SW(k, c), the sweep of chunk c in
-// iteration k, needs y^{k-1}_n of the chunk's slices, which the chain of
-// chunk c in iteration k-1, CH(k-1, c), writes (and that chain must have
-// consumed the F values SW(k, c) overwrites); CH(k, c) needs SW(k, c) and
-// CH(k, c-1).  So the sweep of chunk 0 of the next iteration starts as soon
-// as the chain has passed chunk 0, while the chain works through the later
-// chunks: the sweeps run one after another on this grid's stream, the chains
-// on the companion's high-priority stream, and the serial chain hides under
-// the sweeps.  Every state is computed by the same kernels in the same order
-// as in the unpipelined iteration (a slice's reductions do not depend on the
-// batch), so results are bit-identical.  The sweep of chunk 0 of iteration
-// k+1 is issued before the defect of iteration k is known (it writes only
-// pr_f, never the slices); with tol > 0 the host waits for each iteration's
-// defect before it issues the next iteration's chains.
+// slices, pipelined across iterations: the issue order of pipeline_issue
+// (ns_pipeline.h), whose primitives are here the chunks' sweep graphs on this
+// grid's stream, their chain graphs on the companion's high-priority stream,
+// the copies of y into the F buffers, and one event per (kind, chunk).  The
+// sweep of chunk 0 of the next iteration starts as soon as the chain has
+// passed chunk 0, so the serial chain runs under the sweeps.  Every state is
+// computed by the same kernels in the same order as in the unpipelined
+// iteration (a slice's reductions do not depend on the batch), so results
+// are bit-identical.  The work and any failed solve are read from the device
+// counters after the call.
 template <typename T>
 ns_status parareal_pipelined(ns_grid* g, ns_state slices, int N, int S, int M, double dt,
                              int chunk, int kmax, double tol, int* k_out, double* defects) {
