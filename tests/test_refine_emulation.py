@@ -188,3 +188,41 @@ def test_float_float_refinement_matches_fp64(refine_emulator, dims, bc):
 
 def bc_codes(bc):
     return [BC[x] for x in bc]
+
+
+@pytest.fixture(scope="module")
+def decide_emulator(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("decide_emu")
+    cpp = d / "decide_emu.cpp"
+    cpp.write_text('#include "block_emu.h"\n\n' + _source() + "\n\n" +
+                   open(os.path.join(EMU, "decide_emu_main.cpp")).read())
+    exe = d / "decide_emu"
+    r = subprocess.run([gxx, "-std=c++20", "-O1", "-fsanitize=address,undefined",
+                        "-fno-sanitize-recover=undefined", "-pthread", "-I", EMU, str(cpp), "-o",
+                        str(exe)], capture_output=True, text=True)
+    if r.returncode != 0 and "barrier" in r.stderr and "No such file" in r.stderr:
+        pytest.skip("the host compiler has no <barrier>")
+    assert r.returncode == 0, r.stderr[-3000:]
+    return str(exe)
+
+
+@pytest.mark.parametrize("ratio,tol2,tol2_in,want", [
+    (0.4, 1e-8, 0.5, 1),    # within the state's looser inner tolerance: converged
+    (0.4, 1e-8, 0.0, 0),    # no inner tolerance set: the launch's decides, iterate
+    (0.6, 1e-8, 0.5, 0),    # outside both
+    (1e-9, 1e-8, 0.0, 1),   # within the launch's
+    (1e-9, 1e-8, 1e-10, 1),  # a tighter inner tolerance never overrides the launch's
+])
+def test_convergence_decision_takes_the_looser_tolerance(decide_emulator, ratio, tol2, tol2_in,
+                                                         want):
+    """bicg_decide stops a state when (r, r) <= max(tol2, tol2_in) (b, b): the
+    launch's tolerance, or the looser one an FP32 inner solve was given."""
+    out = subprocess.run([decide_emulator, repr(ratio), repr(tol2), repr(tol2_in), "2", "100"],
+                         capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == want
+    if want == 0:
+        # iterating on: beta = (rho_new / rho_old) (alpha / omega), rho_old := rho_new
+        assert float(out[1]) == (3.0 / 2.0) * (0.5 / 0.25) and float(out[2]) == 3.0
