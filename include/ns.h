@@ -208,7 +208,8 @@ ns_status ns_poisson_solve(ns_grid *grid, const double *b, double *p, int batch,
  * defect max_{n,field} |y^{k+1}_n - y^k_n| <= defect_tol (tol > 0).
  * resume = 0 starts from u0 (coarse sweep first); resume = 1 continues from
  * the y^k held in `slices` and the coarse values G(y^k_n) this grid stored at
- * the end of the previous call with the same slices (NS_ERR_ARG if none).
+ * the end of the previous call with the same slices, n_slices, steps per
+ * slice and dt_fine (NS_ERR_ARG if there is none).
  * *k_done (host) receives the iterations performed, defects (host, kmax
  * entries, may be NULL) the FP64 defect of each. */
 ns_status ns_parareal_iterate(ns_grid *grid, ns_state u0, ns_state slices, int n_slices,

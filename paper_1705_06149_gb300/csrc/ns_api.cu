@@ -135,6 +135,9 @@ struct ns_grid {
     int pr_n = 0;
     const void* pr_slices_u = nullptr;
     bool pr_valid = false;
+    // the slices and steps the stored coarse values belong to
+    int pr_key_n = 0, pr_key_s = 0, pr_key_m = 0;
+    double pr_key_dt = 0.0;
     // graph capture (ns_graph_create): while capturing, every launch goes to
     // `stream` (a capture stream) and the solver loops become conditional
     // while nodes whose bodies are captured on body_stream[0] / [1]
@@ -2017,9 +2020,10 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
     const double dtc = dt * S / M;
     ns_state gs{g->pr_g[0], g->pr_g[1], g->pr_g[2], g->pr_g[3], 1};
     if (resume) {
-        if (!g->pr_valid || g->pr_slices_u != slices.u || g->pr_n < N)
+        if (!g->pr_valid || g->pr_slices_u != slices.u || g->pr_n < N || g->pr_key_n != N ||
+            g->pr_key_s != S || g->pr_key_m != M || g->pr_key_dt != dt)
             return fail(NS_ERR_ARG, "ns_parareal_iterate: resume=1 without stored coarse values "
-                                    "for these slices");
+                                    "for these slices, slice count, steps and dt");
     } else {
         // iteration 0: the serial coarse sweep y_{n+1} = G(y_n)
         NS_TRY(ensure_chain(g));
@@ -2065,6 +2069,10 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
             NS_TRY(st);
             g->pr_valid = true;
             g->pr_slices_u = slices.u;
+            g->pr_key_n = N;
+            g->pr_key_s = S;
+            g->pr_key_m = M;
+            g->pr_key_dt = dt;
             return sync_stream(g);
         }
     }
@@ -2144,6 +2152,10 @@ ns_status parareal_impl(ns_grid* g, ns_state u0, ns_state slices, int N, int S, 
     if (k_done) *k_done = k;
     g->pr_valid = true;
     g->pr_slices_u = slices.u;
+    g->pr_key_n = N;
+    g->pr_key_s = S;
+    g->pr_key_m = M;
+    g->pr_key_dt = dt;
     return sync_stream(g);
 }
 

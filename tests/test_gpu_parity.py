@@ -252,6 +252,14 @@ def test_parareal_resume_and_tolerance():
     with pytest.raises(NSError) as e:
         g.parareal(u0, g.zeros(4), 3, 20, 4, 1e-3, kmax=1, resume=True)
     assert e.value.status == N.NS_ERR_ARG
+    # the stored coarse values belong to 3 slices of 20 fine / 4 coarse steps
+    # of 1e-3: a resume with other ones is refused, the matching one runs
+    for args in ((2, 20, 4, 1e-3), (3, 10, 4, 1e-3), (3, 20, 2, 1e-3), (3, 20, 4, 5e-4)):
+        with pytest.raises(NSError) as e:
+            g.parareal(u0, c_, *args, kmax=1, resume=True)
+        assert e.value.status == N.NS_ERR_ARG, args
+    k5, _ = g.parareal(u0, c_, 3, 20, 4, 1e-3, kmax=1, resume=True)
+    assert k5 == 1
 
 
 # ---------------------------------------------------------------------------
