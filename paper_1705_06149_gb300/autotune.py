@@ -271,6 +271,16 @@ def autotune_tile_z(nx: int, ny: int, nz: int, batch: int = 1, top: int = 3, ste
 COARSE_TILE_Z = (4, 8)
 
 
+def parareal_candidates(nx: int, ny: int, nz: int, slices: int, top: int = 2,
+                        coarse_candidates: Iterable[int] = COARSE_TILE_Z,
+                        sms: Optional[int] = None) -> List[Tuple[int, int]]:
+    """The (tile_z, coarse_tile_z) pairs autotune_parareal times: the `top`
+    seeded tile_z values for a batch of half the slices (the pipelined
+    schedule's chunks), each with every coarse candidate."""
+    order = seed_order(nx, ny, nz, (slices + 1) // 2, sms=sms)
+    return [(tz, ctz) for tz, _ in order[:max(1, top)] for ctz in coarse_candidates]
+
+
 def autotune_parareal(nx: int, ny: int, nz: int, slices: int, fine_steps: int,
                       coarse_steps: int, dt: float, precision: str = "fp32_refine",
                       coarse_candidates: Iterable[int] = COARSE_TILE_Z, top: int = 2,
@@ -309,22 +319,20 @@ def autotune_parareal(nx: int, ny: int, nz: int, slices: int, fine_steps: int,
         init = inputs.random_state(nx, ny, nz, seed=seed, sigma=0.1, bc=bc,
                                    solid=kw.get("solid"))
     times: Dict[str, float] = {}
-    for tz, _ in order[:max(1, top)]:
-        for ctz in coarse_candidates:
-            g = Grid(nx, ny, nz, batch=slices, precision=precision, tile_z=tz,
-                     coarse_tile_z=ctz, **kw)
-            u0 = g.state_from(init)
-            g.project(u0)
-            ys = g.zeros(slices + 1)
-            g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=0)
-            g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=2, resume=True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=iterations,
-                       resume=True)
-            torch.cuda.synchronize()
-            times[f"{tz}/{ctz}"] = 1e3 * (time.perf_counter() - t0) / iterations
-            g.close()
+    for tz, ctz in parareal_candidates(nx, ny, nz, slices, top, coarse_candidates):
+        g = Grid(nx, ny, nz, batch=slices, precision=precision, tile_z=tz, coarse_tile_z=ctz,
+                 **kw)
+        u0 = g.state_from(init)
+        g.project(u0)
+        ys = g.zeros(slices + 1)
+        g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=0)
+        g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=2, resume=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.parareal(u0, ys, slices, fine_steps, coarse_steps, dt, kmax=iterations, resume=True)
+        torch.cuda.synchronize()
+        times[f"{tz}/{ctz}"] = 1e3 * (time.perf_counter() - t0) / iterations
+        g.close()
     best = min(times, key=times.get)
     tz, ctz = (int(x) for x in best.split("/"))
     out = {"tile_z": tz, "coarse_tile_z": ctz, "ms_per_iteration": times,

@@ -57,3 +57,15 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     data = json.loads(path.read_text())
     assert data[key] == {"predict_tile": [4, 8], "tile_z": 2}
     assert at._load_cache()["other"]["tile_z"] == 8
+
+
+def test_parareal_candidates_pair_seeded_sweep_marches_with_the_chain_candidates():
+    # the pipelined schedule sweeps half the slices per launch: the sweep's
+    # candidates are the seed's best marches for that batch, not the full one
+    pairs = at.parareal_candidates(64, 64, 64, 32, top=2, coarse_candidates=(4, 8), sms=152)
+    half = [t for t, _ in at.seed_order(64, 64, 64, 16, sms=152)[:2]]
+    assert pairs == [(tz, ctz) for tz in half for ctz in (4, 8)]
+    assert len(set(pairs)) == 4
+    # an odd slice count rounds the chunk up
+    assert at.parareal_candidates(32, 32, 32, 7, top=1, coarse_candidates=(8,), sms=152) == \
+        [(at.seed_order(32, 32, 32, 4, sms=152)[0][0], 8)]
